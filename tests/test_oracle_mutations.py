@@ -1,0 +1,42 @@
+"""Planted mistakes in the oracle (on the CPU) must each be caught by at least one pin.
+
+The oracle has a test-only switch that introduces one plausible mistake at a time: a dropped
+mass term, a transposed Jacobian inverse, a signed determinant, two swapped local nodes, a
+dropped Duffy factor in the quadrature.  Each must make some pin fail; otherwise the pins
+would not be strong enough to trust the oracle.
+"""
+import pytest
+
+import oracle as O
+from tests import test_oracle_pins as P
+
+PINS = [
+    ("reference_elements", lambda: P.pin_reference_elements()),
+    ("p1_interior_row", lambda: P.pin_p1_interior_row(16)),
+    ("mass_sum_3d", lambda: P.pin_mass_sum_and_stiffness_rows(3, 2, 2, 0.2)),
+    ("poly_repro_2d_p2", lambda: P.pin_polynomial_reproduction(2, 2, 4, 0.2)),
+    ("poly_repro_3d_p2", lambda: P.pin_polynomial_reproduction(3, 2, 2, 0.2)),
+    ("exact_rational_3d_p2", lambda: P.pin_exact_rational(3, 2, 1)),
+    ("quadrature_2d", lambda: P.pin_quadrature_monomials(2, 4)),
+]
+
+
+@pytest.mark.parametrize("code,what", [(1, "drop mass term"), (2, "transposed J^-1"), (3, "signed detJ"),
+                                       (4, "swapped edge nodes"), (5, "dropped Duffy factor")])
+def test_planted_mistake_is_caught(code, what):
+    O.set_mutation(code)
+    caught = []
+    try:
+        for name, pin in PINS:
+            try:
+                pin()
+            except AssertionError:
+                caught.append(name)
+    finally:
+        O.set_mutation(0)
+    assert caught, f"planted mistake '{what}' passed every pin"
+
+
+def test_pins_pass_without_mistake():
+    for name, pin in PINS:
+        pin()
