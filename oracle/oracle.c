@@ -258,7 +258,8 @@ static double geometry(int dim, const double *xv, double *glam /* [(dim+1)][dim]
  *   KAPPA_DIFFUSION: K_ij = sum_q w_q |detJ| kappa(x_q) grad phi_i . grad phi_j, kappa the P1
  *                    interpolant of the vertex values kv[dim+1].
  */
-int oracle_element_matrix(int dim, int p, int form, const double *xv, const double *kv, double *K) {
+int oracle_element_matrix_abs(int dim, int p, int form, const double *xv, const double *kv, double *K,
+                              double *Kabs) {
     int nd = oracle_num_nodes(dim, p), nv = dim + 1;
     int alpha[OR_MAXND * 4];
     double glam[4 * 3], phi[OR_MAXND], dphi[OR_MAXND * 4], grad[OR_MAXND * 3];
@@ -272,6 +273,7 @@ int oracle_element_matrix(int dim, int p, int form, const double *xv, const doub
     double adet = fabs(det);
     if (g_mutation == 3) adet = det; /* planted mistake: signed determinant */
     memset(K, 0, sizeof(double) * nd * nd);
+    if (Kabs) memset(Kabs, 0, sizeof(double) * nd * nd);
     for (int q = 0; q < nq; q++) {
         double lam[4];
         lam[0] = 1.0;
@@ -294,25 +296,49 @@ int oracle_element_matrix(int dim, int p, int form, const double *xv, const doub
         double wq = wts[q] * adet;
         for (int i = 0; i < nd; i++)
             for (int j = 0; j < nd; j++) {
-                double s = 0.0;
+                double s = 0.0, a = 0.0;
                 if (form != OR_MASS) {
-                    double gg = 0.0;
-                    for (int x = 0; x < dim; x++) gg += grad[i * dim + x] * grad[j * dim + x];
+                    double gg = 0.0, ga = 0.0;
+                    for (int x = 0; x < dim; x++) {
+                        gg += grad[i * dim + x] * grad[j * dim + x];
+                        ga += fabs(grad[i * dim + x] * grad[j * dim + x]);
+                    }
                     s += kap * gg;
+                    a += fabs(kap) * ga;
                 }
-                if (form == OR_MASS || (form == OR_HELMHOLTZ && g_mutation != 1))
+                if (form == OR_MASS || (form == OR_HELMHOLTZ && g_mutation != 1)) {
                     s += phi[i] * phi[j];
+                    a += fabs(phi[i] * phi[j]);
+                }
                 K[i * nd + j] += wq * s;
+                if (Kabs) Kabs[i * nd + j] += fabs(wq) * a;
             }
     }
     return nd;
+}
+
+int oracle_element_matrix(int dim, int p, int form, const double *xv, const double *kv, double *K) {
+    return oracle_element_matrix_abs(dim, p, form, xv, kv, K, NULL);
+}
+
+/*
+ * Error scale of element entry (i, j): the larger of the sum of absolute quadrature terms and
+ * the Cauchy-Schwarz bound sqrt(Kabs_ii Kabs_jj).  Every form here gives a symmetric positive
+ * semi-definite element matrix, so |K_ij| <= sqrt(K_ii K_jj) whatever formulation computes it;
+ * the bound keeps the scale meaningful for entries whose quadrature terms all vanish while
+ * another (equally exact) formulation leaves rounding-level residue there.
+ */
+static double entry_scale(const double *Ka, int nd, int i, int j) {
+    double cs = sqrt(Ka[i * nd + i] * Ka[j * nd + j]);
+    return Ka[i * nd + j] > cs ? Ka[i * nd + j] : cs;
 }
 
 /*
  * Element vector b[nd] of the linear form L = f v dx for test space P_p and a coefficient f
  * in P_pf with local values fe[nf]:  b_i = sum_q w_q |detJ| f(x_q) phi_i(x_q).
  */
-int oracle_element_vector(int dim, int p, int pf, const double *xv, const double *fe, double *b) {
+int oracle_element_vector_abs(int dim, int p, int pf, const double *xv, const double *fe, double *b,
+                              double *babs) {
     int nd = oracle_num_nodes(dim, p), nf = oracle_num_nodes(dim, pf);
     int alpha[OR_MAXND * 4], alphaf[OR_MAXND * 4];
     double glam[4 * 3], phi[OR_MAXND], psi[OR_MAXND];
@@ -323,6 +349,7 @@ int oracle_element_vector(int dim, int p, int pf, const double *xv, const double
     if (nq < 0) return -1;
     double adet = fabs(geometry(dim, xv, glam));
     memset(b, 0, sizeof(double) * nd);
+    if (babs) memset(babs, 0, sizeof(double) * nd);
     for (int q = 0; q < nq; q++) {
         double lam[4];
         lam[0] = 1.0;
@@ -332,11 +359,21 @@ int oracle_element_vector(int dim, int p, int pf, const double *xv, const double
         }
         basis_at(dim, p, nd, alpha, lam, phi, NULL);
         basis_at(dim, pf, nf, alphaf, lam, psi, NULL);
-        double f = 0.0;
-        for (int k = 0; k < nf; k++) f += fe[k] * psi[k];
-        for (int i = 0; i < nd; i++) b[i] += wts[q] * adet * f * phi[i];
+        double f = 0.0, fa = 0.0;
+        for (int k = 0; k < nf; k++) {
+            f += fe[k] * psi[k];
+            fa += fabs(fe[k] * psi[k]);
+        }
+        for (int i = 0; i < nd; i++) {
+            b[i] += wts[q] * adet * f * phi[i];
+            if (babs) babs[i] += fabs(wts[q]) * adet * fa * fabs(phi[i]);
+        }
     }
     return nd;
+}
+
+int oracle_element_vector(int dim, int p, int pf, const double *xv, const double *fe, double *b) {
+    return oracle_element_vector_abs(dim, p, pf, xv, fe, b, NULL);
 }
 
 /* ---- sparsity: pattern = union over cells e of {(rmap(e)[i], cmap(e)[j])} (Sec. 4.4.3) ---- */
@@ -410,8 +447,9 @@ static void gather_cell(int dim, int64_t e, const double *coords, const int32_t 
 
 /*
  * par_loop over cells with the Mat argument INC through (map, map) (Sec. 4.4, 4.4.3):
- * vals[pos(map(e)[i], map(e)[j])] += K_e[i][j].  absvals (optional) accumulates |K_e[i][j]|,
- * the scale of the per-entry error bound.  kappa (optional) is a P1 Dat on the vertices,
+ * vals[pos(map(e)[i], map(e)[j])] += K_e[i][j].  absvals (optional) accumulates the per-entry
+ * error scale of every contribution (entry_scale: the sum of absolute quadrature terms, or the
+ * Cauchy-Schwarz bound of the entry if larger).  kappa (optional) is a P1 Dat on the vertices,
  * gathered through coord_map.  vals/absvals are incremented, not cleared.  Returns 0, or -1.
  */
 int oracle_assemble_mat(int dim, int p, int form, int64_t ncell, const int32_t *map,
@@ -419,19 +457,19 @@ int oracle_assemble_mat(int dim, int p, int form, int64_t ncell, const int32_t *
                         const int64_t *rowptr, const int32_t *colidx, double *vals,
                         double *absvals) {
     int nd = oracle_num_nodes(dim, p);
-    double xv[12], kv[4] = {1, 1, 1, 1}, K[OR_MAXND * OR_MAXND];
+    double xv[12], kv[4] = {1, 1, 1, 1}, K[OR_MAXND * OR_MAXND], Ka[OR_MAXND * OR_MAXND];
     if (nd < 0 || nd > OR_MAXND) return -1;
     for (int64_t e = 0; e < ncell; e++) {
         gather_cell(dim, e, coords, coord_map, xv);
         if (kappa)
             for (int m = 0; m <= dim; m++) kv[m] = kappa[coord_map[e * (dim + 1) + m]];
-        if (oracle_element_matrix(dim, p, form, xv, kv, K) != nd) return -1;
+        if (oracle_element_matrix_abs(dim, p, form, xv, kv, K, Ka) != nd) return -1;
         for (int i = 0; i < nd; i++)
             for (int j = 0; j < nd; j++) {
                 int64_t pos = find_col(rowptr, colidx, map[e * nd + i], map[e * nd + j]);
                 if (pos < 0) return -1;
                 vals[pos] += K[i * nd + j];
-                if (absvals) absvals[pos] += fabs(K[i * nd + j]);
+                if (absvals) absvals[pos] += entry_scale(Ka, nd, i, j);
             }
     }
     return 0;
@@ -445,15 +483,15 @@ int oracle_assemble_vec(int dim, int p, int pf, int64_t ncell, const int32_t *ma
                         const double *coords, const int32_t *coord_map, const double *f,
                         const int32_t *fmap, double *b, double *absb) {
     int nd = oracle_num_nodes(dim, p), nf = oracle_num_nodes(dim, pf);
-    double xv[12], fe[OR_MAXND], be[OR_MAXND];
+    double xv[12], fe[OR_MAXND], be[OR_MAXND], ba[OR_MAXND];
     if (nd < 0 || nf < 0) return -1;
     for (int64_t e = 0; e < ncell; e++) {
         gather_cell(dim, e, coords, coord_map, xv);
         for (int k = 0; k < nf; k++) fe[k] = f[fmap[e * nf + k]];
-        if (oracle_element_vector(dim, p, pf, xv, fe, be) != nd) return -1;
+        if (oracle_element_vector_abs(dim, p, pf, xv, fe, be, ba) != nd) return -1;
         for (int i = 0; i < nd; i++) {
             b[map[e * nd + i]] += be[i];
-            if (absb) absb[map[e * nd + i]] += fabs(be[i]);
+            if (absb) absb[map[e * nd + i]] += ba[i];
         }
     }
     return 0;
@@ -462,25 +500,26 @@ int oracle_assemble_vec(int dim, int p, int pf, int64_t ncell, const int32_t *ma
 /*
  * Operator action: assembling the bilinear form with its trial argument replaced by the
  * Function x (the wave listing assembles inner(grad v, grad phi) dx this way, Sec. 6.3):
- * y[map(e)[i]] += sum_j K_e[i][j] x[map(e)[j]].  absy accumulates sum_j |K_e[i][j] x_j|.
+ * y[map(e)[i]] += sum_j K_e[i][j] x[map(e)[j]].  absy accumulates sum_j scale_e(i, j) |x_j| with
+ * the per-entry scale of oracle_assemble_mat.
  */
 int oracle_action(int dim, int p, int form, int64_t ncell, const int32_t *map, const double *coords,
                   const int32_t *coord_map, const double *kappa, const double *x, double *y,
                   double *absy) {
     int nd = oracle_num_nodes(dim, p);
-    double xv[12], kv[4] = {1, 1, 1, 1}, K[OR_MAXND * OR_MAXND];
+    double xv[12], kv[4] = {1, 1, 1, 1}, K[OR_MAXND * OR_MAXND], Ka[OR_MAXND * OR_MAXND];
     if (nd < 0) return -1;
     for (int64_t e = 0; e < ncell; e++) {
         gather_cell(dim, e, coords, coord_map, xv);
         if (kappa)
             for (int m = 0; m <= dim; m++) kv[m] = kappa[coord_map[e * (dim + 1) + m]];
-        if (oracle_element_matrix(dim, p, form, xv, kv, K) != nd) return -1;
+        if (oracle_element_matrix_abs(dim, p, form, xv, kv, K, Ka) != nd) return -1;
         for (int i = 0; i < nd; i++) {
             double s = 0.0, a = 0.0;
             for (int j = 0; j < nd; j++) {
                 double t = K[i * nd + j] * x[map[e * nd + j]];
                 s += t;
-                a += fabs(t);
+                a += entry_scale(Ka, nd, i, j) * fabs(x[map[e * nd + j]]);
             }
             y[map[e * nd + i]] += s;
             if (absy) absy[map[e * nd + i]] += a;
@@ -502,7 +541,7 @@ int oracle_assemble_rows(int dim, int p, int form, int64_t ncell, const int32_t 
                          const int64_t *sel_rowptr, const int32_t *sel_colidx, double *out_vals,
                          double *out_abs) {
     int nd = oracle_num_nodes(dim, p);
-    double xv[12], kv[4] = {1, 1, 1, 1}, K[OR_MAXND * OR_MAXND];
+    double xv[12], kv[4] = {1, 1, 1, 1}, K[OR_MAXND * OR_MAXND], Ka[OR_MAXND * OR_MAXND];
     int64_t *slot = malloc(sizeof(int64_t) * (size_t)(nrows > 0 ? nrows : 1));
     if (!slot || nd < 0) { free(slot); return -1; }
     for (int64_t r = 0; r < nrows; r++) slot[r] = -1;
@@ -514,7 +553,7 @@ int oracle_assemble_rows(int dim, int p, int form, int64_t ncell, const int32_t 
         gather_cell(dim, e, coords, coord_map, xv);
         if (kappa)
             for (int m = 0; m <= dim; m++) kv[m] = kappa[coord_map[e * (dim + 1) + m]];
-        if (oracle_element_matrix(dim, p, form, xv, kv, K) != nd) { free(slot); return -1; }
+        if (oracle_element_matrix_abs(dim, p, form, xv, kv, K, Ka) != nd) { free(slot); return -1; }
         for (int i = 0; i < nd; i++) {
             int64_t s = slot[map[e * nd + i]];
             if (s < 0) continue;
@@ -522,7 +561,7 @@ int oracle_assemble_rows(int dim, int p, int form, int64_t ncell, const int32_t 
                 int64_t pos = find_col(sel_rowptr, sel_colidx, s, map[e * nd + j]);
                 if (pos < 0) { free(slot); return -1; }
                 out_vals[pos] += K[i * nd + j];
-                if (out_abs) out_abs[pos] += fabs(K[i * nd + j]);
+                if (out_abs) out_abs[pos] += entry_scale(Ka, nd, i, j);
             }
         }
     }
