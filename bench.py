@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the cell-wise assembly hot path on GB300.
+
+Workload (default): P2 Lagrange on UnitCubeMesh 64^3 -- 1,572,864 Kuhn tetrahedra, interior vertices
+jittered by uniform +-0.2h (seed 0), 129^3 = 2,146,689 dofs -- Helmholtz form, FP64 global CSR.
+One step = one pass of every row of the hot path over that mesh:
+  sparsity (incidence, per-row sort/unique, CSR, per-cell lookup table) -> zero the Mat ->
+  assemble the CSR Mat -> matrix-free action y = A x (x uniform[-1,1], seed 2).
+Metric: cells/s (cells of the mesh through one whole step per second).
+
+Multi-GPU: the path shards by mesh (independent problems), so N ranks run N replicas with no
+data-path collective (weak scaling); timing is the max over ranks.
+
+--impl reference times the CPU oracle (plain C, FP64) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cells/s assembled (sparsity + CSR assembly + matrix-free action per step)"
+WORKLOADS = {
+    "p2-3d": dict(dim=3, p=2, n=64, jitter=0.2, seed=0,
+                  name="P2 Lagrange UnitCubeMesh 64^3 (1,572,864 Kuhn tets, +-0.2h jitter seed 0, 2,146,689 dofs), "
+                       "Helmholtz, FP64 CSR: sparsity + assembly + matrix-free action"),
+    "p1-2d": dict(dim=2, p=1, n=64, jitter=0.0, seed=0,
+                  name="P1 Lagrange UnitSquareMesh 64x64 (8192 cells, 4225 nodes), Helmholtz, FP64 CSR: "
+                       "sparsity + assembly + matrix-free action"),
+}
+# ncu dram bytes (read + write) per launch of the dominant kernel, with the sha1 of the kernel
+# source they were taken from; reported as null once the source has changed.
+TRAFFIC = {}
+
+
+def _src_hash(name):
+    p = os.path.join(ROOT, "paper_1501_01809_gb300", "csrc", name)
+    with open(p, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal GB300 figure 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fe_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------------------- workload
+
+def make_inputs(wl):
+    from paper_1501_01809_gb300 import meshgen as mg
+    mesh = (mg.unit_square_mesh if wl["dim"] == 2 else mg.unit_cube_mesh)(wl["n"], wl["jitter"], wl["seed"])
+    cmap, nn = mg.cell_node_map(mesh, wl["p"])
+    x = mg.uniform_dat(nn, 2)
+    return mesh, cmap, nn, x
+
+
+def counts_per_cell(dim, p):
+    """Algorithmic bytes and FP64 flops per cell (assembly kernel and action kernel)."""
+    from paper_1501_01809_gb300 import codegen
+    nd = len(codegen.lattice_nodes(dim, p))
+    B = codegen.stiffness_tensor(dim, p)
+    M = codegen.mass_tensor(dim, p)
+    up = [(i, j) for i in range(nd) for j in range(i, nd)]
+    stiff_terms = sum(1 for (i, j) in up for T in B.values() if T[i][j] != 0)
+    mass_terms = sum(1 for (i, j) in up if M[i][j] != 0)
+    geo = 70 if dim == 3 else 25
+    flops_mat = geo + 2 * (stiff_terms + mass_terms)
+    flops_action = flops_mat + 2 * nd * nd
+    return nd, flops_mat, flops_action
+
+
+def run_ours(args, wl, rank, world):
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mesh, cmap, nn, x = make_inputs(wl)
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    t_map = torch.from_numpy(cmap).to(dev)
+    t_cv = torch.from_numpy(mesh.cell_vertex).to(dev)
+    t_xy = torch.from_numpy(mesh.coords).to(dev)
+    t_x = torch.from_numpy(x).to(dev)
+    t_y = torch.zeros_like(t_x)
+    cells, nodes, verts = fe.set_create(ctx, mesh.ncell), fe.set_create(ctx, nn), fe.set_create(ctx, mesh.nvert)
+    M = fe.map_create(ctx, cells, nodes, t_map, validate=True)
+    CM = fe.map_create(ctx, cells, verts, t_cv, validate=True)
+    XY = fe.dat_create(ctx, verts, t_xy)
+    X, Y = fe.dat_create(ctx, nodes, t_x), fe.dat_create(ctx, nodes, t_y)
+    strat = {"push": fe.STRATEGY_PUSH, "pull": fe.STRATEGY_PULL, "auto": fe.STRATEGY_AUTO}[args.strategy]
+    prec = {"fp64": fe.PREC_FP64, "f32x2": fe.PREC_F32X2}[args.precision]
+    K = fe.kernel_create(ctx, fe.FORM_HELMHOLTZ, wl["dim"], wl["p"], precision=prec, strategy=strat)
+    with torch.cuda.stream(stream):
+        sp = fe.sparsity_build(ctx, M, M)
+        A = fe.mat_create(ctx, sp)
+    nrows, ncols, nnz, rowptr, colidx = fe.sparsity_csr(sp)
+    vals = fe.mat_values(A)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fe.sparsity_rebuild(sp)
+        if ev is not None:
+            ev[1].record(stream)
+        fe.mat_zero(A)
+        if ev is not None:
+            ev[2].record(stream)
+        fe.assemble_mat(ctx, K, cells, A, XY, CM, zero_first=False)
+        if ev is not None:
+            ev[3].record(stream)
+        fe.action(ctx, K, cells, X, Y, M, XY, CM, zero_first=True, sp=sp)
+        if ev is not None:
+            ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    fe.sync(ctx)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step(evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        td.barrier()
+    fe.sync(ctx)
+    phases = np.zeros(4)
+    for ev in evs:
+        for p in range(4):
+            phases[p] += ev[p].elapsed_time(ev[p + 1])
+    total_ms = evs[0][0].elapsed_time(evs[-1][4])
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms_step = float(t.item())
+    phase_ms = phases / args.steps
+    # launches of libfe kernels per step: sparsity rebuild 14 (zero, count, zero, max, scan x3, zero, fill,
+    # row sort, scan x3, compact), mat zero 1, assembly 1, action zero + action 2
+    launches = (14 + 1 + 1 + 2) * args.steps
+
+    # ------------------------------------------------------------------- e2e through host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t.cpu())
+        h_in = [(pin(t), t) for t in (t_map, t_cv, t_xy, t_x)]
+        h_out = [(torch.empty(t.shape, dtype=t.dtype, pin_memory=True), t) for t in (rowptr, colidx, vals, t_y)]
+        h2d = sum(h.numel() * h.element_size() for h, _ in h_in)
+        d2h = sum(h.numel() * h.element_size() for h, _ in h_out)
+        ksteps = max(3, min(args.steps, 20))
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for h, d in h_in:
+                    d.copy_(h, non_blocking=True)
+                step()
+                for h, d in h_out:
+                    h.copy_(d, non_blocking=True)
+
+        e2e_step()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms = a.elapsed_time(b) / ksteps
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * mesh.ncell / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+        fe.sync(ctx)
+
+    # ------------------------------------------------------------------- roofline of the dominant kernel
+    peaks, src = _peaks()
+    nd, fl_mat, fl_act = counts_per_cell(wl["dim"], wl["p"])
+    ncell = mesh.ncell
+    bytes_mat = ncell * (nd * 4 + (wl["dim"] + 1) * 4) + mesh.nvert * wl["dim"] * 8 + nnz * 8
+    bytes_act = ncell * (nd * 4 + (wl["dim"] + 1) * 4) + mesh.nvert * wl["dim"] * 8 + 2 * nn * 8
+    kern = {
+        "sparsity": {"ms": phase_ms[0]},
+        "zero": {"ms": phase_ms[1], "bytes": nnz * 8},
+        "assemble": {"ms": phase_ms[2], "bytes": bytes_mat, "flops": ncell * fl_mat},
+        "action": {"ms": phase_ms[3], "bytes": bytes_act, "flops": ncell * fl_act},
+    }
+    for k, v in kern.items():
+        if "bytes" in v and v["ms"] > 0:
+            v["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            v["hbm_frac"] = v["gbs"] / peaks["hbm_gbs"]
+        if "flops" in v and v["ms"] > 0:
+            v["fp64_tflops"] = v["flops"] / (v["ms"] / 1e3) / 1e12
+            v["fp64_frac"] = v["fp64_tflops"] / FP64_PEAK_TFLOPS
+    dom = max(["assemble", "action"], key=lambda k: kern[k]["ms"])
+    dk = kern[dom]
+    fp64_bound = dk["flops"] / (FP64_PEAK_TFLOPS * 1e12) > dk["bytes"] / (peaks["hbm_gbs"] * 1e9)
+    if args.precision == "fp64" and fp64_bound:
+        roof = {"bound": "alu", "achieved": dk["fp64_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": dk["fp64_frac"], "kernel": dom, "peak_source": "derived FP64: 152 SMs x 2 FMA/clk x 2.07 GHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": dk["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": dk["hbm_frac"], "kernel": dom, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    tr = TRAFFIC.get((dom, args.strategy, args.precision))
+    roof["traffic"] = tr[0] if tr and tr[1] == _src_hash("fe_assemble.cu") else None
+    out = {
+        "metric": METRIC, "value": world * ncell / (ms_step / 1e3), "unit": "cells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
+                   "strategy": args.strategy, "precision": args.precision,
+                   "parallelism": f"replicas x{world} (independent meshes, no collective)",
+                   "l2": "inputs larger than L2 (CSR values + lookup table ~650 MB), no flush"},
+        "roofline": roof, "kernels": kern, "gpu_launches": launches, "wall_s_timed": wall,
+        "clocks": clk.summary(), "e2e": e2e,
+    }
+    return out, (mesh, cmap, nn, x)
+
+
+def _oracle_sample(wl, inputs, ncell_sample):
+    """Oracle on the first ncell_sample cells of the workload: sparsity + assembly + action."""
+    import oracle as O
+    mesh, cmap, nn, x = inputs
+    c = np.ascontiguousarray(cmap[:ncell_sample])
+    cv = np.ascontiguousarray(mesh.cell_vertex[:ncell_sample])
+    t0 = time.perf_counter()
+    rp, ci = O.sparsity(c, c, nn, nn)
+    O.assemble_mat(wl["dim"], wl["p"], O.HELMHOLTZ, c, mesh.coords, cv, rp, ci)
+    O.action(wl["dim"], wl["p"], O.HELMHOLTZ, c, mesh.coords, cv, x)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, inputs, ncell_sample):
+    import oracle
+    oracle.build()
+    _oracle_sample(wl, inputs, min(1024, ncell_sample))  # warm
+    dt = _oracle_sample(wl, inputs, ncell_sample)
+    return {"value": ncell_sample / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {ncell_sample} cells of the workload mesh (sparsity + assembly + action), "
+                      f"{dt:.1f} s on 1 host core"}
+
+
+def run_reference(args, wl):
+    import oracle
+    oracle.build()
+    inputs = make_inputs(wl)
+    ns = args.ref_cells
+    for _ in range(args.warmup):
+        _oracle_sample(wl, inputs, ns)
+    times = [_oracle_sample(wl, inputs, ns) for _ in range(args.steps)]
+    ms = 1e3 * sum(times) / len(times)
+    v = ns / (ms / 1e3)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "reference": "CPU FP64 oracle (plain C), bounded sample per step"},
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {ns} cells of the workload mesh per step"},
+            "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="p2-3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--strategy", default="push", choices=["push", "pull", "auto"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "f32x2"])
+    ap.add_argument("--cpu-cells", type=int, default=65536, help="oracle sample size for cpu_baseline")
+    ap.add_argument("--ref-cells", type=int, default=8192, help="oracle sample per step for --impl reference")
+    ap.add_argument("--n", type=int, default=0, help="override the mesh size (profiling on a smaller case)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = dict(WORKLOADS[args.workload])
+    if args.n:
+        wl["n"] = args.n
+        wl["name"] = f"{wl['name']} [n overridden to {args.n}]"
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, wl)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+    out, inputs = run_ours(args, wl, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl, inputs, min(args.cpu_cells, inputs[0].ncell))
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

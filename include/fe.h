@@ -1,0 +1,203 @@
+/*
+ * fe.h -- C ABI of libfe, GB300-native cell-wise finite element assembly.
+ *
+ * The calls follow the data model and execution model of PyOP2 as described in
+ * Rathgeber et al., "Firedrake: automating the finite element method by composing
+ * abstractions" (ACM TOMS), Sec. 4:
+ *   Sets (Sec. 4.1), Maps of constant arity (Sec. 4.2), Dats and Mats (Sec. 4.3),
+ *   parallel loops with access descriptors READ / INC (Sec. 4.4, 4.4.1), Mats assembled
+ *   through a pair of Maps (Sec. 4.4.3), and the form-assembly argument order of the
+ *   Firedrake layer (Sec. 5.1.3: output tensor, then coordinates, then coefficients).
+ *
+ * General conventions
+ *  - Every function returns an fe_status; 0 (FE_OK) on success, a negative code otherwise,
+ *    with a message available from fe_last_error() on the calling thread.  No call aborts.
+ *  - Device buffers passed in (map values, coordinates, coefficient and output vectors) are
+ *    BORROWED: the caller owns them and keeps them alive while any handle refers to them.
+ *    Buffers the library creates (CSR pattern, lookup tables, Mat values, scratch) are
+ *    OWNED by the returned handle and freed by its destroy call; they are allocated through
+ *    the context's allocator (fe_ctx_set_allocator), by default cudaMalloc.
+ *  - Compute calls are asynchronous on the context's CUDA stream.  Errors that only the
+ *    device can detect (map values out of range when checks are on) are reported by the
+ *    next fe_sync() as FE_ERANGE.
+ *  - Cells are simplices: triangles (dim 2) or tetrahedra (dim 3), affine (P1 coordinates).
+ *  - Lagrange P_p local node order (the column order of a cell-node Map): nodes are the
+ *    lattice points sum_m alpha_m x_m / p of the cell (x_m its vertices, |alpha| = p):
+ *    the vertices 0..dim; then each edge (a, b), a < b, in lexicographic order, walked from
+ *    a to b (alpha_a = p - t, alpha_b = t, t = 1..p-1); then each face (a, b, c), a < b < c,
+ *    lexicographic, interior points by descending alpha_a, then alpha_b; then (3D) the cell
+ *    interior by descending alpha_0, alpha_1, alpha_2.
+ *  - Index types: map values int32; CSR rowptr int64, colidx int32 (columns sorted per row).
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fe_status;
+#define FE_OK 0
+#define FE_EINVAL (-1)        /* bad argument (null pointer, size, mismatched sets)          */
+#define FE_EHANDLE (-2)       /* handle belongs to another context or was destroyed           */
+#define FE_ERANGE (-3)        /* a map value lies outside its target set                      */
+#define FE_EARITY (-4)        /* map arity does not match the element of the kernel           */
+#define FE_ENOMEM (-5)        /* the allocator failed                                         */
+#define FE_ECUDA (-6)         /* a CUDA runtime call failed (message has the CUDA error)      */
+#define FE_ETIMEOUT (-7)      /* a bounded device wait gave up                                */
+#define FE_EUNSUPPORTED (-8)  /* form/element/size combination not built into this library   */
+
+typedef struct fe_ctx fe_ctx;
+typedef struct fe_set fe_set;
+typedef struct fe_map fe_map;
+typedef struct fe_dat fe_dat;
+typedef struct fe_sparsity fe_sparsity;
+typedef struct fe_mat fe_mat;
+typedef struct fe_kernel fe_kernel;
+
+/* Forms (Sec. 3.1, Listing 1: a = inner(grad u, grad v) dx, L = f v dx; plus mass and
+ * kappa-weighted diffusion with kappa a P1 Function). */
+typedef enum {
+  FE_FORM_MASS = 1,             /* u v dx                                    */
+  FE_FORM_LAPLACE = 2,          /* inner(grad u, grad v) dx                  */
+  FE_FORM_HELMHOLTZ = 3,        /* inner(grad u, grad v) dx + u v dx         */
+  FE_FORM_KAPPA_DIFFUSION = 4,  /* kappa inner(grad u, grad v) dx, kappa P1  */
+  FE_FORM_SOURCE = 5            /* linear: f v dx, f in P_q                  */
+} fe_form;
+
+/* Arithmetic of the element tensor.  Accumulation into the global Mat/Dat is FP64 always. */
+typedef enum {
+  FE_PREC_FP64 = 0,   /* native IEEE double                                               */
+  FE_PREC_F32X2 = 1   /* pairs of FP32 (error-free transformations), ~2^-46 relative     */
+} fe_precision;
+
+/* How the INC into the global Mat/Dat is executed. */
+typedef enum {
+  FE_STRATEGY_AUTO = 0,
+  FE_STRATEGY_PUSH = 1,  /* one thread per cell, FP64 atomic adds through the lookup table */
+  FE_STRATEGY_PULL = 2   /* one owner per row: gathers its cells' contributions, no atomics,
+                            deterministic (bitwise reproducible) summation order           */
+} fe_strategy;
+
+typedef struct {
+  int form;          /* fe_form                                                           */
+  int dim;           /* 2 (triangles) or 3 (tetrahedra)                                   */
+  int degree;        /* Lagrange degree p of the test (= trial) space                     */
+  int coeff_degree;  /* degree of the coefficient f (FE_FORM_SOURCE); kappa is always P1  */
+  int precision;     /* fe_precision                                                      */
+  int strategy;      /* fe_strategy                                                       */
+} fe_form_desc;
+
+/* A coefficient argument (READ through its own map), Sec. 5.1.3. */
+typedef struct {
+  fe_dat *dat;
+  fe_map *map;
+} fe_arg;
+
+/* Device allocator hooks: alloc(bytes, user) returns a device pointer or NULL. */
+typedef void *(*fe_alloc_fn)(size_t bytes, void *user);
+typedef void (*fe_free_fn)(void *ptr, void *user);
+
+/* Message of the last failing call on this thread ("" if none).  Never NULL. */
+const char *fe_last_error(void);
+
+/* Library version string. */
+const char *fe_version(void);
+
+/* ---------------------------------------------------------------- context
+ * fe_ctx_create: binds a device and a CUDA stream (cudaStream_t passed as void*, borrowed;
+ * NULL = the legacy default stream).  Allocates a small device error-flag buffer.
+ * Errors: FE_EINVAL (out == NULL), FE_ECUDA (bad device). */
+fe_status fe_ctx_create(int device, void *cuda_stream, fe_ctx **out);
+fe_status fe_ctx_set_stream(fe_ctx *ctx, void *cuda_stream);
+/* Replace the allocator for buffers created after this call (NULL, NULL = cudaMalloc). */
+fe_status fe_ctx_set_allocator(fe_ctx *ctx, fe_alloc_fn alloc, fe_free_fn free_fn, void *user);
+/* checks != 0: kernels verify every map value against its target set and flag FE_ERANGE. */
+fe_status fe_ctx_set_checks(fe_ctx *ctx, int checks);
+/* Waits for the context stream, then reports (and clears) any device-side error flag. */
+fe_status fe_sync(fe_ctx *ctx);
+fe_status fe_ctx_destroy(fe_ctx *ctx);
+
+/* ---------------------------------------------------------------- Set (Sec. 4.1)
+ * An abstract entity count; stores no data.  Errors: FE_EINVAL (size < 0). */
+fe_status fe_set_create(fe_ctx *ctx, int64_t size, fe_set **out);
+fe_status fe_set_size(const fe_set *set, int64_t *size);
+fe_status fe_set_destroy(fe_set *set);
+
+/* ---------------------------------------------------------------- Map (Sec. 4.2)
+ * Constant-arity map from -> to.  dev_values: device int32 [from.size][arity], row-major,
+ * borrowed.  validate != 0 runs a range-check kernel and synchronises: FE_ERANGE if any value
+ * lies outside [0, to.size).  Errors: FE_EINVAL (arity < 1, null values with from.size > 0). */
+fe_status fe_map_create(fe_ctx *ctx, fe_set *from, fe_set *to, int arity, const int32_t *dev_values,
+                        int validate, fe_map **out);
+fe_status fe_map_destroy(fe_map *map);
+
+/* ---------------------------------------------------------------- Dat (Sec. 4.3)
+ * A vector of dim float64 values per set element: device [set.size][dim], borrowed. */
+fe_status fe_dat_create(fe_ctx *ctx, fe_set *set, int dim, void *dev_ptr, fe_dat **out);
+fe_status fe_dat_destroy(fe_dat *dat);
+
+/* ---------------------------------------------------------------- Sparsity (Sec. 4.4.3)
+ * Builds on the device the CSR pattern of the union over cells e of
+ * {(rmap(e)[i], cmap(e)[j])}: rows = rmap target set, columns = cmap target set, columns
+ * sorted ascending, no duplicates (bitwise deterministic).  Also builds the per-cell lookup
+ * table giving, for each (e, i, j), the position of cmap(e)[j] within row rmap(e)[i], and the
+ * row -> (cell, local index) incidence used by the row-owner (pull) kernels.  rmap and cmap
+ * must share their source set (the cells).  Owned buffers.  Synchronises the stream once to
+ * learn nnz.  Errors: FE_EINVAL (different source sets), FE_ERANGE (map value out of range),
+ * FE_EUNSUPPORTED (a row with more than 256 columns or more than 4096 candidate entries). */
+fe_status fe_sparsity_build(fe_ctx *ctx, fe_map *rmap, fe_map *cmap, fe_sparsity **out);
+/* Recomputes pattern, lookup table and incidence from the (possibly rewritten) map values into
+ * the existing buffers, asynchronously (no host synchronisation).  The caller guarantees the
+ * pattern size is unchanged; a changed nnz is flagged on the device and reported by fe_sync as
+ * FE_EINVAL.  This is the per-step sparsity build of the benchmark. */
+fe_status fe_sparsity_rebuild(fe_sparsity *sp);
+/* Read-only views of the CSR pattern (device pointers owned by sp). */
+fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols, int64_t *nnz,
+                          const int64_t **rowptr, const int32_t **colidx);
+/* Device pointer to the uint8 lookup table [ncell][arity_r][arity_c] (rank within the row). */
+fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut);
+fe_status fe_sparsity_destroy(fe_sparsity *sp);
+
+/* ---------------------------------------------------------------- Mat (Sec. 4.3, 4.4.3)
+ * FP64 values over a sparsity (owned, [nnz]), write-only to par_loops (INC). */
+fe_status fe_mat_create(fe_ctx *ctx, fe_sparsity *sp, fe_mat **out);
+fe_status fe_mat_values(const fe_mat *mat, double **values);
+fe_status fe_mat_zero(fe_mat *mat);
+fe_status fe_mat_destroy(fe_mat *mat);
+
+/* ---------------------------------------------------------------- Kernel (Sec. 5.2)
+ * Selects the generated local kernel for (form, dim, degree[, coeff_degree], precision,
+ * strategy).  Errors: FE_EUNSUPPORTED if the combination is not compiled in. */
+fe_status fe_kernel_create(fe_ctx *ctx, const fe_form_desc *desc, fe_kernel **out);
+fe_status fe_kernel_destroy(fe_kernel *k);
+
+/* ---------------------------------------------------------------- par_loops (Sec. 4.4, 5.1.3)
+ * fe_assemble_mat: A(INC, (map, map)) over the cells; coords (a Dat of dim float64 per vertex)
+ * READ through coord_map (arity dim+1); coefficients READ through their maps (kappa for
+ * FE_FORM_KAPPA_DIFFUSION: one P1 coefficient).  A's sparsity must have been built from
+ * (map, map).  zero_first != 0 clears A first (MatZeroEntries).
+ * Errors: FE_EINVAL, FE_EARITY, FE_EHANDLE, FE_EUNSUPPORTED. */
+fe_status fe_assemble_mat(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_mat *A, int zero_first,
+                          fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs, int ncoeffs);
+/* fe_assemble_vec: b(INC, test_map) for FE_FORM_SOURCE; coeffs[0] = f (P_q through its map).
+ * For the pull strategy sp must be the sparsity built from (test_map, test_map) (its
+ * incidence is reused); it may be NULL for push. */
+fe_status fe_assemble_vec(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *b, fe_map *test_map,
+                          int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
+                          int ncoeffs, const fe_sparsity *sp);
+/* fe_action: y(INC, map) = A(x) cell by cell without forming A (the bilinear form with its
+ * trial argument replaced by the Function x, as the paper's wave step assembles
+ * inner(grad v, grad phi) dx each step, Sec. 6.3); x READ through map.  sp as for
+ * fe_assemble_vec. */
+fe_status fe_action(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y, fe_map *map,
+                    int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
+                    int ncoeffs, const fe_sparsity *sp);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

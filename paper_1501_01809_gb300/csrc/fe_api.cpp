@@ -1,0 +1,586 @@
+// C ABI of libfe (declared in include/fe.h): handle management, argument validation, the
+// allocator, and the host-side sequencing of the sparsity and assembly kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "fe_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+fe_status fail(fe_status code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+fe_status ok() { return FE_OK; }
+
+fe_status cuda_fail(cudaError_t e, const char *where) {
+  return fail(FE_ECUDA, "%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
+}
+
+#define FE_CHECK_CUDA(call, where)            \
+  do {                                        \
+    cudaError_t _e = (call);                  \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+bool valid(const fe_ctx *c) { return c && c->magic == fe::kMagicCtx; }
+bool valid(const fe_set *s) { return s && s->magic == fe::kMagicSet && valid(s->ctx); }
+bool valid(const fe_map *m) { return m && m->magic == fe::kMagicMap && valid(m->ctx); }
+bool valid(const fe_dat *d) { return d && d->magic == fe::kMagicDat && valid(d->ctx); }
+bool valid(const fe_sparsity *s) { return s && s->magic == fe::kMagicSp && valid(s->ctx); }
+bool valid(const fe_mat *m) { return m && m->magic == fe::kMagicMat && valid(m->ctx); }
+bool valid(const fe_kernel *k) { return k && k->magic == fe::kMagicKer && valid(k->ctx); }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void *dev_alloc(fe_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (c->alloc) return c->alloc(bytes, c->user);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(fe_ctx *c, void *p) {
+  if (!p) return;
+  if (c->free_fn) c->free_fn(p, c->user);
+  else cudaFree(p);
+}
+
+// Reads and clears the device error flags (synchronises the stream).
+fe_status check_device_flags(fe_ctx *c, const char *where) {
+  int h[2] = {0, 0};
+  FE_CHECK_CUDA(cudaMemcpyAsync(h, c->d_err, sizeof h, cudaMemcpyDeviceToHost, c->stream), where);
+  FE_CHECK_CUDA(cudaStreamSynchronize(c->stream), where);
+  if (h[0]) {
+    int z[2] = {0, 0};
+    FE_CHECK_CUDA(cudaMemcpyAsync(c->d_err, z, sizeof z, cudaMemcpyHostToDevice, c->stream), where);
+    FE_CHECK_CUDA(cudaStreamSynchronize(c->stream), where);
+    if (h[0] & fe::ERR_RANGE) return fail(FE_ERANGE, "%s: a map value lies outside its target set (first index %d)", where, h[1]);
+    if (h[0] & fe::ERR_NNZ_CHANGED) return fail(FE_EINVAL, "%s: the rebuilt pattern has a different nnz", where);
+    if (h[0] & fe::ERR_ROW_TOO_LONG)
+      return fail(FE_EUNSUPPORTED, "%s: a row has more than %d columns (row %d)", where, fe::kMaxRowLen, h[1]);
+    if (h[0] & fe::ERR_CAND_OVERFLOW)
+      return fail(FE_EUNSUPPORTED, "%s: a row has more than %d candidate entries (row %d)", where, fe::kMaxCand, h[1]);
+    return fail(FE_ECUDA, "%s: device error flags 0x%x", where, h[0]);
+  }
+  return FE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fe_last_error(void) { return g_err.c_str(); }
+const char *fe_version(void) { return "libfe 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------------------------ context
+fe_status fe_ctx_create(int device, void *cuda_stream, fe_ctx **out) {
+  if (!out) return fail(FE_EINVAL, "fe_ctx_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  FE_CHECK_CUDA(cudaGetDeviceCount(&n), "fe_ctx_create");
+  if (device < 0 || device >= n) return fail(FE_EINVAL, "fe_ctx_create: device %d of %d", device, n);
+  DeviceGuard g(device);
+  FE_CHECK_CUDA(cudaSetDevice(device), "fe_ctx_create");
+  fe_ctx *c = new (std::nothrow) fe_ctx();
+  if (!c) return fail(FE_ENOMEM, "fe_ctx_create: host allocation");
+  c->magic = fe::kMagicCtx;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->checks = 0;
+  if (cudaMalloc(&c->d_err, 4 * sizeof(int)) != cudaSuccess) {
+    delete c;
+    return fail(FE_ENOMEM, "fe_ctx_create: device error flags");
+  }
+  int z[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpy(c->d_err, z, sizeof z, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(c->d_err);
+    delete c;
+    return cuda_fail(e, "fe_ctx_create");
+  }
+  *out = c;
+  return ok();
+}
+
+fe_status fe_ctx_set_stream(fe_ctx *c, void *s) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_ctx_set_stream: invalid context");
+  c->stream = (cudaStream_t)s;
+  return ok();
+}
+
+fe_status fe_ctx_set_allocator(fe_ctx *c, fe_alloc_fn a, fe_free_fn f, void *user) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_ctx_set_allocator: invalid context");
+  if ((a == nullptr) != (f == nullptr)) return fail(FE_EINVAL, "fe_ctx_set_allocator: give both or neither");
+  c->alloc = a;
+  c->free_fn = f;
+  c->user = user;
+  return ok();
+}
+
+fe_status fe_ctx_set_checks(fe_ctx *c, int checks) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_ctx_set_checks: invalid context");
+  c->checks = checks != 0;
+  return ok();
+}
+
+fe_status fe_sync(fe_ctx *c) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_sync: invalid context");
+  DeviceGuard g(c->device);
+  return check_device_flags(c, "fe_sync");
+}
+
+fe_status fe_ctx_destroy(fe_ctx *c) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_ctx_destroy: invalid context");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_err);
+  c->magic = fe::kDead;
+  delete c;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Set
+fe_status fe_set_create(fe_ctx *c, int64_t size, fe_set **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_set_create: invalid context");
+  if (!out || size < 0) return fail(FE_EINVAL, "fe_set_create: bad arguments (size %lld)", (long long)size);
+  fe_set *s = new (std::nothrow) fe_set{fe::kMagicSet, c, size};
+  if (!s) return fail(FE_ENOMEM, "fe_set_create: host allocation");
+  *out = s;
+  return ok();
+}
+
+fe_status fe_set_size(const fe_set *s, int64_t *size) {
+  if (!valid(s) || !size) return fail(FE_EHANDLE, "fe_set_size: invalid set");
+  *size = s->size;
+  return ok();
+}
+
+fe_status fe_set_destroy(fe_set *s) {
+  if (!valid(s)) return fail(FE_EHANDLE, "fe_set_destroy: invalid set");
+  s->magic = fe::kDead;
+  delete s;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Map
+fe_status fe_map_create(fe_ctx *c, fe_set *from, fe_set *to, int arity, const int32_t *values, int validate,
+                        fe_map **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_map_create: invalid context");
+  if (!valid(from) || !valid(to) || from->ctx != c || to->ctx != c)
+    return fail(FE_EHANDLE, "fe_map_create: sets belong to another context");
+  if (!out || arity < 1 || (from->size > 0 && !values))
+    return fail(FE_EINVAL, "fe_map_create: bad arguments (arity %d)", arity);
+  if (to->size > INT32_MAX) return fail(FE_EUNSUPPORTED, "fe_map_create: target set larger than int32");
+  if (validate && from->size > 0) {
+    DeviceGuard g(c->device);
+    FE_CHECK_CUDA(fe::launch_map_validate(values, from->size * arity, to->size, c->d_err, c->stream), "fe_map_create");
+    fe_status st = check_device_flags(c, "fe_map_create");
+    if (st != FE_OK) return st;
+  }
+  fe_map *m = new (std::nothrow) fe_map{fe::kMagicMap, c, from, to, arity, values};
+  if (!m) return fail(FE_ENOMEM, "fe_map_create: host allocation");
+  *out = m;
+  return ok();
+}
+
+fe_status fe_map_destroy(fe_map *m) {
+  if (!valid(m)) return fail(FE_EHANDLE, "fe_map_destroy: invalid map");
+  m->magic = fe::kDead;
+  delete m;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Dat
+fe_status fe_dat_create(fe_ctx *c, fe_set *set, int dim, void *ptr, fe_dat **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_dat_create: invalid context");
+  if (!valid(set) || set->ctx != c) return fail(FE_EHANDLE, "fe_dat_create: set belongs to another context");
+  if (!out || dim < 1 || (set->size > 0 && !ptr)) return fail(FE_EINVAL, "fe_dat_create: bad arguments");
+  fe_dat *d = new (std::nothrow) fe_dat{fe::kMagicDat, c, set, dim, (double *)ptr};
+  if (!d) return fail(FE_ENOMEM, "fe_dat_create: host allocation");
+  *out = d;
+  return ok();
+}
+
+fe_status fe_dat_destroy(fe_dat *d) {
+  if (!valid(d)) return fail(FE_EHANDLE, "fe_dat_destroy: invalid dat");
+  d->magic = fe::kDead;
+  delete d;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Sparsity
+static void sparsity_free(fe_sparsity *sp) {
+  fe_ctx *c = sp->ctx;
+  dev_free(c, sp->rowptr);
+  dev_free(c, sp->colidx);
+  dev_free(c, sp->lut);
+  dev_free(c, sp->adjptr);
+  dev_free(c, sp->adj);
+  dev_free(c, sp->rowcnt);
+  dev_free(c, sp->coltmp);
+  dev_free(c, sp->scan_tmp);
+  dev_free(c, sp->d_maxcnt);
+}
+
+fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_sparsity_build: invalid context");
+  if (!valid(rmap) || !valid(cmap) || rmap->ctx != c || cmap->ctx != c)
+    return fail(FE_EHANDLE, "fe_sparsity_build: maps belong to another context");
+  if (!out) return fail(FE_EINVAL, "fe_sparsity_build: out is NULL");
+  if (rmap->from != cmap->from) return fail(FE_EINVAL, "fe_sparsity_build: row and column maps need the same source set");
+  const int64_t ncell = rmap->from->size;
+  if (ncell * (int64_t)rmap->arity >= INT32_MAX)
+    return fail(FE_EUNSUPPORTED, "fe_sparsity_build: more than 2^31 cell-node incidences");
+  if (rmap->arity > 64 || cmap->arity > 64) return fail(FE_EUNSUPPORTED, "fe_sparsity_build: arity above 64");
+  DeviceGuard g(c->device);
+  fe_sparsity *sp = new (std::nothrow) fe_sparsity();
+  if (!sp) return fail(FE_ENOMEM, "fe_sparsity_build: host allocation");
+  sp->magic = fe::kMagicSp;
+  sp->ctx = c;
+  sp->rmap = rmap;
+  sp->cmap = cmap;
+  sp->nrows = rmap->to->size;
+  sp->ncols = cmap->to->size;
+  sp->ncell = ncell;
+  sp->ndr = rmap->arity;
+  sp->ndc = cmap->arity;
+  const int64_t ninc = ncell * sp->ndr;
+  sp->scan_tmp_elems = fe::scan_tmp_elems(sp->nrows);
+  sp->rowptr = (int64_t *)dev_alloc(c, sizeof(int64_t) * (sp->nrows + 1));
+  sp->adjptr = (int64_t *)dev_alloc(c, sizeof(int64_t) * (sp->nrows + 1));
+  sp->adj = (int32_t *)dev_alloc(c, sizeof(int32_t) * ninc);
+  sp->rowcnt = (int32_t *)dev_alloc(c, sizeof(int32_t) * sp->nrows);
+  sp->coltmp = (int32_t *)dev_alloc(c, sizeof(int32_t) * ninc * sp->ndc);
+  sp->lut = (uint8_t *)dev_alloc(c, (size_t)ninc * sp->ndc);
+  sp->scan_tmp = (int64_t *)dev_alloc(c, sizeof(int64_t) * sp->scan_tmp_elems);
+  sp->d_maxcnt = (int *)dev_alloc(c, sizeof(int));
+  if (!sp->rowptr || !sp->adjptr || !sp->adj || !sp->rowcnt || !sp->coltmp || !sp->lut || !sp->scan_tmp || !sp->d_maxcnt) {
+    sparsity_free(sp);
+    delete sp;
+    return fail(FE_ENOMEM, "fe_sparsity_build: device allocation failed");
+  }
+  // 1. incidence (validates the row map), learn the longest incidence list
+  cudaError_t e = fe::sparsity_incidence(sp, c->stream, c->d_err);
+  int maxcnt = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&maxcnt, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) {
+    sparsity_free(sp);
+    delete sp;
+    return cuda_fail(e, "fe_sparsity_build");
+  }
+  fe_status st = check_device_flags(c, "fe_sparsity_build");
+  if (st == FE_OK && cmap->to->size > 0 && ncell > 0) {
+    e = fe::launch_map_validate(cmap->values, ncell * cmap->arity, cmap->to->size, c->d_err, c->stream);
+    st = e != cudaSuccess ? cuda_fail(e, "fe_sparsity_build") : check_device_flags(c, "fe_sparsity_build");
+  }
+  if (st != FE_OK) {
+    sparsity_free(sp);
+    delete sp;
+    return st;
+  }
+  const int64_t maxcand = (int64_t)maxcnt * sp->ndc;
+  if (maxcand > fe::kMaxCand) {
+    sparsity_free(sp);
+    delete sp;
+    return fail(FE_EUNSUPPORTED, "fe_sparsity_build: a row has %lld candidate entries (limit %d)", (long long)maxcand,
+                fe::kMaxCand);
+  }
+  sp->cap = 32;
+  while (sp->cap < maxcand) sp->cap <<= 1;
+  // 2. rows: sort, ranks, row lengths, rowptr
+  int64_t nnz = 0;
+  e = fe::sparsity_rows(sp, c->stream, c->d_err);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nnz, sp->rowptr + sp->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) {
+    sparsity_free(sp);
+    delete sp;
+    return cuda_fail(e, "fe_sparsity_build");
+  }
+  st = check_device_flags(c, "fe_sparsity_build");
+  if (st != FE_OK) {
+    sparsity_free(sp);
+    delete sp;
+    return st;
+  }
+  sp->nnz = nnz;
+  sp->colidx = (int32_t *)dev_alloc(c, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  if (!sp->colidx) {
+    sparsity_free(sp);
+    delete sp;
+    return fail(FE_ENOMEM, "fe_sparsity_build: colidx allocation");
+  }
+  // 3. compact the unique columns into colidx
+  e = fe::sparsity_compact(sp, c->stream, c->d_err, 0);
+  if (e != cudaSuccess) {
+    sparsity_free(sp);
+    delete sp;
+    return cuda_fail(e, "fe_sparsity_build");
+  }
+  st = check_device_flags(c, "fe_sparsity_build");
+  if (st != FE_OK) {
+    sparsity_free(sp);
+    delete sp;
+    return st;
+  }
+  *out = sp;
+  return ok();
+}
+
+fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
+  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_rebuild: invalid sparsity");
+  fe_ctx *c = sp->ctx;
+  DeviceGuard g(c->device);
+  FE_CHECK_CUDA(fe::sparsity_incidence(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_rows(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_compact(sp, c->stream, c->d_err, 1), "fe_sparsity_rebuild");
+  return ok();
+}
+
+fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols, int64_t *nnz, const int64_t **rowptr,
+                          const int32_t **colidx) {
+  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_csr: invalid sparsity");
+  if (nrows) *nrows = sp->nrows;
+  if (ncols) *ncols = sp->ncols;
+  if (nnz) *nnz = sp->nnz;
+  if (rowptr) *rowptr = sp->rowptr;
+  if (colidx) *colidx = sp->colidx;
+  return ok();
+}
+
+fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut) {
+  if (!valid(sp) || !lut) return fail(FE_EHANDLE, "fe_sparsity_lut: invalid sparsity");
+  *lut = sp->lut;
+  return ok();
+}
+
+fe_status fe_sparsity_destroy(fe_sparsity *sp) {
+  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_destroy: invalid sparsity");
+  DeviceGuard g(sp->ctx->device);
+  cudaStreamSynchronize(sp->ctx->stream);
+  sparsity_free(sp);
+  sp->magic = fe::kDead;
+  delete sp;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Mat
+fe_status fe_mat_create(fe_ctx *c, fe_sparsity *sp, fe_mat **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_mat_create: invalid context");
+  if (!valid(sp) || sp->ctx != c) return fail(FE_EHANDLE, "fe_mat_create: sparsity belongs to another context");
+  if (!out) return fail(FE_EINVAL, "fe_mat_create: out is NULL");
+  DeviceGuard g(c->device);
+  double *v = (double *)dev_alloc(c, sizeof(double) * (sp->nnz > 0 ? sp->nnz : 1));
+  if (!v) return fail(FE_ENOMEM, "fe_mat_create: values allocation (%lld entries)", (long long)sp->nnz);
+  fe_mat *m = new (std::nothrow) fe_mat{fe::kMagicMat, c, sp, v};
+  if (!m) {
+    dev_free(c, v);
+    return fail(FE_ENOMEM, "fe_mat_create: host allocation");
+  }
+  FE_CHECK_CUDA(fe::launch_zero_f64(v, sp->nnz, c->stream), "fe_mat_create");
+  *out = m;
+  return ok();
+}
+
+fe_status fe_mat_values(const fe_mat *m, double **values) {
+  if (!valid(m) || !values) return fail(FE_EHANDLE, "fe_mat_values: invalid mat");
+  *values = m->values;
+  return ok();
+}
+
+fe_status fe_mat_zero(fe_mat *m) {
+  if (!valid(m)) return fail(FE_EHANDLE, "fe_mat_zero: invalid mat");
+  DeviceGuard g(m->ctx->device);
+  FE_CHECK_CUDA(fe::launch_zero_f64(m->values, m->sp->nnz, m->ctx->stream), "fe_mat_zero");
+  return ok();
+}
+
+fe_status fe_mat_destroy(fe_mat *m) {
+  if (!valid(m)) return fail(FE_EHANDLE, "fe_mat_destroy: invalid mat");
+  DeviceGuard g(m->ctx->device);
+  cudaStreamSynchronize(m->ctx->stream);
+  dev_free(m->ctx, m->values);
+  m->magic = fe::kDead;
+  delete m;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Kernel
+static int num_nodes(int dim, int p) {
+  if (dim == 2) return (p + 1) * (p + 2) / 2;
+  if (dim == 3) return (p + 1) * (p + 2) * (p + 3) / 6;
+  return -1;
+}
+
+fe_status fe_kernel_create(fe_ctx *c, const fe_form_desc *d, fe_kernel **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_kernel_create: invalid context");
+  if (!d || !out) return fail(FE_EINVAL, "fe_kernel_create: NULL argument");
+  if (d->dim < 2 || d->dim > 3 || d->degree < 1) return fail(FE_EINVAL, "fe_kernel_create: dim %d degree %d", d->dim, d->degree);
+  if (!fe::kernel_supported(*d))
+    return fail(FE_EUNSUPPORTED, "fe_kernel_create: form %d on P%d (dim %d, coefficient P%d, precision %d) is not built in",
+                d->form, d->degree, d->dim, d->coeff_degree, d->precision);
+  fe_kernel *k = new (std::nothrow) fe_kernel();
+  if (!k) return fail(FE_ENOMEM, "fe_kernel_create: host allocation");
+  k->magic = fe::kMagicKer;
+  k->ctx = c;
+  k->d = *d;
+  k->nd = num_nodes(d->dim, d->degree);
+  k->nf = d->form == FE_FORM_SOURCE ? num_nodes(d->dim, d->coeff_degree) : d->dim + 1;
+  *out = k;
+  return ok();
+}
+
+fe_status fe_kernel_destroy(fe_kernel *k) {
+  if (!valid(k)) return fail(FE_EHANDLE, "fe_kernel_destroy: invalid kernel");
+  k->magic = fe::kDead;
+  delete k;
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ par_loops
+static fe_status common_args(const char *who, fe_ctx *c, fe_kernel *k, fe_set *cells, fe_map *map, fe_dat *coords,
+                             fe_map *coord_map, fe::AsmArgs &a) {
+  if (!valid(c)) return fail(FE_EHANDLE, "%s: invalid context", who);
+  if (!valid(k) || k->ctx != c) return fail(FE_EHANDLE, "%s: invalid kernel", who);
+  if (!valid(cells) || cells->ctx != c) return fail(FE_EHANDLE, "%s: invalid cell set", who);
+  if (!valid(map) || map->ctx != c) return fail(FE_EHANDLE, "%s: invalid map", who);
+  if (!valid(coords) || coords->ctx != c) return fail(FE_EHANDLE, "%s: invalid coordinate dat", who);
+  if (!valid(coord_map) || coord_map->ctx != c) return fail(FE_EHANDLE, "%s: invalid coordinate map", who);
+  if (map->from != cells || coord_map->from != cells) return fail(FE_EINVAL, "%s: maps must start from the iteration set", who);
+  if (map->arity != k->nd) return fail(FE_EARITY, "%s: map arity %d, element has %d nodes", who, map->arity, k->nd);
+  if (coord_map->arity != k->d.dim + 1) return fail(FE_EARITY, "%s: coordinate map arity %d", who, coord_map->arity);
+  if (coords->dim != k->d.dim || coords->set != coord_map->to)
+    return fail(FE_EINVAL, "%s: coordinates must be a dim-%d Dat on the coordinate map's target", who, k->d.dim);
+  memset(&a, 0, sizeof a);
+  a.ncell = cells->size;
+  a.map = map->values;
+  a.coords = coords->data;
+  a.cmapv = coord_map->values;
+  a.nvert = coords->set->size;
+  a.nrows = map->to->size;
+  a.err = c->d_err;
+  a.checks = c->checks;
+  return FE_OK;
+}
+
+static fe_status kappa_arg(const char *who, fe_ctx *c, fe_kernel *k, fe_set *cells, const fe_arg *coeffs, int ncoeffs,
+                           fe::AsmArgs &a) {
+  if (k->d.form != FE_FORM_KAPPA_DIFFUSION) return FE_OK;
+  if (ncoeffs < 1 || !coeffs || !valid(coeffs[0].dat) || !valid(coeffs[0].map) || coeffs[0].dat->ctx != c)
+    return fail(FE_EINVAL, "%s: kappa-diffusion needs one coefficient", who);
+  if (coeffs[0].map->from != cells || coeffs[0].map->arity != k->d.dim + 1 || coeffs[0].dat->set != coeffs[0].map->to ||
+      coeffs[0].dat->dim != 1)
+    return fail(FE_EARITY, "%s: kappa must be a scalar P1 Dat with a map of arity dim+1", who);
+  a.coef = coeffs[0].dat->data;
+  a.coefmap = coeffs[0].map->values;
+  a.ncoef = coeffs[0].dat->set->size;
+  return FE_OK;
+}
+
+fe_status fe_assemble_mat(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_mat *A, int zero_first, fe_dat *coords,
+                          fe_map *coord_map, const fe_arg *coeffs, int ncoeffs) {
+  const char *who = "fe_assemble_mat";
+  if (!valid(A) || A->ctx != c) return fail(FE_EHANDLE, "%s: invalid mat", who);
+  fe::AsmArgs a;
+  fe_status st = common_args(who, c, k, cells, A->sp->rmap, coords, coord_map, a);
+  if (st != FE_OK) return st;
+  if (A->sp->rmap != A->sp->cmap) return fail(FE_EUNSUPPORTED, "%s: only square forms (same test and trial map)", who);
+  if (k->d.form == FE_FORM_SOURCE) return fail(FE_EINVAL, "%s: a linear form assembles into a Dat", who);
+  st = kappa_arg(who, c, k, cells, coeffs, ncoeffs, a);
+  if (st != FE_OK) return st;
+  a.rowptr = A->sp->rowptr;
+  a.lut = A->sp->lut;
+  a.vals = A->values;
+  a.adjptr = A->sp->adjptr;
+  a.adj = A->sp->adj;
+  DeviceGuard g(c->device);
+  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(A->values, A->sp->nnz, c->stream), who);
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_assemble_mat(k->d, a, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);
+  return ok();
+}
+
+fe_status fe_assemble_vec(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *b, fe_map *test_map, int zero_first,
+                          fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs, int ncoeffs, const fe_sparsity *sp) {
+  const char *who = "fe_assemble_vec";
+  fe::AsmArgs a;
+  fe_status st = common_args(who, c, k, cells, test_map, coords, coord_map, a);
+  if (st != FE_OK) return st;
+  if (k->d.form != FE_FORM_SOURCE) return fail(FE_EINVAL, "%s: kernel is not a linear form", who);
+  if (!valid(b) || b->ctx != c || b->set != test_map->to || b->dim != 1)
+    return fail(FE_EINVAL, "%s: b must be a scalar Dat on the test map's target", who);
+  if (ncoeffs < 1 || !coeffs || !valid(coeffs[0].dat) || !valid(coeffs[0].map) || coeffs[0].map->from != cells ||
+      coeffs[0].map->arity != k->nf || coeffs[0].dat->set != coeffs[0].map->to || coeffs[0].dat->dim != 1)
+    return fail(FE_EARITY, "%s: f must be a scalar Dat with a map of arity %d", who, k->nf);
+  a.coef = coeffs[0].dat->data;
+  a.coefmap = coeffs[0].map->values;
+  a.ncoef = coeffs[0].dat->set->size;
+  a.y = b->data;
+  if (sp && valid(sp)) {
+    a.adjptr = sp->adjptr;
+    a.adj = sp->adj;
+  }
+  DeviceGuard g(c->device);
+  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(b->data, b->set->size, c->stream), who);
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_assemble_vec(k->d, a, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);
+  return ok();
+}
+
+fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y, fe_map *map, int zero_first,
+                    fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs, int ncoeffs, const fe_sparsity *sp) {
+  const char *who = "fe_action";
+  fe::AsmArgs a;
+  fe_status st = common_args(who, c, k, cells, map, coords, coord_map, a);
+  if (st != FE_OK) return st;
+  if (k->d.form == FE_FORM_SOURCE) return fail(FE_EINVAL, "%s: the action needs a bilinear form", who);
+  if (!valid(x) || !valid(y) || x->ctx != c || y->ctx != c || x->set != map->to || y->set != map->to || x->dim != 1 ||
+      y->dim != 1)
+    return fail(FE_EINVAL, "%s: x and y must be scalar Dats on the map's target", who);
+  if (x->data == y->data) return fail(FE_EINVAL, "%s: x and y must not alias", who);
+  st = kappa_arg(who, c, k, cells, coeffs, ncoeffs, a);
+  if (st != FE_OK) return st;
+  a.x = x->data;
+  a.y = y->data;
+  if (sp && valid(sp)) {
+    a.adjptr = sp->adjptr;
+    a.adj = sp->adj;
+  }
+  DeviceGuard g(c->device);
+  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(y->data, y->set->size, c->stream), who);
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_action(k->d, a, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal declarations of libfe: handle layouts and the launch functions of the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fe.h"
+
+namespace fe {
+
+constexpr uint32_t kMagicCtx = 0xFE0C7A11u, kMagicSet = 0xFE05E7u, kMagicMap = 0xFE0AA9u,
+                   kMagicDat = 0xFE0DA7u, kMagicSp = 0xFE05BA25u, kMagicMat = 0xFE0AA7u,
+                   kMagicKer = 0xFE0CE2u, kDead = 0xDEADu;
+
+// device error-flag bits (ctx->d_err[0]); d_err[1] keeps the first offending index (low 32 bits)
+enum : int { ERR_RANGE = 1, ERR_ROW_TOO_LONG = 2, ERR_NNZ_CHANGED = 4, ERR_CAND_OVERFLOW = 8 };
+
+// Rows of the CSR pattern are limited to 256 entries so the lookup table fits a byte.
+constexpr int kMaxRowLen = 256;
+// Per-row candidate capacity of the warp-per-row sparsity kernel (incidence x arity).
+constexpr int kMaxCand = 4096;
+
+}  // namespace fe
+
+struct fe_ctx {
+  uint32_t magic;
+  int device;
+  cudaStream_t stream;
+  fe_alloc_fn alloc;
+  fe_free_fn free_fn;
+  void *user;
+  int checks;
+  int *d_err;  // [4] device ints
+};
+
+struct fe_set {
+  uint32_t magic;
+  fe_ctx *ctx;
+  int64_t size;
+};
+
+struct fe_map {
+  uint32_t magic;
+  fe_ctx *ctx;
+  fe_set *from, *to;
+  int arity;
+  const int32_t *values;
+};
+
+struct fe_dat {
+  uint32_t magic;
+  fe_ctx *ctx;
+  fe_set *set;
+  int dim;
+  double *data;
+};
+
+struct fe_sparsity {
+  uint32_t magic;
+  fe_ctx *ctx;
+  fe_map *rmap, *cmap;
+  int64_t nrows, ncols, ncell;
+  int ndr, ndc;
+  int64_t nnz;       // known after build
+  int cap;           // candidate capacity per row used by the sort kernel (power of two)
+  int64_t *rowptr;   // [nrows+1]
+  int32_t *colidx;   // [nnz]
+  uint8_t *lut;      // [ncell*ndr*ndc]
+  int64_t *adjptr;   // [nrows+1]  row -> incidence range
+  int32_t *adj;      // [ncell*ndr] e*ndr+i, sorted within each row
+  int32_t *rowcnt;   // [nrows] scratch: incidence counts / cursors / unique counts
+  int32_t *coltmp;   // [ncell*ndr*ndc] scratch: unique columns at incidence-based offsets
+  int64_t *scan_tmp; // scan block sums
+  int64_t scan_tmp_elems;
+  int *d_maxcnt;     // [1] max incidence count
+};
+
+struct fe_mat {
+  uint32_t magic;
+  fe_ctx *ctx;
+  fe_sparsity *sp;
+  double *values;
+};
+
+struct fe_kernel {
+  uint32_t magic;
+  fe_ctx *ctx;
+  fe_form_desc d;
+  int nd;  // nodes of the test/trial element
+  int nf;  // nodes of the coefficient element (SOURCE) or dim+1 (kappa)
+};
+
+namespace fe {
+
+// ---- scan ----
+int64_t scan_tmp_elems(int64_t n);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.  tmp: scan_tmp_elems(n) int64.
+cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                                      cudaStream_t s);
+
+// ---- maps / sparsity ----
+cudaError_t launch_map_validate(const int32_t *v, int64_t n, int64_t limit, int *err, cudaStream_t s);
+// incidence: counts -> adjptr (scan) -> adj fill; also the max count
+cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err);
+// sort rows, write lut, unique columns (coltmp), row lengths -> rowptr (scan) -> compact colidx.
+// capacity_check: flags ERR_NNZ_CHANGED if rowptr[nrows] != sp->nnz (rebuild); when nnz_known == 0
+// the colidx compaction is skipped (build: host learns nnz first, then calls sparsity_compact).
+cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err);
+cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz);
+
+// ---- fills ----
+cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s);
+
+// ---- assembly ----
+struct AsmArgs {
+  int64_t ncell;
+  const int32_t *map;     // [ncell][nd] test (= trial) map
+  const double *coords;   // [nvert][dim]
+  const int32_t *cmapv;   // [ncell][dim+1] coordinate map
+  int64_t nvert;          // coordinate set size
+  int64_t nrows;          // target set size of map
+  const double *coef;     // kappa (P1) or f values, may be null
+  const int32_t *coefmap; // its map
+  int64_t ncoef;          // size of the coefficient's set
+  // Mat output
+  const int64_t *rowptr;
+  const uint8_t *lut;
+  double *vals;
+  // incidence (pull)
+  const int64_t *adjptr;
+  const int32_t *adj;
+  // vector input/output
+  const double *x;
+  double *y;
+  int *err;
+  int checks;
+};
+cudaError_t launch_assemble_mat(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
+cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
+cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
+bool kernel_supported(const fe_form_desc &d);
+
+}  // namespace fe

@@ -1,0 +1,100 @@
+// Arithmetic policies and affine-simplex geometry for the local kernels.
+#pragma once
+#include <stdint.h>
+
+namespace fe {
+
+// Native IEEE FP64.
+struct OpsF64 {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T mulc(T a, double c) { return a * c; }
+  static __device__ __forceinline__ T fmac(T a, double c, T acc) { return fma(a, c, acc); }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T fma3(T a, T b, T c) { return fma(a, b, c); }
+  static __device__ __forceinline__ T from_f64(double x) { return x; }
+  static __device__ __forceinline__ double to_f64(T x) { return x; }
+};
+
+template <int DIM> struct Geo;
+
+// Barycentric geometry of an affine triangle.  With e_c = x_c - x_0 (c = 1, 2), J = [e1 e2]
+// and a_m = det(J) * grad(lambda_m) (the rows of adj(J)), for m, n >= 1
+//   Lam_mn = |T| grad(lambda_m) . grad(lambda_n) = (a_m . a_n) / (2 |det J|),
+// and the rows/columns of lambda_0 follow from sum_m grad(lambda_m) = 0.
+// Lam is stored over the pairs (m <= n) in lexicographic order; vol = |T| = |det J| / 2.
+template <> struct Geo<2> {
+  static constexpr int NV = 3, NLAM = 6;
+  template <class Ops>
+  static __device__ __forceinline__ void compute(const double (&x)[3][2], typename Ops::T *Lam, typename Ops::T &vol) {
+    using T = typename Ops::T;
+    T e1x = Ops::from_f64(x[1][0] - x[0][0]), e1y = Ops::from_f64(x[1][1] - x[0][1]);
+    T e2x = Ops::from_f64(x[2][0] - x[0][0]), e2y = Ops::from_f64(x[2][1] - x[0][1]);
+    T det = Ops::add(Ops::mul(e1x, e2y), Ops::neg(Ops::mul(e1y, e2x)));
+    double d = Ops::to_f64(det);
+    double adet = d < 0 ? -d : d;
+    double s = 1.0 / (2.0 * adet);
+    vol = Ops::from_f64(0.5 * adet);
+    // a1 = (e2y, -e2x), a2 = (-e1y, e1x)
+    T L11 = Ops::mulc(Ops::add(Ops::mul(e2y, e2y), Ops::mul(e2x, e2x)), s);
+    T L12 = Ops::mulc(Ops::neg(Ops::add(Ops::mul(e2y, e1y), Ops::mul(e2x, e1x))), s);
+    T L22 = Ops::mulc(Ops::add(Ops::mul(e1y, e1y), Ops::mul(e1x, e1x)), s);
+    T L01 = Ops::neg(Ops::add(L11, L12));
+    T L02 = Ops::neg(Ops::add(L12, L22));
+    T L00 = Ops::neg(Ops::add(L01, L02));
+    Lam[0] = L00; Lam[1] = L01; Lam[2] = L02; Lam[3] = L11; Lam[4] = L12; Lam[5] = L22;
+  }
+};
+
+// Barycentric geometry of an affine tetrahedron: a_1 = e2 x e3, a_2 = e3 x e1, a_3 = e1 x e2
+// (= det(J) grad(lambda_m)), det J = e1 . a_1, Lam_mn = (a_m . a_n) / (6 |det J|), vol = |det J| / 6.
+template <> struct Geo<3> {
+  static constexpr int NV = 4, NLAM = 10;
+  template <class Ops>
+  static __device__ __forceinline__ void compute(const double (&x)[4][3], typename Ops::T *Lam, typename Ops::T &vol) {
+    using T = typename Ops::T;
+    T e[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) e[c][k] = Ops::from_f64(x[c + 1][k] - x[0][k]);
+    T a[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+      const T *p = e[(m + 1) % 3], *q = e[(m + 2) % 3];
+      a[m][0] = Ops::add(Ops::mul(p[1], q[2]), Ops::neg(Ops::mul(p[2], q[1])));
+      a[m][1] = Ops::add(Ops::mul(p[2], q[0]), Ops::neg(Ops::mul(p[0], q[2])));
+      a[m][2] = Ops::add(Ops::mul(p[0], q[1]), Ops::neg(Ops::mul(p[1], q[0])));
+    }
+    T det = Ops::add(Ops::add(Ops::mul(e[0][0], a[0][0]), Ops::mul(e[0][1], a[0][1])), Ops::mul(e[0][2], a[0][2]));
+    double d = Ops::to_f64(det);
+    double adet = d < 0 ? -d : d;
+    double s = 1.0 / (6.0 * adet);
+    vol = Ops::from_f64(adet / 6.0);
+    T L[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+      for (int n = m; n < 3; n++) {
+        T dot = Ops::add(Ops::add(Ops::mul(a[m][0], a[n][0]), Ops::mul(a[m][1], a[n][1])), Ops::mul(a[m][2], a[n][2]));
+        L[m][n] = Ops::mulc(dot, s);
+        L[n][m] = L[m][n];
+      }
+    T L0[3];
+#pragma unroll
+    for (int n = 0; n < 3; n++) L0[n] = Ops::neg(Ops::add(Ops::add(L[0][n], L[1][n]), L[2][n]));
+    Lam[0] = Ops::neg(Ops::add(Ops::add(L0[0], L0[1]), L0[2]));
+    Lam[1] = L0[0]; Lam[2] = L0[1]; Lam[3] = L0[2];
+    Lam[4] = L[0][0]; Lam[5] = L[0][1]; Lam[6] = L[0][2];
+    Lam[7] = L[1][1]; Lam[8] = L[1][2];
+    Lam[9] = L[2][2];
+  }
+};
+
+__device__ __forceinline__ void red_add_f64(double *p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+}  // namespace fe

@@ -1,0 +1,342 @@
+"""Thin ctypes binding of libfe (include/fe.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name (without the ``fe_``
+prefix); all computation runs in libfe's CUDA kernels.  PyTorch provides device memory
+(tensors passed in are borrowed; library-owned buffers come from torch's caching allocator
+through fe_ctx_set_allocator) and the CUDA stream (torch's current stream by default).
+There is no CPU fallback: importing this module without a built libfe.so raises, and so does
+creating a context without a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libfe.so")
+
+FE_OK, FE_EINVAL, FE_EHANDLE, FE_ERANGE, FE_EARITY, FE_ENOMEM, FE_ECUDA, FE_ETIMEOUT, FE_EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+FORM_MASS, FORM_LAPLACE, FORM_HELMHOLTZ, FORM_KAPPA_DIFFUSION, FORM_SOURCE = 1, 2, 3, 4, 5
+PREC_FP64, PREC_F32X2 = 0, 1
+STRATEGY_AUTO, STRATEGY_PUSH, STRATEGY_PULL = 0, 1, 2
+
+SYMBOLS = [
+    "fe_last_error", "fe_version", "fe_ctx_create", "fe_ctx_set_stream", "fe_ctx_set_allocator",
+    "fe_ctx_set_checks", "fe_sync", "fe_ctx_destroy", "fe_set_create", "fe_set_size", "fe_set_destroy",
+    "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
+    "fe_sparsity_rebuild", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
+    "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
+    "fe_assemble_mat", "fe_assemble_vec", "fe_action",
+]
+
+
+class FeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class fe_form_desc(C.Structure):
+    _fields_ = [("form", C.c_int), ("dim", C.c_int), ("degree", C.c_int), ("coeff_degree", C.c_int),
+                ("precision", C.c_int), ("strategy", C.c_int)]
+
+
+class fe_arg(C.Structure):
+    _fields_ = [("dat", C.c_void_p), ("map", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Loads libfe.so (built by ``paper_1501_01809_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libfe.so is not built ({_LIB_PATH}); run `python -m paper_1501_01809_gb300.build`")
+    lib = C.CDLL(_LIB_PATH)
+    P, I64, I = C.c_void_p, C.c_int64, C.c_int
+    PP = C.POINTER(C.c_void_p)
+    sig = {
+        "fe_last_error": (C.c_char_p, []), "fe_version": (C.c_char_p, []),
+        "fe_ctx_create": (I, [I, P, PP]), "fe_ctx_set_stream": (I, [P, P]),
+        "fe_ctx_set_allocator": (I, [P, ALLOC_FN, FREE_FN, P]), "fe_ctx_set_checks": (I, [P, I]),
+        "fe_sync": (I, [P]), "fe_ctx_destroy": (I, [P]),
+        "fe_set_create": (I, [P, I64, PP]), "fe_set_size": (I, [P, C.POINTER(I64)]), "fe_set_destroy": (I, [P]),
+        "fe_map_create": (I, [P, P, P, I, P, I, PP]), "fe_map_destroy": (I, [P]),
+        "fe_dat_create": (I, [P, P, I, P, PP]), "fe_dat_destroy": (I, [P]),
+        "fe_sparsity_build": (I, [P, P, P, PP]), "fe_sparsity_rebuild": (I, [P]),
+        "fe_sparsity_csr": (I, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), PP, PP]),
+        "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_destroy": (I, [P]),
+        "fe_mat_create": (I, [P, P, PP]), "fe_mat_values": (I, [P, PP]), "fe_mat_zero": (I, [P]),
+        "fe_mat_destroy": (I, [P]),
+        "fe_kernel_create": (I, [P, C.POINTER(fe_form_desc), PP]), "fe_kernel_destroy": (I, [P]),
+        "fe_assemble_mat": (I, [P, P, P, P, I, P, P, C.POINTER(fe_arg), I]),
+        "fe_assemble_vec": (I, [P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
+        "fe_action": (I, [P, P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != FE_OK:
+        raise FeError(rc, load().fe_last_error().decode())
+
+
+def version() -> str:
+    return load().fe_version().decode()
+
+
+class _CudaView:
+    """__cuda_array_interface__ wrapper so torch can view library-owned device memory."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, n, dtype, owner, device):
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.uint8: "|u1", torch.float64: "<f8"}[dtype]
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    return torch.as_tensor(_CudaView(ptr, (n,), typestr, owner), device=device)
+
+
+class Handle:
+    _destroy = None
+
+    def __init__(self, ptr, ctx, keep=()):
+        self.ptr = ptr
+        self.ctx = ctx
+        self._keep = list(keep)
+
+    def destroy(self):
+        if self.ptr is not None and self._destroy and _lib is not None:
+            getattr(_lib, self._destroy)(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Ctx(Handle):
+    _destroy = "fe_ctx_destroy"
+
+    def __init__(self, ptr, device, stream, alloc_cbs):
+        super().__init__(ptr, None)
+        self.device = device
+        self.stream = stream
+        self._alloc_cbs = alloc_cbs
+
+
+class Set(Handle):
+    _destroy = "fe_set_destroy"
+
+
+class Map(Handle):
+    _destroy = "fe_map_destroy"
+
+
+class Dat(Handle):
+    _destroy = "fe_dat_destroy"
+
+
+class Sparsity(Handle):
+    _destroy = "fe_sparsity_destroy"
+
+
+class Mat(Handle):
+    _destroy = "fe_mat_destroy"
+
+
+class Kernel(Handle):
+    _destroy = "fe_kernel_destroy"
+
+
+def _torch_alloc(nbytes, user):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device())
+    except Exception:
+        return None
+
+
+def _torch_free(ptr, user):
+    try:
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+# ----------------------------------------------------------------------------------- C entry points
+
+def ctx_create(device: int = 0, stream=None, torch_allocator: bool = True, checks: bool = False) -> Ctx:
+    """fe_ctx_create (+ fe_ctx_set_allocator with torch's caching allocator, fe_ctx_set_checks)."""
+    lib = load()
+    if not torch.cuda.is_available():
+        raise RuntimeError("libfe needs a CUDA device; there is no CPU fallback")
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    out = C.c_void_p()
+    _check(lib.fe_ctx_create(device, C.c_void_p(stream.cuda_stream), C.byref(out)))
+    cbs = None
+    if torch_allocator:
+        cbs = (ALLOC_FN(_torch_alloc), FREE_FN(_torch_free))
+        _check(lib.fe_ctx_set_allocator(out, cbs[0], cbs[1], None))
+    if checks:
+        _check(lib.fe_ctx_set_checks(out, 1))
+    return Ctx(out, device, stream, cbs)
+
+
+def ctx_set_stream(ctx: Ctx, stream) -> None:
+    _check(load().fe_ctx_set_stream(ctx.ptr, C.c_void_p(stream.cuda_stream)))
+    ctx.stream = stream
+
+
+def ctx_set_checks(ctx: Ctx, checks: bool) -> None:
+    _check(load().fe_ctx_set_checks(ctx.ptr, int(bool(checks))))
+
+
+def sync(ctx: Ctx) -> None:
+    """fe_sync: waits for the stream and raises on device-side errors (FE_ERANGE ...)."""
+    _check(load().fe_sync(ctx.ptr))
+
+
+def set_create(ctx: Ctx, size: int) -> Set:
+    out = C.c_void_p()
+    _check(load().fe_set_create(ctx.ptr, int(size), C.byref(out)))
+    return Set(out, ctx)
+
+
+def set_size(s: Set) -> int:
+    v = C.c_int64()
+    _check(load().fe_set_size(s.ptr, C.byref(v)))
+    return v.value
+
+
+def _dev_tensor(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+    return t
+
+
+def map_create(ctx: Ctx, frm: Set, to: Set, values: torch.Tensor, validate: bool = False) -> Map:
+    """fe_map_create: values is a device int32 tensor [frm.size, arity] (borrowed)."""
+    values = _dev_tensor(values, torch.int32, "map values")
+    arity = values.shape[1] if values.dim() == 2 else 1
+    out = C.c_void_p()
+    _check(load().fe_map_create(ctx.ptr, frm.ptr, to.ptr, int(arity), C.c_void_p(values.data_ptr()),
+                                int(bool(validate)), C.byref(out)))
+    m = Map(out, ctx, keep=(values, frm, to))
+    m.arity = arity
+    return m
+
+
+def dat_create(ctx: Ctx, s: Set, data: torch.Tensor) -> Dat:
+    """fe_dat_create: data is a device float64 tensor [s.size] or [s.size, dim] (borrowed)."""
+    data = _dev_tensor(data, torch.float64, "dat data")
+    dim = data.shape[1] if data.dim() == 2 else 1
+    out = C.c_void_p()
+    _check(load().fe_dat_create(ctx.ptr, s.ptr, int(dim), C.c_void_p(data.data_ptr()), C.byref(out)))
+    d = Dat(out, ctx, keep=(data, s))
+    d.data = data
+    return d
+
+
+def sparsity_build(ctx: Ctx, rmap: Map, cmap: Map) -> Sparsity:
+    out = C.c_void_p()
+    _check(load().fe_sparsity_build(ctx.ptr, rmap.ptr, cmap.ptr, C.byref(out)))
+    return Sparsity(out, ctx, keep=(rmap, cmap))
+
+
+def sparsity_rebuild(sp: Sparsity) -> None:
+    _check(load().fe_sparsity_rebuild(sp.ptr))
+
+
+def sparsity_csr(sp: Sparsity):
+    """(nrows, ncols, nnz, rowptr view int64 [nrows+1], colidx view int32 [nnz]) -- zero-copy views."""
+    nr, nc, nnz = C.c_int64(), C.c_int64(), C.c_int64()
+    rp, ci = C.c_void_p(), C.c_void_p()
+    _check(load().fe_sparsity_csr(sp.ptr, C.byref(nr), C.byref(nc), C.byref(nnz), C.byref(rp), C.byref(ci)))
+    dev = torch.device("cuda", sp.ctx.device)
+    return (nr.value, nc.value, nnz.value, _view(rp.value, nr.value + 1, torch.int64, sp, dev),
+            _view(ci.value, nnz.value, torch.int32, sp, dev))
+
+
+def sparsity_lut(sp: Sparsity, ncell: int, ndr: int, ndc: int) -> torch.Tensor:
+    p = C.c_void_p()
+    _check(load().fe_sparsity_lut(sp.ptr, C.byref(p)))
+    return _view(p.value, ncell * ndr * ndc, torch.uint8, sp, torch.device("cuda", sp.ctx.device))
+
+
+def mat_create(ctx: Ctx, sp: Sparsity) -> Mat:
+    out = C.c_void_p()
+    _check(load().fe_mat_create(ctx.ptr, sp.ptr, C.byref(out)))
+    return Mat(out, ctx, keep=(sp,))
+
+
+def mat_values(A: Mat) -> torch.Tensor:
+    p = C.c_void_p()
+    _check(load().fe_mat_values(A.ptr, C.byref(p)))
+    nnz = sparsity_csr(A._keep[0])[2]
+    return _view(p.value, nnz, torch.float64, A, torch.device("cuda", A.ctx.device))
+
+
+def mat_zero(A: Mat) -> None:
+    _check(load().fe_mat_zero(A.ptr))
+
+
+def kernel_create(ctx: Ctx, form: int, dim: int, degree: int, coeff_degree: int = 1,
+                  precision: int = PREC_FP64, strategy: int = STRATEGY_AUTO) -> Kernel:
+    d = fe_form_desc(form, dim, degree, coeff_degree, precision, strategy)
+    out = C.c_void_p()
+    _check(load().fe_kernel_create(ctx.ptr, C.byref(d), C.byref(out)))
+    return Kernel(out, ctx)
+
+
+def _args(coeffs):
+    coeffs = list(coeffs or [])
+    arr = (fe_arg * max(1, len(coeffs)))()
+    for i, (d, m) in enumerate(coeffs):
+        arr[i].dat, arr[i].map = d.ptr, m.ptr
+    return arr, len(coeffs)
+
+
+def assemble_mat(ctx: Ctx, k: Kernel, cells: Set, A: Mat, coords: Dat, coord_map: Map,
+                 coeffs=(), zero_first: bool = True) -> None:
+    """fe_assemble_mat: A(INC) over cells; coeffs = [(Dat, Map), ...] READ."""
+    arr, n = _args(coeffs)
+    _check(load().fe_assemble_mat(ctx.ptr, k.ptr, cells.ptr, A.ptr, int(bool(zero_first)), coords.ptr,
+                                  coord_map.ptr, arr, n))
+
+
+def assemble_vec(ctx: Ctx, k: Kernel, cells: Set, b: Dat, test_map: Map, coords: Dat, coord_map: Map,
+                 coeffs=(), zero_first: bool = True, sp: Sparsity | None = None) -> None:
+    arr, n = _args(coeffs)
+    _check(load().fe_assemble_vec(ctx.ptr, k.ptr, cells.ptr, b.ptr, test_map.ptr, int(bool(zero_first)),
+                                  coords.ptr, coord_map.ptr, arr, n, sp.ptr if sp is not None else None))
+
+
+def action(ctx: Ctx, k: Kernel, cells: Set, x: Dat, y: Dat, map_: Map, coords: Dat, coord_map: Map,
+           coeffs=(), zero_first: bool = True, sp: Sparsity | None = None) -> None:
+    arr, n = _args(coeffs)
+    _check(load().fe_action(ctx.ptr, k.ptr, cells.ptr, x.ptr, y.ptr, map_.ptr, int(bool(zero_first)),
+                            coords.ptr, coord_map.ptr, arr, n, sp.ptr if sp is not None else None))

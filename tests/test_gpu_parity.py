@@ -1,0 +1,142 @@
+"""CUDA path vs the CPU oracle on the same seeded inputs (runs on the GB300 machine).
+
+Sparsity: bitwise identical CSR.  Lookup table: exhaustive check that every (e, i, j) points at
+column map(e)[j] of row map(e)[i].  Values: per entry |a - a_ref| <= 1e-12 * S_ij with S_ij the
+sum of |element contributions| (the oracle accumulates S), and relative Frobenius <= 1e-12.
+Sizes span several CTAs and leave ragged tails (cell counts not multiples of the block size).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import problems as PB
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # dim, p, n, jitter
+    (2, 1, 64, 0.0),    # the P1 UnitSquareMesh 64x64 workload (8192 cells)
+    (2, 1, 37, 0.2),
+    (2, 2, 23, 0.2),
+    (2, 3, 9, 0.2),
+    (2, 4, 17, 0.2),
+    (3, 1, 9, 0.2),
+    (3, 2, 7, 0.2),
+    (3, 3, 3, 0.2),
+]
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_01809_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.mark.parametrize("dim,p,n,jit", CASES)
+def test_sparsity_bitwise_and_lut(gpu, dim, p, n, jit):
+    pr = PB.make(dim, p, n, jit, seed=3)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    orp, oci = O.sparsity(pr.cmap, pr.cmap, pr.nnodes, pr.nnodes)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(ci, oci)
+    nd = pr.cmap.shape[1]
+    lut = g.fe.sparsity_lut(g.sparsity(), pr.mesh.ncell, nd, nd).cpu().numpy().reshape(-1, nd, nd).astype(np.int64)
+    pos = rp[pr.cmap][:, :, None] + lut
+    np.testing.assert_array_equal(ci[pos], np.broadcast_to(pr.cmap[:, None, :], pos.shape))
+
+
+@pytest.mark.parametrize("dim,p,n,jit", CASES)
+@pytest.mark.parametrize("form", [1, 2, 3, 4])
+def test_assemble_mat_matches_oracle(gpu, dim, p, n, jit, form):
+    if form == 4 and (dim, p) not in [(2, 1), (2, 2), (2, 4), (3, 1), (3, 2)]:
+        pytest.skip("kappa-diffusion built for P1/P2/P4 triangles and P1/P2 tets")
+    pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    got = g.assemble(form)
+    want, scale = O.assemble_mat(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
+    PB.assert_close_scaled(got, want, scale, 1e-12, f"form {form} P{p} dim {dim}")
+
+
+@pytest.mark.parametrize("dim,p,n,jit", CASES[:1] + CASES[2:3] + CASES[6:7])
+@pytest.mark.parametrize("form", [3, 4])
+def test_action_matches_oracle(gpu, dim, p, n, jit, form):
+    if form == 4 and (dim, p) not in [(2, 1), (2, 2), (2, 4), (3, 1), (3, 2)]:
+        pytest.skip("kappa-diffusion built for P1/P2/P4 triangles and P1/P2 tets")
+    pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr)
+    x = np.random.default_rng(2).uniform(-1, 1, pr.nnodes)
+    got = g.action(form, x)
+    want, scale = O.action(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, x, kappa=pr.kappa)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "action")
+
+
+@pytest.mark.parametrize("dim,p,pf,n", [(2, 1, 1, 64), (2, 2, 2, 11), (2, 2, 1, 11), (2, 4, 1, 6), (3, 1, 1, 5),
+                                         (3, 2, 2, 4), (3, 2, 1, 4)])
+def test_assemble_vec_matches_oracle(gpu, dim, p, pf, n):
+    from paper_1501_01809_gb300 import meshgen as mg
+    pr = PB.make(dim, p, n, 0.2 if n > 6 else 0.0, seed=4)
+    g = PB.GpuProblem(pr)
+    fmap, nf = mg.cell_node_map(pr.mesh, pf)
+    f = mg.uniform_dat(nf, 1)
+    got = g.rhs(f, fmap, pf, nf)
+    want, scale = O.assemble_vec(dim, p, pf, pr.cmap, pr.nnodes, pr.mesh.coords, pr.mesh.cell_vertex, f, fmap)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "rhs")
+
+
+def test_rebuild_is_bitwise_stable(gpu):
+    pr = PB.make(3, 2, 5, 0.2, seed=0)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    lut0 = g.fe.sparsity_lut(g.sparsity(), pr.mesh.ncell, 10, 10).cpu().numpy().copy()
+    for _ in range(2):
+        g.fe.sparsity_rebuild(g.sparsity())
+        g.fe.sync(g.ctx)
+        rp2, ci2 = g.csr()
+        np.testing.assert_array_equal(rp, rp2)
+        np.testing.assert_array_equal(ci, ci2)
+        np.testing.assert_array_equal(lut0, g.fe.sparsity_lut(g.sparsity(), pr.mesh.ncell, 10, 10).cpu().numpy())
+
+
+def test_rectangular_sparsity(gpu):
+    """Rows from P2 nodes, columns from P1 nodes (Sec. 4.4.3: two different maps)."""
+    from paper_1501_01809_gb300 import meshgen as mg
+    pr = PB.make(2, 2, 6, 0.0)
+    g = PB.GpuProblem(pr)
+    c1, n1 = mg.cell_node_map(pr.mesh, 1)
+    s1 = g.fe.set_create(g.ctx, n1)
+    t1 = g.torch.from_numpy(c1).cuda()
+    m1 = g.fe.map_create(g.ctx, g.cells, s1, t1)
+    sp = g.fe.sparsity_build(g.ctx, g.map, m1)
+    nr, nc, nnz, rp, ci = g.fe.sparsity_csr(sp)
+    orp, oci = O.sparsity(pr.cmap, c1, pr.nnodes, n1)
+    assert (nr, nc) == (pr.nnodes, n1)
+    np.testing.assert_array_equal(rp.cpu().numpy(), orp)
+    np.testing.assert_array_equal(ci.cpu().numpy(), oci)
+    lut = g.fe.sparsity_lut(sp, pr.mesh.ncell, 6, 3).cpu().numpy().reshape(-1, 6, 3).astype(np.int64)
+    pos = orp[pr.cmap][:, :, None] + lut
+    np.testing.assert_array_equal(oci[pos], np.broadcast_to(c1[:, None, :], pos.shape))
+
+
+def test_single_cell_and_empty_mesh(gpu):
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(2, 2, 1, 0.0)
+    pr.mesh.cell_vertex = pr.mesh.cell_vertex[:1].copy()
+    pr.cmap = pr.cmap[:1].copy()
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    got = g.assemble(fe.FORM_HELMHOLTZ)
+    want, scale = O.assemble_mat(2, 2, 3, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "one cell")
+    # an empty iteration set assembles nothing and builds an empty pattern over the nodes
+    ctx = g.ctx
+    cells0 = fe.set_create(ctx, 0)
+    import torch
+    m0 = fe.map_create(ctx, cells0, g.nodes, torch.zeros((0, 6), dtype=torch.int32, device="cuda"))
+    sp0 = fe.sparsity_build(ctx, m0, m0)
+    nr, nc, nnz, rp0, ci0 = fe.sparsity_csr(sp0)
+    assert nnz == 0 and int(rp0[-1]) == 0 and nr == pr.nnodes
