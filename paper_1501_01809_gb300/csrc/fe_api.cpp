@@ -315,6 +315,8 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
   }
   sp->cap = 32;
   while (sp->cap < maxcand) sp->cap <<= 1;
+  sp->acap = 4;
+  while (sp->acap < maxcnt) sp->acap += 4;
   // 2. rows: sort, ranks, row lengths, rowptr
   int64_t nnz = 0;
   e = fe::sparsity_rows(sp, c->stream, c->d_err);

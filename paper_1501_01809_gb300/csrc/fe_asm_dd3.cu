@@ -1,0 +1,25 @@
+// Double-float (FP32 pair) instantiations of the assembly kernels on tetrahedra: P1 and P2 (the
+// element tensors of the larger elements are compiled in FP64 only).
+#include "fe_kernels.cuh"
+
+namespace fe {
+using namespace kern;
+using OPS = OpsF32x2;
+
+#define FE_BILINEAR_TABLE(W) \
+  FE_FORMS_FOR(3, 1, W) FE_FORMS_FOR(3, 2, W) FE_KAPPA_FOR(3, 1, W) FE_KAPPA_FOR(3, 2, W)
+
+LaunchFn pick_mat_push_dd3(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(mat_push)
+  return nullptr;
+}
+LaunchFn pick_action_push_dd3(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(action_push)
+  return nullptr;
+}
+LaunchFn pick_vec_push_dd3(const fe_form_desc &d) {
+  FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
+  return nullptr;
+}
+
+}  // namespace fe

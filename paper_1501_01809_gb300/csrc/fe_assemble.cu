@@ -1,238 +1,38 @@
-// Cell-wise assembly par_loops (Sec. 4.4 of the paper): for every cell, staging in (gather the
-// vertex coordinates through the coordinate map and the coefficients through their maps), the
-// local kernel (geometry + generated element-tensor contraction), and staging out (INC into the
-// global CSR Mat through the per-cell lookup table, or into a Dat through the map).
-//
-// Push strategy: one thread per cell, FP64 atomic adds (red.global.add.f64) for the INC.
+// Dispatch of the assembly par_loops to the compiled kernel instantiations.
 #include <cuda_runtime.h>
-#include <stdint.h>
 
 #include "fe_internal.h"
-#include "fe_ops.cuh"
-#include "generated/fe_local.cuh"
 
 namespace fe {
+
+LaunchFn pick_mat_push_f64(const fe_form_desc &d);
+LaunchFn pick_action_push_f64(const fe_form_desc &d);
+LaunchFn pick_vec_push_f64(const fe_form_desc &d);
+LaunchFn pick_mat_push_dd2(const fe_form_desc &d);
+LaunchFn pick_action_push_dd2(const fe_form_desc &d);
+LaunchFn pick_vec_push_dd2(const fe_form_desc &d);
+LaunchFn pick_mat_push_dd3(const fe_form_desc &d);
+LaunchFn pick_action_push_dd3(const fe_form_desc &d);
+LaunchFn pick_vec_push_dd3(const fe_form_desc &d);
+
 namespace {
 
-constexpr int kPushThreads = 128;
-
-__device__ __forceinline__ void flag(int *err, int bit, int64_t idx) {
-  if (atomicOr(err, bit) == 0) err[1] = (int)idx;
-}
-
-template <int DIM, int P, int FORM, class Ops>
-__device__ __forceinline__ void element_upper(const typename Ops::T *Lam, const typename Ops::T &vol,
-                                              const typename Ops::T *kap, typename Ops::T *K) {
-  using E = fe_gen::Elem<DIM, P>;
-  if constexpr (FORM == FE_FORM_MASS) {
-    E::template mass_upper<Ops>(vol, K);
-  } else if constexpr (FORM == FE_FORM_LAPLACE) {
-    E::template stiffness_upper<Ops>(Lam, K);
-  } else if constexpr (FORM == FE_FORM_HELMHOLTZ) {
-    E::template stiffness_upper<Ops>(Lam, K);
-    E::template mass_upper_add<Ops>(vol, K);
-  } else {
-    constexpr int NL = Geo<DIM>::NLAM;
-    typename Ops::T KL[(DIM + 1) * NL];
-#pragma unroll
-    for (int k = 0; k <= DIM; k++)
-#pragma unroll
-      for (int t = 0; t < NL; t++) KL[k * NL + t] = Ops::mul(kap[k], Lam[t]);
-    fe_gen::Kappa<DIM, P>::template upper<Ops>(KL, K);
-  }
-}
-
-// staging in of the vertex coordinates; returns false on an out-of-range coordinate-map value
-template <int DIM>
-__device__ __forceinline__ bool gather_coords(const AsmArgs &a, int64_t e, double (&x)[DIM + 1][DIM], int32_t (&v)[DIM + 1]) {
-  bool ok = true;
-#pragma unroll
-  for (int m = 0; m <= DIM; m++) {
-    v[m] = a.cmapv[e * (DIM + 1) + m];
-    if (a.checks && (v[m] < 0 || v[m] >= a.nvert)) {
-      ok = false;
-      v[m] = 0;
-    }
-#pragma unroll
-    for (int c = 0; c < DIM; c++) x[m][c] = a.coords[(int64_t)v[m] * DIM + c];
-  }
-  return ok;
-}
-
-template <int ND>
-__device__ __forceinline__ bool gather_rows(const AsmArgs &a, int64_t e, int32_t (&rows)[ND]) {
-  bool ok = true;
-#pragma unroll
-  for (int i = 0; i < ND; i++) {
-    rows[i] = a.map[e * ND + i];
-    if (a.checks && (rows[i] < 0 || rows[i] >= a.nrows)) {
-      ok = false;
-      rows[i] = 0;
-    }
-  }
-  return ok;
-}
-
-template <int DIM>
-__device__ __forceinline__ bool gather_kappa(const AsmArgs &a, int64_t e, double (&kap)[DIM + 1]) {
-  bool ok = true;
-#pragma unroll
-  for (int m = 0; m <= DIM; m++) {
-    int32_t v = a.coefmap[e * (DIM + 1) + m];
-    if (a.checks && (v < 0 || v >= a.ncoef)) {
-      ok = false;
-      v = 0;
-    }
-    kap[m] = a.coef[v];
-  }
-  return ok;
-}
-
-// ---------------------------------------------------------------------------- Mat, push, FP64
-template <int DIM, int P, int FORM>
-__global__ void __launch_bounds__(kPushThreads) k_mat_push_f64(const AsmArgs a) {
-  using E = fe_gen::Elem<DIM, P>;
-  constexpr int ND = E::ND;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
-  double x[DIM + 1][DIM], kap[DIM + 1];
-  int32_t v[DIM + 1], rows[ND];
-  bool ok = gather_coords<DIM>(a, e, x, v);
-  ok &= gather_rows<ND>(a, e, rows);
-  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) ok &= gather_kappa<DIM>(a, e, kap);
-  if (!ok) {
-    flag(a.err, ERR_RANGE, e);
-    return;
-  }
-  double Lam[Geo<DIM>::NLAM], vol;
-  Geo<DIM>::template compute<OpsF64>(x, Lam, vol);
-  double K[E::NUP];
-  element_upper<DIM, P, FORM, OpsF64>(Lam, vol, kap, K);
-  const uint8_t *L = a.lut + e * (ND * ND);
-#pragma unroll
-  for (int i = 0; i < ND; i++) {
-    double *rowv = a.vals + a.rowptr[rows[i]];
-#pragma unroll
-    for (int j = 0; j < ND; j++) red_add_f64(rowv + L[i * ND + j], K[E::upper_index(i, j)]);
-  }
-}
-
-// ---------------------------------------------------------------------------- action, push, FP64
-template <int DIM, int P, int FORM>
-__global__ void __launch_bounds__(kPushThreads) k_action_push_f64(const AsmArgs a) {
-  using E = fe_gen::Elem<DIM, P>;
-  constexpr int ND = E::ND;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
-  double x[DIM + 1][DIM], kap[DIM + 1];
-  int32_t v[DIM + 1], rows[ND];
-  bool ok = gather_coords<DIM>(a, e, x, v);
-  ok &= gather_rows<ND>(a, e, rows);
-  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) ok &= gather_kappa<DIM>(a, e, kap);
-  if (!ok) {
-    flag(a.err, ERR_RANGE, e);
-    return;
-  }
-  double xe[ND];
-#pragma unroll
-  for (int j = 0; j < ND; j++) xe[j] = a.x[rows[j]];
-  double Lam[Geo<DIM>::NLAM], vol;
-  Geo<DIM>::template compute<OpsF64>(x, Lam, vol);
-  double K[E::NUP];
-  element_upper<DIM, P, FORM, OpsF64>(Lam, vol, kap, K);
-#pragma unroll
-  for (int i = 0; i < ND; i++) {
-    double yi = 0.0;
-#pragma unroll
-    for (int j = 0; j < ND; j++) yi = fma(K[E::upper_index(i, j)], xe[j], yi);
-    red_add_f64(a.y + rows[i], yi);
-  }
-}
-
-// ---------------------------------------------------------------------------- vector (f v dx), push, FP64
-template <int DIM, int P, int Q>
-__global__ void __launch_bounds__(kPushThreads) k_vec_push_f64(const AsmArgs a) {
-  using S = fe_gen::Source<DIM, P, Q>;
-  constexpr int ND = S::ND, NF = S::NF;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
-  double x[DIM + 1][DIM];
-  int32_t v[DIM + 1], rows[ND];
-  bool ok = gather_coords<DIM>(a, e, x, v);
-  ok &= gather_rows<ND>(a, e, rows);
-  double fe[NF];
-#pragma unroll
-  for (int k = 0; k < NF; k++) {
-    int32_t c = a.coefmap[e * NF + k];
-    if (a.checks && (c < 0 || c >= a.ncoef)) {
-      ok = false;
-      c = 0;
-    }
-    fe[k] = a.coef[c];
-  }
-  if (!ok) {
-    flag(a.err, ERR_RANGE, e);
-    return;
-  }
-  double Lam[Geo<DIM>::NLAM], vol;
-  Geo<DIM>::template compute<OpsF64>(x, Lam, vol);
-  double b[ND];
-  S::template vec<OpsF64>(vol, fe, b);
-#pragma unroll
-  for (int i = 0; i < ND; i++) red_add_f64(a.y + rows[i], b[i]);
-}
-
-unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
-template <int DIM, int P, int FORM>
-cudaError_t mat_push(const AsmArgs &a, cudaStream_t s) {
-  if (a.ncell > 0) k_mat_push_f64<DIM, P, FORM><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
-template <int DIM, int P, int FORM>
-cudaError_t action_push(const AsmArgs &a, cudaStream_t s) {
-  if (a.ncell > 0) k_action_push_f64<DIM, P, FORM><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
-template <int DIM, int P, int Q>
-cudaError_t vec_push(const AsmArgs &a, cudaStream_t s) {
-  if (a.ncell > 0) k_vec_push_f64<DIM, P, Q><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-using LaunchFn = cudaError_t (*)(const AsmArgs &, cudaStream_t);
-
-#define FE_FORMS_FOR(D, P, W)                                               \
-  if (d.dim == D && d.degree == P) {                                        \
-    if (d.form == FE_FORM_MASS) return &W<D, P, FE_FORM_MASS>;              \
-    if (d.form == FE_FORM_LAPLACE) return &W<D, P, FE_FORM_LAPLACE>;        \
-    if (d.form == FE_FORM_HELMHOLTZ) return &W<D, P, FE_FORM_HELMHOLTZ>;    \
-  }
-#define FE_KAPPA_FOR(D, P, W) \
-  if (d.dim == D && d.degree == P && d.form == FE_FORM_KAPPA_DIFFUSION) return &W<D, P, FE_FORM_KAPPA_DIFFUSION>;
-
-#define FE_BILINEAR_TABLE(W)                                                                    \
-  FE_FORMS_FOR(2, 1, W) FE_FORMS_FOR(2, 2, W) FE_FORMS_FOR(2, 3, W) FE_FORMS_FOR(2, 4, W)       \
-  FE_FORMS_FOR(3, 1, W) FE_FORMS_FOR(3, 2, W) FE_FORMS_FOR(3, 3, W)                             \
-  FE_KAPPA_FOR(2, 1, W) FE_KAPPA_FOR(2, 2, W) FE_KAPPA_FOR(2, 4, W) FE_KAPPA_FOR(3, 1, W)       \
-  FE_KAPPA_FOR(3, 2, W)
-
 LaunchFn pick_mat(const fe_form_desc &d) {
-  if (d.precision != FE_PREC_FP64) return nullptr;
-  FE_BILINEAR_TABLE(mat_push)
+  if (d.form == FE_FORM_SOURCE || d.strategy == FE_STRATEGY_PULL) return nullptr;
+  if (d.precision == FE_PREC_FP64) return pick_mat_push_f64(d);
+  if (d.precision == FE_PREC_F32X2) return d.dim == 2 ? pick_mat_push_dd2(d) : pick_mat_push_dd3(d);
   return nullptr;
 }
 LaunchFn pick_action(const fe_form_desc &d) {
-  if (d.precision != FE_PREC_FP64) return nullptr;
-  FE_BILINEAR_TABLE(action_push)
+  if (d.form == FE_FORM_SOURCE || d.strategy == FE_STRATEGY_PULL) return nullptr;
+  if (d.precision == FE_PREC_FP64) return pick_action_push_f64(d);
+  if (d.precision == FE_PREC_F32X2) return d.dim == 2 ? pick_action_push_dd2(d) : pick_action_push_dd3(d);
   return nullptr;
 }
-#define FE_SRC_FOR(D, P, Q) \
-  if (d.dim == D && d.degree == P && d.coeff_degree == Q) return &vec_push<D, P, Q>;
 LaunchFn pick_vec(const fe_form_desc &d) {
-  if (d.precision != FE_PREC_FP64 || d.form != FE_FORM_SOURCE) return nullptr;
-  FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1) FE_SRC_FOR(2, 4, 1)
-  FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
+  if (d.form != FE_FORM_SOURCE || d.strategy == FE_STRATEGY_PULL) return nullptr;
+  if (d.precision == FE_PREC_FP64) return pick_vec_push_f64(d);
+  if (d.precision == FE_PREC_F32X2) return d.dim == 2 ? pick_vec_push_dd2(d) : pick_vec_push_dd3(d);
   return nullptr;
 }
 

@@ -61,7 +61,8 @@ struct fe_sparsity {
   int64_t nrows, ncols, ncell;
   int ndr, ndc;
   int64_t nnz;       // known after build
-  int cap;           // candidate capacity per row used by the sort kernel (power of two)
+  int cap;           // candidate capacity per row of the row kernel (hash table size, power of two)
+  int acap;          // incidence capacity per row (multiple of 4 >= longest incidence list)
   int64_t *rowptr;   // [nrows+1]
   int32_t *colidx;   // [nnz]
   uint8_t *lut;      // [ncell*ndr*ndc]
@@ -134,6 +135,7 @@ struct AsmArgs {
   int *err;
   int checks;
 };
+using LaunchFn = cudaError_t (*)(const AsmArgs &, cudaStream_t);
 cudaError_t launch_assemble_mat(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);

@@ -16,6 +16,10 @@ struct OpsF64 {
   static __device__ __forceinline__ T fma3(T a, T b, T c) { return fma(a, b, c); }
   static __device__ __forceinline__ T from_f64(double x) { return x; }
   static __device__ __forceinline__ double to_f64(T x) { return x; }
+  static __device__ __forceinline__ T diff_f64(double a, double b) { return a - b; }
+  static __device__ __forceinline__ T recip(T x) { return 1.0 / x; }
+  static __device__ __forceinline__ T abs(T x) { return fabs(x); }
+  static __device__ __forceinline__ T scale(T x, float s) { return x * (double)s; }
 };
 
 template <int DIM> struct Geo;
@@ -30,17 +34,16 @@ template <> struct Geo<2> {
   template <class Ops>
   static __device__ __forceinline__ void compute(const double (&x)[3][2], typename Ops::T *Lam, typename Ops::T &vol) {
     using T = typename Ops::T;
-    T e1x = Ops::from_f64(x[1][0] - x[0][0]), e1y = Ops::from_f64(x[1][1] - x[0][1]);
-    T e2x = Ops::from_f64(x[2][0] - x[0][0]), e2y = Ops::from_f64(x[2][1] - x[0][1]);
+    T e1x = Ops::diff_f64(x[1][0], x[0][0]), e1y = Ops::diff_f64(x[1][1], x[0][1]);
+    T e2x = Ops::diff_f64(x[2][0], x[0][0]), e2y = Ops::diff_f64(x[2][1], x[0][1]);
     T det = Ops::add(Ops::mul(e1x, e2y), Ops::neg(Ops::mul(e1y, e2x)));
-    double d = Ops::to_f64(det);
-    double adet = d < 0 ? -d : d;
-    double s = 1.0 / (2.0 * adet);
-    vol = Ops::from_f64(0.5 * adet);
+    T adet = Ops::abs(det);
+    T s = Ops::scale(Ops::recip(adet), 0.5f);
+    vol = Ops::scale(adet, 0.5f);
     // a1 = (e2y, -e2x), a2 = (-e1y, e1x)
-    T L11 = Ops::mulc(Ops::add(Ops::mul(e2y, e2y), Ops::mul(e2x, e2x)), s);
-    T L12 = Ops::mulc(Ops::neg(Ops::add(Ops::mul(e2y, e1y), Ops::mul(e2x, e1x))), s);
-    T L22 = Ops::mulc(Ops::add(Ops::mul(e1y, e1y), Ops::mul(e1x, e1x)), s);
+    T L11 = Ops::mul(Ops::add(Ops::mul(e2y, e2y), Ops::mul(e2x, e2x)), s);
+    T L12 = Ops::mul(Ops::neg(Ops::add(Ops::mul(e2y, e1y), Ops::mul(e2x, e1x))), s);
+    T L22 = Ops::mul(Ops::add(Ops::mul(e1y, e1y), Ops::mul(e1x, e1x)), s);
     T L01 = Ops::neg(Ops::add(L11, L12));
     T L02 = Ops::neg(Ops::add(L12, L22));
     T L00 = Ops::neg(Ops::add(L01, L02));
@@ -59,7 +62,7 @@ template <> struct Geo<3> {
 #pragma unroll
     for (int c = 0; c < 3; c++)
 #pragma unroll
-      for (int k = 0; k < 3; k++) e[c][k] = Ops::from_f64(x[c + 1][k] - x[0][k]);
+      for (int k = 0; k < 3; k++) e[c][k] = Ops::diff_f64(x[c + 1][k], x[0][k]);
     T a[3][3];
 #pragma unroll
     for (int m = 0; m < 3; m++) {
@@ -69,17 +72,16 @@ template <> struct Geo<3> {
       a[m][2] = Ops::add(Ops::mul(p[0], q[1]), Ops::neg(Ops::mul(p[1], q[0])));
     }
     T det = Ops::add(Ops::add(Ops::mul(e[0][0], a[0][0]), Ops::mul(e[0][1], a[0][1])), Ops::mul(e[0][2], a[0][2]));
-    double d = Ops::to_f64(det);
-    double adet = d < 0 ? -d : d;
-    double s = 1.0 / (6.0 * adet);
-    vol = Ops::from_f64(adet / 6.0);
+    T adet = Ops::abs(det);
+    T s = Ops::mulc(Ops::recip(adet), 1.0 / 6.0);
+    vol = Ops::mulc(adet, 1.0 / 6.0);
     T L[3][3];
 #pragma unroll
     for (int m = 0; m < 3; m++)
 #pragma unroll
       for (int n = m; n < 3; n++) {
         T dot = Ops::add(Ops::add(Ops::mul(a[m][0], a[n][0]), Ops::mul(a[m][1], a[n][1])), Ops::mul(a[m][2], a[n][2]));
-        L[m][n] = Ops::mulc(dot, s);
+        L[m][n] = Ops::mul(dot, s);
         L[n][m] = L[m][n];
       }
     T L0[3];

@@ -3,10 +3,11 @@
 // table that replaces the column search of MatSetValues, the row -> (cell, local index)
 // incidence used by the row-owner kernels, a device-wide scan and small fill kernels.
 //
-// Everything is row-centric and deterministic: each row's incidence list is sorted, its
-// candidate columns are sorted with a warp bitonic network in shared memory, duplicates are
-// dropped, and ranks are written to the lookup table.  The CSR result is bitwise identical
-// to a sort-unique of the pair set regardless of the atomics' ordering in the incidence fill.
+// Everything is row-centric and deterministic: each row's incidence list is put in ascending
+// order, its candidate columns are deduplicated in a shared-memory hash table, the unique
+// columns are ranked by counting, and the ranks go to the lookup table.  The CSR result is
+// bitwise identical to a sort-unique of the pair set whatever the ordering of the atomics in
+// the incidence fill.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -149,7 +150,7 @@ __global__ void k_max_count(const int32_t *__restrict__ cnt, int64_t n, int *out
 }
 
 // incidence fill: adj[adjptr[r] + slot] = k (k = e*ndr + i); slot order is arbitrary here and
-// made canonical by the row sort.
+// made canonical by the row kernel.
 __global__ void k_inc_fill(const int32_t *__restrict__ rmap, int64_t n, int64_t nrows,
                            const int64_t *__restrict__ adjptr, int32_t *cursor, int32_t *__restrict__ adj) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -160,114 +161,174 @@ __global__ void k_inc_fill(const int32_t *__restrict__ rmap, int64_t n, int64_t 
   }
 }
 
-__device__ __forceinline__ void warp_bitonic_sort(uint64_t *s, int P) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = lane; t < (P >> 1); t += 32) {
-        int lo = 2 * j * (t / j) + (t % j), hi = lo + j;
-        bool up = (lo & k) == 0;
-        uint64_t a = s[lo], b = s[hi];
-        if ((a > b) == up) {
-          s[lo] = b;
-          s[hi] = a;
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
 __device__ __forceinline__ int next_pow2(int x) {
-  int p = 2;
+  int p = 32;
   while (p < x) p <<= 1;
   return p;
 }
 
-// One warp per row.  Shared memory per warp: cap uint64 keys.
-//  1. sort the row's incidence list (e*ndr+i ascending) and write it back
-//  2. candidates key = (col << 20) | (a*ndc + j), sort
-//  3. unique columns -> coltmp[adjptr[r]*ndc + rank]; ranks -> lut[(adj[a])*ndc + j]
-//  4. rowcnt[r] = number of unique columns
-__global__ void k_rows_sort(int64_t nrows, int ndr, int ndc, const int32_t *__restrict__ cmap,
-                            const int64_t *__restrict__ adjptr, int32_t *__restrict__ adj,
-                            int32_t *__restrict__ rowlen, int32_t *__restrict__ coltmp,
-                            uint8_t *__restrict__ lut, int cap, int *err) {
-  extern __shared__ uint64_t smem[];
+__device__ __forceinline__ uint32_t hash_slot(uint32_t key, int logH) { return (key * 2654435761u) >> (32 - logH); }
+
+// For distinct values v[0..n) in shared memory (v 16-byte aligned), rank[q] = #{s : v[s] < v[q]},
+// written for q = lane, lane + 32, ...: one pass of broadcast 16-byte loads per round of 32.
+template <class F>
+__device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &&sink) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    const int q = base + lane;
+    const uint32_t mine = q < n ? v[q] : 0xFFFFFFFFu;
+    int cnt = 0, s = 0;
+    for (; s + 4 <= n; s += 4) {
+      const uint4 w = *reinterpret_cast<const uint4 *>(v + s);
+      cnt += (w.x < mine) + (w.y < mine) + (w.z < mine) + (w.w < mine);
+    }
+    for (; s < n; s++) cnt += v[s] < mine;
+    if (q < n) sink(q, cnt);
+  }
+}
+
+struct RowsParams {
+  int64_t nrows;
+  int ndr, ndc;
+  const int32_t *cmap;
+  const int64_t *adjptr;
+  int32_t *adj;
+  int32_t *rowlen;
+  int32_t *coltmp;
+  uint8_t *lut;
+  int cap, acap;      // candidate capacity per row (power of two), incidence capacity (multiple of 4)
+  uint64_t mdiv_ndr;  // floor(2^64 / ndr) + 1: exact k / ndr = __umul64hi(k, mdiv_ndr) for k < 2^32
+  uint32_t mdiv_ndc;  // floor(2^32 / ndc) + 1: exact t / ndc = __umulhi(t, mdiv_ndc) for t < 2^26
+  int *err;
+};
+
+__device__ __forceinline__ uint32_t div_ndr(uint32_t k, const RowsParams &p) {
+  return p.ndr == 1 ? k : (uint32_t)__umul64hi((uint64_t)k, p.mdiv_ndr);
+}
+__device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
+  return p.ndc == 1 ? t : __umulhi(t, p.mdiv_ndc);
+}
+
+// One warp per row r of the pattern (rows = target set of the row map):
+//  1. rank the row's incidence list {e*ndr + i : rmap(e)[i] = r} (all distinct) and store it in
+//     ascending order, in shared memory and back to adj (canonical order);
+//  2. insert every candidate column cmap(e)[j] of every incident cell into a shared-memory hash
+//     table sized to the row (deduplication), remembering each candidate's slot;
+//  3. compact the unique columns (remembering their slots) and rank them by counting;
+//     write them to coltmp at the row's incidence-based offset in ascending order and their
+//     ranks into the table;
+//  4. lut[(e*ndr + i)*ndc + j] = rank of the candidate's slot; rowlen[r] = number of unique columns.
+// Shared memory per warp (32-bit words): hkey[cap], hrank[cap], ucol[cap], uslot[cap], cslot[cap],
+// adju[acap], adjs[acap].
+__global__ void k_rows_build(const RowsParams p) {
+  extern __shared__ __align__(16) int32_t smem_i[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  uint64_t *s = smem + (size_t)wid * cap;
-  for (int64_t r = (int64_t)blockIdx.x * wpb + wid; r < nrows; r += (int64_t)gridDim.x * wpb) {
-    const int64_t a0 = adjptr[r];
-    const int na = (int)(adjptr[r + 1] - a0);
+  const int cap = p.cap;
+  int32_t *hkey = smem_i + (size_t)wid * (5 * cap + 2 * p.acap);
+  int32_t *hrank = hkey + cap;
+  uint32_t *ucol = reinterpret_cast<uint32_t *>(hrank + cap);
+  int32_t *uslot = reinterpret_cast<int32_t *>(ucol + cap);
+  int32_t *cslot = uslot + cap;
+  uint32_t *adju = reinterpret_cast<uint32_t *>(cslot + cap);
+  uint32_t *adjs = adju + p.acap;
+  const int ndc = p.ndc;
+  for (int64_t r = (int64_t)blockIdx.x * wpb + wid; r < p.nrows; r += (int64_t)gridDim.x * wpb) {
+    const int64_t a0 = p.adjptr[r];
+    const int na = (int)(p.adjptr[r + 1] - a0);
     const int ncand = na * ndc;
-    if (ncand > cap || na > (1 << 20) / (ndc > 0 ? ndc : 1)) {
-      if (lane == 0) flag(err, ERR_CAND_OVERFLOW, r);
-      if (lane == 0) rowlen[r] = 0;
+    if (na > p.acap || ncand > cap) {
+      if (lane == 0) {
+        flag(p.err, ERR_CAND_OVERFLOW, r);
+        p.rowlen[r] = 0;
+      }
       continue;
     }
     if (na == 0) {
-      if (lane == 0) rowlen[r] = 0;
+      if (lane == 0) p.rowlen[r] = 0;
       continue;
     }
+    const int H = next_pow2(ncand);  // <= cap
+    int logH = 5;
+    while ((1 << logH) < H) logH++;
     // 1. canonical incidence order
-    int Pa = next_pow2(na);
-    for (int t = lane; t < Pa; t += 32) s[t] = t < na ? (uint64_t)(uint32_t)adj[a0 + t] : ~0ull;
+    for (int t = lane; t < na; t += 32) adju[t] = (uint32_t)p.adj[a0 + t];
+    for (int t = lane; t < H; t += 32) hkey[t] = -1;
     __syncwarp();
-    warp_bitonic_sort(s, Pa);
-    for (int t = lane; t < na; t += 32) adj[a0 + t] = (int32_t)(uint32_t)s[t];
+    warp_rank_distinct(adju, na, [&](int q, int rk) { adjs[rk] = adju[q]; });
     __syncwarp();
-    // 2. candidates
-    int P = next_pow2(ncand);
-    for (int t = lane; t < P; t += 32) {
-      uint64_t key = ~0ull;
-      if (t < ncand) {
-        int a = t / ndc, j = t - a * ndc;
-        int32_t k = adj[a0 + a];
-        int64_t e = k / ndr;
-        uint32_t col = (uint32_t)cmap[e * ndc + j];
-        key = ((uint64_t)col << 20) | (uint64_t)t;
+    for (int t = lane; t < na; t += 32) p.adj[a0 + t] = (int32_t)adjs[t];
+    // 2. insert candidates, remember their slots
+    for (int t = lane; t < ncand; t += 32) {
+      const uint32_t a = div_ndc((uint32_t)t, p);
+      const uint32_t j = (uint32_t)t - a * (uint32_t)ndc;
+      const uint32_t e = div_ndr(adjs[a], p);
+      const int32_t col = p.cmap[(int64_t)e * ndc + j];
+      uint32_t h = hash_slot((uint32_t)col, logH);
+      for (int q = 0; q < H; q++) {
+        const int32_t prev = atomicCAS(&hkey[h], -1, col);
+        if (prev == -1 || prev == col) break;
+        h = (h + 1) & (H - 1);
       }
-      s[t] = key;
+      cslot[t] = (int32_t)h;
     }
     __syncwarp();
-    warp_bitonic_sort(s, P);
-    // 3. ranks
-    int carry = 0;
-    for (int c0 = 0; c0 < ncand; c0 += 32) {
-      int t = c0 + lane;
-      uint64_t key = t < ncand ? s[t] : ~0ull;
-      uint32_t col = (uint32_t)(key >> 20);
-      bool head = false;
-      if (t < ncand) head = (t == 0) || ((uint32_t)(s[t - 1] >> 20) != col);
-      unsigned hm = __ballot_sync(0xffffffffu, head);
-      int rank = carry + __popc(hm & ((2u << lane) - 1u)) - 1;
-      if (t < ncand) {
-        int orig = (int)(key & 0xFFFFFu);
-        int a = orig / ndc, j = orig - a * ndc;
-        if (rank < kMaxRowLen) lut[(int64_t)adj[a0 + a] * ndc + j] = (uint8_t)rank;
-        if (head) coltmp[a0 * ndc + rank] = (int32_t)col;
+    // 3. compact the unique columns, rank them, write them in ascending order
+    int nu = 0;
+    for (int b = 0; b < H; b += 32) {
+      const int32_t key = hkey[b + lane];
+      const unsigned m = __ballot_sync(0xffffffffu, key >= 0);
+      if (key >= 0) {
+        const int pos = nu + __popc(m & ((1u << lane) - 1u));
+        ucol[pos] = (uint32_t)key;
+        uslot[pos] = b + lane;
       }
-      carry += __popc(hm);
+      nu += __popc(m);
+    }
+    __syncwarp();
+    int32_t *outc = p.coltmp + a0 * ndc;
+    warp_rank_distinct(ucol, nu, [&](int q, int rk) {
+      hrank[uslot[q]] = rk;
+      outc[rk] = (int32_t)ucol[q];
+    });
+    __syncwarp();
+    // 4. rank of every candidate -> lookup table (candidate t = (a, j) of incident k = adjs[a])
+    for (int t = lane; t < ncand; t += 32) {
+      const uint32_t a = div_ndc((uint32_t)t, p);
+      const uint32_t j = (uint32_t)t - a * (uint32_t)ndc;
+      const int rank = hrank[cslot[t]];
+      if (rank < kMaxRowLen) p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank;
     }
     if (lane == 0) {
-      rowlen[r] = carry;
-      if (carry > kMaxRowLen) flag(err, ERR_ROW_TOO_LONG, r);
+      p.rowlen[r] = nu;
+      if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
     }
     __syncwarp();
   }
 }
 
-// warp per row: colidx[rowptr[r] + k] = coltmp[adjptr[r]*ndc + k]; guarded against a pattern that
-// grew beyond the allocated nnz (rebuild with different maps).
+// One warp per 32 consecutive rows: colidx[rowptr[r] + k] = coltmp[adjptr[r]*ndc + k].  Guarded
+// against a pattern that grew beyond the allocated nnz (rebuild with different maps).
 __global__ void k_rows_compact(int64_t nrows, int ndc, const int64_t *__restrict__ adjptr,
                                const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coltmp,
                                int32_t *__restrict__ colidx, int64_t nnz_cap, int check_nnz, int *err) {
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   if (check_nnz && blockIdx.x == 0 && threadIdx.x == 0 && rowptr[nrows] != nnz_cap) flag(err, ERR_NNZ_CHANGED, nrows);
-  for (int64_t r = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); r < nrows; r += (int64_t)gridDim.x * wpb) {
-    int64_t b = rowptr[r], n = rowptr[r + 1] - b, src = adjptr[r] * ndc;
-    if (b + n > nnz_cap) continue;
-    for (int64_t k = lane; k < n; k += 32) colidx[b + k] = coltmp[src + k];
+  for (int64_t r0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; r0 < nrows;
+       r0 += (int64_t)gridDim.x * wpb * 32) {
+    const int64_t r = r0 + lane;
+    long long b = 0, n = 0, src = 0;
+    if (r < nrows) {
+      b = rowptr[r];
+      n = rowptr[r + 1] - b;
+      src = adjptr[r] * ndc;
+    }
+    const int nq = (int)(nrows - r0 < 32 ? nrows - r0 : 32);
+    for (int q = 0; q < nq; q++) {
+      long long bq = __shfl_sync(0xffffffffu, b, q), cq = __shfl_sync(0xffffffffu, n, q);
+      long long sq = __shfl_sync(0xffffffffu, src, q);
+      if (bq + cq > nnz_cap) continue;
+      for (long long k = lane; k < cq; k += 32) colidx[bq + k] = coltmp[sq + k];
+    }
   }
 }
 
@@ -321,23 +382,37 @@ cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err) {
 }
 
 cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err) {
-  const int warps = 4;
-  size_t smem = (size_t)warps * sp->cap * sizeof(uint64_t);
+  RowsParams p;
+  p.nrows = sp->nrows;
+  p.ndr = sp->ndr;
+  p.ndc = sp->ndc;
+  p.cmap = sp->cmap->values;
+  p.adjptr = sp->adjptr;
+  p.adj = sp->adj;
+  p.rowlen = sp->rowcnt;
+  p.coltmp = sp->coltmp;
+  p.lut = sp->lut;
+  p.cap = sp->cap;
+  p.acap = sp->acap;
+  p.mdiv_ndr = sp->ndr > 1 ? (~0ull / (uint64_t)sp->ndr) + 1 : 0;
+  p.mdiv_ndc = sp->ndc > 1 ? (uint32_t)((0xFFFFFFFFull / (uint64_t)sp->ndc) + 1) : 0;
+  p.err = err;
+  const size_t per_warp = (size_t)(5 * sp->cap + 2 * sp->acap) * sizeof(int32_t);
+  int warps = 8;
+  while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
+  const size_t smem = warps * per_warp;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_rows_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_rows_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  if (sp->nrows > 0)
-    k_rows_sort<<<grid_for(sp->nrows, warps, 152 * 32), warps * 32, smem, s>>>(
-        sp->nrows, sp->ndr, sp->ndc, sp->cmap->values, sp->adjptr, sp->adj, sp->rowcnt, sp->coltmp, sp->lut,
-        sp->cap, err);
+  if (sp->nrows > 0) k_rows_build<<<grid_for(sp->nrows, warps, 152 * 32), warps * 32, smem, s>>>(p);
   return exclusive_scan_i32_to_i64(sp->rowcnt, sp->rowptr, sp->nrows, sp->scan_tmp, s);
 }
 
 cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz) {
   const int warps = 8;
   if (sp->nrows > 0)
-    k_rows_compact<<<grid_for(sp->nrows, warps, 152 * 16), warps * 32, 0, s>>>(
+    k_rows_compact<<<grid_for((sp->nrows + 31) / 32, warps, 152 * 16), warps * 32, 0, s>>>(
         sp->nrows, sp->ndc, sp->adjptr, sp->rowptr, sp->coltmp, sp->colidx, sp->nnz, check_nnz, err);
   return cudaGetLastError();
 }

@@ -140,3 +140,58 @@ def test_single_cell_and_empty_mesh(gpu):
     sp0 = fe.sparsity_build(ctx, m0, m0)
     nr, nc, nnz, rp0, ci0 = fe.sparsity_csr(sp0)
     assert nnz == 0 and int(rp0[-1]) == 0 and nr == pr.nnodes
+
+
+# ------------------------------------------------------------------ double-float (FP32 pair) element tensors
+DD_CASES = [(2, 1, 64, 0.0), (2, 1, 37, 0.2), (2, 2, 23, 0.2), (3, 1, 9, 0.2), (3, 2, 7, 0.2)]
+
+
+@pytest.mark.parametrize("dim,p,n,jit", DD_CASES)
+@pytest.mark.parametrize("form", [1, 2, 3, 4])
+def test_assemble_mat_f32x2_matches_oracle(gpu, dim, p, n, jit, form):
+    """FP32-pair element tensors, FP64 global accumulation: same 1e-12 per-entry bound."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    got = g.assemble(form, precision=fe.PREC_F32X2)
+    want, scale = O.assemble_mat(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
+    PB.assert_close_scaled(got, want, scale, 1e-12, f"f32x2 form {form} P{p} dim {dim}")
+
+
+@pytest.mark.parametrize("dim,p,n,jit", DD_CASES)
+@pytest.mark.parametrize("form", [3, 4])
+def test_action_f32x2_matches_oracle(gpu, dim, p, n, jit, form):
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr)
+    x = np.random.default_rng(2).uniform(-1, 1, pr.nnodes)
+    got = g.action(form, x, precision=fe.PREC_F32X2)
+    want, scale = O.action(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, x, kappa=pr.kappa)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "f32x2 action")
+
+
+@pytest.mark.parametrize("dim,p,pf,n", [(2, 1, 1, 64), (2, 2, 2, 11), (3, 2, 2, 4), (3, 2, 1, 4)])
+def test_assemble_vec_f32x2_matches_oracle(gpu, dim, p, pf, n):
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+    pr = PB.make(dim, p, n, 0.2 if n > 6 else 0.0, seed=4)
+    g = PB.GpuProblem(pr)
+    fmap, nf = mg.cell_node_map(pr.mesh, pf)
+    f = mg.uniform_dat(nf, 1)
+    got = g.rhs(f, fmap, pf, nf, precision=fe.PREC_F32X2)
+    want, scale = O.assemble_vec(dim, p, pf, pr.cmap, pr.nnodes, pr.mesh.coords, pr.mesh.cell_vertex, f, fmap)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "f32x2 rhs")
+
+
+def test_f32x2_extreme_scales(gpu):
+    """Tiny and huge cell sizes (coordinates scaled by 2^-30 and 2^20): relative accuracy holds."""
+    from paper_1501_01809_gb300 import fe
+    for scale_x in [2.0 ** -30, 3.0e-7, 2.0 ** 20]:
+        pr = PB.make(3, 2, 3, 0.2, seed=3)
+        pr.mesh.coords = pr.mesh.coords * scale_x
+        g = PB.GpuProblem(pr)
+        rp, ci = g.csr()
+        got = g.assemble(3, precision=fe.PREC_F32X2)
+        want, scale = O.assemble_mat(3, 2, 3, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci)
+        PB.assert_close_scaled(got, want, scale, 1e-12, f"f32x2 coordinates x {scale_x}")
