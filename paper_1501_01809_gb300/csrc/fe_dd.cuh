@@ -141,6 +141,18 @@ struct OpsF32x2 {
   }
   static __device__ __forceinline__ T abs(T x) { return x.hi < 0.0f ? neg(x) : x; }
   static __device__ __forceinline__ T scale(T x, float s) { return {__fmul_rn(x.hi, s), __fmul_rn(x.lo, s)}; }  // s a power of two
+  // FP32's exponent range is narrow: the geometry normalises each cell's edge vectors
+  static constexpr bool kNormalise = true;
+  static __device__ __forceinline__ int exponent(T x) {
+    const int e = (int)((__float_as_uint(x.hi) >> 23) & 0xFF);
+    return e == 0 ? -1000 : e - 127;
+  }
+  // x * 2^k, exact, for results inside the normal range; k split in two steps of |k| <= 126
+  static __device__ __forceinline__ T ldexp2(T x, int k) {
+    const int k1 = k / 2, k2 = k - k1;
+    const float s1 = __uint_as_float((uint32_t)(k1 + 127) << 23), s2 = __uint_as_float((uint32_t)(k2 + 127) << 23);
+    return {__fmul_rn(__fmul_rn(x.hi, s1), s2), __fmul_rn(__fmul_rn(x.lo, s1), s2)};
+  }
 };
 
 }  // namespace fe

@@ -20,7 +20,33 @@ struct OpsF64 {
   static __device__ __forceinline__ T recip(T x) { return 1.0 / x; }
   static __device__ __forceinline__ T abs(T x) { return fabs(x); }
   static __device__ __forceinline__ T scale(T x, float s) { return x * (double)s; }
+  // FP64 has the exponent range for any mesh: no per-cell normalisation
+  static constexpr bool kNormalise = false;
+  static __device__ __forceinline__ int exponent(T) { return 0; }
+  static __device__ __forceinline__ T ldexp2(T x, int) { return x; }
 };
+
+// Per-cell power-of-two normalisation for arithmetic with a narrow exponent range: the edge
+// vectors are scaled by 2^-k (k = the exponent of their largest component) before any product,
+// and the results rescaled exactly at the end (Lam by 2^(k(DIM-2)), vol by 2^(k DIM)).
+template <class Ops, int DIM>
+__device__ __forceinline__ int normalise_edges(typename Ops::T (&e)[DIM][DIM]) {
+  if constexpr (!Ops::kNormalise) {
+    return 0;
+  } else {
+    int k = -1000;
+#pragma unroll
+    for (int c = 0; c < DIM; c++)
+#pragma unroll
+      for (int d = 0; d < DIM; d++) k = max(k, Ops::exponent(e[c][d]));
+    if (k == -1000) return 0;
+#pragma unroll
+    for (int c = 0; c < DIM; c++)
+#pragma unroll
+      for (int d = 0; d < DIM; d++) e[c][d] = Ops::ldexp2(e[c][d], -k);
+    return k;
+  }
+}
 
 template <int DIM> struct Geo;
 
@@ -34,12 +60,17 @@ template <> struct Geo<2> {
   template <class Ops>
   static __device__ __forceinline__ void compute(const double (&x)[3][2], typename Ops::T *Lam, typename Ops::T &vol) {
     using T = typename Ops::T;
-    T e1x = Ops::diff_f64(x[1][0], x[0][0]), e1y = Ops::diff_f64(x[1][1], x[0][1]);
-    T e2x = Ops::diff_f64(x[2][0], x[0][0]), e2y = Ops::diff_f64(x[2][1], x[0][1]);
+    T ev[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+#pragma unroll
+      for (int k = 0; k < 2; k++) ev[c][k] = Ops::diff_f64(x[c + 1][k], x[0][k]);
+    const int kexp = normalise_edges<Ops, 2>(ev);
+    const T e1x = ev[0][0], e1y = ev[0][1], e2x = ev[1][0], e2y = ev[1][1];
     T det = Ops::add(Ops::mul(e1x, e2y), Ops::neg(Ops::mul(e1y, e2x)));
     T adet = Ops::abs(det);
     T s = Ops::scale(Ops::recip(adet), 0.5f);
-    vol = Ops::scale(adet, 0.5f);
+    vol = Ops::ldexp2(Ops::scale(adet, 0.5f), 2 * kexp);
     // a1 = (e2y, -e2x), a2 = (-e1y, e1x)
     T L11 = Ops::mul(Ops::add(Ops::mul(e2y, e2y), Ops::mul(e2x, e2x)), s);
     T L12 = Ops::mul(Ops::neg(Ops::add(Ops::mul(e2y, e1y), Ops::mul(e2x, e1x))), s);
@@ -63,6 +94,7 @@ template <> struct Geo<3> {
     for (int c = 0; c < 3; c++)
 #pragma unroll
       for (int k = 0; k < 3; k++) e[c][k] = Ops::diff_f64(x[c + 1][k], x[0][k]);
+    const int kexp = normalise_edges<Ops, 3>(e);
     T a[3][3];
 #pragma unroll
     for (int m = 0; m < 3; m++) {
@@ -74,14 +106,14 @@ template <> struct Geo<3> {
     T det = Ops::add(Ops::add(Ops::mul(e[0][0], a[0][0]), Ops::mul(e[0][1], a[0][1])), Ops::mul(e[0][2], a[0][2]));
     T adet = Ops::abs(det);
     T s = Ops::mulc(Ops::recip(adet), 1.0 / 6.0);
-    vol = Ops::mulc(adet, 1.0 / 6.0);
+    vol = Ops::ldexp2(Ops::mulc(adet, 1.0 / 6.0), 3 * kexp);
     T L[3][3];
 #pragma unroll
     for (int m = 0; m < 3; m++)
 #pragma unroll
       for (int n = m; n < 3; n++) {
         T dot = Ops::add(Ops::add(Ops::mul(a[m][0], a[n][0]), Ops::mul(a[m][1], a[n][1])), Ops::mul(a[m][2], a[n][2]));
-        L[m][n] = Ops::mul(dot, s);
+        L[m][n] = Ops::ldexp2(Ops::mul(dot, s), kexp);
         L[n][m] = L[m][n];
       }
     T L0[3];
