@@ -162,6 +162,33 @@ fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols,
 fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut);
 fe_status fe_sparsity_destroy(fe_sparsity *sp);
 
+/* ---------------------------------------------------------------- Sparsity without allocation
+ * The paper has no counterpart to this call.  It computes exactly what fe_sparsity_build
+ * computes (same kernels, bitwise identical pattern and lookup table) for callers that must not
+ * allocate device memory: code whose device memory is a budget owned by another runtime (an
+ * arena or pool that stray cudaMalloc calls would bypass or overrun), and code that cannot
+ * afford cudaMalloc's latency and device-wide synchronisation where it builds patterns.
+ * There is no context or handle: inputs and outputs are the caller's device buffers, and the
+ * kernels' scratch is one static device array of about 23 MB that every GPU loading the library
+ * holds until the process exits.  Limits (FE_EUNSUPPORTED beyond them): nrows <= 262144,
+ * ncell * arity_r <= 1048576, ncell * arity_r * arity_c <= 4194304, per-row limits as for
+ * fe_sparsity_build.
+ *   rmap, cmap  device int32 [ncell][arity_r], [ncell][arity_c] (read)
+ *   rowptr      device int64 [nrows + 1] (written)
+ *   colidx      device int32 [colidx_capacity] (written); NULL = size query: rowptr and lut are
+ *               written, *nnz is set, colidx is not touched
+ *   lut         device uint8 [ncell][arity_r][arity_c] (written), rank of cmap(e)[j] in row rmap(e)[i]
+ *   nnz         host, set to the number of entries of the pattern
+ * Errors: FE_EINVAL (bad argument, or colidx_capacity < nnz -- nnz is still reported),
+ * FE_ERANGE (a map value outside its target set), FE_EUNSUPPORTED, FE_ECUDA.
+ * Synchronises cuda_stream (it reads nnz).  The first call on a device looks up the array's
+ * device address with that device current; make it before any stream capture on that device.
+ * All calls share the array and it keeps the last call's contents (each call clears what must
+ * start at zero); calls that overlap on the GPU race on it, so serialise them. */
+fe_status fe_sparsity_build_noalloc(const int32_t *rmap, int arity_r, const int32_t *cmap, int arity_c, int64_t ncell,
+                                    int64_t nrows, int64_t ncols, int64_t *rowptr, int32_t *colidx,
+                                    int64_t colidx_capacity, uint8_t *lut, int64_t *nnz, void *cuda_stream);
+
 /* ---------------------------------------------------------------- Mat (Sec. 4.3, 4.4.3)
  * FP64 values over a sparsity (owned, [nnz]), write-only to par_loops (INC). */
 fe_status fe_mat_create(fe_ctx *ctx, fe_sparsity *sp, fe_mat **out);

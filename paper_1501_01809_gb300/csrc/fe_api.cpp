@@ -366,6 +366,15 @@ fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
   return ok();
 }
 
+fe_status fe_sparsity_build_noalloc(const int32_t *rmap, int arity_r, const int32_t *cmap, int arity_c, int64_t ncell,
+                                    int64_t nrows, int64_t ncols, int64_t *rowptr, int32_t *colidx,
+                                    int64_t colidx_capacity, uint8_t *lut, int64_t *nnz, void *cuda_stream) {
+  fe_status st = fe::sparsity_build_noalloc(rmap, arity_r, cmap, arity_c, ncell, nrows, ncols, rowptr, colidx,
+                                            colidx_capacity, lut, nnz, (cudaStream_t)cuda_stream);
+  if (st != FE_OK) return fail(st, "%s", fe::noalloc_message());
+  return ok();
+}
+
 fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols, int64_t *nnz, const int64_t **rowptr,
                           const int32_t **colidx) {
   if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_csr: invalid sparsity");

@@ -110,6 +110,14 @@ cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int chec
 
 // ---- fills ----
 cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s);
+cudaError_t launch_zero_i32(int32_t *p, int64_t n, cudaStream_t s);
+
+// ---- sparsity without device allocation (static scratch, fe_noalloc.cu) ----
+fe_status sparsity_build_noalloc(const int32_t *rmap, int ndr, const int32_t *cmap, int ndc, int64_t ncell,
+                                 int64_t nrows, int64_t ncols, int64_t *rowptr, int32_t *colidx,
+                                 int64_t colidx_capacity, uint8_t *lut, int64_t *nnz_out, cudaStream_t s);
+const char *noalloc_message();
+size_t noalloc_scratch_bytes();
 
 // ---- assembly ----
 struct AsmArgs {

@@ -361,6 +361,12 @@ cudaError_t launch_map_validate(const int32_t *v, int64_t n, int64_t limit, int 
   return cudaGetLastError();
 }
 
+cudaError_t launch_zero_i32(int32_t *p, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_zero_i32<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_zero_f64<<<grid_for((n + 1) / 2, 256, 152 * 8), 256, 0, s>>>(p, n);

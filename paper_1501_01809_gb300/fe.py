@@ -26,7 +26,7 @@ SYMBOLS = [
     "fe_last_error", "fe_version", "fe_ctx_create", "fe_ctx_set_stream", "fe_ctx_set_allocator",
     "fe_ctx_set_checks", "fe_sync", "fe_ctx_destroy", "fe_set_create", "fe_set_size", "fe_set_destroy",
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
-    "fe_sparsity_rebuild", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
+    "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
     "fe_assemble_mat", "fe_assemble_vec", "fe_action",
 ]
@@ -76,6 +76,7 @@ def load():
         "fe_map_create": (I, [P, P, P, I, P, I, PP]), "fe_map_destroy": (I, [P]),
         "fe_dat_create": (I, [P, P, I, P, PP]), "fe_dat_destroy": (I, [P]),
         "fe_sparsity_build": (I, [P, P, P, PP]), "fe_sparsity_rebuild": (I, [P]),
+        "fe_sparsity_build_noalloc": (I, [P, I, P, I, I64, I64, I64, P, P, I64, P, C.POINTER(I64), P]),
         "fe_sparsity_csr": (I, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), PP, PP]),
         "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_destroy": (I, [P]),
         "fe_mat_create": (I, [P, P, PP]), "fe_mat_values": (I, [P, PP]), "fe_mat_zero": (I, [P]),
@@ -269,6 +270,33 @@ def sparsity_build(ctx: Ctx, rmap: Map, cmap: Map) -> Sparsity:
 
 def sparsity_rebuild(sp: Sparsity) -> None:
     _check(load().fe_sparsity_rebuild(sp.ptr))
+
+
+def sparsity_build_noalloc(rmap: torch.Tensor, cmap: torch.Tensor, nrows: int, ncols: int, rowptr: torch.Tensor,
+                           colidx: torch.Tensor | None, lut: torch.Tensor, stream=None) -> int:
+    """fe_sparsity_build_noalloc: pattern and lookup table into caller buffers, no device allocation.
+
+    For callers that must not allocate device memory; scratch is a static device array with fixed
+    size limits (see include/fe.h).  colidx None = size query.  Returns nnz.
+    """
+    rmap = _dev_tensor(rmap, torch.int32, "rmap")
+    cmap = _dev_tensor(cmap, torch.int32, "cmap")
+    rowptr = _dev_tensor(rowptr, torch.int64, "rowptr")
+    lut = _dev_tensor(lut, torch.uint8, "lut")
+    cap = 0
+    cptr = None
+    if colidx is not None:
+        colidx = _dev_tensor(colidx, torch.int32, "colidx")
+        cap, cptr = colidx.numel(), C.c_void_p(colidx.data_ptr())
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    nnz = C.c_int64(0)
+    ncell = rmap.shape[0]
+    _check(load().fe_sparsity_build_noalloc(C.c_void_p(rmap.data_ptr()), int(rmap.shape[1]), C.c_void_p(cmap.data_ptr()),
+                                            int(cmap.shape[1]), int(ncell), int(nrows), int(ncols),
+                                            C.c_void_p(rowptr.data_ptr()), cptr, int(cap), C.c_void_p(lut.data_ptr()),
+                                            C.byref(nnz), C.c_void_p(stream.cuda_stream)))
+    return nnz.value
 
 
 def sparsity_csr(sp: Sparsity):
