@@ -1,9 +1,10 @@
 // Sparsity build that allocates no device memory: the same device kernels as fe_sparsity_build,
 // with their scratch taken from one file-scope static device array instead of the allocator.
 //
-// It serves callers that cannot allocate device memory themselves: code running where
-// cudaMalloc is unavailable or forbidden (inside a host callback or a stream-ordered region,
-// under a memory budget owned by another runtime, in an allocator-free embedding).
+// It serves callers that must not allocate device memory themselves: code whose device memory
+// is a budget owned by another runtime (an arena or pool that stray cudaMalloc calls would bypass
+// or overrun), and code that cannot afford cudaMalloc's latency and device-wide synchronisation
+// where it builds patterns.
 //
 // The array (kScratchBytes, about 23 MB) is part of the module and stays resident on every device
 // that loads the library until the process exits.  Its device address is looked up once per
