@@ -171,16 +171,19 @@ def run_ours(args, wl, rank, world):
     nrows, ncols, nnz, rowptr, colidx = fe.sparsity_csr(sp)
     vals = fe.mat_values(A)
 
+    pull = args.strategy in ("pull", "auto")
+
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
         fe.sparsity_rebuild(sp)
         if ev is not None:
             ev[1].record(stream)
-        fe.mat_zero(A)
+        if not pull:  # the pull row owners overwrite (zero_first) instead: no separate zero pass
+            fe.mat_zero(A)
         if ev is not None:
             ev[2].record(stream)
-        fe.assemble_mat(ctx, K, cells, A, XY, CM, zero_first=False)
+        fe.assemble_mat(ctx, K, cells, A, XY, CM, zero_first=pull)
         if ev is not None:
             ev[3].record(stream)
         fe.action(ctx, K, cells, X, Y, M, XY, CM, zero_first=True, sp=sp)
@@ -217,8 +220,9 @@ def run_ours(args, wl, rank, world):
         ms_step = float(t.item())
     phase_ms = phases / args.steps
     # launches of libfe kernels per step: sparsity rebuild 14 (zero, count, zero, max, scan x3, zero, fill,
-    # row sort, scan x3, compact), mat zero 1, assembly 1, action zero + action 2
-    launches = (14 + 1 + 1 + 2) * args.steps
+    # row sort, scan x3, compact); push: mat zero 1, assembly 1, action zero + action 2; pull: assembly 2
+    # (element, row), action 2 (element, row)
+    launches = (14 + (4 if pull else 4)) * args.steps
 
     # ------------------------------------------------------------------- e2e through host buffers
     e2e = None
@@ -265,12 +269,12 @@ def run_ours(args, wl, rank, world):
     bytes_sp = (ncell * nd * 4 * 2 + (nn + 1) * 8 * 2 + ncell * nd * 4 * 2 + nnz * 4 + ncell * nd * nd)
     kern = {
         "sparsity": {"ms": phase_ms[0], "bytes": bytes_sp},
-        "zero": {"ms": phase_ms[1], "bytes": nnz * 8},
+        "zero": {"ms": phase_ms[1], "bytes": nnz * 8 if not pull else 0},
         "assemble": {"ms": phase_ms[2], "bytes": bytes_mat, "flops": ncell * fl_mat},
         "action": {"ms": phase_ms[3], "bytes": bytes_act, "flops": ncell * fl_act},
     }
     for k, v in kern.items():
-        if "bytes" in v and v["ms"] > 0:
+        if "bytes" in v and v["ms"] > 0 and v["bytes"] > 0:
             v["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
             v["hbm_frac"] = v["gbs"] / peaks["hbm_gbs"]
         if "flops" in v and v["ms"] > 0:

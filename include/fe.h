@@ -76,10 +76,14 @@ typedef enum {
 
 /* How the INC into the global Mat/Dat is executed. */
 typedef enum {
-  FE_STRATEGY_AUTO = 0,
+  FE_STRATEGY_AUTO = 0,  /* PULL when the row incidence is at hand (a Mat's sparsity, or the
+                            sparsity passed to a vector par_loop), PUSH otherwise            */
   FE_STRATEGY_PUSH = 1,  /* one thread per cell, FP64 atomic adds through the lookup table */
-  FE_STRATEGY_PULL = 2   /* one owner per row: gathers its cells' contributions, no atomics,
-                            deterministic (bitwise reproducible) summation order           */
+  FE_STRATEGY_PULL = 2   /* staged: element tensors stored per cell, then one owner per row
+                            sums its cells' contributions in the fixed incidence order --
+                            no atomics, bitwise reproducible results; uses a staging buffer
+                            (ncell x upper triangle, or ncell x nodes, values) per Mat or
+                            sparsity, allocated on first use                                 */
 } fe_strategy;
 
 typedef struct {

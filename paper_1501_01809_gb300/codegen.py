@@ -376,6 +376,29 @@ def emit_element(dim: int, p: int) -> str:
     for u, (i, j) in enumerate(up):
         lines.append(f"    K[{u}] = Ops::mulc(vol, {_num(M[i][j])});")
     lines.append("  }")
+    # fused action: each K_ij is formed and consumed at once (y_i += K_ij x_j, y_j += K_ij x_i), so the
+    # element matrix is never live as a whole
+    lines.append("  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper("
+                 "const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {")
+    lines.append("    typename Ops::T k;")
+    for u, (i, j) in enumerate(up):
+        terms = [(kk, B[mn][i][j]) for kk, mn in enumerate(pairs) if B[mn][i][j] != 0]
+        m = M[i][j]
+        parts = []
+        if terms:
+            parts.append(f"if constexpr (STIFF) {{ k = {_term_chain(terms, 'Lam')}; }} else {{ k = Ops::zero(); }}")
+        else:
+            parts.append("k = Ops::zero();")
+        if m != 0:
+            parts.append(f"if constexpr (MASS) {{ k = Ops::fmac(vol, {_num(m)}, k); }}")
+        if not terms and m == 0:
+            continue
+        guard = "" if terms and m != 0 else ("if constexpr (STIFF) " if terms else "if constexpr (MASS) ")
+        body = " ".join(parts) + f" y[{i}] = Ops::fma3(k, x[{j}], y[{i}]);"
+        if i != j:
+            body += f" y[{j}] = Ops::fma3(k, x[{i}], y[{j}]);"
+        lines.append(f"    {guard}{{ {body} }}")
+    lines.append("  }")
     # upper index maps as constexpr functions
     lines.append("  __host__ __device__ static constexpr int upper_index(int i, int j) {")
     lines.append(f"    return i <= j ? i * {nd} - (i * (i - 1)) / 2 + (j - i) : j * {nd} - (j * (j - 1)) / 2 + (i - j);")

@@ -248,6 +248,7 @@ static void sparsity_free(fe_sparsity *sp) {
   dev_free(c, sp->coltmp);
   dev_free(c, sp->scan_tmp);
   dev_free(c, sp->d_maxcnt);
+  dev_free(c, sp->vstage);
 }
 
 fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out) {
@@ -333,6 +334,18 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
     return st;
   }
   sp->nnz = nnz;
+  {
+    int mr = 0;
+    e = fe::launch_max_i32(sp->rowcnt, sp->nrows, sp->d_maxcnt, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&mr, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      sparsity_free(sp);
+      delete sp;
+      return cuda_fail(e, "fe_sparsity_build");
+    }
+    sp->maxrow = mr;
+  }
   sp->colidx = (int32_t *)dev_alloc(c, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
   if (!sp->colidx) {
     sparsity_free(sp);
@@ -410,7 +423,7 @@ fe_status fe_mat_create(fe_ctx *c, fe_sparsity *sp, fe_mat **out) {
   DeviceGuard g(c->device);
   double *v = (double *)dev_alloc(c, sizeof(double) * (sp->nnz > 0 ? sp->nnz : 1));
   if (!v) return fail(FE_ENOMEM, "fe_mat_create: values allocation (%lld entries)", (long long)sp->nnz);
-  fe_mat *m = new (std::nothrow) fe_mat{fe::kMagicMat, c, sp, v};
+  fe_mat *m = new (std::nothrow) fe_mat{fe::kMagicMat, c, sp, v, nullptr, 0};
   if (!m) {
     dev_free(c, v);
     return fail(FE_ENOMEM, "fe_mat_create: host allocation");
@@ -438,6 +451,7 @@ fe_status fe_mat_destroy(fe_mat *m) {
   DeviceGuard g(m->ctx->device);
   cudaStreamSynchronize(m->ctx->stream);
   dev_free(m->ctx, m->values);
+  dev_free(m->ctx, m->stage);
   m->magic = fe::kDead;
   delete m;
   return ok();
@@ -515,6 +529,16 @@ static fe_status kappa_arg(const char *who, fe_ctx *c, fe_kernel *k, fe_set *cel
   return FE_OK;
 }
 
+// Staging buffers of the pull strategy, allocated on first use and kept with their owner.
+static fe_status ensure_stage(fe_ctx *c, void **buf, size_t *have, size_t need, const char *who) {
+  if (*buf && *have >= need) return FE_OK;
+  dev_free(c, *buf);
+  *buf = dev_alloc(c, need);
+  *have = *buf ? need : 0;
+  if (!*buf) return fail(FE_ENOMEM, "%s: staging buffer of %zu bytes", who, need);
+  return FE_OK;
+}
+
 fe_status fe_assemble_mat(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_mat *A, int zero_first, fe_dat *coords,
                           fe_map *coord_map, const fe_arg *coeffs, int ncoeffs) {
   const char *who = "fe_assemble_mat";
@@ -531,12 +555,35 @@ fe_status fe_assemble_mat(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_mat *A, int
   a.vals = A->values;
   a.adjptr = A->sp->adjptr;
   a.adj = A->sp->adj;
+  a.rowcap = A->sp->maxrow;
+  a.zero_first = zero_first;
   DeviceGuard g(c->device);
-  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(A->values, A->sp->nnz, c->stream), who);
+  const bool pull = fe::resolve_strategy(k->d, true) == FE_STRATEGY_PULL;
+  if (pull) {
+    st = ensure_stage(c, &A->stage, &A->stage_bytes, fe::stage_bytes_mat(k->d, cells->size), who);
+    if (st != FE_OK) return st;
+    a.stage = A->stage;
+  } else if (zero_first) {
+    FE_CHECK_CUDA(fe::launch_zero_f64(A->values, A->sp->nnz, c->stream), who);
+  }
   int unsup = 0;
   FE_CHECK_CUDA(fe::launch_assemble_mat(k->d, a, c->stream, &unsup), who);
   if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);
   return ok();
+}
+
+// The row incidence used by the pull strategy of a vector par_loop: that of a sparsity built from
+// (map, map).  AUTO uses it when given; PULL requires it.
+static fe_status pull_incidence(const char *who, fe_ctx *c, fe_kernel *k, fe_set *cells, fe_map *map,
+                                const fe_sparsity *sp, fe::AsmArgs &a) {
+  const bool have = sp && valid(sp) && sp->ctx == c;
+  if (have && (sp->rmap != map || sp->ncell != cells->size))
+    return fail(FE_EINVAL, "%s: the sparsity was not built from this map", who);
+  if (fe::resolve_strategy(k->d, have) != FE_STRATEGY_PULL) return FE_OK;
+  if (!have) return fail(FE_EINVAL, "%s: the pull strategy needs the sparsity built from (map, map)", who);
+  a.adjptr = sp->adjptr;
+  a.adj = sp->adj;
+  return FE_OK;
 }
 
 fe_status fe_assemble_vec(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *b, fe_map *test_map, int zero_first,
@@ -555,12 +602,18 @@ fe_status fe_assemble_vec(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *b, fe_
   a.coefmap = coeffs[0].map->values;
   a.ncoef = coeffs[0].dat->set->size;
   a.y = b->data;
-  if (sp && valid(sp)) {
-    a.adjptr = sp->adjptr;
-    a.adj = sp->adj;
-  }
+  a.zero_first = zero_first;
+  st = pull_incidence(who, c, k, cells, test_map, sp, a);
+  if (st != FE_OK) return st;
   DeviceGuard g(c->device);
-  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(b->data, b->set->size, c->stream), who);
+  if (a.adj) {
+    fe_sparsity *msp = const_cast<fe_sparsity *>(sp);
+    st = ensure_stage(c, &msp->vstage, &msp->vstage_bytes, fe::stage_bytes_vec(k->d, cells->size, k->nd), who);
+    if (st != FE_OK) return st;
+    a.stage = msp->vstage;
+  } else if (zero_first) {
+    FE_CHECK_CUDA(fe::launch_zero_f64(b->data, b->set->size, c->stream), who);
+  }
   int unsup = 0;
   FE_CHECK_CUDA(fe::launch_assemble_vec(k->d, a, c->stream, &unsup), who);
   if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);
@@ -582,12 +635,18 @@ fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y
   if (st != FE_OK) return st;
   a.x = x->data;
   a.y = y->data;
-  if (sp && valid(sp)) {
-    a.adjptr = sp->adjptr;
-    a.adj = sp->adj;
-  }
+  a.zero_first = zero_first;
+  st = pull_incidence(who, c, k, cells, map, sp, a);
+  if (st != FE_OK) return st;
   DeviceGuard g(c->device);
-  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(y->data, y->set->size, c->stream), who);
+  if (a.adj) {
+    fe_sparsity *msp = const_cast<fe_sparsity *>(sp);
+    st = ensure_stage(c, &msp->vstage, &msp->vstage_bytes, fe::stage_bytes_vec(k->d, cells->size, k->nd), who);
+    if (st != FE_OK) return st;
+    a.stage = msp->vstage;
+  } else if (zero_first) {
+    FE_CHECK_CUDA(fe::launch_zero_f64(y->data, y->set->size, c->stream), who);
+  }
   int unsup = 0;
   FE_CHECK_CUDA(fe::launch_action(k->d, a, c->stream, &unsup), who);
   if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);

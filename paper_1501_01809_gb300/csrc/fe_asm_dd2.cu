@@ -9,6 +9,7 @@ using OPS = OpsF32x2;
 #define FE_BILINEAR_TABLE(W) \
   FE_FORMS_FOR(2, 1, W) FE_FORMS_FOR(2, 2, W) FE_KAPPA_FOR(2, 1, W) FE_KAPPA_FOR(2, 2, W)
 
+#define VEC vec_push
 LaunchFn pick_mat_push_dd2(const fe_form_desc &d) {
   FE_BILINEAR_TABLE(mat_push)
   return nullptr;
@@ -21,5 +22,21 @@ LaunchFn pick_vec_push_dd2(const fe_form_desc &d) {
   FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1)
   return nullptr;
 }
+#undef VEC
+
+#define VEC vec_pull
+LaunchFn pick_mat_pull_dd2(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(mat_pull)
+  return nullptr;
+}
+LaunchFn pick_action_pull_dd2(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(action_pull)
+  return nullptr;
+}
+LaunchFn pick_vec_pull_dd2(const fe_form_desc &d) {
+  FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1)
+  return nullptr;
+}
+#undef VEC
 
 }  // namespace fe

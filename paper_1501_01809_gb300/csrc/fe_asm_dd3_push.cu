@@ -1,5 +1,5 @@
-// Double-float (FP32 pair) instantiations of the assembly kernels on tetrahedra: P1 and P2 (the
-// element tensors of the larger elements are compiled in FP64 only).
+// Double-float (FP32 pair) instantiations of the push assembly kernels on tetrahedra: P1 and P2
+// for mass, Laplace and Helmholtz (kappa-diffusion and larger elements are compiled in FP64 only).
 #include "fe_kernels.cuh"
 
 namespace fe {
@@ -7,8 +7,9 @@ using namespace kern;
 using OPS = OpsF32x2;
 
 #define FE_BILINEAR_TABLE(W) \
-  FE_FORMS_FOR(3, 1, W) FE_FORMS_FOR(3, 2, W) FE_KAPPA_FOR(3, 1, W) FE_KAPPA_FOR(3, 2, W)
+  FE_FORMS_FOR(3, 1, W) FE_FORMS_FOR(3, 2, W)
 
+#define VEC vec_push
 LaunchFn pick_mat_push_dd3(const fe_form_desc &d) {
   FE_BILINEAR_TABLE(mat_push)
   return nullptr;
@@ -21,5 +22,6 @@ LaunchFn pick_vec_push_dd3(const fe_form_desc &d) {
   FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
   return nullptr;
 }
+#undef VEC
 
 }  // namespace fe

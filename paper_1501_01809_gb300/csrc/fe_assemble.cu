@@ -14,49 +14,90 @@ LaunchFn pick_vec_push_dd2(const fe_form_desc &d);
 LaunchFn pick_mat_push_dd3(const fe_form_desc &d);
 LaunchFn pick_action_push_dd3(const fe_form_desc &d);
 LaunchFn pick_vec_push_dd3(const fe_form_desc &d);
+LaunchFn pick_mat_pull_f64(const fe_form_desc &d);
+LaunchFn pick_action_pull_f64(const fe_form_desc &d);
+LaunchFn pick_vec_pull_f64(const fe_form_desc &d);
+LaunchFn pick_mat_pull_dd2(const fe_form_desc &d);
+LaunchFn pick_action_pull_dd2(const fe_form_desc &d);
+LaunchFn pick_vec_pull_dd2(const fe_form_desc &d);
+LaunchFn pick_mat_pull_dd3(const fe_form_desc &d);
+LaunchFn pick_action_pull_dd3(const fe_form_desc &d);
+LaunchFn pick_vec_pull_dd3(const fe_form_desc &d);
 
 namespace {
 
-LaunchFn pick_mat(const fe_form_desc &d) {
-  if (d.form == FE_FORM_SOURCE || d.strategy == FE_STRATEGY_PULL) return nullptr;
-  if (d.precision == FE_PREC_FP64) return pick_mat_push_f64(d);
-  if (d.precision == FE_PREC_F32X2) return d.dim == 2 ? pick_mat_push_dd2(d) : pick_mat_push_dd3(d);
+// strategy: FE_STRATEGY_PUSH or FE_STRATEGY_PULL (already resolved)
+LaunchFn pick_mat(const fe_form_desc &d, int strategy) {
+  if (d.form == FE_FORM_SOURCE) return nullptr;
+  const bool pull = strategy == FE_STRATEGY_PULL;
+  if (d.precision == FE_PREC_FP64) return pull ? pick_mat_pull_f64(d) : pick_mat_push_f64(d);
+  if (d.precision == FE_PREC_F32X2) {
+    if (d.dim == 2) return pull ? pick_mat_pull_dd2(d) : pick_mat_push_dd2(d);
+    return pull ? pick_mat_pull_dd3(d) : pick_mat_push_dd3(d);
+  }
   return nullptr;
 }
-LaunchFn pick_action(const fe_form_desc &d) {
-  if (d.form == FE_FORM_SOURCE || d.strategy == FE_STRATEGY_PULL) return nullptr;
-  if (d.precision == FE_PREC_FP64) return pick_action_push_f64(d);
-  if (d.precision == FE_PREC_F32X2) return d.dim == 2 ? pick_action_push_dd2(d) : pick_action_push_dd3(d);
+LaunchFn pick_action(const fe_form_desc &d, int strategy) {
+  if (d.form == FE_FORM_SOURCE) return nullptr;
+  const bool pull = strategy == FE_STRATEGY_PULL;
+  if (d.precision == FE_PREC_FP64) return pull ? pick_action_pull_f64(d) : pick_action_push_f64(d);
+  if (d.precision == FE_PREC_F32X2) {
+    if (d.dim == 2) return pull ? pick_action_pull_dd2(d) : pick_action_push_dd2(d);
+    return pull ? pick_action_pull_dd3(d) : pick_action_push_dd3(d);
+  }
   return nullptr;
 }
-LaunchFn pick_vec(const fe_form_desc &d) {
-  if (d.form != FE_FORM_SOURCE || d.strategy == FE_STRATEGY_PULL) return nullptr;
-  if (d.precision == FE_PREC_FP64) return pick_vec_push_f64(d);
-  if (d.precision == FE_PREC_F32X2) return d.dim == 2 ? pick_vec_push_dd2(d) : pick_vec_push_dd3(d);
+LaunchFn pick_vec(const fe_form_desc &d, int strategy) {
+  if (d.form != FE_FORM_SOURCE) return nullptr;
+  const bool pull = strategy == FE_STRATEGY_PULL;
+  if (d.precision == FE_PREC_FP64) return pull ? pick_vec_pull_f64(d) : pick_vec_push_f64(d);
+  if (d.precision == FE_PREC_F32X2) {
+    if (d.dim == 2) return pull ? pick_vec_pull_dd2(d) : pick_vec_push_dd2(d);
+    return pull ? pick_vec_pull_dd3(d) : pick_vec_push_dd3(d);
+  }
   return nullptr;
 }
+
+int nodes_of(int dim, int p) { return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6; }
 
 }  // namespace
 
+int resolve_strategy(const fe_form_desc &d, bool have_incidence) {
+  if (d.strategy == FE_STRATEGY_PUSH) return FE_STRATEGY_PUSH;
+  if (d.strategy == FE_STRATEGY_PULL) return FE_STRATEGY_PULL;
+  return have_incidence ? FE_STRATEGY_PULL : FE_STRATEGY_PUSH;
+}
+
+size_t stage_bytes_mat(const fe_form_desc &d, int64_t ncell) {
+  const int nd = nodes_of(d.dim, d.degree);
+  const size_t elem = d.precision == FE_PREC_F32X2 ? 2 * sizeof(float) : sizeof(double);
+  return (size_t)ncell * (size_t)(nd * (nd + 1) / 2) * elem;
+}
+
+size_t stage_bytes_vec(const fe_form_desc &d, int64_t ncell, int nd) {
+  const size_t elem = d.precision == FE_PREC_F32X2 ? 2 * sizeof(float) : sizeof(double);
+  return (size_t)ncell * (size_t)nd * elem;
+}
+
 bool kernel_supported(const fe_form_desc &d) {
-  if (d.form == FE_FORM_SOURCE) return pick_vec(d) != nullptr;
-  return pick_mat(d) != nullptr;
+  if (d.form == FE_FORM_SOURCE) return pick_vec(d, FE_STRATEGY_PUSH) != nullptr;
+  return pick_mat(d, FE_STRATEGY_PUSH) != nullptr;
 }
 
 cudaError_t launch_assemble_mat(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
-  LaunchFn f = pick_mat(d);
+  LaunchFn f = pick_mat(d, resolve_strategy(d, a.adj != nullptr));
   *unsupported = f == nullptr;
   return f ? f(a, s) : cudaSuccess;
 }
 
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
-  LaunchFn f = pick_action(d);
+  LaunchFn f = pick_action(d, resolve_strategy(d, a.adj != nullptr));
   *unsupported = f == nullptr;
   return f ? f(a, s) : cudaSuccess;
 }
 
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
-  LaunchFn f = pick_vec(d);
+  LaunchFn f = pick_vec(d, resolve_strategy(d, a.adj != nullptr));
   *unsupported = f == nullptr;
   return f ? f(a, s) : cudaSuccess;
 }

@@ -73,6 +73,9 @@ struct fe_sparsity {
   int64_t *scan_tmp; // scan block sums
   int64_t scan_tmp_elems;
   int *d_maxcnt;     // [1] max incidence count
+  int maxrow;        // longest row (entries), known after build
+  void *vstage;      // staging of element vectors for pull action / linear form (lazily allocated)
+  size_t vstage_bytes;
 };
 
 struct fe_mat {
@@ -80,6 +83,8 @@ struct fe_mat {
   fe_ctx *ctx;
   fe_sparsity *sp;
   double *values;
+  void *stage;  // staging of element matrices for pull assembly (lazily allocated)
+  size_t stage_bytes;
 };
 
 struct fe_kernel {
@@ -107,6 +112,7 @@ cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err);
 // the colidx compaction is skipped (build: host learns nnz first, then calls sparsity_compact).
 cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err);
 cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz);
+cudaError_t launch_max_i32(const int32_t *v, int64_t n, int *out, cudaStream_t s);
 
 // ---- fills ----
 cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s);
@@ -142,8 +148,17 @@ struct AsmArgs {
   double *y;
   int *err;
   int checks;
+  // staged pull
+  void *stage;     // ncell * NUP (Mat) or ncell * ND (action, vector) element values
+  int rowcap;      // longest row of the pattern (shared-memory accumulators per row owner)
+  int zero_first;  // row kernels overwrite instead of adding
 };
 using LaunchFn = cudaError_t (*)(const AsmArgs &, cudaStream_t);
+// strategy resolved for a call (AUTO -> PULL when the row incidence is available)
+int resolve_strategy(const fe_form_desc &d, bool have_incidence);
+// bytes of the staging buffer for a pull Mat (ncell * NUP) or vector (ncell * ND) of this kernel
+size_t stage_bytes_mat(const fe_form_desc &d, int64_t ncell);
+size_t stage_bytes_vec(const fe_form_desc &d, int64_t ncell, int nd);
 cudaError_t launch_assemble_mat(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);

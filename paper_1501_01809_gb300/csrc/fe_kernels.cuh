@@ -149,17 +149,25 @@ __global__ void __launch_bounds__(kPushThreads) k_action_push(const AsmArgs a) {
   for (int j = 0; j < ND; j++) xe[j] = Ops::from_f64(a.x[rows[j]]);
   T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
   Geo<DIM>::template compute<Ops>(x, Lam, vol);
+  T ye[ND];
+  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) {
 #pragma unroll
-  for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
-  T K[E::NUP];
-  element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
+    for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
+    T K[E::NUP];
+    element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
 #pragma unroll
-  for (int i = 0; i < ND; i++) {
-    T yi = Ops::mul(K[E::upper_index(i, 0)], xe[0]);
+    for (int i = 0; i < ND; i++) {
+      ye[i] = Ops::mul(K[E::upper_index(i, 0)], xe[0]);
 #pragma unroll
-    for (int j = 1; j < ND; j++) yi = Ops::fma3(K[E::upper_index(i, j)], xe[j], yi);
-    red_add_f64(a.y + rows[i], Ops::to_f64(yi));
+      for (int j = 1; j < ND; j++) ye[i] = Ops::fma3(K[E::upper_index(i, j)], xe[j], ye[i]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ND; i++) ye[i] = Ops::zero();
+    E::template action_upper<Ops, FORM != FE_FORM_MASS, FORM != FE_FORM_LAPLACE>(Lam, vol, xe, ye);
   }
+#pragma unroll
+  for (int i = 0; i < ND; i++) red_add_f64(a.y + rows[i], Ops::to_f64(ye[i]));
 }
 
 // ---------------------------------------------------------------------------- vector (f v dx), push
@@ -198,6 +206,173 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
   for (int i = 0; i < ND; i++) red_add_f64(a.y + rows[i], Ops::to_f64(b[i]));
 }
 
+// ---------------------------------------------------------------------------- staged pull
+// Deterministic INC without atomics, in two kernels.  (1) One thread per cell stores its element
+// tensor (the upper triangle of K_e for a Mat, the element vector for the action and the linear
+// form) with plain stores to a staging buffer.  (2) One thread per row, the row's owner, walks the
+// row's incidence list {(e, i)} -- ascending, fixed by the sparsity build -- and adds the
+// contributions in that order; a Mat row accumulates in shared memory (slots given by the lookup
+// table) and is written once.  The summation order is the same on every run: results are bitwise
+// reproducible.
+
+template <int DIM, int P, int FORM, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_mat_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+  using T = typename Ops::T;
+  using E = fe_gen::Elem<DIM, P>;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= a.ncell) return;
+  double x[DIM + 1][DIM], kap[DIM + 1];
+  int32_t v[DIM + 1];
+  bool ok = gather_coords<DIM>(a, e, x, v);
+  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) ok &= gather_kappa<DIM>(a, e, kap);
+  if (!ok) {
+    flag(a.err, ERR_RANGE, e);
+    return;
+  }
+  T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
+  Geo<DIM>::template compute<Ops>(x, Lam, vol);
+#pragma unroll
+  for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
+  T K[E::NUP];
+  element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
+  T *out = stage + e * E::NUP;
+#pragma unroll
+  for (int u = 0; u < E::NUP; u++) out[u] = K[u];
+}
+
+template <int DIM, int P, int FORM, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_action_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+  using T = typename Ops::T;
+  using E = fe_gen::Elem<DIM, P>;
+  constexpr int ND = E::ND;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= a.ncell) return;
+  double x[DIM + 1][DIM], kap[DIM + 1];
+  int32_t v[DIM + 1], rows[ND];
+  bool ok = gather_coords<DIM>(a, e, x, v);
+  ok &= gather_rows<ND>(a, e, rows);
+  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) ok &= gather_kappa<DIM>(a, e, kap);
+  if (!ok) {
+    flag(a.err, ERR_RANGE, e);
+    return;
+  }
+  T xe[ND];
+#pragma unroll
+  for (int j = 0; j < ND; j++) xe[j] = Ops::from_f64(a.x[rows[j]]);
+  T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
+  Geo<DIM>::template compute<Ops>(x, Lam, vol);
+  T ye[ND];
+  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) {
+#pragma unroll
+    for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
+    T K[E::NUP];
+    element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
+#pragma unroll
+    for (int i = 0; i < ND; i++) {
+      ye[i] = Ops::mul(K[E::upper_index(i, 0)], xe[0]);
+#pragma unroll
+      for (int j = 1; j < ND; j++) ye[i] = Ops::fma3(K[E::upper_index(i, j)], xe[j], ye[i]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ND; i++) ye[i] = Ops::zero();
+    E::template action_upper<Ops, FORM != FE_FORM_MASS, FORM != FE_FORM_LAPLACE>(Lam, vol, xe, ye);
+  }
+  T *out = stage + e * ND;
+#pragma unroll
+  for (int i = 0; i < ND; i++) out[i] = ye[i];
+}
+
+template <int DIM, int P, int Q, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_vec_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+  using T = typename Ops::T;
+  using S = fe_gen::Source<DIM, P, Q>;
+  constexpr int ND = S::ND, NF = S::NF;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= a.ncell) return;
+  double x[DIM + 1][DIM];
+  int32_t v[DIM + 1];
+  bool ok = gather_coords<DIM>(a, e, x, v);
+  double fed[NF];
+#pragma unroll
+  for (int k = 0; k < NF; k++) {
+    int32_t c = a.coefmap[e * NF + k];
+    if (a.checks && (c < 0 || c >= a.ncoef)) {
+      ok = false;
+      c = 0;
+    }
+    fed[k] = a.coef[c];
+  }
+  if (!ok) {
+    flag(a.err, ERR_RANGE, e);
+    return;
+  }
+  T Lam[Geo<DIM>::NLAM], vol, fe[NF];
+  Geo<DIM>::template compute<Ops>(x, Lam, vol);
+#pragma unroll
+  for (int k = 0; k < NF; k++) fe[k] = Ops::from_f64(fed[k]);
+  T b[ND];
+  S::template vec<Ops>(vol, fe, b);
+  T *out = stage + e * ND;
+#pragma unroll
+  for (int i = 0; i < ND; i++) out[i] = b[i];
+}
+
+// Row owners of a Mat: y-independent.  Shared memory: per thread rowcap accumulators, element q of
+// thread t at q*T + t.  INC semantics: the row's values are read once (unless zero_first) and
+// written once.
+template <int ND, class Ops>
+__global__ void k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr, const int32_t *__restrict__ adj,
+                           const int64_t *__restrict__ rowptr, const uint8_t *__restrict__ lut,
+                           const typename Ops::T *__restrict__ stage, double *__restrict__ vals, int rowcap,
+                           int zero_first, int *err) {
+  using T = typename Ops::T;
+  constexpr int NUP = ND * (ND + 1) / 2;
+  extern __shared__ __align__(16) unsigned char smp[];
+  T *acc = reinterpret_cast<T *>(smp) + threadIdx.x;
+  const int TB = blockDim.x;
+  for (int64_t r = blockIdx.x * (int64_t)TB + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * TB) {
+    const int64_t b = rowptr[r];
+    const int len = (int)(rowptr[r + 1] - b);
+    if (len > rowcap) {
+      flag(err, ERR_ROW_TOO_LONG, r);
+      continue;
+    }
+    for (int q = 0; q < len; q++) acc[q * TB] = Ops::zero();
+    const int64_t a0 = adjptr[r], a1 = adjptr[r + 1];
+    for (int64_t ai = a0; ai < a1; ai++) {
+      const int32_t k = adj[ai];
+      const int32_t e = k / ND, i = k - e * ND;
+      const T *Ke = stage + (int64_t)e * NUP;
+      const uint8_t *L = lut + (int64_t)k * ND;
+#pragma unroll
+      for (int j = 0; j < ND; j++) {
+        const int u = i <= j ? i * ND - (i * (i - 1)) / 2 + (j - i) : j * ND - (j * (j - 1)) / 2 + (i - j);
+        const int q = L[j];
+        acc[q * TB] = Ops::add(acc[q * TB], Ke[u]);
+      }
+    }
+    double *out = vals + b;
+    for (int q = 0; q < len; q++) {
+      const double v = Ops::to_f64(acc[q * TB]);
+      out[q] = zero_first ? v : out[q] + v;
+    }
+  }
+}
+
+// Row owners of a Dat: y[r] (+)= sum over the row's incidence list of stage[e*ND + i], in order.
+template <int ND, class Ops>
+__global__ void k_vec_pull(int64_t nrows, const int64_t *__restrict__ adjptr, const int32_t *__restrict__ adj,
+                           const typename Ops::T *__restrict__ stage, double *__restrict__ y, int zero_first) {
+  using T = typename Ops::T;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
+    T s = Ops::zero();
+    for (int64_t ai = adjptr[r]; ai < adjptr[r + 1]; ai++) s = Ops::add(s, stage[adj[ai]]);
+    const double v = Ops::to_f64(s);
+    y[r] = zero_first ? v : y[r] + v;
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <int DIM, int P, int FORM, class Ops>
@@ -210,6 +385,53 @@ cudaError_t action_push(const AsmArgs &a, cudaStream_t s) {
   if (a.ncell > 0) k_action_push<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
+// The staging buffer (a.stage) holds ncell * NUP (Mat) or ncell * ND (action, vector) values of
+// the arithmetic type; AsmArgs.zero_first selects overwrite instead of INC in the row kernels.
+inline int pull_blocks(int64_t n, int t) {
+  int64_t b = (n + t - 1) / t;
+  return (int)(b < 1 ? 1 : b > 152 * 32 ? 152 * 32 : b);
+}
+
+template <int DIM, int P, int FORM, class Ops>
+cudaError_t mat_pull(const AsmArgs &a, cudaStream_t s) {
+  using E = fe_gen::Elem<DIM, P>;
+  using T = typename Ops::T;
+  T *stage = static_cast<T *>(a.stage);
+  if (a.ncell > 0) k_mat_elem<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a, stage);
+  const int TB = 64;
+  const size_t smem = (size_t)a.rowcap * TB * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_mat_pull<E::ND, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (a.nrows > 0)
+    k_mat_pull<E::ND, Ops><<<pull_blocks(a.nrows, TB), TB, smem, s>>>(a.nrows, a.adjptr, a.adj, a.rowptr, a.lut, stage,
+                                                                       a.vals, a.rowcap, a.zero_first, a.err);
+  return cudaGetLastError();
+}
+
+template <int DIM, int P, int FORM, class Ops>
+cudaError_t action_pull(const AsmArgs &a, cudaStream_t s) {
+  using E = fe_gen::Elem<DIM, P>;
+  using T = typename Ops::T;
+  T *stage = static_cast<T *>(a.stage);
+  if (a.ncell > 0) k_action_elem<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a, stage);
+  if (a.nrows > 0)
+    k_vec_pull<E::ND, Ops><<<pull_blocks(a.nrows, 256), 256, 0, s>>>(a.nrows, a.adjptr, a.adj, stage, a.y, a.zero_first);
+  return cudaGetLastError();
+}
+
+template <int DIM, int P, int Q, class Ops>
+cudaError_t vec_pull(const AsmArgs &a, cudaStream_t s) {
+  using S = fe_gen::Source<DIM, P, Q>;
+  using T = typename Ops::T;
+  T *stage = static_cast<T *>(a.stage);
+  if (a.ncell > 0) k_vec_elem<DIM, P, Q, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a, stage);
+  if (a.nrows > 0)
+    k_vec_pull<S::ND, Ops><<<pull_blocks(a.nrows, 256), 256, 0, s>>>(a.nrows, a.adjptr, a.adj, stage, a.y, a.zero_first);
+  return cudaGetLastError();
+}
+
 template <int DIM, int P, int Q, class Ops>
 cudaError_t vec_push(const AsmArgs &a, cudaStream_t s) {
   if (a.ncell > 0) k_vec_push<DIM, P, Q, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
@@ -226,7 +448,7 @@ cudaError_t vec_push(const AsmArgs &a, cudaStream_t s) {
 #define FE_KAPPA_FOR(D, P, W) \
   if (d.dim == D && d.degree == P && d.form == FE_FORM_KAPPA_DIFFUSION) return &W<D, P, FE_FORM_KAPPA_DIFFUSION, OPS>;
 #define FE_SRC_FOR(D, P, Q) \
-  if (d.dim == D && d.degree == P && d.coeff_degree == Q) return &vec_push<D, P, Q, OPS>;
+  if (d.dim == D && d.degree == P && d.coeff_degree == Q) return &VEC<D, P, Q, OPS>;
 
 }  // namespace kern
 }  // namespace fe

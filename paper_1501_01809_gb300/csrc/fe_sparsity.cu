@@ -367,6 +367,12 @@ cudaError_t launch_zero_i32(int32_t *p, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_max_i32(const int32_t *v, int64_t n, int *out, cudaStream_t s) {
+  k_zero_i32<<<1, 32, 0, s>>>(out, 1);
+  if (n > 0) k_max_count<<<grid_for(n, 256, 152 * 4), 256, 0, s>>>(v, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_zero_f64<<<grid_for((n + 1) / 2, 256, 152 * 8), 256, 0, s>>>(p, n);

@@ -38,6 +38,15 @@ template <> struct Elem<2, 1> {
     K[4] = Ops::mulc(vol, 0.08333333333333333);
     K[5] = Ops::mulc(vol, 0.16666666666666666);
   }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Lam[0]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.16666666666666666, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Lam[1]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08333333333333333, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Lam[2]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08333333333333333, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    { if constexpr (STIFF) { k = Lam[3]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.16666666666666666, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Lam[4]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08333333333333333, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    { if constexpr (STIFF) { k = Lam[5]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.16666666666666666, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+  }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 3 - (i * (i - 1)) / 2 + (j - i) : j * 3 - (j * (j - 1)) / 2 + (i - j);
   }
@@ -112,6 +121,30 @@ template <> struct Elem<2, 2> {
     K[18] = Ops::mulc(vol, 0.17777777777777778);
     K[19] = Ops::mulc(vol, 0.08888888888888889);
     K[20] = Ops::mulc(vol, 0.17777777777777778);
+  }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Lam[0]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.03333333333333333, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[1], -0.3333333333333333); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.005555555555555556, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[2], -0.3333333333333333); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.005555555555555556, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::mulc(Lam[1], 1.3333333333333333); } else { k = Ops::zero(); } y[0] = Ops::fma3(k, x[3], y[0]); y[3] = Ops::fma3(k, x[0], y[3]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::mulc(Lam[2], 1.3333333333333333); } else { k = Ops::zero(); } y[0] = Ops::fma3(k, x[4], y[0]); y[4] = Ops::fma3(k, x[0], y[4]); }
+    if constexpr (MASS) { k = Ops::zero(); if constexpr (MASS) { k = Ops::fmac(vol, -0.022222222222222223, k); } y[0] = Ops::fma3(k, x[5], y[0]); y[5] = Ops::fma3(k, x[0], y[5]); }
+    { if constexpr (STIFF) { k = Lam[3]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.03333333333333333, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[4], -0.3333333333333333); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.005555555555555556, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::mulc(Lam[1], 1.3333333333333333); } else { k = Ops::zero(); } y[1] = Ops::fma3(k, x[3], y[1]); y[3] = Ops::fma3(k, x[1], y[3]); }
+    if constexpr (MASS) { k = Ops::zero(); if constexpr (MASS) { k = Ops::fmac(vol, -0.022222222222222223, k); } y[1] = Ops::fma3(k, x[4], y[1]); y[4] = Ops::fma3(k, x[1], y[4]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::mulc(Lam[4], 1.3333333333333333); } else { k = Ops::zero(); } y[1] = Ops::fma3(k, x[5], y[1]); y[5] = Ops::fma3(k, x[1], y[5]); }
+    { if constexpr (STIFF) { k = Lam[5]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.03333333333333333, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+    if constexpr (MASS) { k = Ops::zero(); if constexpr (MASS) { k = Ops::fmac(vol, -0.022222222222222223, k); } y[2] = Ops::fma3(k, x[3], y[2]); y[3] = Ops::fma3(k, x[2], y[3]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::mulc(Lam[2], 1.3333333333333333); } else { k = Ops::zero(); } y[2] = Ops::fma3(k, x[4], y[2]); y[4] = Ops::fma3(k, x[2], y[4]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::mulc(Lam[4], 1.3333333333333333); } else { k = Ops::zero(); } y[2] = Ops::fma3(k, x[5], y[2]); y[5] = Ops::fma3(k, x[2], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 2.6666666666666665, Ops::fmac(Lam[1], 2.6666666666666665, Ops::mulc(Lam[0], 2.6666666666666665))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.17777777777777778, k); } y[3] = Ops::fma3(k, x[3], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 2.6666666666666665, Ops::fmac(Lam[2], 1.3333333333333333, Ops::fmac(Lam[1], 1.3333333333333333, Ops::mulc(Lam[0], 1.3333333333333333)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08888888888888889, k); } y[3] = Ops::fma3(k, x[4], y[3]); y[4] = Ops::fma3(k, x[3], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.3333333333333333, Ops::fmac(Lam[3], 1.3333333333333333, Ops::fmac(Lam[2], 2.6666666666666665, Ops::mulc(Lam[1], 1.3333333333333333)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08888888888888889, k); } y[3] = Ops::fma3(k, x[5], y[3]); y[5] = Ops::fma3(k, x[3], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 2.6666666666666665, Ops::fmac(Lam[2], 2.6666666666666665, Ops::mulc(Lam[0], 2.6666666666666665))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.17777777777777778, k); } y[4] = Ops::fma3(k, x[4], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.3333333333333333, Ops::fmac(Lam[4], 1.3333333333333333, Ops::fmac(Lam[2], 1.3333333333333333, Ops::mulc(Lam[1], 2.6666666666666665)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08888888888888889, k); } y[4] = Ops::fma3(k, x[5], y[4]); y[5] = Ops::fma3(k, x[4], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 2.6666666666666665, Ops::fmac(Lam[4], 2.6666666666666665, Ops::mulc(Lam[3], 2.6666666666666665))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.17777777777777778, k); } y[5] = Ops::fma3(k, x[5], y[5]); }
   }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 6 - (i * (i - 1)) / 2 + (j - i) : j * 6 - (j * (j - 1)) / 2 + (i - j);
@@ -289,6 +322,64 @@ template <> struct Elem<2, 3> {
     K[52] = Ops::mulc(vol, 0.08035714285714286);
     K[53] = Ops::mulc(vol, 0.024107142857142858);
     K[54] = Ops::mulc(vol, 0.2892857142857143);
+  }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[0], 0.85); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.01130952380952381, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[1], 0.175); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001636904761904762, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[2], 0.175); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001636904761904762, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[1], 1.425, Ops::mulc(Lam[0], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0026785714285714286, k); } y[0] = Ops::fma3(k, x[3], y[0]); y[3] = Ops::fma3(k, x[0], y[3]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[1], -0.6, Ops::mulc(Lam[0], 0.075)); } else { k = Ops::zero(); } y[0] = Ops::fma3(k, x[4], y[0]); y[4] = Ops::fma3(k, x[0], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 1.425, Ops::mulc(Lam[0], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0026785714285714286, k); } y[0] = Ops::fma3(k, x[5], y[0]); y[5] = Ops::fma3(k, x[0], y[5]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.6, Ops::mulc(Lam[0], 0.075)); } else { k = Ops::zero(); } y[0] = Ops::fma3(k, x[6], y[0]); y[6] = Ops::fma3(k, x[0], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.075, Ops::mulc(Lam[1], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[0] = Ops::fma3(k, x[7], y[0]); y[7] = Ops::fma3(k, x[0], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.075, Ops::mulc(Lam[1], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[0] = Ops::fma3(k, x[8], y[0]); y[8] = Ops::fma3(k, x[0], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.225, Ops::fmac(Lam[1], 0.225, Ops::mulc(Lam[0], 0.225))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.005357142857142857, k); } y[0] = Ops::fma3(k, x[9], y[0]); y[9] = Ops::fma3(k, x[0], y[9]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[3], 0.85); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.01130952380952381, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[4], 0.175); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001636904761904762, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.075, Ops::mulc(Lam[1], -0.6)); } else { k = Ops::zero(); } y[1] = Ops::fma3(k, x[3], y[1]); y[3] = Ops::fma3(k, x[1], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.075, Ops::mulc(Lam[1], 1.425)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0026785714285714286, k); } y[1] = Ops::fma3(k, x[4], y[1]); y[4] = Ops::fma3(k, x[1], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.075, Ops::mulc(Lam[1], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[1] = Ops::fma3(k, x[5], y[1]); y[5] = Ops::fma3(k, x[1], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.075, Ops::mulc(Lam[1], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[1] = Ops::fma3(k, x[6], y[1]); y[6] = Ops::fma3(k, x[1], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.425, Ops::mulc(Lam[3], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0026785714285714286, k); } y[1] = Ops::fma3(k, x[7], y[1]); y[7] = Ops::fma3(k, x[1], y[7]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.6, Ops::mulc(Lam[3], 0.075)); } else { k = Ops::zero(); } y[1] = Ops::fma3(k, x[8], y[1]); y[8] = Ops::fma3(k, x[1], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.225, Ops::fmac(Lam[3], 0.225, Ops::mulc(Lam[1], 0.225))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.005357142857142857, k); } y[1] = Ops::fma3(k, x[9], y[1]); y[9] = Ops::fma3(k, x[1], y[9]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[5], 0.85); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.01130952380952381, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.075, Ops::mulc(Lam[2], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[2] = Ops::fma3(k, x[3], y[2]); y[3] = Ops::fma3(k, x[2], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.075, Ops::mulc(Lam[2], 0.075)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[2] = Ops::fma3(k, x[4], y[2]); y[4] = Ops::fma3(k, x[2], y[4]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.075, Ops::mulc(Lam[2], -0.6)); } else { k = Ops::zero(); } y[2] = Ops::fma3(k, x[5], y[2]); y[5] = Ops::fma3(k, x[2], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.075, Ops::mulc(Lam[2], 1.425)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0026785714285714286, k); } y[2] = Ops::fma3(k, x[6], y[2]); y[6] = Ops::fma3(k, x[2], y[6]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.075, Ops::mulc(Lam[4], -0.6)); } else { k = Ops::zero(); } y[2] = Ops::fma3(k, x[7], y[2]); y[7] = Ops::fma3(k, x[2], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.075, Ops::mulc(Lam[4], 1.425)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0026785714285714286, k); } y[2] = Ops::fma3(k, x[8], y[2]); y[8] = Ops::fma3(k, x[2], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.225, Ops::fmac(Lam[4], 0.225, Ops::mulc(Lam[2], 0.225))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.005357142857142857, k); } y[2] = Ops::fma3(k, x[9], y[2]); y[9] = Ops::fma3(k, x[2], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 3.375, Ops::fmac(Lam[1], 3.375, Ops::mulc(Lam[0], 3.375))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08035714285714286, k); } y[3] = Ops::fma3(k, x[3], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.675, Ops::fmac(Lam[1], 1.35, Ops::mulc(Lam[0], -0.675))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.028125, k); } y[3] = Ops::fma3(k, x[4], y[3]); y[4] = Ops::fma3(k, x[3], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 3.375, Ops::fmac(Lam[2], 1.6875, Ops::fmac(Lam[1], 1.6875, Ops::mulc(Lam[0], 1.6875)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.04017857142857143, k); } y[3] = Ops::fma3(k, x[5], y[3]); y[5] = Ops::fma3(k, x[3], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.675, Ops::fmac(Lam[2], -0.3375, Ops::fmac(Lam[1], -0.3375, Ops::mulc(Lam[0], -0.3375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.020089285714285716, k); } y[3] = Ops::fma3(k, x[6], y[3]); y[6] = Ops::fma3(k, x[3], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.3375, Ops::fmac(Lam[3], -0.3375, Ops::fmac(Lam[2], -0.675, Ops::mulc(Lam[1], -0.3375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.020089285714285716, k); } y[3] = Ops::fma3(k, x[7], y[3]); y[7] = Ops::fma3(k, x[3], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.3375, Ops::fmac(Lam[3], -0.3375, Ops::fmac(Lam[2], -0.675, Ops::mulc(Lam[1], -0.3375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.008035714285714285, k); } y[3] = Ops::fma3(k, x[8], y[3]); y[8] = Ops::fma3(k, x[3], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 2.025, Ops::fmac(Lam[3], 2.025, Ops::fmac(Lam[2], 4.05, Ops::mulc(Lam[1], 2.025)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[3] = Ops::fma3(k, x[9], y[3]); y[9] = Ops::fma3(k, x[3], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 3.375, Ops::fmac(Lam[1], 3.375, Ops::mulc(Lam[0], 3.375))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08035714285714286, k); } y[4] = Ops::fma3(k, x[4], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.675, Ops::fmac(Lam[2], -0.3375, Ops::fmac(Lam[1], -0.3375, Ops::mulc(Lam[0], -0.3375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.020089285714285716, k); } y[4] = Ops::fma3(k, x[5], y[4]); y[5] = Ops::fma3(k, x[4], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.675, Ops::fmac(Lam[2], -0.3375, Ops::fmac(Lam[1], -0.3375, Ops::mulc(Lam[0], -0.3375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.008035714285714285, k); } y[4] = Ops::fma3(k, x[6], y[4]); y[6] = Ops::fma3(k, x[4], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.6875, Ops::fmac(Lam[3], 1.6875, Ops::fmac(Lam[2], 3.375, Ops::mulc(Lam[1], 1.6875)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.04017857142857143, k); } y[4] = Ops::fma3(k, x[7], y[4]); y[7] = Ops::fma3(k, x[4], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.3375, Ops::fmac(Lam[3], -0.3375, Ops::fmac(Lam[2], -0.675, Ops::mulc(Lam[1], -0.3375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.020089285714285716, k); } y[4] = Ops::fma3(k, x[8], y[4]); y[8] = Ops::fma3(k, x[4], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 4.05, Ops::fmac(Lam[2], 2.025, Ops::fmac(Lam[1], 2.025, Ops::mulc(Lam[0], 2.025)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[4] = Ops::fma3(k, x[9], y[4]); y[9] = Ops::fma3(k, x[4], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.375, Ops::fmac(Lam[2], 3.375, Ops::mulc(Lam[0], 3.375))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08035714285714286, k); } y[5] = Ops::fma3(k, x[5], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.675, Ops::fmac(Lam[2], 1.35, Ops::mulc(Lam[0], -0.675))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.028125, k); } y[5] = Ops::fma3(k, x[6], y[5]); y[6] = Ops::fma3(k, x[5], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.3375, Ops::fmac(Lam[4], -0.3375, Ops::fmac(Lam[2], -0.3375, Ops::mulc(Lam[1], -0.675)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.008035714285714285, k); } y[5] = Ops::fma3(k, x[7], y[5]); y[7] = Ops::fma3(k, x[5], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.3375, Ops::fmac(Lam[4], -0.3375, Ops::fmac(Lam[2], -0.3375, Ops::mulc(Lam[1], -0.675)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.020089285714285716, k); } y[5] = Ops::fma3(k, x[8], y[5]); y[8] = Ops::fma3(k, x[5], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 2.025, Ops::fmac(Lam[4], 2.025, Ops::fmac(Lam[2], 2.025, Ops::mulc(Lam[1], 4.05)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[5] = Ops::fma3(k, x[9], y[5]); y[9] = Ops::fma3(k, x[5], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.375, Ops::fmac(Lam[2], 3.375, Ops::mulc(Lam[0], 3.375))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08035714285714286, k); } y[6] = Ops::fma3(k, x[6], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.3375, Ops::fmac(Lam[4], -0.3375, Ops::fmac(Lam[2], -0.3375, Ops::mulc(Lam[1], -0.675)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.020089285714285716, k); } y[6] = Ops::fma3(k, x[7], y[6]); y[7] = Ops::fma3(k, x[6], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.6875, Ops::fmac(Lam[4], 1.6875, Ops::fmac(Lam[2], 1.6875, Ops::mulc(Lam[1], 3.375)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.04017857142857143, k); } y[6] = Ops::fma3(k, x[8], y[6]); y[8] = Ops::fma3(k, x[6], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 4.05, Ops::fmac(Lam[2], 2.025, Ops::fmac(Lam[1], 2.025, Ops::mulc(Lam[0], 2.025)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[6] = Ops::fma3(k, x[9], y[6]); y[9] = Ops::fma3(k, x[6], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.375, Ops::fmac(Lam[4], 3.375, Ops::mulc(Lam[3], 3.375))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08035714285714286, k); } y[7] = Ops::fma3(k, x[7], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.675, Ops::fmac(Lam[4], 1.35, Ops::mulc(Lam[3], -0.675))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.028125, k); } y[7] = Ops::fma3(k, x[8], y[7]); y[8] = Ops::fma3(k, x[7], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 2.025, Ops::fmac(Lam[4], 2.025, Ops::fmac(Lam[2], 2.025, Ops::mulc(Lam[1], 4.05)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[7] = Ops::fma3(k, x[9], y[7]); y[9] = Ops::fma3(k, x[7], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.375, Ops::fmac(Lam[4], 3.375, Ops::mulc(Lam[3], 3.375))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.08035714285714286, k); } y[8] = Ops::fma3(k, x[8], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 2.025, Ops::fmac(Lam[3], 2.025, Ops::fmac(Lam[2], 4.05, Ops::mulc(Lam[1], 2.025)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[8] = Ops::fma3(k, x[9], y[8]); y[9] = Ops::fma3(k, x[8], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 8.1, Ops::fmac(Lam[4], 8.1, Ops::fmac(Lam[3], 8.1, Ops::fmac(Lam[2], 8.1, Ops::fmac(Lam[1], 8.1, Ops::mulc(Lam[0], 8.1)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.2892857142857143, k); } y[9] = Ops::fma3(k, x[9], y[9]); }
   }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 10 - (i * (i - 1)) / 2 + (j - i) : j * 10 - (j * (j - 1)) / 2 + (i - j);
@@ -662,6 +753,129 @@ template <> struct Elem<2, 4> {
     K[118] = Ops::mulc(vol, -0.02708994708994709);
     K[119] = Ops::mulc(vol, 0.18962962962962962);
   }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[0], 0.746031746031746); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0051146384479717815, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[1], -0.11322751322751323); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0004761904761904762, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[2], -0.11322751322751323); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0004761904761904762, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[1], 1.5576719576719578, Ops::mulc(Lam[0], 0.25396825396825395)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[0] = Ops::fma3(k, x[3], y[0]); y[3] = Ops::fma3(k, x[0], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[1], -0.8507936507936508, Ops::mulc(Lam[0], 0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0014109347442680777, k); } y[0] = Ops::fma3(k, x[4], y[0]); y[4] = Ops::fma3(k, x[0], y[4]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[1], 0.40634920634920635, Ops::mulc(Lam[0], -0.08465608465608465)); } else { k = Ops::zero(); } y[0] = Ops::fma3(k, x[5], y[0]); y[5] = Ops::fma3(k, x[0], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 1.5576719576719578, Ops::mulc(Lam[0], 0.25396825396825395)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[0] = Ops::fma3(k, x[6], y[0]); y[6] = Ops::fma3(k, x[0], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.8507936507936508, Ops::mulc(Lam[0], 0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0014109347442680777, k); } y[0] = Ops::fma3(k, x[7], y[0]); y[7] = Ops::fma3(k, x[0], y[7]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.40634920634920635, Ops::mulc(Lam[0], -0.08465608465608465)); } else { k = Ops::zero(); } y[0] = Ops::fma3(k, x[8], y[0]); y[8] = Ops::fma3(k, x[0], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.08465608465608465, Ops::mulc(Lam[1], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0019753086419753087, k); } y[0] = Ops::fma3(k, x[9], y[0]); y[9] = Ops::fma3(k, x[0], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.08465608465608465, Ops::mulc(Lam[1], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.00021164021164021165, k); } y[0] = Ops::fma3(k, x[10], y[0]); y[10] = Ops::fma3(k, x[0], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.08465608465608465, Ops::mulc(Lam[1], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0019753086419753087, k); } y[0] = Ops::fma3(k, x[11], y[0]); y[11] = Ops::fma3(k, x[0], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.6349206349206349, Ops::fmac(Lam[1], 0.6349206349206349, Ops::mulc(Lam[0], 0.4656084656084656))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[0] = Ops::fma3(k, x[12], y[0]); y[12] = Ops::fma3(k, x[0], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.042328042328042326, Ops::fmac(Lam[1], -0.042328042328042326, Ops::mulc(Lam[0], -0.21164021164021163))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0028218694885361554, k); } y[0] = Ops::fma3(k, x[13], y[0]); y[13] = Ops::fma3(k, x[0], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.042328042328042326, Ops::fmac(Lam[1], -0.042328042328042326, Ops::mulc(Lam[0], -0.21164021164021163))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0028218694885361554, k); } y[0] = Ops::fma3(k, x[14], y[0]); y[14] = Ops::fma3(k, x[0], y[14]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[3], 0.746031746031746); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0051146384479717815, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[4], -0.11322751322751323); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0004761904761904762, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.08465608465608465, Ops::mulc(Lam[1], 0.40634920634920635)); } else { k = Ops::zero(); } y[1] = Ops::fma3(k, x[3], y[1]); y[3] = Ops::fma3(k, x[1], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.08465608465608465, Ops::mulc(Lam[1], -0.8507936507936508)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0014109347442680777, k); } y[1] = Ops::fma3(k, x[4], y[1]); y[4] = Ops::fma3(k, x[1], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.25396825396825395, Ops::mulc(Lam[1], 1.5576719576719578)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[1] = Ops::fma3(k, x[5], y[1]); y[5] = Ops::fma3(k, x[1], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.08465608465608465, Ops::mulc(Lam[1], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0019753086419753087, k); } y[1] = Ops::fma3(k, x[6], y[1]); y[6] = Ops::fma3(k, x[1], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.08465608465608465, Ops::mulc(Lam[1], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.00021164021164021165, k); } y[1] = Ops::fma3(k, x[7], y[1]); y[7] = Ops::fma3(k, x[1], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.08465608465608465, Ops::mulc(Lam[1], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0019753086419753087, k); } y[1] = Ops::fma3(k, x[8], y[1]); y[8] = Ops::fma3(k, x[1], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.5576719576719578, Ops::mulc(Lam[3], 0.25396825396825395)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[1] = Ops::fma3(k, x[9], y[1]); y[9] = Ops::fma3(k, x[1], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.8507936507936508, Ops::mulc(Lam[3], 0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0014109347442680777, k); } y[1] = Ops::fma3(k, x[10], y[1]); y[10] = Ops::fma3(k, x[1], y[10]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.40634920634920635, Ops::mulc(Lam[3], -0.08465608465608465)); } else { k = Ops::zero(); } y[1] = Ops::fma3(k, x[11], y[1]); y[11] = Ops::fma3(k, x[1], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.042328042328042326, Ops::fmac(Lam[3], -0.21164021164021163, Ops::mulc(Lam[1], -0.042328042328042326))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0028218694885361554, k); } y[1] = Ops::fma3(k, x[12], y[1]); y[12] = Ops::fma3(k, x[1], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.6349206349206349, Ops::fmac(Lam[3], 0.4656084656084656, Ops::mulc(Lam[1], 0.6349206349206349))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[1] = Ops::fma3(k, x[13], y[1]); y[13] = Ops::fma3(k, x[1], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.042328042328042326, Ops::fmac(Lam[3], -0.21164021164021163, Ops::mulc(Lam[1], -0.042328042328042326))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0028218694885361554, k); } y[1] = Ops::fma3(k, x[14], y[1]); y[14] = Ops::fma3(k, x[1], y[14]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[5], 0.746031746031746); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0051146384479717815, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.08465608465608465, Ops::mulc(Lam[2], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0019753086419753087, k); } y[2] = Ops::fma3(k, x[3], y[2]); y[3] = Ops::fma3(k, x[2], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.08465608465608465, Ops::mulc(Lam[2], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.00021164021164021165, k); } y[2] = Ops::fma3(k, x[4], y[2]); y[4] = Ops::fma3(k, x[2], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.08465608465608465, Ops::mulc(Lam[2], -0.08465608465608465)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0019753086419753087, k); } y[2] = Ops::fma3(k, x[5], y[2]); y[5] = Ops::fma3(k, x[2], y[5]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.08465608465608465, Ops::mulc(Lam[2], 0.40634920634920635)); } else { k = Ops::zero(); } y[2] = Ops::fma3(k, x[6], y[2]); y[6] = Ops::fma3(k, x[2], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08465608465608465, Ops::mulc(Lam[2], -0.8507936507936508)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0014109347442680777, k); } y[2] = Ops::fma3(k, x[7], y[2]); y[7] = Ops::fma3(k, x[2], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.25396825396825395, Ops::mulc(Lam[2], 1.5576719576719578)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[2] = Ops::fma3(k, x[8], y[2]); y[8] = Ops::fma3(k, x[2], y[8]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.08465608465608465, Ops::mulc(Lam[4], 0.40634920634920635)); } else { k = Ops::zero(); } y[2] = Ops::fma3(k, x[9], y[2]); y[9] = Ops::fma3(k, x[2], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08465608465608465, Ops::mulc(Lam[4], -0.8507936507936508)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0014109347442680777, k); } y[2] = Ops::fma3(k, x[10], y[2]); y[10] = Ops::fma3(k, x[2], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.25396825396825395, Ops::mulc(Lam[4], 1.5576719576719578)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[2] = Ops::fma3(k, x[11], y[2]); y[11] = Ops::fma3(k, x[2], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.21164021164021163, Ops::fmac(Lam[4], -0.042328042328042326, Ops::mulc(Lam[2], -0.042328042328042326))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0028218694885361554, k); } y[2] = Ops::fma3(k, x[12], y[2]); y[12] = Ops::fma3(k, x[2], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.21164021164021163, Ops::fmac(Lam[4], -0.042328042328042326, Ops::mulc(Lam[2], -0.042328042328042326))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0028218694885361554, k); } y[2] = Ops::fma3(k, x[13], y[2]); y[13] = Ops::fma3(k, x[2], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.4656084656084656, Ops::fmac(Lam[4], 0.6349206349206349, Ops::mulc(Lam[2], 0.6349206349206349))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0028218694885361554, k); } y[2] = Ops::fma3(k, x[14], y[2]); y[14] = Ops::fma3(k, x[2], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 4.1989417989417985, Ops::fmac(Lam[1], 4.1989417989417985, Ops::mulc(Lam[0], 3.657142857142857))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.045149911816578486, k); } y[3] = Ops::fma3(k, x[3], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -1.5238095238095237, Ops::fmac(Lam[1], 1.0497354497354496, Ops::mulc(Lam[0], -1.3206349206349206))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.022574955908289243, k); } y[3] = Ops::fma3(k, x[4], y[3]); y[4] = Ops::fma3(k, x[3], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.6772486772486772, Ops::fmac(Lam[1], -0.6772486772486772, Ops::mulc(Lam[0], 0.6772486772486772))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.013544973544973546, k); } y[3] = Ops::fma3(k, x[5], y[3]); y[5] = Ops::fma3(k, x[3], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 4.1989417989417985, Ops::fmac(Lam[2], 2.0994708994708993, Ops::fmac(Lam[1], 2.0994708994708993, Ops::mulc(Lam[0], 1.8285714285714285)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[3] = Ops::fma3(k, x[6], y[3]); y[6] = Ops::fma3(k, x[3], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -1.5238095238095237, Ops::fmac(Lam[2], -0.9312169312169312, Ops::fmac(Lam[1], -0.5925925925925926, Ops::mulc(Lam[0], -0.728042328042328)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.016931216931216932, k); } y[3] = Ops::fma3(k, x[7], y[3]); y[7] = Ops::fma3(k, x[3], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.6772486772486772, Ops::fmac(Lam[2], 0.4740740740740741, Ops::fmac(Lam[1], 0.20317460317460317, Ops::mulc(Lam[0], 0.20317460317460317)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.009029982363315696, k); } y[3] = Ops::fma3(k, x[8], y[3]); y[8] = Ops::fma3(k, x[3], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.20317460317460317, Ops::fmac(Lam[3], 0.20317460317460317, Ops::fmac(Lam[2], 0.6772486772486772, Ops::mulc(Lam[1], 0.4740740740740741)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.009029982363315696, k); } y[3] = Ops::fma3(k, x[9], y[3]); y[9] = Ops::fma3(k, x[3], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.08465608465608465, Ops::fmac(Lam[3], 0.08465608465608465, Ops::fmac(Lam[2], 0.3047619047619048, Ops::mulc(Lam[1], 0.2201058201058201)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001128747795414462, k); } y[3] = Ops::fma3(k, x[10], y[3]); y[10] = Ops::fma3(k, x[3], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.20317460317460317, Ops::fmac(Lam[3], 0.20317460317460317, Ops::fmac(Lam[2], 0.40634920634920635, Ops::mulc(Lam[1], 0.20317460317460317)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[3] = Ops::fma3(k, x[11], y[3]); y[11] = Ops::fma3(k, x[3], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 3.250793650793651, Ops::fmac(Lam[3], 3.250793650793651, Ops::fmac(Lam[2], 5.147089947089947, Ops::fmac(Lam[1], 3.250793650793651, Ops::mulc(Lam[0], 0.2708994708994709))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[3] = Ops::fma3(k, x[12], y[3]); y[12] = Ops::fma3(k, x[3], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.5417989417989418, Ops::fmac(Lam[3], -0.5417989417989418, Ops::fmac(Lam[2], -0.8126984126984127, Ops::mulc(Lam[0], 0.8126984126984127)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[3] = Ops::fma3(k, x[13], y[3]); y[13] = Ops::fma3(k, x[3], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.5417989417989418, Ops::fmac(Lam[3], -0.5417989417989418, Ops::fmac(Lam[2], -1.3544973544973544, Ops::fmac(Lam[1], -0.5417989417989418, Ops::mulc(Lam[0], 0.2708994708994709))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.004514991181657848, k); } y[3] = Ops::fma3(k, x[14], y[3]); y[14] = Ops::fma3(k, x[3], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 4.901587301587302, Ops::fmac(Lam[1], 3.8857142857142857, Ops::mulc(Lam[0], 4.901587301587302))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05587301587301587, k); } y[4] = Ops::fma3(k, x[4], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -1.3206349206349206, Ops::fmac(Lam[1], 1.0497354497354496, Ops::mulc(Lam[0], -1.5238095238095237))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.022574955908289243, k); } y[4] = Ops::fma3(k, x[5], y[4]); y[5] = Ops::fma3(k, x[4], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -1.5238095238095237, Ops::fmac(Lam[2], -0.5925925925925926, Ops::fmac(Lam[1], -0.9312169312169312, Ops::mulc(Lam[0], -0.728042328042328)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.016931216931216932, k); } y[4] = Ops::fma3(k, x[6], y[4]); y[6] = Ops::fma3(k, x[4], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.7873015873015873, Ops::fmac(Lam[2], -0.39365079365079364, Ops::fmac(Lam[1], -0.39365079365079364, Ops::mulc(Lam[0], -0.2920634920634921)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0008465608465608466, k); } y[4] = Ops::fma3(k, x[7], y[4]); y[7] = Ops::fma3(k, x[4], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.3047619047619048, Ops::fmac(Lam[2], 0.2201058201058201, Ops::fmac(Lam[1], 0.08465608465608465, Ops::mulc(Lam[0], 0.08465608465608465)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001128747795414462, k); } y[4] = Ops::fma3(k, x[8], y[4]); y[8] = Ops::fma3(k, x[4], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.5925925925925926, Ops::fmac(Lam[3], -0.728042328042328, Ops::fmac(Lam[2], -1.5238095238095237, Ops::mulc(Lam[1], -0.9312169312169312)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.016931216931216932, k); } y[4] = Ops::fma3(k, x[9], y[4]); y[9] = Ops::fma3(k, x[4], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.39365079365079364, Ops::fmac(Lam[3], -0.2920634920634921, Ops::fmac(Lam[2], -0.7873015873015873, Ops::mulc(Lam[1], -0.39365079365079364)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0008465608465608466, k); } y[4] = Ops::fma3(k, x[10], y[4]); y[10] = Ops::fma3(k, x[4], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.2201058201058201, Ops::fmac(Lam[3], 0.08465608465608465, Ops::fmac(Lam[2], 0.3047619047619048, Ops::mulc(Lam[1], 0.08465608465608465)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001128747795414462, k); } y[4] = Ops::fma3(k, x[11], y[4]); y[11] = Ops::fma3(k, x[4], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 4.673015873015873, Ops::fmac(Lam[3], -1.0158730158730158, Ops::fmac(Lam[2], 1.8285714285714285, Ops::fmac(Lam[1], 1.8285714285714285, Ops::mulc(Lam[0], 2.641269841269841))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.006772486772486773, k); } y[4] = Ops::fma3(k, x[12], y[4]); y[12] = Ops::fma3(k, x[4], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.8285714285714285, Ops::fmac(Lam[3], 2.641269841269841, Ops::fmac(Lam[2], 4.673015873015873, Ops::fmac(Lam[1], 1.8285714285714285, Ops::mulc(Lam[0], -1.0158730158730158))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.006772486772486773, k); } y[4] = Ops::fma3(k, x[13], y[4]); y[13] = Ops::fma3(k, x[4], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -1.4222222222222223, Ops::fmac(Lam[3], -0.6095238095238096, Ops::fmac(Lam[2], -1.4222222222222223, Ops::fmac(Lam[1], -1.0158730158730158, Ops::mulc(Lam[0], -0.6095238095238096))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.013544973544973546, k); } y[4] = Ops::fma3(k, x[14], y[4]); y[14] = Ops::fma3(k, x[4], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 3.657142857142857, Ops::fmac(Lam[1], 4.1989417989417985, Ops::mulc(Lam[0], 4.1989417989417985))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.045149911816578486, k); } y[5] = Ops::fma3(k, x[5], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.6772486772486772, Ops::fmac(Lam[2], 0.20317460317460317, Ops::fmac(Lam[1], 0.4740740740740741, Ops::mulc(Lam[0], 0.20317460317460317)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.009029982363315696, k); } y[5] = Ops::fma3(k, x[6], y[5]); y[6] = Ops::fma3(k, x[5], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.3047619047619048, Ops::fmac(Lam[2], 0.08465608465608465, Ops::fmac(Lam[1], 0.2201058201058201, Ops::mulc(Lam[0], 0.08465608465608465)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001128747795414462, k); } y[5] = Ops::fma3(k, x[7], y[5]); y[7] = Ops::fma3(k, x[5], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.40634920634920635, Ops::fmac(Lam[2], 0.20317460317460317, Ops::fmac(Lam[1], 0.20317460317460317, Ops::mulc(Lam[0], 0.20317460317460317)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[5] = Ops::fma3(k, x[8], y[5]); y[8] = Ops::fma3(k, x[5], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 2.0994708994708993, Ops::fmac(Lam[3], 1.8285714285714285, Ops::fmac(Lam[2], 4.1989417989417985, Ops::mulc(Lam[1], 2.0994708994708993)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[5] = Ops::fma3(k, x[9], y[5]); y[9] = Ops::fma3(k, x[5], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.9312169312169312, Ops::fmac(Lam[3], -0.728042328042328, Ops::fmac(Lam[2], -1.5238095238095237, Ops::mulc(Lam[1], -0.5925925925925926)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.016931216931216932, k); } y[5] = Ops::fma3(k, x[10], y[5]); y[10] = Ops::fma3(k, x[5], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.4740740740740741, Ops::fmac(Lam[3], 0.20317460317460317, Ops::fmac(Lam[2], 0.6772486772486772, Ops::mulc(Lam[1], 0.20317460317460317)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.009029982363315696, k); } y[5] = Ops::fma3(k, x[11], y[5]); y[11] = Ops::fma3(k, x[5], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.8126984126984127, Ops::fmac(Lam[3], 0.8126984126984127, Ops::fmac(Lam[2], -0.5417989417989418, Ops::mulc(Lam[0], -0.5417989417989418)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[5] = Ops::fma3(k, x[12], y[5]); y[12] = Ops::fma3(k, x[5], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 5.147089947089947, Ops::fmac(Lam[3], 0.2708994708994709, Ops::fmac(Lam[2], 3.250793650793651, Ops::fmac(Lam[1], 3.250793650793651, Ops::mulc(Lam[0], 3.250793650793651))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[5] = Ops::fma3(k, x[13], y[5]); y[13] = Ops::fma3(k, x[5], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -1.3544973544973544, Ops::fmac(Lam[3], 0.2708994708994709, Ops::fmac(Lam[2], -0.5417989417989418, Ops::fmac(Lam[1], -0.5417989417989418, Ops::mulc(Lam[0], -0.5417989417989418))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.004514991181657848, k); } y[5] = Ops::fma3(k, x[14], y[5]); y[14] = Ops::fma3(k, x[5], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 4.1989417989417985, Ops::fmac(Lam[2], 4.1989417989417985, Ops::mulc(Lam[0], 3.657142857142857))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.045149911816578486, k); } y[6] = Ops::fma3(k, x[6], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.5238095238095237, Ops::fmac(Lam[2], 1.0497354497354496, Ops::mulc(Lam[0], -1.3206349206349206))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.022574955908289243, k); } y[6] = Ops::fma3(k, x[7], y[6]); y[7] = Ops::fma3(k, x[6], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.6772486772486772, Ops::fmac(Lam[2], -0.6772486772486772, Ops::mulc(Lam[0], 0.6772486772486772))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.013544973544973546, k); } y[6] = Ops::fma3(k, x[8], y[6]); y[8] = Ops::fma3(k, x[6], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.20317460317460317, Ops::fmac(Lam[4], 0.20317460317460317, Ops::fmac(Lam[2], 0.20317460317460317, Ops::mulc(Lam[1], 0.40634920634920635)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[6] = Ops::fma3(k, x[9], y[6]); y[9] = Ops::fma3(k, x[6], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08465608465608465, Ops::fmac(Lam[4], 0.08465608465608465, Ops::fmac(Lam[2], 0.2201058201058201, Ops::mulc(Lam[1], 0.3047619047619048)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001128747795414462, k); } y[6] = Ops::fma3(k, x[10], y[6]); y[10] = Ops::fma3(k, x[6], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.20317460317460317, Ops::fmac(Lam[4], 0.20317460317460317, Ops::fmac(Lam[2], 0.4740740740740741, Ops::mulc(Lam[1], 0.6772486772486772)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.009029982363315696, k); } y[6] = Ops::fma3(k, x[11], y[6]); y[11] = Ops::fma3(k, x[6], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.250793650793651, Ops::fmac(Lam[4], 3.250793650793651, Ops::fmac(Lam[2], 3.250793650793651, Ops::fmac(Lam[1], 5.147089947089947, Ops::mulc(Lam[0], 0.2708994708994709))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[6] = Ops::fma3(k, x[12], y[6]); y[12] = Ops::fma3(k, x[6], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.5417989417989418, Ops::fmac(Lam[4], -0.5417989417989418, Ops::fmac(Lam[2], -0.5417989417989418, Ops::fmac(Lam[1], -1.3544973544973544, Ops::mulc(Lam[0], 0.2708994708994709))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.004514991181657848, k); } y[6] = Ops::fma3(k, x[13], y[6]); y[13] = Ops::fma3(k, x[6], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.5417989417989418, Ops::fmac(Lam[4], -0.5417989417989418, Ops::fmac(Lam[1], -0.8126984126984127, Ops::mulc(Lam[0], 0.8126984126984127)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[6] = Ops::fma3(k, x[14], y[6]); y[14] = Ops::fma3(k, x[6], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 4.901587301587302, Ops::fmac(Lam[2], 3.8857142857142857, Ops::mulc(Lam[0], 4.901587301587302))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05587301587301587, k); } y[7] = Ops::fma3(k, x[7], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.3206349206349206, Ops::fmac(Lam[2], 1.0497354497354496, Ops::mulc(Lam[0], -1.5238095238095237))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.022574955908289243, k); } y[7] = Ops::fma3(k, x[8], y[7]); y[8] = Ops::fma3(k, x[7], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08465608465608465, Ops::fmac(Lam[4], 0.2201058201058201, Ops::fmac(Lam[2], 0.08465608465608465, Ops::mulc(Lam[1], 0.3047619047619048)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.001128747795414462, k); } y[7] = Ops::fma3(k, x[9], y[7]); y[9] = Ops::fma3(k, x[7], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.2920634920634921, Ops::fmac(Lam[4], -0.39365079365079364, Ops::fmac(Lam[2], -0.39365079365079364, Ops::mulc(Lam[1], -0.7873015873015873)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0008465608465608466, k); } y[7] = Ops::fma3(k, x[10], y[7]); y[10] = Ops::fma3(k, x[7], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.728042328042328, Ops::fmac(Lam[4], -0.5925925925925926, Ops::fmac(Lam[2], -0.9312169312169312, Ops::mulc(Lam[1], -1.5238095238095237)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.016931216931216932, k); } y[7] = Ops::fma3(k, x[11], y[7]); y[11] = Ops::fma3(k, x[7], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.0158730158730158, Ops::fmac(Lam[4], 4.673015873015873, Ops::fmac(Lam[2], 1.8285714285714285, Ops::fmac(Lam[1], 1.8285714285714285, Ops::mulc(Lam[0], 2.641269841269841))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.006772486772486773, k); } y[7] = Ops::fma3(k, x[12], y[7]); y[12] = Ops::fma3(k, x[7], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.6095238095238096, Ops::fmac(Lam[4], -1.4222222222222223, Ops::fmac(Lam[2], -1.0158730158730158, Ops::fmac(Lam[1], -1.4222222222222223, Ops::mulc(Lam[0], -0.6095238095238096))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.013544973544973546, k); } y[7] = Ops::fma3(k, x[13], y[7]); y[13] = Ops::fma3(k, x[7], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 2.641269841269841, Ops::fmac(Lam[4], 1.8285714285714285, Ops::fmac(Lam[2], 1.8285714285714285, Ops::fmac(Lam[1], 4.673015873015873, Ops::mulc(Lam[0], -1.0158730158730158))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.006772486772486773, k); } y[7] = Ops::fma3(k, x[14], y[7]); y[14] = Ops::fma3(k, x[7], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.657142857142857, Ops::fmac(Lam[2], 4.1989417989417985, Ops::mulc(Lam[0], 4.1989417989417985))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.045149911816578486, k); } y[8] = Ops::fma3(k, x[8], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.20317460317460317, Ops::fmac(Lam[4], 0.4740740740740741, Ops::fmac(Lam[2], 0.20317460317460317, Ops::mulc(Lam[1], 0.6772486772486772)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.009029982363315696, k); } y[8] = Ops::fma3(k, x[9], y[8]); y[9] = Ops::fma3(k, x[8], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.728042328042328, Ops::fmac(Lam[4], -0.9312169312169312, Ops::fmac(Lam[2], -0.5925925925925926, Ops::mulc(Lam[1], -1.5238095238095237)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.016931216931216932, k); } y[8] = Ops::fma3(k, x[10], y[8]); y[10] = Ops::fma3(k, x[8], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.8285714285714285, Ops::fmac(Lam[4], 2.0994708994708993, Ops::fmac(Lam[2], 2.0994708994708993, Ops::mulc(Lam[1], 4.1989417989417985)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[8] = Ops::fma3(k, x[11], y[8]); y[11] = Ops::fma3(k, x[8], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.8126984126984127, Ops::fmac(Lam[4], -0.8126984126984127, Ops::fmac(Lam[1], -0.5417989417989418, Ops::mulc(Lam[0], -0.5417989417989418)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[8] = Ops::fma3(k, x[12], y[8]); y[12] = Ops::fma3(k, x[8], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.2708994708994709, Ops::fmac(Lam[4], -1.3544973544973544, Ops::fmac(Lam[2], -0.5417989417989418, Ops::fmac(Lam[1], -0.5417989417989418, Ops::mulc(Lam[0], -0.5417989417989418))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.004514991181657848, k); } y[8] = Ops::fma3(k, x[13], y[8]); y[13] = Ops::fma3(k, x[8], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.2708994708994709, Ops::fmac(Lam[4], 5.147089947089947, Ops::fmac(Lam[2], 3.250793650793651, Ops::fmac(Lam[1], 3.250793650793651, Ops::mulc(Lam[0], 3.250793650793651))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[8] = Ops::fma3(k, x[14], y[8]); y[14] = Ops::fma3(k, x[8], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 4.1989417989417985, Ops::fmac(Lam[4], 4.1989417989417985, Ops::mulc(Lam[3], 3.657142857142857))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.045149911816578486, k); } y[9] = Ops::fma3(k, x[9], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.5238095238095237, Ops::fmac(Lam[4], 1.0497354497354496, Ops::mulc(Lam[3], -1.3206349206349206))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.022574955908289243, k); } y[9] = Ops::fma3(k, x[10], y[9]); y[10] = Ops::fma3(k, x[9], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.6772486772486772, Ops::fmac(Lam[4], -0.6772486772486772, Ops::mulc(Lam[3], 0.6772486772486772))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.013544973544973546, k); } y[9] = Ops::fma3(k, x[11], y[9]); y[11] = Ops::fma3(k, x[9], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.5417989417989418, Ops::fmac(Lam[4], -0.5417989417989418, Ops::fmac(Lam[3], 0.2708994708994709, Ops::fmac(Lam[2], -0.5417989417989418, Ops::mulc(Lam[1], -1.3544973544973544))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.004514991181657848, k); } y[9] = Ops::fma3(k, x[12], y[9]); y[12] = Ops::fma3(k, x[9], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.250793650793651, Ops::fmac(Lam[4], 3.250793650793651, Ops::fmac(Lam[3], 0.2708994708994709, Ops::fmac(Lam[2], 3.250793650793651, Ops::mulc(Lam[1], 5.147089947089947))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[9] = Ops::fma3(k, x[13], y[9]); y[13] = Ops::fma3(k, x[9], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.5417989417989418, Ops::fmac(Lam[3], 0.8126984126984127, Ops::fmac(Lam[2], -0.5417989417989418, Ops::mulc(Lam[1], -0.8126984126984127)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[9] = Ops::fma3(k, x[14], y[9]); y[14] = Ops::fma3(k, x[9], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 4.901587301587302, Ops::fmac(Lam[4], 3.8857142857142857, Ops::mulc(Lam[3], 4.901587301587302))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05587301587301587, k); } y[10] = Ops::fma3(k, x[10], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.3206349206349206, Ops::fmac(Lam[4], 1.0497354497354496, Ops::mulc(Lam[3], -1.5238095238095237))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.022574955908289243, k); } y[10] = Ops::fma3(k, x[11], y[10]); y[11] = Ops::fma3(k, x[10], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.6095238095238096, Ops::fmac(Lam[4], -1.0158730158730158, Ops::fmac(Lam[3], -0.6095238095238096, Ops::fmac(Lam[2], -1.4222222222222223, Ops::mulc(Lam[1], -1.4222222222222223))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.013544973544973546, k); } y[10] = Ops::fma3(k, x[12], y[10]); y[12] = Ops::fma3(k, x[10], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.0158730158730158, Ops::fmac(Lam[4], 1.8285714285714285, Ops::fmac(Lam[3], 2.641269841269841, Ops::fmac(Lam[2], 4.673015873015873, Ops::mulc(Lam[1], 1.8285714285714285))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.006772486772486773, k); } y[10] = Ops::fma3(k, x[13], y[10]); y[13] = Ops::fma3(k, x[10], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 2.641269841269841, Ops::fmac(Lam[4], 1.8285714285714285, Ops::fmac(Lam[3], -1.0158730158730158, Ops::fmac(Lam[2], 1.8285714285714285, Ops::mulc(Lam[1], 4.673015873015873))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.006772486772486773, k); } y[10] = Ops::fma3(k, x[14], y[10]); y[14] = Ops::fma3(k, x[10], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 3.657142857142857, Ops::fmac(Lam[4], 4.1989417989417985, Ops::mulc(Lam[3], 4.1989417989417985))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.045149911816578486, k); } y[11] = Ops::fma3(k, x[11], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.2708994708994709, Ops::fmac(Lam[4], -0.5417989417989418, Ops::fmac(Lam[3], -0.5417989417989418, Ops::fmac(Lam[2], -1.3544973544973544, Ops::mulc(Lam[1], -0.5417989417989418))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.004514991181657848, k); } y[11] = Ops::fma3(k, x[12], y[11]); y[12] = Ops::fma3(k, x[11], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.8126984126984127, Ops::fmac(Lam[3], -0.5417989417989418, Ops::fmac(Lam[2], -0.8126984126984127, Ops::mulc(Lam[1], -0.5417989417989418)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.004514991181657848, k); } y[11] = Ops::fma3(k, x[13], y[11]); y[13] = Ops::fma3(k, x[11], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.2708994708994709, Ops::fmac(Lam[4], 3.250793650793651, Ops::fmac(Lam[3], 3.250793650793651, Ops::fmac(Lam[2], 5.147089947089947, Ops::mulc(Lam[1], 3.250793650793651))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.022574955908289243, k); } y[11] = Ops::fma3(k, x[14], y[11]); y[14] = Ops::fma3(k, x[11], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 11.377777777777778, Ops::fmac(Lam[4], 11.377777777777778, Ops::fmac(Lam[3], 11.377777777777778, Ops::fmac(Lam[2], 11.377777777777778, Ops::fmac(Lam[1], 11.377777777777778, Ops::mulc(Lam[0], 11.377777777777778)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.18962962962962962, k); } y[12] = Ops::fma3(k, x[12], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.6253968253968254, Ops::fmac(Lam[4], 1.6253968253968254, Ops::fmac(Lam[3], -1.6253968253968254, Ops::fmac(Lam[2], 1.6253968253968254, Ops::fmac(Lam[1], 4.876190476190477, Ops::mulc(Lam[0], -1.6253968253968254)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.02708994708994709, k); } y[12] = Ops::fma3(k, x[13], y[12]); y[13] = Ops::fma3(k, x[12], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.6253968253968254, Ops::fmac(Lam[4], 1.6253968253968254, Ops::fmac(Lam[3], 1.6253968253968254, Ops::fmac(Lam[2], 4.876190476190477, Ops::fmac(Lam[1], 1.6253968253968254, Ops::mulc(Lam[0], -1.6253968253968254)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.02708994708994709, k); } y[12] = Ops::fma3(k, x[14], y[12]); y[14] = Ops::fma3(k, x[12], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 11.377777777777778, Ops::fmac(Lam[4], 11.377777777777778, Ops::fmac(Lam[3], 11.377777777777778, Ops::fmac(Lam[2], 11.377777777777778, Ops::fmac(Lam[1], 11.377777777777778, Ops::mulc(Lam[0], 11.377777777777778)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.18962962962962962, k); } y[13] = Ops::fma3(k, x[13], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -1.6253968253968254, Ops::fmac(Lam[4], 4.876190476190477, Ops::fmac(Lam[3], -1.6253968253968254, Ops::fmac(Lam[2], 1.6253968253968254, Ops::fmac(Lam[1], 1.6253968253968254, Ops::mulc(Lam[0], 1.6253968253968254)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.02708994708994709, k); } y[13] = Ops::fma3(k, x[14], y[13]); y[14] = Ops::fma3(k, x[13], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 11.377777777777778, Ops::fmac(Lam[4], 11.377777777777778, Ops::fmac(Lam[3], 11.377777777777778, Ops::fmac(Lam[2], 11.377777777777778, Ops::fmac(Lam[1], 11.377777777777778, Ops::mulc(Lam[0], 11.377777777777778)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.18962962962962962, k); } y[14] = Ops::fma3(k, x[14], y[14]); }
+  }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 15 - (i * (i - 1)) / 2 + (j - i) : j * 15 - (j * (j - 1)) / 2 + (i - j);
   }
@@ -709,6 +923,19 @@ template <> struct Elem<3, 1> {
     K[7] = Ops::mulc(vol, 0.1);
     K[8] = Ops::mulc(vol, 0.05);
     K[9] = Ops::mulc(vol, 0.1);
+  }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Lam[0]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.1, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Lam[1]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Lam[2]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    { if constexpr (STIFF) { k = Lam[3]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05, k); } y[0] = Ops::fma3(k, x[3], y[0]); y[3] = Ops::fma3(k, x[0], y[3]); }
+    { if constexpr (STIFF) { k = Lam[4]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.1, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Lam[5]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    { if constexpr (STIFF) { k = Lam[6]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05, k); } y[1] = Ops::fma3(k, x[3], y[1]); y[3] = Ops::fma3(k, x[1], y[3]); }
+    { if constexpr (STIFF) { k = Lam[7]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.1, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+    { if constexpr (STIFF) { k = Lam[8]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.05, k); } y[2] = Ops::fma3(k, x[3], y[2]); y[3] = Ops::fma3(k, x[2], y[3]); }
+    { if constexpr (STIFF) { k = Lam[9]; } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.1, k); } y[3] = Ops::fma3(k, x[3], y[3]); }
   }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 4 - (i * (i - 1)) / 2 + (j - i) : j * 4 - (j * (j - 1)) / 2 + (i - j);
@@ -892,6 +1119,64 @@ template <> struct Elem<3, 2> {
     K[52] = Ops::mulc(vol, 0.0761904761904762);
     K[53] = Ops::mulc(vol, 0.0380952380952381);
     K[54] = Ops::mulc(vol, 0.0761904761904762);
+  }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[0], 0.6); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.014285714285714285, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[1], -0.2); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.002380952380952381, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[2], -0.2); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.002380952380952381, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[3], -0.2); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.002380952380952381, k); } y[0] = Ops::fma3(k, x[3], y[0]); y[3] = Ops::fma3(k, x[0], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[1], 0.6, Ops::mulc(Lam[0], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[0] = Ops::fma3(k, x[4], y[0]); y[4] = Ops::fma3(k, x[0], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.6, Ops::mulc(Lam[0], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[0] = Ops::fma3(k, x[5], y[0]); y[5] = Ops::fma3(k, x[0], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.6, Ops::mulc(Lam[0], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[0] = Ops::fma3(k, x[6], y[0]); y[6] = Ops::fma3(k, x[0], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.2, Ops::mulc(Lam[1], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[0] = Ops::fma3(k, x[7], y[0]); y[7] = Ops::fma3(k, x[0], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.2, Ops::mulc(Lam[1], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[0] = Ops::fma3(k, x[8], y[0]); y[8] = Ops::fma3(k, x[0], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.2, Ops::mulc(Lam[2], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[0] = Ops::fma3(k, x[9], y[0]); y[9] = Ops::fma3(k, x[0], y[9]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[4], 0.6); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.014285714285714285, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[5], -0.2); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.002380952380952381, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[6], -0.2); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.002380952380952381, k); } y[1] = Ops::fma3(k, x[3], y[1]); y[3] = Ops::fma3(k, x[1], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.2, Ops::mulc(Lam[1], 0.6)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[1] = Ops::fma3(k, x[4], y[1]); y[4] = Ops::fma3(k, x[1], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.2, Ops::mulc(Lam[1], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[1] = Ops::fma3(k, x[5], y[1]); y[5] = Ops::fma3(k, x[1], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.2, Ops::mulc(Lam[1], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[1] = Ops::fma3(k, x[6], y[1]); y[6] = Ops::fma3(k, x[1], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.6, Ops::mulc(Lam[4], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[1] = Ops::fma3(k, x[7], y[1]); y[7] = Ops::fma3(k, x[1], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.6, Ops::mulc(Lam[4], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[1] = Ops::fma3(k, x[8], y[1]); y[8] = Ops::fma3(k, x[1], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.2, Ops::mulc(Lam[5], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[1] = Ops::fma3(k, x[9], y[1]); y[9] = Ops::fma3(k, x[1], y[9]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[7], 0.6); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.014285714285714285, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[8], -0.2); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.002380952380952381, k); } y[2] = Ops::fma3(k, x[3], y[2]); y[3] = Ops::fma3(k, x[2], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.2, Ops::mulc(Lam[2], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[2] = Ops::fma3(k, x[4], y[2]); y[4] = Ops::fma3(k, x[2], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.2, Ops::mulc(Lam[2], 0.6)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[2] = Ops::fma3(k, x[5], y[2]); y[5] = Ops::fma3(k, x[2], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2, Ops::mulc(Lam[2], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[2] = Ops::fma3(k, x[6], y[2]); y[6] = Ops::fma3(k, x[2], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.2, Ops::mulc(Lam[5], 0.6)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[2] = Ops::fma3(k, x[7], y[2]); y[7] = Ops::fma3(k, x[2], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2, Ops::mulc(Lam[5], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[2] = Ops::fma3(k, x[8], y[2]); y[8] = Ops::fma3(k, x[2], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.6, Ops::mulc(Lam[7], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[2] = Ops::fma3(k, x[9], y[2]); y[9] = Ops::fma3(k, x[2], y[9]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[9], 0.6); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.014285714285714285, k); } y[3] = Ops::fma3(k, x[3], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.2, Ops::mulc(Lam[3], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[3] = Ops::fma3(k, x[4], y[3]); y[4] = Ops::fma3(k, x[3], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2, Ops::mulc(Lam[3], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[3] = Ops::fma3(k, x[5], y[3]); y[5] = Ops::fma3(k, x[3], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2, Ops::mulc(Lam[3], 0.6)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[3] = Ops::fma3(k, x[6], y[3]); y[6] = Ops::fma3(k, x[3], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2, Ops::mulc(Lam[6], -0.2)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.014285714285714285, k); } y[3] = Ops::fma3(k, x[7], y[3]); y[7] = Ops::fma3(k, x[3], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2, Ops::mulc(Lam[6], 0.6)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[3] = Ops::fma3(k, x[8], y[3]); y[8] = Ops::fma3(k, x[3], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2, Ops::mulc(Lam[8], 0.6)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.009523809523809525, k); } y[3] = Ops::fma3(k, x[9], y[3]); y[9] = Ops::fma3(k, x[3], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.6, Ops::fmac(Lam[1], 1.6, Ops::mulc(Lam[0], 1.6))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0761904761904762, k); } y[4] = Ops::fma3(k, x[4], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.6, Ops::fmac(Lam[2], 0.8, Ops::fmac(Lam[1], 0.8, Ops::mulc(Lam[0], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[4] = Ops::fma3(k, x[5], y[4]); y[5] = Ops::fma3(k, x[4], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 1.6, Ops::fmac(Lam[3], 0.8, Ops::fmac(Lam[1], 0.8, Ops::mulc(Lam[0], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[4] = Ops::fma3(k, x[6], y[4]); y[6] = Ops::fma3(k, x[4], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.8, Ops::fmac(Lam[4], 0.8, Ops::fmac(Lam[2], 1.6, Ops::mulc(Lam[1], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[4] = Ops::fma3(k, x[7], y[4]); y[7] = Ops::fma3(k, x[4], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.8, Ops::fmac(Lam[4], 0.8, Ops::fmac(Lam[3], 1.6, Ops::mulc(Lam[1], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[4] = Ops::fma3(k, x[8], y[4]); y[8] = Ops::fma3(k, x[4], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.8, Ops::fmac(Lam[5], 0.8, Ops::fmac(Lam[3], 0.8, Ops::mulc(Lam[2], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.01904761904761905, k); } y[4] = Ops::fma3(k, x[9], y[4]); y[9] = Ops::fma3(k, x[4], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 1.6, Ops::fmac(Lam[2], 1.6, Ops::mulc(Lam[0], 1.6))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0761904761904762, k); } y[5] = Ops::fma3(k, x[5], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.6, Ops::fmac(Lam[3], 0.8, Ops::fmac(Lam[2], 0.8, Ops::mulc(Lam[0], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[5] = Ops::fma3(k, x[6], y[5]); y[6] = Ops::fma3(k, x[5], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.8, Ops::fmac(Lam[5], 0.8, Ops::fmac(Lam[2], 0.8, Ops::mulc(Lam[1], 1.6)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[5] = Ops::fma3(k, x[7], y[5]); y[7] = Ops::fma3(k, x[5], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.8, Ops::fmac(Lam[5], 0.8, Ops::fmac(Lam[3], 0.8, Ops::mulc(Lam[1], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.01904761904761905, k); } y[5] = Ops::fma3(k, x[8], y[5]); y[8] = Ops::fma3(k, x[5], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.8, Ops::fmac(Lam[7], 0.8, Ops::fmac(Lam[3], 1.6, Ops::mulc(Lam[2], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[5] = Ops::fma3(k, x[9], y[5]); y[9] = Ops::fma3(k, x[5], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.6, Ops::fmac(Lam[3], 1.6, Ops::mulc(Lam[0], 1.6))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0761904761904762, k); } y[6] = Ops::fma3(k, x[6], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.8, Ops::fmac(Lam[6], 0.8, Ops::fmac(Lam[2], 0.8, Ops::mulc(Lam[1], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.01904761904761905, k); } y[6] = Ops::fma3(k, x[7], y[6]); y[7] = Ops::fma3(k, x[6], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.8, Ops::fmac(Lam[6], 0.8, Ops::fmac(Lam[3], 0.8, Ops::mulc(Lam[1], 1.6)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[6] = Ops::fma3(k, x[8], y[6]); y[8] = Ops::fma3(k, x[6], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.8, Ops::fmac(Lam[8], 0.8, Ops::fmac(Lam[3], 0.8, Ops::mulc(Lam[2], 1.6)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[6] = Ops::fma3(k, x[9], y[6]); y[9] = Ops::fma3(k, x[6], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 1.6, Ops::fmac(Lam[5], 1.6, Ops::mulc(Lam[4], 1.6))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0761904761904762, k); } y[7] = Ops::fma3(k, x[7], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.6, Ops::fmac(Lam[6], 0.8, Ops::fmac(Lam[5], 0.8, Ops::mulc(Lam[4], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[7] = Ops::fma3(k, x[8], y[7]); y[8] = Ops::fma3(k, x[7], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.8, Ops::fmac(Lam[7], 0.8, Ops::fmac(Lam[6], 1.6, Ops::mulc(Lam[5], 0.8)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[7] = Ops::fma3(k, x[9], y[7]); y[9] = Ops::fma3(k, x[7], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.6, Ops::fmac(Lam[6], 1.6, Ops::mulc(Lam[4], 1.6))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0761904761904762, k); } y[8] = Ops::fma3(k, x[8], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.8, Ops::fmac(Lam[8], 0.8, Ops::fmac(Lam[6], 0.8, Ops::mulc(Lam[5], 1.6)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0380952380952381, k); } y[8] = Ops::fma3(k, x[9], y[8]); y[9] = Ops::fma3(k, x[8], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.6, Ops::fmac(Lam[8], 1.6, Ops::mulc(Lam[7], 1.6))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0761904761904762, k); } y[9] = Ops::fma3(k, x[9], y[9]); }
   }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 10 - (i * (i - 1)) / 2 + (j - i) : j * 10 - (j * (j - 1)) / 2 + (i - j);
@@ -1480,6 +1765,219 @@ template <> struct Elem<3, 3> {
     K[207] = Ops::mulc(vol, 0.09642857142857143);
     K[208] = Ops::mulc(vol, 0.048214285714285716);
     K[209] = Ops::mulc(vol, 0.09642857142857143);
+  }
+  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper(const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {
+    typename Ops::T k;
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[0], 0.35714285714285715); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0035714285714285713, k); } y[0] = Ops::fma3(k, x[0], y[0]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[1], 0.06785714285714285); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0004464285714285714, k); } y[0] = Ops::fma3(k, x[1], y[0]); y[1] = Ops::fma3(k, x[0], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[2], 0.06785714285714285); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0004464285714285714, k); } y[0] = Ops::fma3(k, x[2], y[0]); y[2] = Ops::fma3(k, x[0], y[2]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[3], 0.06785714285714285); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0004464285714285714, k); } y[0] = Ops::fma3(k, x[3], y[0]); y[3] = Ops::fma3(k, x[0], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[1], 0.36964285714285716, Ops::mulc(Lam[0], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[0] = Ops::fma3(k, x[4], y[0]); y[4] = Ops::fma3(k, x[0], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[1], -0.20892857142857144, Ops::mulc(Lam[0], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[0] = Ops::fma3(k, x[5], y[0]); y[5] = Ops::fma3(k, x[0], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.36964285714285716, Ops::mulc(Lam[0], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[0] = Ops::fma3(k, x[6], y[0]); y[6] = Ops::fma3(k, x[0], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.20892857142857144, Ops::mulc(Lam[0], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[0] = Ops::fma3(k, x[7], y[0]); y[7] = Ops::fma3(k, x[0], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.36964285714285716, Ops::mulc(Lam[0], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[0] = Ops::fma3(k, x[8], y[0]); y[8] = Ops::fma3(k, x[0], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.20892857142857144, Ops::mulc(Lam[0], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[0] = Ops::fma3(k, x[9], y[0]); y[9] = Ops::fma3(k, x[0], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[0] = Ops::fma3(k, x[10], y[0]); y[10] = Ops::fma3(k, x[0], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[0] = Ops::fma3(k, x[11], y[0]); y[11] = Ops::fma3(k, x[0], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[0] = Ops::fma3(k, x[12], y[0]); y[12] = Ops::fma3(k, x[0], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[0] = Ops::fma3(k, x[13], y[0]); y[13] = Ops::fma3(k, x[0], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.08035714285714286, Ops::mulc(Lam[2], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[0] = Ops::fma3(k, x[14], y[0]); y[14] = Ops::fma3(k, x[0], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.08035714285714286, Ops::mulc(Lam[2], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[0] = Ops::fma3(k, x[15], y[0]); y[15] = Ops::fma3(k, x[0], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[2], -0.09642857142857143, Ops::fmac(Lam[1], -0.09642857142857143, Ops::mulc(Lam[0], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[0] = Ops::fma3(k, x[16], y[0]); y[16] = Ops::fma3(k, x[0], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.09642857142857143, Ops::fmac(Lam[1], -0.09642857142857143, Ops::mulc(Lam[0], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[0] = Ops::fma3(k, x[17], y[0]); y[17] = Ops::fma3(k, x[0], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], -0.09642857142857143, Ops::fmac(Lam[2], -0.09642857142857143, Ops::mulc(Lam[0], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[0] = Ops::fma3(k, x[18], y[0]); y[18] = Ops::fma3(k, x[0], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[3], 0.19285714285714287, Ops::fmac(Lam[2], 0.19285714285714287, Ops::mulc(Lam[1], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.008035714285714285, k); } y[0] = Ops::fma3(k, x[19], y[0]); y[19] = Ops::fma3(k, x[0], y[19]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[4], 0.35714285714285715); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0035714285714285713, k); } y[1] = Ops::fma3(k, x[1], y[1]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[5], 0.06785714285714285); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0004464285714285714, k); } y[1] = Ops::fma3(k, x[2], y[1]); y[2] = Ops::fma3(k, x[1], y[2]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[6], 0.06785714285714285); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0004464285714285714, k); } y[1] = Ops::fma3(k, x[3], y[1]); y[3] = Ops::fma3(k, x[1], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 0.08035714285714286, Ops::mulc(Lam[1], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[1] = Ops::fma3(k, x[4], y[1]); y[4] = Ops::fma3(k, x[1], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.20892857142857144, Ops::mulc(Lam[1], 0.36964285714285716)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[1] = Ops::fma3(k, x[5], y[1]); y[5] = Ops::fma3(k, x[1], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[1] = Ops::fma3(k, x[6], y[1]); y[6] = Ops::fma3(k, x[1], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[1] = Ops::fma3(k, x[7], y[1]); y[7] = Ops::fma3(k, x[1], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[1] = Ops::fma3(k, x[8], y[1]); y[8] = Ops::fma3(k, x[1], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.08035714285714286, Ops::mulc(Lam[1], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[1] = Ops::fma3(k, x[9], y[1]); y[9] = Ops::fma3(k, x[1], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.36964285714285716, Ops::mulc(Lam[4], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[1] = Ops::fma3(k, x[10], y[1]); y[10] = Ops::fma3(k, x[1], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.20892857142857144, Ops::mulc(Lam[4], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[1] = Ops::fma3(k, x[11], y[1]); y[11] = Ops::fma3(k, x[1], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.36964285714285716, Ops::mulc(Lam[4], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[1] = Ops::fma3(k, x[12], y[1]); y[12] = Ops::fma3(k, x[1], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.20892857142857144, Ops::mulc(Lam[4], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[1] = Ops::fma3(k, x[13], y[1]); y[13] = Ops::fma3(k, x[1], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.08035714285714286, Ops::mulc(Lam[5], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[1] = Ops::fma3(k, x[14], y[1]); y[14] = Ops::fma3(k, x[1], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.08035714285714286, Ops::mulc(Lam[5], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[1] = Ops::fma3(k, x[15], y[1]); y[15] = Ops::fma3(k, x[1], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.09642857142857143, Ops::fmac(Lam[4], 0.19285714285714287, Ops::mulc(Lam[1], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[1] = Ops::fma3(k, x[16], y[1]); y[16] = Ops::fma3(k, x[1], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.09642857142857143, Ops::fmac(Lam[4], 0.19285714285714287, Ops::mulc(Lam[1], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[1] = Ops::fma3(k, x[17], y[1]); y[17] = Ops::fma3(k, x[1], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.19285714285714287, Ops::fmac(Lam[5], 0.19285714285714287, Ops::mulc(Lam[1], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.008035714285714285, k); } y[1] = Ops::fma3(k, x[18], y[1]); y[18] = Ops::fma3(k, x[1], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.09642857142857143, Ops::fmac(Lam[5], -0.09642857142857143, Ops::mulc(Lam[4], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[1] = Ops::fma3(k, x[19], y[1]); y[19] = Ops::fma3(k, x[1], y[19]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[7], 0.35714285714285715); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0035714285714285713, k); } y[2] = Ops::fma3(k, x[2], y[2]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[8], 0.06785714285714285); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0004464285714285714, k); } y[2] = Ops::fma3(k, x[3], y[2]); y[3] = Ops::fma3(k, x[2], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08035714285714286, Ops::mulc(Lam[2], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[2] = Ops::fma3(k, x[4], y[2]); y[4] = Ops::fma3(k, x[2], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.08035714285714286, Ops::mulc(Lam[2], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[2] = Ops::fma3(k, x[5], y[2]); y[5] = Ops::fma3(k, x[2], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.08035714285714286, Ops::mulc(Lam[2], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[2] = Ops::fma3(k, x[6], y[2]); y[6] = Ops::fma3(k, x[2], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.20892857142857144, Ops::mulc(Lam[2], 0.36964285714285716)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[2] = Ops::fma3(k, x[7], y[2]); y[7] = Ops::fma3(k, x[2], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[2], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[2] = Ops::fma3(k, x[8], y[2]); y[8] = Ops::fma3(k, x[2], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[2], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[2] = Ops::fma3(k, x[9], y[2]); y[9] = Ops::fma3(k, x[2], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.08035714285714286, Ops::mulc(Lam[5], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[2] = Ops::fma3(k, x[10], y[2]); y[10] = Ops::fma3(k, x[2], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.20892857142857144, Ops::mulc(Lam[5], 0.36964285714285716)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[2] = Ops::fma3(k, x[11], y[2]); y[11] = Ops::fma3(k, x[2], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[5], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[2] = Ops::fma3(k, x[12], y[2]); y[12] = Ops::fma3(k, x[2], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[5], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[2] = Ops::fma3(k, x[13], y[2]); y[13] = Ops::fma3(k, x[2], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.36964285714285716, Ops::mulc(Lam[7], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[2] = Ops::fma3(k, x[14], y[2]); y[14] = Ops::fma3(k, x[2], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.20892857142857144, Ops::mulc(Lam[7], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[2] = Ops::fma3(k, x[15], y[2]); y[15] = Ops::fma3(k, x[2], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.19285714285714287, Ops::fmac(Lam[5], -0.09642857142857143, Ops::mulc(Lam[2], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[2] = Ops::fma3(k, x[16], y[2]); y[16] = Ops::fma3(k, x[2], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.19285714285714287, Ops::fmac(Lam[5], 0.19285714285714287, Ops::mulc(Lam[2], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.008035714285714285, k); } y[2] = Ops::fma3(k, x[17], y[2]); y[17] = Ops::fma3(k, x[2], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.09642857142857143, Ops::fmac(Lam[7], 0.19285714285714287, Ops::mulc(Lam[2], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[2] = Ops::fma3(k, x[18], y[2]); y[18] = Ops::fma3(k, x[2], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.09642857142857143, Ops::fmac(Lam[7], 0.19285714285714287, Ops::mulc(Lam[5], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[2] = Ops::fma3(k, x[19], y[2]); y[19] = Ops::fma3(k, x[2], y[19]); }
+    { if constexpr (STIFF) { k = Ops::mulc(Lam[9], 0.35714285714285715); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0035714285714285713, k); } y[3] = Ops::fma3(k, x[3], y[3]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.08035714285714286, Ops::mulc(Lam[3], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[3] = Ops::fma3(k, x[4], y[3]); y[4] = Ops::fma3(k, x[3], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.08035714285714286, Ops::mulc(Lam[3], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[3] = Ops::fma3(k, x[5], y[3]); y[5] = Ops::fma3(k, x[3], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[3], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[3] = Ops::fma3(k, x[6], y[3]); y[6] = Ops::fma3(k, x[3], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[3], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[3] = Ops::fma3(k, x[7], y[3]); y[7] = Ops::fma3(k, x[3], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.08035714285714286, Ops::mulc(Lam[3], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[3] = Ops::fma3(k, x[8], y[3]); y[8] = Ops::fma3(k, x[3], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.20892857142857144, Ops::mulc(Lam[3], 0.36964285714285716)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[3] = Ops::fma3(k, x[9], y[3]); y[9] = Ops::fma3(k, x[3], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[6], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[3] = Ops::fma3(k, x[10], y[3]); y[10] = Ops::fma3(k, x[3], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.08035714285714286, Ops::mulc(Lam[6], 0.08035714285714286)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0006696428571428571, k); } y[3] = Ops::fma3(k, x[11], y[3]); y[11] = Ops::fma3(k, x[3], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.08035714285714286, Ops::mulc(Lam[6], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[3] = Ops::fma3(k, x[12], y[3]); y[12] = Ops::fma3(k, x[3], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.20892857142857144, Ops::mulc(Lam[6], 0.36964285714285716)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[3] = Ops::fma3(k, x[13], y[3]); y[13] = Ops::fma3(k, x[3], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.08035714285714286, Ops::mulc(Lam[8], -0.20892857142857144)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0013392857142857143, k); } y[3] = Ops::fma3(k, x[14], y[3]); y[14] = Ops::fma3(k, x[3], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.20892857142857144, Ops::mulc(Lam[8], 0.36964285714285716)); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0026785714285714286, k); } y[3] = Ops::fma3(k, x[15], y[3]); y[15] = Ops::fma3(k, x[3], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.19285714285714287, Ops::fmac(Lam[6], 0.19285714285714287, Ops::mulc(Lam[3], 0.19285714285714287))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.008035714285714285, k); } y[3] = Ops::fma3(k, x[16], y[3]); y[16] = Ops::fma3(k, x[3], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.19285714285714287, Ops::fmac(Lam[6], -0.09642857142857143, Ops::mulc(Lam[3], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[3] = Ops::fma3(k, x[17], y[3]); y[17] = Ops::fma3(k, x[3], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.19285714285714287, Ops::fmac(Lam[8], -0.09642857142857143, Ops::mulc(Lam[3], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[3] = Ops::fma3(k, x[18], y[3]); y[18] = Ops::fma3(k, x[3], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.19285714285714287, Ops::fmac(Lam[8], -0.09642857142857143, Ops::mulc(Lam[6], -0.09642857142857143))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.0040178571428571425, k); } y[3] = Ops::fma3(k, x[19], y[3]); y[19] = Ops::fma3(k, x[3], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.1571428571428573, Ops::fmac(Lam[1], 1.1571428571428573, Ops::mulc(Lam[0], 1.4464285714285714))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[4] = Ops::fma3(k, x[4], y[4]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], -0.43392857142857144, Ops::fmac(Lam[1], 0.2892857142857143, Ops::mulc(Lam[0], -0.43392857142857144))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[4] = Ops::fma3(k, x[5], y[4]); y[5] = Ops::fma3(k, x[4], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.1571428571428573, Ops::fmac(Lam[2], 0.5785714285714286, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], 0.7232142857142857)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[4] = Ops::fma3(k, x[6], y[4]); y[6] = Ops::fma3(k, x[4], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.43392857142857144, Ops::fmac(Lam[2], -0.2892857142857143, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[4] = Ops::fma3(k, x[7], y[4]); y[7] = Ops::fma3(k, x[4], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 1.1571428571428573, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], 0.7232142857142857)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[4] = Ops::fma3(k, x[8], y[4]); y[8] = Ops::fma3(k, x[4], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.43392857142857144, Ops::fmac(Lam[3], -0.2892857142857143, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[4] = Ops::fma3(k, x[9], y[4]); y[9] = Ops::fma3(k, x[4], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[2], -0.43392857142857144, Ops::mulc(Lam[1], -0.2892857142857143)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[4] = Ops::fma3(k, x[10], y[4]); y[10] = Ops::fma3(k, x[4], y[10]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[2], -0.2892857142857143, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[11], y[4]); y[11] = Ops::fma3(k, x[4], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], -0.43392857142857144, Ops::mulc(Lam[1], -0.2892857142857143)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[4] = Ops::fma3(k, x[12], y[4]); y[12] = Ops::fma3(k, x[4], y[12]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[13], y[4]); y[13] = Ops::fma3(k, x[4], y[13]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.14464285714285716)))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[14], y[4]); y[14] = Ops::fma3(k, x[4], y[14]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.14464285714285716)))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[15], y[4]); y[15] = Ops::fma3(k, x[4], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[4], 0.5785714285714286, Ops::fmac(Lam[2], 1.4464285714285714, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], -0.2892857142857143))))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[16], y[4]); y[16] = Ops::fma3(k, x[4], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[4], 0.5785714285714286, Ops::fmac(Lam[3], 1.4464285714285714, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], -0.2892857142857143))))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[17], y[4]); y[17] = Ops::fma3(k, x[4], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[3], 0.7232142857142857, Ops::fmac(Lam[2], 0.7232142857142857, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))))); } else { k = Ops::zero(); } y[4] = Ops::fma3(k, x[18], y[4]); y[18] = Ops::fma3(k, x[4], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::fmac(Lam[2], -0.2892857142857143, Ops::mulc(Lam[1], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[4] = Ops::fma3(k, x[19], y[4]); y[19] = Ops::fma3(k, x[4], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[4], 1.4464285714285714, Ops::fmac(Lam[1], 1.1571428571428573, Ops::mulc(Lam[0], 1.1571428571428573))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[5] = Ops::fma3(k, x[5], y[5]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.43392857142857144, Ops::fmac(Lam[2], -0.14464285714285716, Ops::fmac(Lam[1], -0.2892857142857143, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[5] = Ops::fma3(k, x[6], y[5]); y[6] = Ops::fma3(k, x[5], y[6]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[2], -0.14464285714285716, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[7], y[5]); y[7] = Ops::fma3(k, x[5], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.43392857142857144, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[1], -0.2892857142857143, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[5] = Ops::fma3(k, x[8], y[5]); y[8] = Ops::fma3(k, x[5], y[8]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[9], y[5]); y[9] = Ops::fma3(k, x[5], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[4], 0.7232142857142857, Ops::fmac(Lam[2], 1.1571428571428573, Ops::mulc(Lam[1], 0.5785714285714286)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[5] = Ops::fma3(k, x[10], y[5]); y[10] = Ops::fma3(k, x[5], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[2], -0.43392857142857144, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[5] = Ops::fma3(k, x[11], y[5]); y[11] = Ops::fma3(k, x[5], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[4], 0.7232142857142857, Ops::fmac(Lam[3], 1.1571428571428573, Ops::mulc(Lam[1], 0.5785714285714286)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[5] = Ops::fma3(k, x[12], y[5]); y[12] = Ops::fma3(k, x[5], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], -0.43392857142857144, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[5] = Ops::fma3(k, x[13], y[5]); y[13] = Ops::fma3(k, x[5], y[13]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.14464285714285716)))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[14], y[5]); y[14] = Ops::fma3(k, x[5], y[14]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.14464285714285716)))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[15], y[5]); y[15] = Ops::fma3(k, x[5], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[5], 1.4464285714285714, Ops::fmac(Lam[4], -0.2892857142857143, Ops::fmac(Lam[2], 0.5785714285714286, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], 0.5785714285714286))))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[16], y[5]); y[16] = Ops::fma3(k, x[5], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 1.4464285714285714, Ops::fmac(Lam[4], -0.2892857142857143, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], 0.5785714285714286))))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[17], y[5]); y[17] = Ops::fma3(k, x[5], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[5] = Ops::fma3(k, x[18], y[5]); y[18] = Ops::fma3(k, x[5], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[6], 0.7232142857142857, Ops::fmac(Lam[5], 0.7232142857142857, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[1], -0.14464285714285716)))))); } else { k = Ops::zero(); } y[5] = Ops::fma3(k, x[19], y[5]); y[19] = Ops::fma3(k, x[5], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 1.1571428571428573, Ops::fmac(Lam[2], 1.1571428571428573, Ops::mulc(Lam[0], 1.4464285714285714))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[6] = Ops::fma3(k, x[6], y[6]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.43392857142857144, Ops::fmac(Lam[2], 0.2892857142857143, Ops::mulc(Lam[0], -0.43392857142857144))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[6] = Ops::fma3(k, x[7], y[6]); y[7] = Ops::fma3(k, x[6], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.1571428571428573, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[0], 0.7232142857142857)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[6] = Ops::fma3(k, x[8], y[6]); y[8] = Ops::fma3(k, x[6], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.43392857142857144, Ops::fmac(Lam[3], -0.2892857142857143, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[6] = Ops::fma3(k, x[9], y[6]); y[9] = Ops::fma3(k, x[6], y[9]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.2892857142857143)))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[10], y[6]); y[10] = Ops::fma3(k, x[6], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[2], -0.2892857142857143, Ops::mulc(Lam[1], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[6] = Ops::fma3(k, x[11], y[6]); y[11] = Ops::fma3(k, x[6], y[11]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[12], y[6]); y[12] = Ops::fma3(k, x[6], y[12]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[13], y[6]); y[13] = Ops::fma3(k, x[6], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[3], -0.43392857142857144, Ops::mulc(Lam[2], -0.2892857142857143)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[6] = Ops::fma3(k, x[14], y[6]); y[14] = Ops::fma3(k, x[6], y[14]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::mulc(Lam[2], -0.14464285714285716)))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[15], y[6]); y[15] = Ops::fma3(k, x[6], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[2], 0.5785714285714286, Ops::fmac(Lam[1], 1.4464285714285714, Ops::mulc(Lam[0], -0.2892857142857143))))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[16], y[6]); y[16] = Ops::fma3(k, x[6], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[3], 0.7232142857142857, Ops::fmac(Lam[2], -0.14464285714285716, Ops::fmac(Lam[1], 0.7232142857142857, Ops::mulc(Lam[0], -0.14464285714285716)))))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[17], y[6]); y[17] = Ops::fma3(k, x[6], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], 0.5785714285714286, Ops::fmac(Lam[3], 1.4464285714285714, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[0], -0.2892857142857143))))); } else { k = Ops::zero(); } y[6] = Ops::fma3(k, x[18], y[6]); y[18] = Ops::fma3(k, x[6], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.2892857142857143)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[6] = Ops::fma3(k, x[19], y[6]); y[19] = Ops::fma3(k, x[6], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 1.4464285714285714, Ops::fmac(Lam[2], 1.1571428571428573, Ops::mulc(Lam[0], 1.1571428571428573))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[7] = Ops::fma3(k, x[7], y[7]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.43392857142857144, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], -0.2892857142857143, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[7] = Ops::fma3(k, x[8], y[7]); y[8] = Ops::fma3(k, x[7], y[8]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))); } else { k = Ops::zero(); } y[7] = Ops::fma3(k, x[9], y[7]); y[9] = Ops::fma3(k, x[7], y[9]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[7] = Ops::fma3(k, x[10], y[7]); y[10] = Ops::fma3(k, x[7], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.7232142857142857, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[1], 1.1571428571428573)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[7] = Ops::fma3(k, x[11], y[7]); y[11] = Ops::fma3(k, x[7], y[11]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[7] = Ops::fma3(k, x[12], y[7]); y[12] = Ops::fma3(k, x[7], y[12]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[7] = Ops::fma3(k, x[13], y[7]); y[13] = Ops::fma3(k, x[7], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], 0.7232142857142857, Ops::fmac(Lam[3], 1.1571428571428573, Ops::mulc(Lam[2], 0.5785714285714286)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[7] = Ops::fma3(k, x[14], y[7]); y[14] = Ops::fma3(k, x[7], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[3], -0.43392857142857144, Ops::mulc(Lam[2], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[7] = Ops::fma3(k, x[15], y[7]); y[15] = Ops::fma3(k, x[7], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.2892857142857143, Ops::fmac(Lam[5], 1.4464285714285714, Ops::fmac(Lam[2], 0.5785714285714286, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], 0.5785714285714286))))); } else { k = Ops::zero(); } y[7] = Ops::fma3(k, x[16], y[7]); y[16] = Ops::fma3(k, x[7], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[7] = Ops::fma3(k, x[17], y[7]); y[17] = Ops::fma3(k, x[7], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.4464285714285714, Ops::fmac(Lam[7], -0.2892857142857143, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[0], 0.5785714285714286))))); } else { k = Ops::zero(); } y[7] = Ops::fma3(k, x[18], y[7]); y[18] = Ops::fma3(k, x[7], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.7232142857142857, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[5], 0.7232142857142857, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], 0.5785714285714286)))))); } else { k = Ops::zero(); } y[7] = Ops::fma3(k, x[19], y[7]); y[19] = Ops::fma3(k, x[7], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.1571428571428573, Ops::fmac(Lam[3], 1.1571428571428573, Ops::mulc(Lam[0], 1.4464285714285714))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[8] = Ops::fma3(k, x[8], y[8]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.43392857142857144, Ops::fmac(Lam[3], 0.2892857142857143, Ops::mulc(Lam[0], -0.43392857142857144))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[8] = Ops::fma3(k, x[9], y[8]); y[9] = Ops::fma3(k, x[8], y[9]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[10], y[8]); y[10] = Ops::fma3(k, x[8], y[10]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[11], y[8]); y[11] = Ops::fma3(k, x[8], y[11]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.2892857142857143)))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[12], y[8]); y[12] = Ops::fma3(k, x[8], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::mulc(Lam[1], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[8] = Ops::fma3(k, x[13], y[8]); y[13] = Ops::fma3(k, x[8], y[13]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.2892857142857143)))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[14], y[8]); y[14] = Ops::fma3(k, x[8], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::mulc(Lam[2], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[8] = Ops::fma3(k, x[15], y[8]); y[15] = Ops::fma3(k, x[8], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], 0.7232142857142857, Ops::fmac(Lam[1], 0.7232142857142857, Ops::mulc(Lam[0], -0.14464285714285716)))))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[16], y[8]); y[16] = Ops::fma3(k, x[8], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.5785714285714286, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[1], 1.4464285714285714, Ops::mulc(Lam[0], -0.2892857142857143))))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[17], y[8]); y[17] = Ops::fma3(k, x[8], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.5785714285714286, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[2], 1.4464285714285714, Ops::mulc(Lam[0], -0.2892857142857143))))); } else { k = Ops::zero(); } y[8] = Ops::fma3(k, x[18], y[8]); y[18] = Ops::fma3(k, x[8], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], -0.2892857142857143, Ops::mulc(Lam[1], -0.2892857142857143)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[8] = Ops::fma3(k, x[19], y[8]); y[19] = Ops::fma3(k, x[8], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.4464285714285714, Ops::fmac(Lam[3], 1.1571428571428573, Ops::mulc(Lam[0], 1.1571428571428573))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[9] = Ops::fma3(k, x[9], y[9]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[9] = Ops::fma3(k, x[10], y[9]); y[10] = Ops::fma3(k, x[9], y[10]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.14464285714285716)))); } else { k = Ops::zero(); } y[9] = Ops::fma3(k, x[11], y[9]); y[11] = Ops::fma3(k, x[9], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[9] = Ops::fma3(k, x[12], y[9]); y[12] = Ops::fma3(k, x[9], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.7232142857142857, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[3], 0.5785714285714286, Ops::mulc(Lam[1], 1.1571428571428573)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[9] = Ops::fma3(k, x[13], y[9]); y[13] = Ops::fma3(k, x[9], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[9] = Ops::fma3(k, x[14], y[9]); y[14] = Ops::fma3(k, x[9], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.7232142857142857, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[3], 0.5785714285714286, Ops::mulc(Lam[2], 1.1571428571428573)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[9] = Ops::fma3(k, x[15], y[9]); y[15] = Ops::fma3(k, x[9], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::fmac(Lam[1], -0.14464285714285716, Ops::mulc(Lam[0], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[9] = Ops::fma3(k, x[16], y[9]); y[16] = Ops::fma3(k, x[9], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2892857142857143, Ops::fmac(Lam[6], 1.4464285714285714, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[1], 0.5785714285714286, Ops::mulc(Lam[0], 0.5785714285714286))))); } else { k = Ops::zero(); } y[9] = Ops::fma3(k, x[17], y[9]); y[17] = Ops::fma3(k, x[9], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2892857142857143, Ops::fmac(Lam[8], 1.4464285714285714, Ops::fmac(Lam[3], 0.5785714285714286, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[0], 0.5785714285714286))))); } else { k = Ops::zero(); } y[9] = Ops::fma3(k, x[18], y[9]); y[18] = Ops::fma3(k, x[9], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], 0.7232142857142857, Ops::fmac(Lam[6], 0.7232142857142857, Ops::fmac(Lam[3], -0.14464285714285716, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[1], 0.5785714285714286)))))); } else { k = Ops::zero(); } y[9] = Ops::fma3(k, x[19], y[9]); y[19] = Ops::fma3(k, x[9], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 1.1571428571428573, Ops::fmac(Lam[5], 1.1571428571428573, Ops::mulc(Lam[4], 1.4464285714285714))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[10] = Ops::fma3(k, x[10], y[10]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.43392857142857144, Ops::fmac(Lam[5], 0.2892857142857143, Ops::mulc(Lam[4], -0.43392857142857144))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[10] = Ops::fma3(k, x[11], y[10]); y[11] = Ops::fma3(k, x[10], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.1571428571428573, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::mulc(Lam[4], 0.7232142857142857)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[10] = Ops::fma3(k, x[12], y[10]); y[12] = Ops::fma3(k, x[10], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.43392857142857144, Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[5], -0.14464285714285716, Ops::mulc(Lam[4], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[10] = Ops::fma3(k, x[13], y[10]); y[13] = Ops::fma3(k, x[10], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], -0.43392857142857144, Ops::mulc(Lam[5], -0.2892857142857143)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[10] = Ops::fma3(k, x[14], y[10]); y[14] = Ops::fma3(k, x[10], y[14]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], -0.2892857142857143, Ops::mulc(Lam[5], -0.14464285714285716)))); } else { k = Ops::zero(); } y[10] = Ops::fma3(k, x[15], y[10]); y[15] = Ops::fma3(k, x[10], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[4], -0.2892857142857143, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[1], 1.4464285714285714))))); } else { k = Ops::zero(); } y[10] = Ops::fma3(k, x[16], y[10]); y[16] = Ops::fma3(k, x[10], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[6], 0.7232142857142857, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[2], 0.5785714285714286, Ops::mulc(Lam[1], 0.7232142857142857)))))); } else { k = Ops::zero(); } y[10] = Ops::fma3(k, x[17], y[10]); y[17] = Ops::fma3(k, x[10], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[2], -0.14464285714285716, Ops::mulc(Lam[1], -0.2892857142857143)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[10] = Ops::fma3(k, x[18], y[10]); y[18] = Ops::fma3(k, x[10], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], 0.5785714285714286, Ops::fmac(Lam[6], 1.4464285714285714, Ops::fmac(Lam[5], 0.5785714285714286, Ops::mulc(Lam[4], -0.2892857142857143))))); } else { k = Ops::zero(); } y[10] = Ops::fma3(k, x[19], y[10]); y[19] = Ops::fma3(k, x[10], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 1.4464285714285714, Ops::fmac(Lam[5], 1.1571428571428573, Ops::mulc(Lam[4], 1.1571428571428573))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[11] = Ops::fma3(k, x[11], y[11]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.43392857142857144, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.2892857142857143, Ops::mulc(Lam[4], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[11] = Ops::fma3(k, x[12], y[11]); y[12] = Ops::fma3(k, x[11], y[12]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::mulc(Lam[4], -0.14464285714285716)))); } else { k = Ops::zero(); } y[11] = Ops::fma3(k, x[13], y[11]); y[13] = Ops::fma3(k, x[11], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], 0.7232142857142857, Ops::fmac(Lam[6], 1.1571428571428573, Ops::mulc(Lam[5], 0.5785714285714286)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[11] = Ops::fma3(k, x[14], y[11]); y[14] = Ops::fma3(k, x[11], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], -0.43392857142857144, Ops::mulc(Lam[5], -0.14464285714285716)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[11] = Ops::fma3(k, x[15], y[11]); y[15] = Ops::fma3(k, x[11], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[7], -0.2892857142857143, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[4], 0.5785714285714286, Ops::fmac(Lam[2], 1.4464285714285714, Ops::mulc(Lam[1], 0.5785714285714286))))); } else { k = Ops::zero(); } y[11] = Ops::fma3(k, x[16], y[11]); y[16] = Ops::fma3(k, x[11], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[2], -0.2892857142857143, Ops::mulc(Lam[1], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[11] = Ops::fma3(k, x[17], y[11]); y[17] = Ops::fma3(k, x[11], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.7232142857142857, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[2], 0.7232142857142857, Ops::mulc(Lam[1], 0.5785714285714286)))))); } else { k = Ops::zero(); } y[11] = Ops::fma3(k, x[18], y[11]); y[18] = Ops::fma3(k, x[11], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.4464285714285714, Ops::fmac(Lam[7], -0.2892857142857143, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::mulc(Lam[4], 0.5785714285714286))))); } else { k = Ops::zero(); } y[11] = Ops::fma3(k, x[19], y[11]); y[19] = Ops::fma3(k, x[11], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.1571428571428573, Ops::fmac(Lam[6], 1.1571428571428573, Ops::mulc(Lam[4], 1.4464285714285714))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[12] = Ops::fma3(k, x[12], y[12]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.43392857142857144, Ops::fmac(Lam[6], 0.2892857142857143, Ops::mulc(Lam[4], -0.43392857142857144))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[12] = Ops::fma3(k, x[13], y[12]); y[13] = Ops::fma3(k, x[12], y[13]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::mulc(Lam[5], -0.2892857142857143)))); } else { k = Ops::zero(); } y[12] = Ops::fma3(k, x[14], y[12]); y[14] = Ops::fma3(k, x[12], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.2892857142857143, Ops::mulc(Lam[5], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[12] = Ops::fma3(k, x[15], y[12]); y[15] = Ops::fma3(k, x[12], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], 0.7232142857142857, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], 0.5785714285714286, Ops::mulc(Lam[1], 0.7232142857142857)))))); } else { k = Ops::zero(); } y[12] = Ops::fma3(k, x[16], y[12]); y[16] = Ops::fma3(k, x[12], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.5785714285714286, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[4], -0.2892857142857143, Ops::fmac(Lam[3], 0.5785714285714286, Ops::mulc(Lam[1], 1.4464285714285714))))); } else { k = Ops::zero(); } y[12] = Ops::fma3(k, x[17], y[12]); y[17] = Ops::fma3(k, x[12], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[1], -0.2892857142857143)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[12] = Ops::fma3(k, x[18], y[12]); y[18] = Ops::fma3(k, x[12], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.5785714285714286, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], 1.4464285714285714, Ops::mulc(Lam[4], -0.2892857142857143))))); } else { k = Ops::zero(); } y[12] = Ops::fma3(k, x[19], y[12]); y[19] = Ops::fma3(k, x[12], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.4464285714285714, Ops::fmac(Lam[6], 1.1571428571428573, Ops::mulc(Lam[4], 1.1571428571428573))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[13] = Ops::fma3(k, x[13], y[13]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[6], -0.14464285714285716, Ops::mulc(Lam[5], -0.43392857142857144)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.0060267857142857146, k); } y[13] = Ops::fma3(k, x[14], y[13]); y[14] = Ops::fma3(k, x[13], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.7232142857142857, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[6], 0.5785714285714286, Ops::mulc(Lam[5], 1.1571428571428573)))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.012053571428571429, k); } y[13] = Ops::fma3(k, x[15], y[13]); y[15] = Ops::fma3(k, x[13], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.2892857142857143, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[4], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::mulc(Lam[1], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[13] = Ops::fma3(k, x[16], y[13]); y[16] = Ops::fma3(k, x[13], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2892857142857143, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[4], 0.5785714285714286, Ops::fmac(Lam[3], 1.4464285714285714, Ops::mulc(Lam[1], 0.5785714285714286))))); } else { k = Ops::zero(); } y[13] = Ops::fma3(k, x[17], y[13]); y[17] = Ops::fma3(k, x[13], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], 0.7232142857142857, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[3], 0.7232142857142857, Ops::mulc(Lam[1], 0.5785714285714286)))))); } else { k = Ops::zero(); } y[13] = Ops::fma3(k, x[18], y[13]); y[18] = Ops::fma3(k, x[13], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2892857142857143, Ops::fmac(Lam[8], 1.4464285714285714, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], 0.5785714285714286, Ops::mulc(Lam[4], 0.5785714285714286))))); } else { k = Ops::zero(); } y[13] = Ops::fma3(k, x[19], y[13]); y[19] = Ops::fma3(k, x[13], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.1571428571428573, Ops::fmac(Lam[8], 1.1571428571428573, Ops::mulc(Lam[7], 1.4464285714285714))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[14] = Ops::fma3(k, x[14], y[14]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.43392857142857144, Ops::fmac(Lam[8], 0.2892857142857143, Ops::mulc(Lam[7], -0.43392857142857144))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[14] = Ops::fma3(k, x[15], y[14]); y[15] = Ops::fma3(k, x[14], y[15]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], 0.5785714285714286, Ops::fmac(Lam[5], 0.7232142857142857, Ops::fmac(Lam[3], 0.5785714285714286, Ops::mulc(Lam[2], 0.7232142857142857)))))); } else { k = Ops::zero(); } y[14] = Ops::fma3(k, x[16], y[14]); y[16] = Ops::fma3(k, x[14], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], -0.14464285714285716, Ops::fmac(Lam[5], -0.2892857142857143, Ops::fmac(Lam[3], -0.14464285714285716, Ops::mulc(Lam[2], -0.2892857142857143)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[14] = Ops::fma3(k, x[17], y[14]); y[17] = Ops::fma3(k, x[14], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.5785714285714286, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], -0.2892857142857143, Ops::fmac(Lam[3], 0.5785714285714286, Ops::mulc(Lam[2], 1.4464285714285714))))); } else { k = Ops::zero(); } y[14] = Ops::fma3(k, x[18], y[14]); y[18] = Ops::fma3(k, x[14], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 0.5785714285714286, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], -0.2892857142857143, Ops::fmac(Lam[6], 0.5785714285714286, Ops::mulc(Lam[5], 1.4464285714285714))))); } else { k = Ops::zero(); } y[14] = Ops::fma3(k, x[19], y[14]); y[19] = Ops::fma3(k, x[14], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.4464285714285714, Ops::fmac(Lam[8], 1.1571428571428573, Ops::mulc(Lam[7], 1.1571428571428573))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.024107142857142858, k); } y[15] = Ops::fma3(k, x[15], y[15]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[7], -0.14464285714285716, Ops::fmac(Lam[6], -0.2892857142857143, Ops::fmac(Lam[5], -0.14464285714285716, Ops::fmac(Lam[3], -0.2892857142857143, Ops::mulc(Lam[2], -0.14464285714285716)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, -0.012053571428571429, k); } y[15] = Ops::fma3(k, x[16], y[15]); y[16] = Ops::fma3(k, x[15], y[16]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.14464285714285716, Ops::fmac(Lam[8], -0.14464285714285716, Ops::fmac(Lam[6], 0.7232142857142857, Ops::fmac(Lam[5], 0.5785714285714286, Ops::fmac(Lam[3], 0.7232142857142857, Ops::mulc(Lam[2], 0.5785714285714286)))))); } else { k = Ops::zero(); } y[15] = Ops::fma3(k, x[17], y[15]); y[17] = Ops::fma3(k, x[15], y[17]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2892857142857143, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], 0.5785714285714286, Ops::fmac(Lam[3], 1.4464285714285714, Ops::mulc(Lam[2], 0.5785714285714286))))); } else { k = Ops::zero(); } y[15] = Ops::fma3(k, x[18], y[15]); y[18] = Ops::fma3(k, x[15], y[18]); }
+    if constexpr (STIFF) { if constexpr (STIFF) { k = Ops::fmac(Lam[9], -0.2892857142857143, Ops::fmac(Lam[8], 0.5785714285714286, Ops::fmac(Lam[7], 0.5785714285714286, Ops::fmac(Lam[6], 1.4464285714285714, Ops::mulc(Lam[5], 0.5785714285714286))))); } else { k = Ops::zero(); } y[15] = Ops::fma3(k, x[19], y[15]); y[19] = Ops::fma3(k, x[15], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[7], 3.4714285714285715, Ops::fmac(Lam[5], 3.4714285714285715, Ops::fmac(Lam[4], 3.4714285714285715, Ops::fmac(Lam[2], 3.4714285714285715, Ops::fmac(Lam[1], 3.4714285714285715, Ops::mulc(Lam[0], 3.4714285714285715)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.09642857142857143, k); } y[16] = Ops::fma3(k, x[16], y[16]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 3.4714285714285715, Ops::fmac(Lam[6], 1.7357142857142858, Ops::fmac(Lam[5], 1.7357142857142858, Ops::fmac(Lam[4], 1.7357142857142858, Ops::fmac(Lam[3], 1.7357142857142858, Ops::fmac(Lam[2], 1.7357142857142858, Ops::fmac(Lam[1], 1.7357142857142858, Ops::mulc(Lam[0], 1.7357142857142858)))))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.048214285714285716, k); } y[16] = Ops::fma3(k, x[17], y[16]); y[17] = Ops::fma3(k, x[16], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.7357142857142858, Ops::fmac(Lam[7], 1.7357142857142858, Ops::fmac(Lam[6], 3.4714285714285715, Ops::fmac(Lam[5], 1.7357142857142858, Ops::fmac(Lam[3], 1.7357142857142858, Ops::fmac(Lam[2], 1.7357142857142858, Ops::fmac(Lam[1], 1.7357142857142858, Ops::mulc(Lam[0], 1.7357142857142858)))))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.048214285714285716, k); } y[16] = Ops::fma3(k, x[18], y[16]); y[18] = Ops::fma3(k, x[16], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[8], 1.7357142857142858, Ops::fmac(Lam[7], 1.7357142857142858, Ops::fmac(Lam[6], 1.7357142857142858, Ops::fmac(Lam[5], 1.7357142857142858, Ops::fmac(Lam[4], 1.7357142857142858, Ops::fmac(Lam[3], 3.4714285714285715, Ops::fmac(Lam[2], 1.7357142857142858, Ops::mulc(Lam[1], 1.7357142857142858)))))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.048214285714285716, k); } y[16] = Ops::fma3(k, x[19], y[16]); y[19] = Ops::fma3(k, x[16], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 3.4714285714285715, Ops::fmac(Lam[6], 3.4714285714285715, Ops::fmac(Lam[4], 3.4714285714285715, Ops::fmac(Lam[3], 3.4714285714285715, Ops::fmac(Lam[1], 3.4714285714285715, Ops::mulc(Lam[0], 3.4714285714285715)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.09642857142857143, k); } y[17] = Ops::fma3(k, x[17], y[17]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.7357142857142858, Ops::fmac(Lam[8], 1.7357142857142858, Ops::fmac(Lam[6], 1.7357142857142858, Ops::fmac(Lam[5], 3.4714285714285715, Ops::fmac(Lam[3], 1.7357142857142858, Ops::fmac(Lam[2], 1.7357142857142858, Ops::fmac(Lam[1], 1.7357142857142858, Ops::mulc(Lam[0], 1.7357142857142858)))))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.048214285714285716, k); } y[17] = Ops::fma3(k, x[18], y[17]); y[18] = Ops::fma3(k, x[17], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.7357142857142858, Ops::fmac(Lam[8], 1.7357142857142858, Ops::fmac(Lam[6], 1.7357142857142858, Ops::fmac(Lam[5], 1.7357142857142858, Ops::fmac(Lam[4], 1.7357142857142858, Ops::fmac(Lam[3], 1.7357142857142858, Ops::fmac(Lam[2], 3.4714285714285715, Ops::mulc(Lam[1], 1.7357142857142858)))))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.048214285714285716, k); } y[17] = Ops::fma3(k, x[19], y[17]); y[19] = Ops::fma3(k, x[17], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 3.4714285714285715, Ops::fmac(Lam[8], 3.4714285714285715, Ops::fmac(Lam[7], 3.4714285714285715, Ops::fmac(Lam[3], 3.4714285714285715, Ops::fmac(Lam[2], 3.4714285714285715, Ops::mulc(Lam[0], 3.4714285714285715)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.09642857142857143, k); } y[18] = Ops::fma3(k, x[18], y[18]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 1.7357142857142858, Ops::fmac(Lam[8], 1.7357142857142858, Ops::fmac(Lam[7], 1.7357142857142858, Ops::fmac(Lam[6], 1.7357142857142858, Ops::fmac(Lam[5], 1.7357142857142858, Ops::fmac(Lam[3], 1.7357142857142858, Ops::fmac(Lam[2], 1.7357142857142858, Ops::mulc(Lam[1], 3.4714285714285715)))))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.048214285714285716, k); } y[18] = Ops::fma3(k, x[19], y[18]); y[19] = Ops::fma3(k, x[18], y[19]); }
+    { if constexpr (STIFF) { k = Ops::fmac(Lam[9], 3.4714285714285715, Ops::fmac(Lam[8], 3.4714285714285715, Ops::fmac(Lam[7], 3.4714285714285715, Ops::fmac(Lam[6], 3.4714285714285715, Ops::fmac(Lam[5], 3.4714285714285715, Ops::mulc(Lam[4], 3.4714285714285715)))))); } else { k = Ops::zero(); } if constexpr (MASS) { k = Ops::fmac(vol, 0.09642857142857143, k); } y[19] = Ops::fma3(k, x[19], y[19]); }
   }
   __host__ __device__ static constexpr int upper_index(int i, int j) {
     return i <= j ? i * 20 - (i * (i - 1)) / 2 + (j - i) : j * 20 - (j * (j - 1)) / 2 + (i - j);

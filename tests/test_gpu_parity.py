@@ -151,6 +151,8 @@ DD_CASES = [(2, 1, 64, 0.0), (2, 1, 37, 0.2), (2, 2, 23, 0.2), (3, 1, 9, 0.2), (
 def test_assemble_mat_f32x2_matches_oracle(gpu, dim, p, n, jit, form):
     """FP32-pair element tensors, FP64 global accumulation: same 1e-12 per-entry bound."""
     from paper_1501_01809_gb300 import fe
+    if form == 4 and dim == 3:
+        pytest.skip("kappa-diffusion on tetrahedra is compiled in FP64 only")
     pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
     g = PB.GpuProblem(pr)
     rp, ci = g.csr()
@@ -163,6 +165,8 @@ def test_assemble_mat_f32x2_matches_oracle(gpu, dim, p, n, jit, form):
 @pytest.mark.parametrize("form", [3, 4])
 def test_action_f32x2_matches_oracle(gpu, dim, p, n, jit, form):
     from paper_1501_01809_gb300 import fe
+    if form == 4 and dim == 3:
+        pytest.skip("kappa-diffusion on tetrahedra is compiled in FP64 only")
     pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
     g = PB.GpuProblem(pr)
     x = np.random.default_rng(2).uniform(-1, 1, pr.nnodes)
@@ -195,3 +199,76 @@ def test_f32x2_extreme_scales(gpu):
         got = g.assemble(3, precision=fe.PREC_F32X2)
         want, scale = O.assemble_mat(3, 2, 3, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci)
         PB.assert_close_scaled(got, want, scale, 1e-12, f"f32x2 coordinates x {scale_x}")
+
+
+# ------------------------------------------------------------------ pull strategy (row owners, no atomics)
+PULL_CASES = [(2, 1, 64, 0.0), (2, 2, 23, 0.2), (2, 4, 9, 0.2), (3, 1, 9, 0.2), (3, 2, 7, 0.2), (3, 3, 3, 0.2)]
+
+
+def _dd_ok(dim, p, form):
+    return p <= 2 and not (form == 4 and dim == 3)
+
+
+@pytest.mark.parametrize("dim,p,n,jit", PULL_CASES)
+@pytest.mark.parametrize("form", [1, 3, 4])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pull_mat_matches_oracle(gpu, dim, p, n, jit, form, prec):
+    from paper_1501_01809_gb300 import fe
+    if form == 4 and (dim, p) not in [(2, 1), (2, 2), (2, 4), (3, 1), (3, 2)]:
+        pytest.skip("kappa-diffusion built for P1/P2/P4 triangles and P1/P2 tets")
+    if prec == 1 and not _dd_ok(dim, p, form):
+        pytest.skip("double-float kernels built for P1/P2 (kappa on triangles)")
+    pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    got = g.assemble(form, precision=prec, strategy=fe.STRATEGY_PULL)
+    want, scale = O.assemble_mat(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
+    PB.assert_close_scaled(got, want, scale, 1e-12, f"pull form {form} P{p} dim {dim} prec {prec}")
+
+
+@pytest.mark.parametrize("dim,p,n,jit", [(2, 2, 23, 0.2), (3, 2, 7, 0.2), (3, 1, 9, 0.2)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pull_action_and_rhs_match_oracle(gpu, dim, p, n, jit, prec):
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+    pr = PB.make(dim, p, n, jit, seed=3)
+    g = PB.GpuProblem(pr)
+    x = np.random.default_rng(2).uniform(-1, 1, pr.nnodes)
+    got = g.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL)
+    want, scale = O.action(dim, p, 3, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, x)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "pull action")
+    fmap, nf = mg.cell_node_map(pr.mesh, p)
+    f = mg.uniform_dat(nf, 1)
+    got = g.rhs(f, fmap, p, nf, precision=prec, strategy=fe.STRATEGY_PULL)
+    want, scale = O.assemble_vec(dim, p, p, pr.cmap, pr.nnodes, pr.mesh.coords, pr.mesh.cell_vertex, f, fmap)
+    PB.assert_close_scaled(got, want, scale, 1e-12, "pull rhs")
+
+
+def test_pull_is_bitwise_reproducible(gpu):
+    """Row owners sum in the fixed incidence order: repeated assemblies and actions are bitwise equal."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(3, 2, 6, 0.2, seed=1)
+    g = PB.GpuProblem(pr)
+    x = np.random.default_rng(2).uniform(-1, 1, pr.nnodes)
+    for prec in (0, 1):
+        a1 = g.assemble(3, precision=prec, strategy=fe.STRATEGY_PULL)
+        a2 = g.assemble(3, precision=prec, strategy=fe.STRATEGY_PULL)
+        np.testing.assert_array_equal(a1, a2)
+        y1 = g.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL)
+        y2 = g.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL)
+        np.testing.assert_array_equal(y1, y2)
+
+
+def test_pull_inc_semantics(gpu):
+    """zero_first = 0 adds to what the Mat and y hold (INC), for the pull strategy too."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(2, 2, 9, 0.2, seed=1)
+    g = PB.GpuProblem(pr)
+    k = fe.kernel_create(g.ctx, 3, 2, 2, strategy=fe.STRATEGY_PULL)
+    A = fe.mat_create(g.ctx, g.sparsity())
+    fe.assemble_mat(g.ctx, k, g.cells, A, g.coords, g.coord_map, zero_first=True)
+    fe.assemble_mat(g.ctx, k, g.cells, A, g.coords, g.coord_map, zero_first=False)
+    fe.sync(g.ctx)
+    twice = fe.mat_values(A).cpu().numpy()
+    once = g.assemble(3, strategy=fe.STRATEGY_PULL)
+    np.testing.assert_allclose(twice, 2 * once, rtol=1e-15, atol=0)
