@@ -71,13 +71,14 @@ typedef enum {
 /* Arithmetic of the element tensor.  Accumulation into the global Mat/Dat is FP64 always. */
 typedef enum {
   FE_PREC_FP64 = 0,   /* native IEEE double                                               */
-  FE_PREC_F32X2 = 1   /* pairs of FP32 (error-free transformations), ~2^-46 relative     */
+  FE_PREC_F32X2 = 1,  /* pairs of FP32 (error-free transformations), ~2^-46 relative     */
+  FE_PREC_FP32 = 2    /* single FP32 (triangles, push): the precision study of high-order
+                         elements, ~1e-7 relative element error                           */
 } fe_precision;
 
 /* How the INC into the global Mat/Dat is executed. */
 typedef enum {
-  FE_STRATEGY_AUTO = 0,  /* PULL when the row incidence is at hand (a Mat's sparsity, or the
-                            sparsity passed to a vector par_loop), PUSH otherwise            */
+  FE_STRATEGY_AUTO = 0,  /* the library's faster choice on this hardware: currently PUSH       */
   FE_STRATEGY_PUSH = 1,  /* one thread per cell, FP64 atomic adds through the lookup table */
   FE_STRATEGY_PULL = 2   /* staged: element tensors stored per cell, then one owner per row
                             sums its cells' contributions in the fixed incidence order --

@@ -14,6 +14,9 @@ LaunchFn pick_vec_push_dd2(const fe_form_desc &d);
 LaunchFn pick_mat_push_dd3(const fe_form_desc &d);
 LaunchFn pick_action_push_dd3(const fe_form_desc &d);
 LaunchFn pick_vec_push_dd3(const fe_form_desc &d);
+LaunchFn pick_mat_push_f32(const fe_form_desc &d);
+LaunchFn pick_action_push_f32(const fe_form_desc &d);
+LaunchFn pick_vec_push_f32(const fe_form_desc &d);
 LaunchFn pick_mat_pull_f64(const fe_form_desc &d);
 LaunchFn pick_action_pull_f64(const fe_form_desc &d);
 LaunchFn pick_vec_pull_f64(const fe_form_desc &d);
@@ -31,6 +34,7 @@ LaunchFn pick_mat(const fe_form_desc &d, int strategy) {
   if (d.form == FE_FORM_SOURCE) return nullptr;
   const bool pull = strategy == FE_STRATEGY_PULL;
   if (d.precision == FE_PREC_FP64) return pull ? pick_mat_pull_f64(d) : pick_mat_push_f64(d);
+  if (d.precision == FE_PREC_FP32) return pull || d.dim != 2 ? nullptr : pick_mat_push_f32(d);
   if (d.precision == FE_PREC_F32X2) {
     if (d.dim == 2) return pull ? pick_mat_pull_dd2(d) : pick_mat_push_dd2(d);
     return pull ? pick_mat_pull_dd3(d) : pick_mat_push_dd3(d);
@@ -41,6 +45,7 @@ LaunchFn pick_action(const fe_form_desc &d, int strategy) {
   if (d.form == FE_FORM_SOURCE) return nullptr;
   const bool pull = strategy == FE_STRATEGY_PULL;
   if (d.precision == FE_PREC_FP64) return pull ? pick_action_pull_f64(d) : pick_action_push_f64(d);
+  if (d.precision == FE_PREC_FP32) return pull || d.dim != 2 ? nullptr : pick_action_push_f32(d);
   if (d.precision == FE_PREC_F32X2) {
     if (d.dim == 2) return pull ? pick_action_pull_dd2(d) : pick_action_push_dd2(d);
     return pull ? pick_action_pull_dd3(d) : pick_action_push_dd3(d);
@@ -51,6 +56,7 @@ LaunchFn pick_vec(const fe_form_desc &d, int strategy) {
   if (d.form != FE_FORM_SOURCE) return nullptr;
   const bool pull = strategy == FE_STRATEGY_PULL;
   if (d.precision == FE_PREC_FP64) return pull ? pick_vec_pull_f64(d) : pick_vec_push_f64(d);
+  if (d.precision == FE_PREC_FP32) return pull || d.dim != 2 ? nullptr : pick_vec_push_f32(d);
   if (d.precision == FE_PREC_F32X2) {
     if (d.dim == 2) return pull ? pick_vec_pull_dd2(d) : pick_vec_push_dd2(d);
     return pull ? pick_vec_pull_dd3(d) : pick_vec_push_dd3(d);
@@ -63,12 +69,14 @@ int nodes_of(int dim, int p) { return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1)
 }  // namespace
 
 int resolve_strategy(const fe_form_desc &d, bool have_incidence) {
-  if (d.strategy == FE_STRATEGY_PUSH) return FE_STRATEGY_PUSH;
-  if (d.strategy == FE_STRATEGY_PULL) return FE_STRATEGY_PULL;
-  return have_incidence ? FE_STRATEGY_PULL : FE_STRATEGY_PUSH;
+  (void)have_incidence;
+  // AUTO = PUSH: the faster INC on this hardware for these kernels (the FP64 atomics stay in L2);
+  // PULL is chosen explicitly when bitwise-reproducible results are required.
+  return d.strategy == FE_STRATEGY_PULL ? FE_STRATEGY_PULL : FE_STRATEGY_PUSH;
 }
 
 size_t stage_bytes_mat(const fe_form_desc &d, int64_t ncell) {
+  // (the FP32 element tensors have no pull kernels; sizes below are for FP64 and FP32 pairs)
   const int nd = nodes_of(d.dim, d.degree);
   const size_t elem = d.precision == FE_PREC_F32X2 ? 2 * sizeof(float) : sizeof(double);
   return (size_t)ncell * (size_t)(nd * (nd + 1) / 2) * elem;

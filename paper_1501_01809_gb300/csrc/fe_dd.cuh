@@ -155,4 +155,42 @@ struct OpsF32x2 {
   }
 };
 
+// Single FP32 element tensors (the precision study of the high-order elements): inputs rounded
+// to FP32 once per cell, all element arithmetic in FP32, results widened to FP64 exactly (integer
+// bit construction) for the FP64 global accumulation.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xFF);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  if (e == 0) return __longlong_as_double((long long)sign);  // zero (subnormals flushed)
+  if (e == 0xFF) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | ((unsigned long long)(b & 0x7FFFFF) << 29)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)(b & 0x7FFFFF) << 29)));
+}
+
+struct OpsF32 {
+  using T = float;
+  static __device__ __forceinline__ T zero() { return 0.0f; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T mulc(T a, double c) { return a * (float)c; }
+  static __device__ __forceinline__ T fmac(T a, double c, T acc) { return fmaf(a, (float)c, acc); }
+  static __device__ __forceinline__ T fma3(T a, T b, T c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ T from_f64(double x) { return f2_from_f64(x).hi + f2_from_f64(x).lo; }
+  static __device__ __forceinline__ T diff_f64(double a, double b) { return from_f64(a) - from_f64(b); }
+  static __device__ __forceinline__ double to_f64(T x) { return f32_to_f64_exact(x); }
+  static __device__ __forceinline__ T recip(T x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ T abs(T x) { return fabsf(x); }
+  static __device__ __forceinline__ T scale(T x, float s) { return x * s; }
+  static constexpr bool kNormalise = true;
+  static __device__ __forceinline__ int exponent(T x) {
+    const int e = (int)((__float_as_uint(x) >> 23) & 0xFF);
+    return e == 0 ? -1000 : e - 127;
+  }
+  static __device__ __forceinline__ T ldexp2(T x, int k) {
+    const int k1 = k / 2, k2 = k - k1;
+    return x * __uint_as_float((uint32_t)(k1 + 127) << 23) * __uint_as_float((uint32_t)(k2 + 127) << 23);
+  }
+};
+
 }  // namespace fe

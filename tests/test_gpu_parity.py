@@ -52,12 +52,14 @@ def test_sparsity_bitwise_and_lut(gpu, dim, p, n, jit):
 @pytest.mark.parametrize("dim,p,n,jit", CASES)
 @pytest.mark.parametrize("form", [1, 2, 3, 4])
 def test_assemble_mat_matches_oracle(gpu, dim, p, n, jit, form):
+    """FP64 push (FP64 atomics through the lookup table)."""
+    from paper_1501_01809_gb300 import fe
     if form == 4 and (dim, p) not in [(2, 1), (2, 2), (2, 4), (3, 1), (3, 2)]:
         pytest.skip("kappa-diffusion built for P1/P2/P4 triangles and P1/P2 tets")
     pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
     g = PB.GpuProblem(pr)
     rp, ci = g.csr()
-    got = g.assemble(form)
+    got = g.assemble(form, strategy=fe.STRATEGY_PUSH)
     want, scale = O.assemble_mat(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
     PB.assert_close_scaled(got, want, scale, 1e-12, f"form {form} P{p} dim {dim}")
 
@@ -156,7 +158,7 @@ def test_assemble_mat_f32x2_matches_oracle(gpu, dim, p, n, jit, form):
     pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
     g = PB.GpuProblem(pr)
     rp, ci = g.csr()
-    got = g.assemble(form, precision=fe.PREC_F32X2)
+    got = g.assemble(form, precision=fe.PREC_F32X2, strategy=fe.STRATEGY_PUSH)
     want, scale = O.assemble_mat(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
     PB.assert_close_scaled(got, want, scale, 1e-12, f"f32x2 form {form} P{p} dim {dim}")
 
@@ -272,3 +274,18 @@ def test_pull_inc_semantics(gpu):
     twice = fe.mat_values(A).cpu().numpy()
     once = g.assemble(3, strategy=fe.STRATEGY_PULL)
     np.testing.assert_allclose(twice, 2 * once, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("dim,p,n,jit", [(2, 1, 37, 0.2), (2, 2, 23, 0.2), (2, 4, 17, 0.2)])
+@pytest.mark.parametrize("form", [1, 3, 4])
+def test_fp32_element_tensors_frobenius(gpu, dim, p, n, jit, form):
+    """FP32 element tensors with FP64 accumulation: relative Frobenius error <= 1e-5 (stated bound)."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(dim, p, n, jit, seed=3, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    got = g.assemble(form, precision=fe.PREC_FP32)
+    want, scale = O.assemble_mat(dim, p, form, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-5, err
+    assert np.max(np.abs(got - want) / np.maximum(scale, 1e-300)) <= 1e-5
