@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cells/s assembled (sparsity + CSR assembly + matrix-free action per step)"
+METRIC_BATCH = "cells/s assembled (CSR + RHS of every mesh of the batch per step, sparsity cached)"
 WORKLOADS = {
     "p2-3d": dict(dim=3, p=2, n=64, jitter=0.2, seed=0,
                   name="P2 Lagrange UnitCubeMesh 64^3 (1,572,864 Kuhn tets, +-0.2h jitter seed 0, 2,146,689 dofs), "
@@ -37,6 +38,10 @@ WORKLOADS = {
     "p1-2d": dict(dim=2, p=1, n=64, jitter=0.0, seed=0,
                   name="P1 Lagrange UnitSquareMesh 64x64 (8192 cells, 4225 nodes), Helmholtz, FP64 CSR: "
                        "sparsity + assembly + matrix-free action"),
+    "batch": dict(count=2048, seed=4, lo=8, hi=256,
+                  name="2048 UnitSquareMesh n x n meshes, n log-uniform in [8,256] (seed 4), each P1 or P2 "
+                       "(Bernoulli 1/2), Helmholtz CSR + RHS f v dx (f uniform[-1,1] per node, seed 1000+i), "
+                       "one persistent launch under a CUDA graph, tuned tile and grid"),
 }
 # ncu dram bytes (read + write) per launch of the dominant kernel, with the sha1 of the kernel
 # source they were taken from; reported as null once the source has changed.
@@ -309,6 +314,190 @@ def run_ours(args, wl, rank, world):
     return out, (mesh, cmap, nn, x)
 
 
+# ------------------------------------------------------------------------------ batched workload
+
+def make_batch_inputs(wl):
+    """Per mesh (n, p, mesh, cell-node map, nodes, f); meshes of equal (n, p) share host arrays only."""
+    from paper_1501_01809_gb300 import meshgen as mg
+    ns, ps = mg.batch_mesh_sizes(wl["count"], wl["seed"], wl["lo"], wl["hi"])
+    cache, out = {}, []
+    for i, (n, p) in enumerate(zip(ns, ps)):
+        key = (int(n), int(p))
+        if key not in cache:
+            mesh = mg.unit_square_mesh(key[0])
+            cmap, nn = mg.cell_node_map(mesh, key[1])
+            cache[key] = (mesh, cmap, nn)
+        mesh, cmap, nn = cache[key]
+        out.append((key[0], key[1], mesh, cmap, nn, mg.uniform_dat(nn, 1000 + i)))
+    return out
+
+
+def _concat_to_device(arrays, dev):
+    """One device buffer holding all arrays back to back; returns (buffer, [views])."""
+    import torch
+    flat = np.concatenate([a.ravel() for a in arrays])
+    buf = torch.from_numpy(flat).to(dev)
+    views, off = [], 0
+    for a in arrays:
+        views.append(buf[off:off + a.size].view(a.shape))
+        off += a.size
+    return buf, views
+
+
+def run_batch(args, wl, rank, world):
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    meshes = make_batch_inputs(wl)
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    prec = {"fp64": fe.PREC_FP64, "f32x2": fe.PREC_F32X2}[args.precision]
+    kmat = {p: fe.kernel_create(ctx, fe.FORM_HELMHOLTZ, 2, p, precision=prec) for p in (1, 2)}
+    kvec = {p: fe.kernel_create(ctx, fe.FORM_SOURCE, 2, p, coeff_degree=p, precision=prec) for p in (1, 2)}
+    host = {"map": [m[3] for m in meshes], "cv": [m[2].cell_vertex for m in meshes],
+            "xy": [m[2].coords for m in meshes], "f": [m[5] for m in meshes]}
+    bufs, views = {}, {}
+    for k, arrs in host.items():
+        bufs[k], views[k] = _concat_to_device(arrs, dev)
+    items, objs = [], []
+    ncell_tot = nnz_tot = bytes_alg = 0
+    with torch.cuda.stream(stream):
+        for i, (n, p, mesh, cmap, nn, f) in enumerate(meshes):
+            cells, nodes, verts = fe.set_create(ctx, mesh.ncell), fe.set_create(ctx, nn), fe.set_create(ctx, mesh.nvert)
+            M = fe.map_create(ctx, cells, nodes, views["map"][i])
+            CM = fe.map_create(ctx, cells, verts, views["cv"][i])
+            XY = fe.dat_create(ctx, verts, views["xy"][i])
+            F = fe.dat_create(ctx, nodes, views["f"][i])
+            sp = fe.sparsity_build(ctx, M, M)
+            nnz = fe.sparsity_csr(sp)[2]
+            items.append(dict(kmat=kmat[p], kvec=kvec[p], cells=cells, sp=sp, coords=XY, coord_map=CM, f=(F, M)))
+            objs.append((cells, nodes, M, CM, XY, F, sp, p))
+            nd = 3 if p == 1 else 6
+            ncell_tot += mesh.ncell
+            nnz_tot += nnz
+            # algorithmic bytes: maps and coordinates read once, f read once, CSR values and RHS written once
+            bytes_alg += mesh.ncell * (nd + 3) * 4 + mesh.nvert * 16 + nn * 8 + nnz * 8 + nn * 8
+        B = fe.batch_create(ctx, items)
+    fe.sync(ctx)
+    tile, grid, tune_ms = fe.batch_tune(B, reps=3)
+
+    def time_loop(fn, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / k
+
+    step = lambda: fe.batch_assemble(B, use_graph=True)
+    for _ in range(args.warmup):
+        step()
+    fe.sync(ctx)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        ms_step = time_loop(step, args.steps)
+        wall = time.perf_counter() - t0
+    if dist:
+        td.barrier()
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms_step = float(t.item())
+    fe.sync(ctx)
+    # the same batch without the graph, and the plain path: one Mat zero + one Mat launch + one RHS
+    # launch per mesh (its own Mat and RHS), both on the same stream
+    ksmall = max(3, min(args.steps, 20))
+    eager_ms = time_loop(lambda: fe.batch_assemble(B, use_graph=False), ksmall)
+    mats, rhs = [], []
+    for (cells, nodes, M, CM, XY, F, sp, p) in objs:
+        mats.append(fe.mat_create(ctx, sp))
+        t_b = torch.empty(fe.sparsity_csr(sp)[0], dtype=torch.float64, device=dev)
+        rhs.append((t_b, fe.dat_create(ctx, nodes, t_b)))
+
+    def plain():
+        for (cells, nodes, M, CM, XY, F, sp, p), A, (_, Bv) in zip(objs, mats, rhs):
+            fe.mat_zero(A)
+            fe.assemble_mat(ctx, kmat[p], cells, A, XY, CM)
+            fe.assemble_vec(ctx, kvec[p], cells, Bv, M, XY, CM, [(F, M)], zero_first=True)
+
+    plain()
+    fe.sync(ctx)
+    plain_ms = time_loop(plain, ksmall)
+    fe.sync(ctx)
+    # batched results equal the plain ones (spot check of the largest mesh's RHS, relative 1e-12)
+    big = int(np.argmax([m[2].ncell for m in meshes]))
+    rb = fe.batch_values(B, big)[1]
+    drift = float((rb - rhs[big][0]).abs().max() / max(1e-300, float(rhs[big][0].abs().max())))
+
+    e2e = None
+    if not args.no_e2e:
+        vals_all, rhs_all = fe.batch_buffers(B)
+        h_in = [(torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t.cpu()), t) for t in bufs.values()]
+        h_out = [(torch.empty(t.shape, dtype=t.dtype, pin_memory=True), t) for t in (vals_all, rhs_all)]
+        h2d = sum(h.numel() * h.element_size() for h, _ in h_in)
+        d2h = sum(h.numel() * h.element_size() for h, _ in h_out)
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for h, d in h_in:
+                    d.copy_(h, non_blocking=True)
+                step()
+                for h, d in h_out:
+                    h.copy_(d, non_blocking=True)
+
+        e2e_step()
+        stream.synchronize()
+        e2e_ms = time_loop(e2e_step, ksmall)
+        e2e = {"value": world * ncell_tot / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+        fe.sync(ctx)
+
+    peaks, src = _peaks()
+    gbs = bytes_alg / (ms_step / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "kernel": "batch step (k_batch_zero + k_batch_assemble, one graph)", "traffic": None,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    out = {
+        "metric": METRIC_BATCH, "value": world * ncell_tot / (ms_step / 1e3), "unit": "cells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "meshes": len(meshes), "cells_per_gpu": ncell_tot, "nnz": nnz_tot,
+                   "precision": ("element tensors in FP32 pairs (double-float), FP64 global accumulation"
+                                 if args.precision == "f32x2" else "FP64 throughout"),
+                   "tuned": {"tile_cells": tile, "grid": grid, "ms": tune_ms},
+                   "batched_eager_ms": eager_ms, "plain_per_mesh_ms": plain_ms,
+                   "plain_cells_per_s": ncell_tot / (plain_ms / 1e3), "speedup_vs_plain": plain_ms / ms_step,
+                   "plain_launches_per_step": 3 * len(meshes), "max_rel_diff_vs_plain_rhs": drift,
+                   "parallelism": f"replicas x{world} (independent batches, no collective)",
+                   "l2": f"inputs larger than L2 (CSR values {8 * nnz_tot / 1e9:.2f} GB), no flush"},
+        "roofline": roof, "gpu_launches": 2 * args.steps, "wall_s_timed": wall, "clocks": clk.summary(), "e2e": e2e,
+    }
+    return out, meshes
+
+
+def batch_cpu_sample(meshes, budget_s):
+    """Oracle on the first meshes of the batch (sparsity + CSR + RHS) until budget_s seconds are spent."""
+    import oracle as O
+    cells, t0 = 0, time.perf_counter()
+    for (n, p, mesh, cmap, nn, f) in meshes:
+        rp, ci = O.sparsity(cmap, cmap, nn, nn)
+        O.assemble_mat(2, p, O.HELMHOLTZ, cmap, mesh.coords, mesh.cell_vertex, rp, ci)
+        O.assemble_vec(2, p, p, cmap, nn, mesh.coords, mesh.cell_vertex, f, cmap)
+        cells += mesh.ncell
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return cells, time.perf_counter() - t0
+
+
 def _oracle_sample(wl, inputs, ncell_sample):
     """Oracle on the first ncell_sample cells of the workload: sparsity + assembly + action."""
     import oracle as O
@@ -335,6 +524,20 @@ def cpu_baseline(wl, inputs, ncell_sample):
 def run_reference(args, wl):
     import oracle
     oracle.build()
+    if "count" in wl:
+        meshes = make_batch_inputs(wl)
+        batch_cpu_sample(meshes[:4], 1.0)
+        res = [batch_cpu_sample(meshes, args.ref_seconds) for _ in range(args.steps)]
+        v = sum(c for c, _ in res) / sum(t for _, t in res)
+        ms = 1e3 * sum(t for _, t in res) / len(res)
+        return {"impl": "reference", "metric": METRIC_BATCH, "value": v, "unit": "cells/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "reference": "CPU FP64 oracle (plain C), first meshes of the "
+                                                                "batch per step (bounded time)"},
+                "cpu_baseline": {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"first meshes of the batch, about {args.ref_seconds} s per step"},
+                "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     inputs = make_inputs(wl)
     ns = args.ref_cells
     for _ in range(args.warmup):
@@ -362,6 +565,7 @@ def main():
     ap.add_argument("--precision", default="f32x2", choices=["fp64", "f32x2"])
     ap.add_argument("--cpu-cells", type=int, default=65536, help="oracle sample size for cpu_baseline")
     ap.add_argument("--ref-cells", type=int, default=8192, help="oracle sample per step for --impl reference")
+    ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle seconds per step (batch workload)")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size (profiling on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -369,7 +573,10 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     wl = dict(WORKLOADS[args.workload])
-    if args.n:
+    if args.n and "count" in wl:
+        wl["count"] = args.n
+        wl["name"] = f"{wl['name']} [count overridden to {args.n}]"
+    elif args.n:
         wl["n"] = args.n
         wl["name"] = f"{wl['name']} [n overridden to {args.n}]"
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -383,9 +590,20 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
-    out, inputs = run_ours(args, wl, rank, world)
+    if "count" in wl:
+        out, meshes = run_batch(args, wl, rank, world)
+    else:
+        out, inputs = run_ours(args, wl, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and "count" in wl:
+            import oracle
+            oracle.build()
+            batch_cpu_sample(meshes[:4], 1.0)
+            cells, dt = batch_cpu_sample(meshes, 15.0)
+            out["cpu_baseline"] = {"value": cells / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"first meshes of the batch ({cells} cells: sparsity + CSR + RHS), "
+                                             f"{dt:.1f} s on 1 host core"}
+        elif world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(wl, inputs, min(args.cpu_cells, inputs[0].ncell))
         print(json.dumps(out))
     if world > 1:

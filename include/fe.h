@@ -229,6 +229,33 @@ fe_status fe_action(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat 
                     int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
                     int ncoeffs, const fe_sparsity *sp);
 
+/* ---------------------------------------------------------------- batches of meshes
+ * Many independent problems assembled together (the fixed per-par_loop overhead the paper
+ * identifies as the limit of strong scaling, Sec. 6.4.2, paid once for the whole batch).  Each
+ * item is one Mat (bilinear kmat, push) with an optional right-hand side (kvec = f v dx with f in
+ * the same space, coefficient f): Mass, Laplace or Helmholtz on P1 or P2 triangles, FP64 or
+ * double-float.  The batch owns one contiguous buffer of all items' CSR values and one of all
+ * right-hand sides (views by fe_batch_values).  fe_batch_assemble zeroes both and assembles every
+ * item in one persistent launch: CTAs take (item, cell range) tiles from a device work counter.
+ * use_graph != 0 captures the two launches once into a CUDA graph on the context stream and
+ * replays it.  fe_batch_tune times tile sizes and grid sizes on the batch (synchronising) and keeps
+ * the fastest.  Errors: FE_EUNSUPPORTED (element/form/precision), FE_EINVAL, FE_ENOMEM, FE_ECUDA. */
+typedef struct fe_batch fe_batch;
+typedef struct {
+  fe_kernel *kmat;        /* bilinear form (its strategy is ignored: push)                   */
+  fe_kernel *kvec;        /* FE_FORM_SOURCE with coeff_degree = degree, or NULL               */
+  fe_set *cells;
+  fe_sparsity *sp;        /* built from (map, map) of this item                               */
+  fe_dat *coords;         /* dim-2 vertex coordinates                                         */
+  fe_map *coord_map;      /* cells -> vertices, arity 3                                       */
+  fe_arg f;               /* coefficient of the linear form (ignored if kvec is NULL)         */
+} fe_batch_item;
+fe_status fe_batch_create(fe_ctx *ctx, int nitems, const fe_batch_item *items, fe_batch **out);
+fe_status fe_batch_values(const fe_batch *b, int item, double **values, int64_t *nnz, double **rhs, int64_t *nrows);
+fe_status fe_batch_tune(fe_batch *b, int reps, int *tile_cells, int *grid, float *ms_per_step);
+fe_status fe_batch_assemble(fe_batch *b, int use_graph);
+fe_status fe_batch_destroy(fe_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

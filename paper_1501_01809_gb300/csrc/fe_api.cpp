@@ -653,4 +653,54 @@ fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y
   return ok();
 }
 
+// ------------------------------------------------------------------------------------ batches
+static void *batch_alloc(fe_ctx *c, size_t n) { return dev_alloc(c, n); }
+static void batch_release(fe_ctx *c, void *p) { dev_free(c, p); }
+
+fe_status fe_batch_create(fe_ctx *c, int n, const fe_batch_item *items, fe_batch **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_batch_create: invalid context");
+  if (n < 0 || (n > 0 && !items) || !out) return fail(FE_EINVAL, "fe_batch_create: bad arguments");
+  for (int i = 0; i < n; i++) {
+    const fe_batch_item &it = items[i];
+    if (!valid(it.kmat) || it.kmat->ctx != c || (it.kvec && (!valid(it.kvec) || it.kvec->ctx != c)) ||
+        !valid(it.cells) || it.cells->ctx != c || !valid(it.sp) || it.sp->ctx != c || !valid(it.coords) ||
+        it.coords->ctx != c || !valid(it.coord_map) || it.coord_map->ctx != c ||
+        (it.kvec && (!valid(it.f.dat) || !valid(it.f.map) || it.f.dat->ctx != c || it.f.map->ctx != c)))
+      return fail(FE_EHANDLE, "fe_batch_create: item %d has an invalid handle", i);
+  }
+  DeviceGuard g(c->device);
+  fe_status st = fe::batch_create(c, n, items, batch_alloc, batch_release, out);
+  if (st != FE_OK) return fail(st, "%s", fe::batch_message()[0] ? fe::batch_message() : "fe_batch_create failed");
+  return ok();
+}
+
+fe_status fe_batch_values(const fe_batch *b, int item, double **values, int64_t *nnz, double **rhs, int64_t *nrows) {
+  if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_values: invalid batch");
+  if (fe::batch_views(b, item, values, nnz, rhs, nrows) != FE_OK) return fail(FE_EINVAL, "fe_batch_values: item %d", item);
+  return ok();
+}
+
+fe_status fe_batch_tune(fe_batch *b, int reps, int *tile_cells, int *grid, float *ms) {
+  if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_tune: invalid batch");
+  DeviceGuard g(fe::batch_ctx(b)->device);
+  fe_status st = fe::batch_tune(b, reps, tile_cells, grid, ms);
+  if (st != FE_OK) return fail(st, "%s", fe::batch_message());
+  return ok();
+}
+
+fe_status fe_batch_assemble(fe_batch *b, int use_graph) {
+  if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_assemble: invalid batch");
+  DeviceGuard g(fe::batch_ctx(b)->device);
+  fe_status st = fe::batch_assemble(b, use_graph);
+  if (st != FE_OK) return fail(st, "%s", fe::batch_message());
+  return ok();
+}
+
+fe_status fe_batch_destroy(fe_batch *b) {
+  if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_destroy: invalid batch");
+  DeviceGuard g(fe::batch_ctx(b)->device);
+  fe::batch_destroy(b, batch_release);
+  return ok();
+}
+
 }  // extern "C"

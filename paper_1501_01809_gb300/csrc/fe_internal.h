@@ -123,6 +123,17 @@ fe_status sparsity_build_noalloc(const int32_t *rmap, int ndr, const int32_t *cm
                                  int64_t nrows, int64_t ncols, int64_t *rowptr, int32_t *colidx,
                                  int64_t colidx_capacity, uint8_t *lut, int64_t *nnz_out, cudaStream_t s);
 const char *noalloc_message();
+
+// ---- batches (fe_batch.cu) ----
+fe_status batch_create(fe_ctx *c, int n, const fe_batch_item *items, void *(*alloc)(fe_ctx *, size_t),
+                       void (*release)(fe_ctx *, void *), fe_batch **out);
+bool batch_valid(const fe_batch *b);
+fe_status batch_views(const fe_batch *b, int i, double **vals, int64_t *nnz, double **rhs, int64_t *nrows);
+fe_status batch_assemble(fe_batch *b, int use_graph);
+fe_status batch_tune(fe_batch *b, int reps, int *best_tile, int *best_grid, float *best_ms);
+void batch_destroy(fe_batch *b, void (*release)(fe_ctx *, void *));
+const char *batch_message();
+fe_ctx *batch_ctx(const fe_batch *b);
 size_t noalloc_scratch_bytes();
 
 // ---- assembly ----

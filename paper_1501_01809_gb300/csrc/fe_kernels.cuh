@@ -93,13 +93,12 @@ __device__ __forceinline__ bool gather_kappa(const AsmArgs &a, int64_t e, double
 }
 
 // ---------------------------------------------------------------------------- Mat, push
+// One cell: gather, geometry, element tensor, 100 (P2 tet) FP64 atomic adds through the lookup table.
 template <int DIM, int P, int FORM, class Ops>
-__global__ void __launch_bounds__(kPushThreads) k_mat_push(const AsmArgs a) {
+__device__ __forceinline__ void mat_push_cell(const AsmArgs &a, int64_t e) {
   using T = typename Ops::T;
   using E = fe_gen::Elem<DIM, P>;
   constexpr int ND = E::ND;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
   double x[DIM + 1][DIM], kap[DIM + 1];
   int32_t v[DIM + 1], rows[ND];
   bool ok = gather_coords<DIM>(a, e, x, v);
@@ -125,6 +124,12 @@ __global__ void __launch_bounds__(kPushThreads) k_mat_push(const AsmArgs a) {
 #pragma unroll
     for (int j = 0; j < ND; j++) red_add_f64(rowv + L[i * ND + j], Kd[E::upper_index(i, j)]);
   }
+}
+
+template <int DIM, int P, int FORM, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_mat_push(const AsmArgs a) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < a.ncell) mat_push_cell<DIM, P, FORM, Ops>(a, e);
 }
 
 // ---------------------------------------------------------------------------- action, push
@@ -172,12 +177,10 @@ __global__ void __launch_bounds__(kPushThreads) k_action_push(const AsmArgs a) {
 
 // ---------------------------------------------------------------------------- vector (f v dx), push
 template <int DIM, int P, int Q, class Ops>
-__global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
+__device__ __forceinline__ void vec_push_cell(const AsmArgs &a, int64_t e) {
   using T = typename Ops::T;
   using S = fe_gen::Source<DIM, P, Q>;
   constexpr int ND = S::ND, NF = S::NF;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
   double x[DIM + 1][DIM];
   int32_t v[DIM + 1], rows[ND];
   bool ok = gather_coords<DIM>(a, e, x, v);
@@ -204,6 +207,12 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
   S::template vec<Ops>(vol, fe, b);
 #pragma unroll
   for (int i = 0; i < ND; i++) red_add_f64(a.y + rows[i], Ops::to_f64(b[i]));
+}
+
+template <int DIM, int P, int Q, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < a.ncell) vec_push_cell<DIM, P, Q, Ops>(a, e);
 }
 
 // ---------------------------------------------------------------------------- staged pull

@@ -28,7 +28,8 @@ SYMBOLS = [
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
     "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
-    "fe_assemble_mat", "fe_assemble_vec", "fe_action",
+    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
+    "fe_batch_assemble", "fe_batch_destroy",
 ]
 
 
@@ -45,6 +46,11 @@ class fe_form_desc(C.Structure):
 
 class fe_arg(C.Structure):
     _fields_ = [("dat", C.c_void_p), ("map", C.c_void_p)]
+
+
+class fe_batch_item(C.Structure):
+    _fields_ = [("kmat", C.c_void_p), ("kvec", C.c_void_p), ("cells", C.c_void_p), ("sp", C.c_void_p),
+                ("coords", C.c_void_p), ("coord_map", C.c_void_p), ("f", fe_arg)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -85,6 +91,10 @@ def load():
         "fe_assemble_mat": (I, [P, P, P, P, I, P, P, C.POINTER(fe_arg), I]),
         "fe_assemble_vec": (I, [P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
         "fe_action": (I, [P, P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
+        "fe_batch_create": (I, [P, I, C.POINTER(fe_batch_item), PP]),
+        "fe_batch_values": (I, [P, I, PP, C.POINTER(I64), PP, C.POINTER(I64)]),
+        "fe_batch_tune": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_float)]),
+        "fe_batch_assemble": (I, [P, I]), "fe_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -171,6 +181,10 @@ class Mat(Handle):
 
 class Kernel(Handle):
     _destroy = "fe_kernel_destroy"
+
+
+class Batch(Handle):
+    _destroy = "fe_batch_destroy"
 
 
 def _torch_alloc(nbytes, user):
@@ -368,3 +382,55 @@ def action(ctx: Ctx, k: Kernel, cells: Set, x: Dat, y: Dat, map_: Map, coords: D
     arr, n = _args(coeffs)
     _check(load().fe_action(ctx.ptr, k.ptr, cells.ptr, x.ptr, y.ptr, map_.ptr, int(bool(zero_first)),
                             coords.ptr, coord_map.ptr, arr, n, sp.ptr if sp is not None else None))
+
+
+def batch_create(ctx: Ctx, items) -> Batch:
+    """fe_batch_create: items = [dict(kmat=, kvec=None, cells=, sp=, coords=, coord_map=, f=(Dat, Map) or None)]."""
+    arr = (fe_batch_item * max(1, len(items)))()
+    keep = []
+    for i, it in enumerate(items):
+        f = it.get("f")
+        arr[i].kmat = it["kmat"].ptr
+        arr[i].kvec = it["kvec"].ptr if it.get("kvec") is not None else None
+        arr[i].cells, arr[i].sp = it["cells"].ptr, it["sp"].ptr
+        arr[i].coords, arr[i].coord_map = it["coords"].ptr, it["coord_map"].ptr
+        if f is not None:
+            arr[i].f.dat, arr[i].f.map = f[0].ptr, f[1].ptr
+        keep.append(it)
+    out = C.c_void_p()
+    _check(load().fe_batch_create(ctx.ptr, len(items), arr, C.byref(out)))
+    return Batch(out, ctx, keep=(keep,))
+
+
+def batch_values(b: Batch, item: int):
+    """(values view [nnz] float64, rhs view [nrows] float64) of one item."""
+    v, r = C.c_void_p(), C.c_void_p()
+    nnz, nr = C.c_int64(), C.c_int64()
+    _check(load().fe_batch_values(b.ptr, int(item), C.byref(v), C.byref(nnz), C.byref(r), C.byref(nr)))
+    dev = torch.device("cuda", b.ctx.device)
+    return _view(v.value, nnz.value, torch.float64, b, dev), _view(r.value, nr.value, torch.float64, b, dev)
+
+
+def batch_tune(b: Batch, reps: int = 3):
+    t, g, ms = C.c_int(), C.c_int(), C.c_float()
+    _check(load().fe_batch_tune(b.ptr, int(reps), C.byref(t), C.byref(g), C.byref(ms)))
+    return t.value, g.value, ms.value
+
+
+def batch_assemble(b: Batch, use_graph: bool = True) -> None:
+    _check(load().fe_batch_assemble(b.ptr, int(bool(use_graph))))
+
+
+def batch_buffers(b: Batch):
+    """(all CSR values, all right-hand sides) of the batch as two flat views, items back to back."""
+    lib, n = load(), len(b._keep[0]) if b._keep else 0
+    dev = torch.device("cuda", b.ctx.device)
+    if n == 0:
+        return torch.empty(0, dtype=torch.float64, device=dev), torch.empty(0, dtype=torch.float64, device=dev)
+    v0, r0, vl, rl = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    nnz, nr = C.c_int64(), C.c_int64()
+    _check(lib.fe_batch_values(b.ptr, 0, C.byref(v0), None, C.byref(r0), None))
+    _check(lib.fe_batch_values(b.ptr, n - 1, C.byref(vl), C.byref(nnz), C.byref(rl), C.byref(nr)))
+    nv = (vl.value - v0.value) // 8 + nnz.value
+    nrr = (rl.value - r0.value) // 8 + nr.value
+    return _view(v0.value, nv, torch.float64, b, dev), _view(r0.value, nrr, torch.float64, b, dev)

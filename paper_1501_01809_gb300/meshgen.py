@@ -175,13 +175,12 @@ def lagrange_nodes(dim: int, p: int) -> np.ndarray:
 
 def cell_node_map(mesh: Mesh, p: int) -> tuple[np.ndarray, int]:
     """Cell -> P_p node map ``[ncell, nd]`` int32 and the number of nodes ``(p n + 1)^dim``."""
-    alpha = lagrange_nodes(mesh.dim, p)                                       # [nd, d+1]
-    vg = mesh.vgrid[mesh.cell_vertex]                                         # [ncell, d+1, d]
-    fine = np.einsum("km,cmx->ckx", alpha, vg)                                # [ncell, nd, d]
+    alpha = lagrange_nodes(mesh.dim, p).astype(np.int64)                      # [nd, d+1]
     m = p * mesh.n + 1
-    ids = fine[..., 0] + m * fine[..., 1]
-    if mesh.dim == 3:
-        ids = ids + m * m * fine[..., 2]
+    # node k of a cell sits at fine-grid point sum_v alpha[k, v] * vgrid[v]; its id is linear in it
+    w = m ** np.arange(mesh.dim, dtype=np.int64)                              # [d]
+    vid = mesh.vgrid.astype(np.int64) @ w                                     # fine-grid id / p per vertex
+    ids = vid[mesh.cell_vertex] @ alpha.T                                     # [ncell, nd]
     return ids.astype(np.int32), m ** mesh.dim
 
 

@@ -117,3 +117,32 @@ def assert_close_scaled(got, want, scale, rtol=1e-12, what=""):
     nrm = np.linalg.norm(want)
     if nrm > 0:
         assert np.linalg.norm(got - want) <= rtol * nrm, what
+
+
+class GpuBatch:
+    """Several problems in one context, batched: bilinear form `forms[i]` plus f v dx with f in the
+    same space (f = uniform_dat(nnodes, seed + i))."""
+
+    def __init__(self, problems, forms, precisions, seed=11):
+        import torch
+        from paper_1501_01809_gb300 import fe
+        self.fe, self.torch = fe, torch
+        self.ctx = fe.ctx_create(0)
+        self.gp = [GpuProblem(pr, ctx=self.ctx) for pr in problems]
+        self.problems, self.forms, self.precisions = problems, forms, precisions
+        self.f = [np.random.default_rng(seed + i).uniform(-1, 1, pr.nnodes) for i, pr in enumerate(problems)]
+        items = []
+        self._keep = []
+        for g, pr, form, prec, f in zip(self.gp, problems, forms, precisions, self.f):
+            kmat = fe.kernel_create(self.ctx, form, pr.dim, pr.p, precision=prec)
+            kvec = fe.kernel_create(self.ctx, fe.FORM_SOURCE, pr.dim, pr.p, coeff_degree=pr.p, precision=prec)
+            tf = torch.from_numpy(f).cuda()
+            F = fe.dat_create(self.ctx, g.nodes, tf)
+            self._keep += [kmat, kvec, tf, F]
+            items.append(dict(kmat=kmat, kvec=kvec, cells=g.cells, sp=g.sparsity(), coords=g.coords,
+                              coord_map=g.coord_map, f=(F, g.map)))
+        self.batch = fe.batch_create(self.ctx, items)
+
+    def results(self, i):
+        v, r = self.fe.batch_values(self.batch, i)
+        return v.cpu().numpy(), r.cpu().numpy()
