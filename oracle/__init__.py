@@ -64,6 +64,10 @@ def _load():
                                          _f64p]
     lib.oracle_eval_function.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, _i32p, _f64p, _i32p,
                                          _f64p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.oracle_dirichlet_apply.argtypes = [C.c_int64, _i64p, _i32p, _f64p, _f64p,
+                                           np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS"), C.c_void_p]
+    lib.oracle_cg_jacobi.argtypes = [C.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, C.c_double, C.c_int,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
     _lib = lib
     return lib
 
@@ -206,3 +210,23 @@ def eval_function(dim, p, qdeg, cmap, coords, coord_map, u):
     xq, wq, uq = np.zeros(ncell * nq * dim), np.zeros(ncell * nq), np.zeros(ncell * nq)
     lib.oracle_eval_function(*args, xq.ctypes.data, wq.ctypes.data, uq.ctypes.data)
     return xq.reshape(-1, dim), wq, uq
+
+
+def dirichlet_apply(rowptr, colidx, vals, b, is_bc, g=None):
+    """Symmetric elimination of u = g on the rows flagged in is_bc; returns new (vals, b)."""
+    vals = np.array(vals, dtype=np.float64, copy=True)
+    b = np.array(b, dtype=np.float64, copy=True)
+    gk = None if g is None else _c(g, np.float64)
+    _load().oracle_dirichlet_apply(b.size, _c(rowptr, np.int64), _c(colidx, np.int32), vals, b,
+                                   _c(is_bc, np.uint8), None if gk is None else gk.ctypes.data)
+    return vals, b
+
+
+def cg_jacobi(rowptr, colidx, vals, b, x0=None, rtol=1e-8, maxit=100000):
+    """Jacobi-preconditioned CG; returns (x, iterations, ||r||, ||b||). iterations = -1: not SPD."""
+    b = _c(b, np.float64)
+    x = np.zeros(b.size) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    rn, bn = C.c_double(), C.c_double()
+    it = _load().oracle_cg_jacobi(b.size, _c(rowptr, np.int64), _c(colidx, np.int32), _c(vals, np.float64), b, x,
+                                  float(rtol), int(maxit), C.byref(rn), C.byref(bn))
+    return x, it, rn.value, bn.value

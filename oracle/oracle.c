@@ -5,7 +5,8 @@
  * the INC access descriptor and staging in/out (Sec. 4.4.1), Mats assembled through a
  * pair of maps (Sec. 4.4.3), and the forms of the Poisson listing (Sec. 3.1, Listing 1:
  * a = inner(grad u, grad v) dx, L = f v dx) extended by a mass term (Helmholtz) and a
- * P1 coefficient kappa (diffusion).
+ * P1 coefficient kappa (diffusion); for solves, strong Dirichlet conditions by symmetric
+ * elimination (Sec. 3.1) and Jacobi-preconditioned conjugate gradients (Sec. 6.2).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the benchmark's
  * CPU-baseline leg may load this library.  It shares no code, header, table or constant
@@ -607,4 +608,108 @@ int oracle_eval_function(int dim, int p, int qdeg, int64_t ncell, const int32_t 
         }
     }
     return nq;
+}
+
+/*
+ * Strong Dirichlet conditions u = g on the boundary nodes, applied to an assembled system by
+ * symmetric elimination (the Poisson listing of Sec. 3.1 assembles A and b "with the boundary
+ * conditions applied"; Sec. 6.2 states u = 0 on Gamma_D).  Written out from the definition:
+ * for every row i that is not a boundary row, b_i <- b_i - sum_{j boundary} A_ij g_j and
+ * A_ij <- 0 for boundary j; for every boundary row i, A_ij <- delta_ij and b_i <- g_i.
+ * Rows are processed in order, entries of a row in CSR order.  g == NULL means g = 0.
+ */
+void oracle_dirichlet_apply(int64_t nrows, const int64_t *rowptr, const int32_t *colidx, double *vals, double *b,
+                            const uint8_t *is_bc, const double *g) {
+    for (int64_t i = 0; i < nrows; i++) {
+        if (is_bc[i]) {
+            for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) vals[k] = (colidx[k] == i) ? 1.0 : 0.0;
+            b[i] = g ? g[i] : 0.0;
+            continue;
+        }
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            int32_t j = colidx[k];
+            if (!is_bc[j]) continue;
+            double gj = g ? g[j] : 0.0;
+            if (g_mutation == 6) b[i] += vals[k] * gj; /* planted mistake: lift with the wrong sign */
+            else b[i] -= vals[k] * gj;
+            if (g_mutation != 7) vals[k] = 0.0; /* planted mistake (7): keep the boundary columns */
+        }
+    }
+}
+
+/* y = A x for a CSR matrix, entries of a row in CSR order */
+static void csr_matvec(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *vals, const double *x,
+                       double *y) {
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++) s += vals[k] * x[colidx[k]];
+        y[i] = s;
+    }
+}
+
+static double dot(int64_t n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/*
+ * Conjugate gradients (Hestenes and Stiefel, the solver the Poisson experiment of Sec. 6.2 uses)
+ * with the Jacobi preconditioner M = diag(A), in the textbook order:
+ *   r = b - A x, z = M^-1 r, p = z, rz = r.z
+ *   while ||r|| > rtol ||b|| and it < maxit:
+ *     q = A p; alpha = rz / p.q; x += alpha p; r -= alpha q; z = M^-1 r;
+ *     rz' = r.z; beta = rz' / rz; p = z + beta p; rz = rz'; it++
+ * x holds the initial guess on entry and the iterate on return.  Returns the number of
+ * iterations, or -1 when a diagonal entry is not positive or p.q <= 0 (A not SPD);
+ * *rnorm = ||r|| and *bnorm = ||b|| (2-norms, every dot product a plain ordered sum in FP64).
+ */
+int oracle_cg_jacobi(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *vals, const double *b,
+                     double *x, double rtol, int maxit, double *rnorm, double *bnorm) {
+    double *r = malloc(sizeof(double) * (n > 0 ? n : 1)), *z = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *p = malloc(sizeof(double) * (n > 0 ? n : 1)), *q = malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *dinv = malloc(sizeof(double) * (n > 0 ? n : 1));
+    int it = 0, bad = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double d = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++)
+            if (colidx[k] == i) d = vals[k];
+        if (!(d > 0.0)) bad = 1;
+        dinv[i] = 1.0 / d;
+    }
+    csr_matvec(n, rowptr, colidx, vals, x, q);
+    for (int64_t i = 0; i < n; i++) {
+        r[i] = b[i] - q[i];
+        z[i] = dinv[i] * r[i];
+        p[i] = z[i];
+    }
+    double rz = dot(n, r, z), bn = sqrt(dot(n, b, b)), rn = sqrt(dot(n, r, r));
+    while (!bad && rn > rtol * bn && it < maxit) {
+        csr_matvec(n, rowptr, colidx, vals, p, q);
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0)) {
+            bad = 1;
+            break;
+        }
+        double alpha = (g_mutation == 9 ? dot(n, r, r) : rz) / pq; /* planted mistake (9): r.r for r.z */
+        for (int64_t i = 0; i < n; i++) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            z[i] = dinv[i] * r[i];
+        }
+        double rz1 = dot(n, r, z);
+        double beta = rz1 / rz;
+        for (int64_t i = 0; i < n; i++) p[i] = (g_mutation == 8 ? r[i] : z[i]) + beta * p[i]; /* (8): r for z */
+        rz = rz1;
+        rn = sqrt(dot(n, r, r));
+        it++;
+    }
+    *rnorm = rn;
+    *bnorm = bn;
+    free(r);
+    free(z);
+    free(p);
+    free(q);
+    free(dinv);
+    return bad ? -1 : it;
 }

@@ -36,7 +36,8 @@ import numpy as np
 
 __all__ = [
     "Mesh", "unit_square_mesh", "unit_cube_mesh", "lagrange_nodes", "cell_node_map",
-    "node_coordinates", "uniform_dat", "lognormal_dat", "batch_mesh_sizes",
+    "node_coordinates", "uniform_dat", "lognormal_dat", "batch_mesh_sizes", "boundary_nodes",
+    "manufactured_sine", "serve_requests",
 ]
 
 
@@ -211,3 +212,38 @@ def batch_mesh_sizes(count: int, seed: int, lo: int = 8, hi: int = 256) -> tuple
     n = np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))).astype(np.int64)
     p = 1 + (rng.uniform(size=count) < 0.5).astype(np.int64)
     return n, p
+
+
+def boundary_nodes(mesh: Mesh, p: int) -> np.ndarray:
+    """uint8 mask over the P_p nodes: 1 where the node lies on the boundary of [0,1]^dim.
+
+    Node ids enumerate the fine lattice (p n + 1)^dim with x fastest, so the test is exact
+    integer arithmetic on the lattice index."""
+    m = p * mesh.n + 1
+    ids = np.arange(m ** mesh.dim, dtype=np.int64)
+    on = np.zeros(ids.size, dtype=bool)
+    for _ in range(mesh.dim):
+        c = ids % m
+        on |= (c == 0) | (c == m - 1)
+        ids //= m
+    return on.astype(np.uint8)
+
+
+def manufactured_sine(mesh: Mesh, p: int, k: int, m: int) -> tuple[np.ndarray, np.ndarray]:
+    """Nodal values of u = sin(k pi x) sin(m pi y) and of f = (k^2 + m^2) pi^2 u at the P_p nodes of
+    a triangle mesh (-lap u = f in the unit square, u = 0 on its boundary)."""
+    X = node_coordinates(mesh, p)
+    u = np.sin(k * np.pi * X[:, 0]) * np.sin(m * np.pi * X[:, 1])
+    return (k * k + m * m) * np.pi ** 2 * u, u
+
+
+def serve_requests(count: int, seed: int, rate: float, lo: int = 16, hi: int = 512):
+    """Poisson-process arrivals (exponential gaps, mean 1/rate seconds) of solve requests:
+    (arrival_s, n log-uniform in [lo, hi], degree P1/P2 with probability 1/2, k, m uniform in 1..4)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count)) if rate > 0 else np.zeros(count)
+    n = np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))).astype(np.int64)
+    p = 1 + (rng.uniform(size=count) < 0.5).astype(np.int64)
+    k = rng.integers(1, 5, size=count)
+    mm = rng.integers(1, 5, size=count)
+    return [(float(t[i]), int(n[i]), int(p[i]), int(k[i]), int(mm[i])) for i in range(count)]

@@ -2,13 +2,16 @@
 
 The oracle has a test-only switch that introduces one plausible mistake at a time: a dropped
 mass term, a transposed Jacobian inverse, a signed determinant, two swapped local nodes, a
-dropped Duffy factor in the quadrature.  Each must make some pin fail; otherwise the pins
+dropped Duffy factor in the quadrature, a Dirichlet lift with the wrong sign, boundary columns
+left in place, a CG search direction built from the unpreconditioned residual, a CG step length
+from r.r instead of r.z.  Each must make some pin fail; otherwise the pins
 would not be strong enough to trust the oracle.
 """
 import pytest
 
 import oracle as O
 from tests import test_oracle_pins as P
+from tests import test_oracle_solve as S
 
 PINS = [
     ("reference_elements", lambda: P.pin_reference_elements()),
@@ -18,11 +21,18 @@ PINS = [
     ("poly_repro_3d_p2", lambda: P.pin_polynomial_reproduction(3, 2, 2, 0.2)),
     ("exact_rational_3d_p2", lambda: P.pin_exact_rational(3, 2, 1)),
     ("quadrature_2d", lambda: P.pin_quadrature_monomials(2, 4)),
+    ("reduced_system", lambda: S.pin_reduced_system()),
+    ("harmonic_p2", lambda: S.pin_harmonic_reproduction(2)),
+    ("cg_dense_spd", lambda: S.pin_cg_dense_spd()),
+    ("cg_diagonal", lambda: S.pin_cg_diagonal()),
 ]
 
 
 @pytest.mark.parametrize("code,what", [(1, "drop mass term"), (2, "transposed J^-1"), (3, "signed detJ"),
-                                       (4, "swapped edge nodes"), (5, "dropped Duffy factor")])
+                                       (4, "swapped edge nodes"), (5, "dropped Duffy factor"),
+                                       (6, "Dirichlet lift with the wrong sign"),
+                                       (7, "boundary columns kept"), (8, "CG direction from r, not z"),
+                                       (9, "CG step length from r.r")])
 def test_planted_mistake_is_caught(code, what):
     O.set_mutation(code)
     caught = []
