@@ -256,6 +256,98 @@ fe_status fe_batch_tune(fe_batch *b, int reps, int *tile_cells, int *grid, float
 fe_status fe_batch_assemble(fe_batch *b, int use_graph);
 fe_status fe_batch_destroy(fe_batch *b);
 
+/* ---------------------------------------------------------------- boundary conditions
+ * Strong Dirichlet conditions u = g on the rows flagged in is_bc, by symmetric elimination of the
+ * assembled system (the Poisson listing of Sec. 3.1 assembles A and b with its boundary condition
+ * applied; Sec. 6.2 states u = 0 on the Dirichlet boundary).  For every row i not flagged,
+ * b_i -= sum over flagged j of A_ij g_j and A_ij = 0 for flagged j; every flagged row becomes the
+ * identity row with b_i = g_i.  A must be square (built from (map, map)); b a scalar Dat on its
+ * rows.  is_bc: device uint8[nrows] (non-zero = boundary).  g: device double[nrows], or NULL for
+ * g = 0.  One thread per row; deterministic.  Enqueued on the context stream. */
+fe_status fe_dirichlet_apply(fe_ctx *ctx, fe_mat *A, fe_dat *b, const uint8_t *is_bc, const double *g);
+
+/* ---------------------------------------------------------------- batched Jacobi-CG
+ * Conjugate gradients with the Jacobi preconditioner M = diag(A) (the Poisson experiment of
+ * Sec. 6.2 solves with CG) for many independent SPD CSR systems at once: every fe_cg_iterate runs
+ * `iters` iterations of all added, unfinished systems with two persistent launches per iteration
+ * (captured once into a CUDA graph when use_graph != 0, replayed on the context stream).  Dot
+ * products are FP64 sums over fixed tiles of 1024 rows added in tile order (Globals with SUM
+ * access, Sec. 4.4.2), so a system's iterates are bitwise the same alone or beside others.
+ * Stopping test after every iteration: ||r||_2 <= rtol ||b||_2, or maxit iterations.
+ * fe_cg_add reads A (values and pattern) and b, and updates x (initial guess on entry, iterate
+ * after each call) in place; A, b and x must stay alive until fe_cg_remove.  fe_cg_poll
+ * synchronises the context stream and reports, for slots 0..nslots-1: status (FE_CG_* below,
+ * -1 for a free slot), iterations, ||r|| and ||b||.  fe_cg_remove synchronises, then frees the
+ * slot's vectors.  Errors: FE_EINVAL (no free slot, bad sizes), FE_ENOMEM, FE_ECUDA. */
+#define FE_CG_RUNNING 0
+#define FE_CG_CONVERGED 1
+#define FE_CG_MAXIT 2
+#define FE_CG_BREAKDOWN 3   /* a diagonal entry or p.Ap not positive: A is not SPD */
+typedef struct fe_cg fe_cg;
+fe_status fe_cg_create(fe_ctx *ctx, int max_systems, fe_cg **out);
+fe_status fe_cg_add(fe_cg *cg, fe_mat *A, fe_dat *b, fe_dat *x, double rtol, int maxit, int *slot);
+fe_status fe_cg_iterate(fe_cg *cg, int iters, int use_graph);
+fe_status fe_cg_poll(fe_cg *cg, int nslots, int *status, int *iters, double *rnorm, double *bnorm);
+fe_status fe_cg_remove(fe_cg *cg, int slot);
+fe_status fe_cg_destroy(fe_cg *cg);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop for Poisson solves on triangle meshes: -lap u = f, u = 0 on the flagged nodes;
+ * a = inner(grad u, grad v) dx and L = f v dx (f given by its P_p nodal values) assembled with the
+ * deterministic pull strategy, Dirichlet elimination, then Jacobi-CG.  fe_server_run processes
+ * every submitted request: it admits requests in arrival order (arrival_s seconds after the call
+ * starts) while fewer than max_active are iterating and the request's worst-case device footprint
+ * fits beside what is held within hbm_budget; it advances all admitted systems together
+ * (iters_per_tick CG iterations between status polls); a converged system's solution is copied to
+ * x_out and all its device memory is freed at once.  A request whose footprint alone exceeds the
+ * budget is refused.  max_active = 1 gives the plain one-request-at-a-time path with the same
+ * kernels.  Host arrays of a request must stay valid until fe_server_run returns.  Device memory
+ * is drawn from the context's allocator and counted exactly (fe_server_stats). */
+#define FE_SOLVE_PENDING 0
+#define FE_SOLVE_CONVERGED 1
+#define FE_SOLVE_MAXIT 2
+#define FE_SOLVE_BREAKDOWN 3
+#define FE_SOLVE_REFUSED 4
+typedef struct fe_server fe_server;
+typedef struct {
+  size_t hbm_budget;       /* bytes the server may hold on the device at once (its own tables included) */
+  int max_active;          /* systems iterating together; 1 = one request at a time                   */
+  int iters_per_tick;      /* CG iterations between status polls                                        */
+  double rtol;             /* relative residual tolerance                                               */
+  int maxit;
+  int precision;           /* element tensors: FE_PREC_FP64 or FE_PREC_F32X2                            */
+} fe_server_config;
+typedef struct {
+  int degree;              /* 1 or 2                                                                    */
+  int64_t ncell, nnodes, nvert;
+  const int32_t *cell_node;   /* host [ncell][(p+1)(p+2)/2]                                             */
+  const int32_t *cell_vertex; /* host [ncell][3]                                                        */
+  const double *coords;       /* host [nvert][2]                                                        */
+  const double *f;            /* host [nnodes] nodal values of the source                               */
+  const uint8_t *is_bc;       /* host [nnodes], non-zero on the Dirichlet boundary                      */
+  double *x_out;              /* host [nnodes], the solution on completion                              */
+  double arrival_s;           /* seconds after fe_server_run starts                                     */
+} fe_solve_request;
+typedef struct {
+  int status;              /* FE_SOLVE_*                                                                */
+  int iters;
+  double rnorm, bnorm;
+  double admitted_s, finished_s;   /* seconds after fe_server_run started                               */
+  size_t bytes;            /* device bytes held while the request was iterating                         */
+  size_t estimate;         /* worst-case footprint charged at admission (bounds the bytes held while built) */
+} fe_solve_result;
+typedef struct {
+  size_t peak_bytes, live_bytes, base_bytes;
+  int submitted, converged, refused, estimate_misses;
+  double run_s;
+} fe_server_stats;
+fe_status fe_server_create(fe_ctx *ctx, const fe_server_config *cfg, fe_server **out);
+fe_status fe_server_submit(fe_server *srv, const fe_solve_request *req, int64_t *id);
+fe_status fe_server_run(fe_server *srv);
+fe_status fe_server_result(const fe_server *srv, int64_t id, fe_solve_result *out);
+fe_status fe_server_stats_get(const fe_server *srv, fe_server_stats *out);
+fe_status fe_server_destroy(fe_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,29 @@
 
 #include "fe_internal.h"
 
+namespace fe {
+// Device memory through the context's allocator (cudaMalloc when none is set), 256-byte granules.
+void *dev_alloc(fe_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (c->alloc) return c->alloc(bytes, c->user);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(fe_ctx *c, void *p) {
+  if (!p) return;
+  if (c->free_fn) c->free_fn(p, c->user);
+  else cudaFree(p);
+}
+}  // namespace fe
+using fe::dev_alloc;
+using fe::dev_free;
+
 namespace {
 
 thread_local std::string g_err;
@@ -55,23 +78,6 @@ struct DeviceGuard {
   }
 };
 
-void *dev_alloc(fe_ctx *c, size_t bytes) {
-  if (bytes == 0) bytes = 16;
-  bytes = (bytes + 255) & ~size_t(255);
-  if (c->alloc) return c->alloc(bytes, c->user);
-  void *p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return p;
-}
-
-void dev_free(fe_ctx *c, void *p) {
-  if (!p) return;
-  if (c->free_fn) c->free_fn(p, c->user);
-  else cudaFree(p);
-}
 
 // Reads and clears the device error flags (synchronises the stream).
 fe_status check_device_flags(fe_ctx *c, const char *where) {
@@ -373,6 +379,7 @@ fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
   if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_rebuild: invalid sparsity");
   fe_ctx *c = sp->ctx;
   DeviceGuard g(c->device);
+  if (!sp->coltmp) return fail(FE_EINVAL, "fe_sparsity_rebuild: the pattern's build scratch was released");
   FE_CHECK_CUDA(fe::sparsity_incidence(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_rows(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_compact(sp, c->stream, c->d_err, 1), "fe_sparsity_rebuild");
@@ -700,6 +707,124 @@ fe_status fe_batch_destroy(fe_batch *b) {
   if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_destroy: invalid batch");
   DeviceGuard g(fe::batch_ctx(b)->device);
   fe::batch_destroy(b, batch_release);
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Dirichlet
+fe_status fe_dirichlet_apply(fe_ctx *c, fe_mat *A, fe_dat *b, const uint8_t *is_bc, const double *g) {
+  const char *who = "fe_dirichlet_apply";
+  if (!valid(c)) return fail(FE_EHANDLE, "%s: invalid context", who);
+  if (!valid(A) || A->ctx != c || !valid(b) || b->ctx != c) return fail(FE_EHANDLE, "%s: invalid mat or dat", who);
+  const fe_sparsity *sp = A->sp;
+  if (sp->rmap != sp->cmap || sp->nrows != sp->ncols) return fail(FE_EINVAL, "%s: A must be square", who);
+  if (b->set != sp->rmap->to || b->dim != 1) return fail(FE_EINVAL, "%s: b must be a scalar Dat on A's rows", who);
+  if (sp->nrows > 0 && !is_bc) return fail(FE_EINVAL, "%s: is_bc is NULL", who);
+  DeviceGuard gd(c->device);
+  FE_CHECK_CUDA(fe::launch_dirichlet(sp->nrows, sp->rowptr, sp->colidx, A->values, b->data, is_bc, g, c->stream), who);
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ CG
+fe_status fe_cg_create(fe_ctx *c, int max_systems, fe_cg **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_cg_create: invalid context");
+  if (max_systems < 1 || max_systems > (1 << 20) || !out) return fail(FE_EINVAL, "fe_cg_create: bad arguments");
+  DeviceGuard g(c->device);
+  fe_status st = fe::cg_create(c, max_systems, out);
+  if (st != FE_OK) return fail(st, "%s", fe::solve_message()[0] ? fe::solve_message() : "fe_cg_create failed");
+  return ok();
+}
+
+fe_status fe_cg_add(fe_cg *cg, fe_mat *A, fe_dat *b, fe_dat *x, double rtol, int maxit, int *slot) {
+  const char *who = "fe_cg_add";
+  if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "%s: invalid engine", who);
+  fe_ctx *c = fe::cg_ctx(cg);
+  if (!valid(A) || A->ctx != c || !valid(b) || b->ctx != c || !valid(x) || x->ctx != c)
+    return fail(FE_EHANDLE, "%s: A, b and x must belong to the engine's context", who);
+  const fe_sparsity *sp = A->sp;
+  if (sp->rmap != sp->cmap || sp->nrows != sp->ncols) return fail(FE_EINVAL, "%s: A must be square", who);
+  if (b->set != sp->rmap->to || x->set != sp->rmap->to || b->dim != 1 || x->dim != 1 || b->data == x->data)
+    return fail(FE_EINVAL, "%s: b and x must be distinct scalar Dats on A's rows", who);
+  if (!(rtol >= 0.0) || maxit < 0 || !slot) return fail(FE_EINVAL, "%s: bad rtol, maxit or slot", who);
+  DeviceGuard g(c->device);
+  fe_status st = fe::cg_add(cg, sp->rowptr, sp->colidx, A->values, sp->nrows, b->data, x->data, rtol, maxit, slot);
+  if (st != FE_OK) return fail(st, "%s", fe::solve_message());
+  return ok();
+}
+
+fe_status fe_cg_iterate(fe_cg *cg, int iters, int use_graph) {
+  if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "fe_cg_iterate: invalid engine");
+  if (iters < 0) return fail(FE_EINVAL, "fe_cg_iterate: iters < 0");
+  DeviceGuard g(fe::cg_ctx(cg)->device);
+  fe_status st = fe::cg_iterate(cg, iters, use_graph);
+  if (st != FE_OK) return fail(st, "%s", fe::solve_message());
+  return ok();
+}
+
+fe_status fe_cg_poll(fe_cg *cg, int nslots, int *status, int *iters, double *rnorm, double *bnorm) {
+  if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "fe_cg_poll: invalid engine");
+  DeviceGuard g(fe::cg_ctx(cg)->device);
+  fe_status st = fe::cg_poll(cg, nslots, status, iters, rnorm, bnorm);
+  if (st != FE_OK) return fail(st, "%s", fe::solve_message());
+  return ok();
+}
+
+fe_status fe_cg_remove(fe_cg *cg, int slot) {
+  if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "fe_cg_remove: invalid engine");
+  DeviceGuard g(fe::cg_ctx(cg)->device);
+  fe_status st = fe::cg_remove(cg, slot);
+  if (st != FE_OK) return fail(st, "%s", fe::solve_message());
+  return ok();
+}
+
+fe_status fe_cg_destroy(fe_cg *cg) {
+  if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "fe_cg_destroy: invalid engine");
+  DeviceGuard g(fe::cg_ctx(cg)->device);
+  fe::cg_destroy(cg);
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ serving
+fe_status fe_server_create(fe_ctx *c, const fe_server_config *cfg, fe_server **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_server_create: invalid context");
+  if (!cfg || !out) return fail(FE_EINVAL, "fe_server_create: bad arguments");
+  DeviceGuard g(c->device);
+  fe_status st = fe::server_create(c, cfg, out);
+  if (st != FE_OK) return fail(st, "%s", fe::server_message());
+  return ok();
+}
+
+fe_status fe_server_submit(fe_server *srv, const fe_solve_request *req, int64_t *id) {
+  if (!fe::server_valid(srv)) return fail(FE_EHANDLE, "fe_server_submit: invalid server");
+  if (!req) return fail(FE_EINVAL, "fe_server_submit: req is NULL");
+  fe_status st = fe::server_submit(srv, req, id);
+  if (st != FE_OK) return fail(st, "%s", fe::server_message());
+  return ok();
+}
+
+fe_status fe_server_run(fe_server *srv) {
+  if (!fe::server_valid(srv)) return fail(FE_EHANDLE, "fe_server_run: invalid server");
+  DeviceGuard g(fe::server_ctx(srv)->device);
+  fe_status st = fe::server_run(srv);
+  if (st != FE_OK) return fail(st, "%s", fe::server_message());
+  return ok();
+}
+
+fe_status fe_server_result(const fe_server *srv, int64_t id, fe_solve_result *out) {
+  if (!fe::server_valid(srv)) return fail(FE_EHANDLE, "fe_server_result: invalid server");
+  if (!out || fe::server_result(srv, id, out) != FE_OK) return fail(FE_EINVAL, "fe_server_result: no request %lld", (long long)id);
+  return ok();
+}
+
+fe_status fe_server_stats_get(const fe_server *srv, fe_server_stats *out) {
+  if (!fe::server_valid(srv)) return fail(FE_EHANDLE, "fe_server_stats_get: invalid server");
+  if (!out) return fail(FE_EINVAL, "fe_server_stats_get: out is NULL");
+  return fe::server_stats(srv, out) == FE_OK ? ok() : fail(FE_EINVAL, "fe_server_stats_get failed");
+}
+
+fe_status fe_server_destroy(fe_server *srv) {
+  if (!fe::server_valid(srv)) return fail(FE_EHANDLE, "fe_server_destroy: invalid server");
+  DeviceGuard g(fe::server_ctx(srv)->device);
+  fe::server_destroy(srv);
   return ok();
 }
 

@@ -124,6 +124,10 @@ fe_status sparsity_build_noalloc(const int32_t *rmap, int ndr, const int32_t *cm
                                  int64_t colidx_capacity, uint8_t *lut, int64_t *nnz_out, cudaStream_t s);
 const char *noalloc_message();
 
+// ---- device memory through the context's allocator (fe_api.cpp) ----
+void *dev_alloc(fe_ctx *c, size_t bytes);
+void dev_free(fe_ctx *c, void *p);
+
 // ---- batches (fe_batch.cu) ----
 fe_status batch_create(fe_ctx *c, int n, const fe_batch_item *items, void *(*alloc)(fe_ctx *, size_t),
                        void (*release)(fe_ctx *, void *), fe_batch **out);
@@ -134,6 +138,31 @@ fe_status batch_tune(fe_batch *b, int reps, int *best_tile, int *best_grid, floa
 void batch_destroy(fe_batch *b, void (*release)(fe_ctx *, void *));
 const char *batch_message();
 fe_ctx *batch_ctx(const fe_batch *b);
+
+// ---- Dirichlet and CG (fe_solve.cu) ----
+cudaError_t launch_dirichlet(int64_t nrows, const int64_t *rowptr, const int32_t *colidx, double *vals, double *b,
+                             const uint8_t *is_bc, const double *g, cudaStream_t s);
+fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out);
+bool cg_valid(const fe_cg *h);
+fe_ctx *cg_ctx(const fe_cg *h);
+fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const double *vals, int64_t nrows,
+                 const double *b, double *x, double rtol, int maxit, int *slot);
+fe_status cg_iterate(fe_cg *h, int iters, int use_graph);
+fe_status cg_poll(fe_cg *h, int n, int *status, int *iters, double *rnorm, double *bnorm);
+fe_status cg_remove(fe_cg *h, int slot);
+void cg_destroy(fe_cg *h);
+const char *solve_message();
+
+// ---- request loop (fe_serve.cpp) ----
+fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server **out);
+bool server_valid(const fe_server *h);
+fe_ctx *server_ctx(const fe_server *h);
+fe_status server_submit(fe_server *h, const fe_solve_request *r, int64_t *id);
+fe_status server_run(fe_server *h);
+fe_status server_result(const fe_server *h, int64_t id, fe_solve_result *out);
+fe_status server_stats(const fe_server *h, fe_server_stats *out);
+void server_destroy(fe_server *h);
+const char *server_message();
 size_t noalloc_scratch_bytes();
 
 // ---- assembly ----

@@ -1,0 +1,413 @@
+// Request loop for assemble-and-solve requests: admission by device-memory budget, continuous
+// batching of the Jacobi-CG iterations of every admitted system, retirement as each converges.
+//
+// Each request is a Poisson problem on its own mesh (the Poisson listing of Sec. 3.1 and the
+// experiment of Sec. 6.2): a = inner(grad u, grad v) dx and L = f v dx assembled with the
+// deterministic row-owner (pull) strategy, u = 0 on the flagged boundary nodes by symmetric
+// elimination, then CG with M = diag(A).  Every step runs in this library's kernels; the loop
+// itself is host code that decides what to launch.
+//
+// Loop, until every submitted request has finished or been refused:
+//   1. admit, in arrival order, requests that have arrived while a slot is free and the
+//      request's worst-case device footprint fits in the budget beside what is held (a request
+//      larger than the whole budget is refused; a request that does not fit yet waits, and so do
+//      the ones behind it);
+//   2. if systems are iterating: one tick of `iters_per_tick` CG iterations for all of them
+//      (a captured graph), then a status poll; converged systems copy their solution to the host
+//      and free everything they held;
+//   3. otherwise sleep until the next arrival.
+// Memory is accounted exactly: the server routes its allocations through a counting allocator
+// that forwards to the context's own allocator.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fe_internal.h"
+
+namespace fe {
+namespace {
+
+struct Holding {  // device objects of one admitted request
+  fe_set *cells = nullptr, *nodes = nullptr, *verts = nullptr;
+  fe_map *M = nullptr, *CM = nullptr;
+  fe_dat *XY = nullptr, *F = nullptr, *B = nullptr, *X = nullptr;
+  fe_sparsity *sp = nullptr;
+  fe_mat *A = nullptr;
+  void *d_map = nullptr, *d_cv = nullptr, *d_xy = nullptr, *d_f = nullptr, *d_bc = nullptr, *d_b = nullptr,
+       *d_x = nullptr;
+  int slot = -1;
+};
+
+struct Req {
+  fe_solve_request in;
+  fe_solve_result res;
+  size_t estimate;
+  Holding h;
+};
+
+thread_local char g_vmsg[512];
+
+}  // namespace
+
+struct Server {
+  fe_ctx *parent;
+  fe_ctx *ctx;  // same device and stream as the parent, counting allocator
+  fe_server_config cfg;
+  fe_kernel *klap[3] = {nullptr, nullptr, nullptr}, *ksrc[3] = {nullptr, nullptr, nullptr};
+  fe_cg *cg = nullptr;
+  std::vector<Req> reqs;
+  // accounting
+  std::unordered_map<void *, std::pair<size_t, int64_t>> live;  // pointer -> (bytes, owner; -1 = server)
+  std::vector<size_t> owner_bytes;
+  int64_t owner = -1;
+  size_t base_bytes = 0, live_bytes = 0, peak_bytes = 0, reserved = 0;
+  int estimate_misses = 0;
+  double run_s = 0.0;
+};
+
+}  // namespace fe
+
+struct fe_server {
+  uint32_t magic;
+  fe::Server *s;
+};
+
+namespace fe {
+namespace {
+constexpr uint32_t kMagicServer = 0xFE05E2E5u;
+
+void *count_alloc(size_t bytes, void *user) {
+  Server *s = static_cast<Server *>(user);
+  fe_ctx *p = s->parent;
+  void *ptr = nullptr;
+  if (p->alloc) {
+    ptr = p->alloc(bytes, p->user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (!ptr) return nullptr;
+  s->live[ptr] = {bytes, s->owner};
+  s->live_bytes += bytes;
+  s->peak_bytes = std::max(s->peak_bytes, s->live_bytes);
+  if (s->owner >= 0) s->owner_bytes[s->owner] += bytes;
+  else s->base_bytes += bytes;
+  return ptr;
+}
+
+void count_free(void *ptr, void *user) {
+  Server *s = static_cast<Server *>(user);
+  auto it = s->live.find(ptr);
+  if (it != s->live.end()) {
+    const size_t b = it->second.first;
+    const int64_t o = it->second.second;
+    s->live_bytes -= b;
+    if (o >= 0) s->owner_bytes[o] -= b;
+    else s->base_bytes -= b;
+    s->live.erase(it);
+  }
+  fe_ctx *p = s->parent;
+  if (p->free_fn) p->free_fn(ptr, p->user);
+  else cudaFree(ptr);
+}
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int nodes_p(int p) { return (p + 1) * (p + 2) / 2; }
+
+// Worst-case device bytes of one request (every allocation it makes, at its largest, while it
+// is built; nnz bounded by the cell-node incidences times the arity).
+size_t estimate_bytes(const fe_solve_request &r) {
+  const size_t nd = nodes_p(r.degree), ncell = r.ncell, nn = r.nnodes, nv = r.nvert;
+  const size_t ninc = ncell * nd, nnz = ninc * nd;
+  auto a = [](size_t b) { return (std::max<size_t>(b, 16) + 255) & ~size_t(255); };
+  size_t t = 0;
+  t += a(4 * ninc) + a(12 * ncell) + a(16 * nv) + a(8 * nn) + a(nn) + a(8 * nn) + a(8 * nn);  // inputs, b, x
+  t += 2 * a(8 * (nn + 1)) + a(4 * ninc) + a(4 * nn) + a(4 * ninc * nd) + a(ninc * nd) +
+       a(8 * scan_tmp_elems((int64_t)nn)) + a(4) + a(4 * nnz);                                  // sparsity
+  t += a(8 * nnz) + a(8 * ncell * nd * (nd + 1) / 2) + a(8 * ncell * nd);                       // Mat, staging
+  t += 6 * a(8 * nn) + a(24 * (nn / 1024 + 1));                                                 // CG vectors
+  return t;
+}
+
+#define SV_TRY(expr)                                   \
+  do {                                                 \
+    fe_status _st = (expr);                            \
+    if (_st != FE_OK) return _st;                      \
+  } while (0)
+
+fe_status copy_in(Server *s, void **dst, const void *src, size_t bytes) {
+  *dst = dev_alloc(s->ctx, bytes);
+  if (!*dst) return FE_ENOMEM;
+  if (bytes == 0) return FE_OK;
+  return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s->ctx->stream) == cudaSuccess ? FE_OK : FE_ECUDA;
+}
+
+void release(Server *s, Req &q) {
+  Holding &h = q.h;
+  const int64_t saved = s->owner;
+  s->owner = &q - s->reqs.data();
+  if (h.slot >= 0) fe_cg_remove(s->cg, h.slot);
+  cudaStreamSynchronize(s->ctx->stream);
+  if (h.A) fe_mat_destroy(h.A);
+  if (h.sp) fe_sparsity_destroy(h.sp);
+  for (fe_dat *d : {h.XY, h.F, h.B, h.X})
+    if (d) fe_dat_destroy(d);
+  for (fe_map *m : {h.M, h.CM})
+    if (m) fe_map_destroy(m);
+  for (fe_set *t : {h.cells, h.nodes, h.verts})
+    if (t) fe_set_destroy(t);
+  for (void *p : {h.d_map, h.d_cv, h.d_xy, h.d_f, h.d_bc, h.d_b, h.d_x}) dev_free(s->ctx, p);
+  h = Holding();
+  s->owner = saved;
+}
+
+// Build one request's system on the device and hand it to the CG engine.
+fe_status admit(Server *s, Req &q) {
+  const fe_solve_request &r = q.in;
+  Holding &h = q.h;
+  fe_ctx *c = s->ctx;
+  const int nd = nodes_p(r.degree);
+  cudaStream_t st = c->stream;
+  SV_TRY(copy_in(s, &h.d_map, r.cell_node, sizeof(int32_t) * r.ncell * nd));
+  SV_TRY(copy_in(s, &h.d_cv, r.cell_vertex, sizeof(int32_t) * r.ncell * 3));
+  SV_TRY(copy_in(s, &h.d_xy, r.coords, sizeof(double) * r.nvert * 2));
+  SV_TRY(copy_in(s, &h.d_f, r.f, sizeof(double) * r.nnodes));
+  SV_TRY(copy_in(s, &h.d_bc, r.is_bc, r.nnodes));
+  h.d_b = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
+  h.d_x = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
+  if (!h.d_b || !h.d_x) return FE_ENOMEM;
+  if (cudaMemsetAsync(h.d_x, 0, sizeof(double) * r.nnodes, st) != cudaSuccess) return FE_ECUDA;
+  SV_TRY(fe_set_create(c, r.ncell, &h.cells));
+  SV_TRY(fe_set_create(c, r.nnodes, &h.nodes));
+  SV_TRY(fe_set_create(c, r.nvert, &h.verts));
+  SV_TRY(fe_map_create(c, h.cells, h.nodes, nd, (const int32_t *)h.d_map, 1, &h.M));
+  SV_TRY(fe_map_create(c, h.cells, h.verts, 3, (const int32_t *)h.d_cv, 1, &h.CM));
+  SV_TRY(fe_dat_create(c, h.verts, 2, (double *)h.d_xy, &h.XY));
+  SV_TRY(fe_dat_create(c, h.nodes, 1, (double *)h.d_f, &h.F));
+  SV_TRY(fe_dat_create(c, h.nodes, 1, (double *)h.d_b, &h.B));
+  SV_TRY(fe_dat_create(c, h.nodes, 1, (double *)h.d_x, &h.X));
+  SV_TRY(fe_sparsity_build(c, h.M, h.M, &h.sp));
+  SV_TRY(fe_mat_create(c, h.sp, &h.A));
+  SV_TRY(fe_assemble_mat(c, s->klap[r.degree], h.cells, h.A, 1, h.XY, h.CM, nullptr, 0));
+  fe_arg fa{h.F, h.M};
+  SV_TRY(fe_assemble_vec(c, s->ksrc[r.degree], h.cells, h.B, h.M, 1, h.XY, h.CM, &fa, 1, h.sp));
+  if (launch_dirichlet(r.nnodes, h.sp->rowptr, h.sp->colidx, h.A->values, (double *)h.d_b,
+                       (const uint8_t *)h.d_bc, nullptr, st) != cudaSuccess)
+    return FE_ECUDA;
+  // transient buffers of the build: staging of the row-owner sums and the pattern scratch
+  dev_free(c, h.A->stage);
+  h.A->stage = nullptr;
+  h.A->stage_bytes = 0;
+  dev_free(c, h.sp->vstage);
+  h.sp->vstage = nullptr;
+  h.sp->vstage_bytes = 0;
+  dev_free(c, h.sp->coltmp);
+  h.sp->coltmp = nullptr;
+  SV_TRY(fe_cg_add(s->cg, h.A, h.B, h.X, s->cfg.rtol, s->cfg.maxit, &h.slot));
+  return FE_OK;
+}
+
+void server_free(Server *s) {
+  if (!s) return;
+  for (Req &q : s->reqs) release(s, q);
+  if (s->cg) fe_cg_destroy(s->cg);
+  for (int p = 1; p <= 2; p++) {
+    if (s->klap[p]) fe_kernel_destroy(s->klap[p]);
+    if (s->ksrc[p]) fe_kernel_destroy(s->ksrc[p]);
+  }
+  if (s->ctx) fe_ctx_destroy(s->ctx);
+  delete s;
+}
+}  // namespace
+
+const char *server_message() { return g_vmsg; }
+
+fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server **out) {
+  g_vmsg[0] = 0;
+  if (cfg->max_active < 1 || cfg->iters_per_tick < 1 || !(cfg->rtol > 0.0) || cfg->maxit < 1 ||
+      (cfg->precision != FE_PREC_FP64 && cfg->precision != FE_PREC_F32X2)) {
+    snprintf(g_vmsg, sizeof g_vmsg, "fe_server_create: bad configuration");
+    return FE_EINVAL;
+  }
+  Server *s = new (std::nothrow) Server();
+  if (!s) return FE_ENOMEM;
+  s->parent = parent;
+  s->cfg = *cfg;
+  fe_status st = fe_ctx_create(parent->device, parent->stream, &s->ctx);
+  if (st == FE_OK) st = fe_ctx_set_allocator(s->ctx, count_alloc, count_free, s);
+  for (int p = 1; p <= 2 && st == FE_OK; p++) {
+    fe_form_desc d{FE_FORM_LAPLACE, 2, p, 0, cfg->precision, FE_STRATEGY_PULL};
+    st = fe_kernel_create(s->ctx, &d, &s->klap[p]);
+    fe_form_desc v{FE_FORM_SOURCE, 2, p, p, cfg->precision, FE_STRATEGY_PULL};
+    if (st == FE_OK) st = fe_kernel_create(s->ctx, &v, &s->ksrc[p]);
+  }
+  if (st == FE_OK) st = fe_cg_create(s->ctx, cfg->max_active, &s->cg);
+  if (st != FE_OK) {
+    snprintf(g_vmsg, sizeof g_vmsg, "fe_server_create: %s", fe_last_error());
+    server_free(s);
+    return st;
+  }
+  fe_server *h = new (std::nothrow) fe_server{kMagicServer, s};
+  if (!h) {
+    server_free(s);
+    return FE_ENOMEM;
+  }
+  *out = h;
+  return FE_OK;
+}
+
+bool server_valid(const fe_server *h) { return h && h->magic == kMagicServer && h->s; }
+fe_ctx *server_ctx(const fe_server *h) { return h->s->parent; }
+
+fe_status server_submit(fe_server *h, const fe_solve_request *r, int64_t *id) {
+  Server *s = h->s;
+  g_vmsg[0] = 0;
+  if ((r->degree != 1 && r->degree != 2) || r->ncell < 0 || r->nnodes < 0 || r->nvert < 0 ||
+      (r->ncell > 0 && (!r->cell_node || !r->cell_vertex || !r->coords)) ||
+      (r->nnodes > 0 && (!r->f || !r->is_bc || !r->x_out)) || !(r->arrival_s >= 0.0)) {
+    snprintf(g_vmsg, sizeof g_vmsg, "fe_server_submit: bad request");
+    return FE_EINVAL;
+  }
+  Req q;
+  memset(&q.res, 0, sizeof q.res);
+  q.in = *r;
+  q.estimate = estimate_bytes(*r);
+  q.res.estimate = q.estimate;
+  q.res.status = FE_SOLVE_PENDING;
+  s->reqs.push_back(q);
+  s->owner_bytes.push_back(0);
+  if (id) *id = (int64_t)s->reqs.size() - 1;
+  return FE_OK;
+}
+
+fe_status server_run(fe_server *h) {
+  Server *s = h->s;
+  g_vmsg[0] = 0;
+  const fe_server_config &cfg = s->cfg;
+  std::vector<int64_t> order;
+  for (int64_t i = 0; i < (int64_t)s->reqs.size(); i++)
+    if (s->reqs[i].res.status == FE_SOLVE_PENDING) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t a, int64_t b) { return s->reqs[a].in.arrival_s < s->reqs[b].in.arrival_s; });
+  size_t next = 0;
+  std::vector<int64_t> active;            // request ids iterating
+  std::vector<int64_t> slot_owner(cfg.max_active, -1);
+  std::vector<int> st_status(cfg.max_active), st_iters(cfg.max_active);
+  std::vector<double> st_r(cfg.max_active), st_b(cfg.max_active);
+  const auto t0 = std::chrono::steady_clock::now();
+  size_t held = 0;  // sum of charges of the admitted requests
+  while (next < order.size() || !active.empty()) {
+    // 1. admission, in arrival order
+    while (next < order.size() && (int)active.size() < cfg.max_active) {
+      Req &q = s->reqs[order[next]];
+      if (q.in.arrival_s > now_s(t0)) break;
+      if (s->base_bytes + q.estimate > cfg.hbm_budget) {
+        q.res.status = FE_SOLVE_REFUSED;
+        q.res.admitted_s = q.res.finished_s = now_s(t0);
+        next++;
+        continue;
+      }
+      if (s->base_bytes + held + q.estimate > cfg.hbm_budget) break;  // wait for memory
+      const int64_t id = order[next];
+      q.res.admitted_s = now_s(t0);
+      s->owner = id;
+      fe_status st = admit(s, q);
+      s->owner = -1;
+      if (st != FE_OK) {
+        snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)id, fe_last_error());
+        release(s, q);
+        return st;
+      }
+      if (s->owner_bytes[id] > q.estimate) s->estimate_misses++;
+      q.res.bytes = s->owner_bytes[id];
+      held += q.res.bytes;
+      slot_owner[q.h.slot] = id;
+      active.push_back(id);
+      next++;
+    }
+    if (active.empty()) {
+      if (next < order.size()) {
+        const double wait = s->reqs[order[next]].in.arrival_s - now_s(t0);
+        if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
+      }
+      continue;
+    }
+    // 2. one tick of CG for every admitted system, then retire the finished ones
+    fe_status st = fe_cg_iterate(s->cg, cfg.iters_per_tick, 1);
+    if (st == FE_OK) st = fe_cg_poll(s->cg, cfg.max_active, st_status.data(), st_iters.data(), st_r.data(), st_b.data());
+    if (st != FE_OK) {
+      snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: %s", fe_last_error());
+      return st;
+    }
+    for (size_t k = 0; k < active.size();) {
+      const int64_t id = active[k];
+      Req &q = s->reqs[id];
+      const int sl = q.h.slot;
+      if (st_status[sl] == 0) {
+        k++;
+        continue;
+      }
+      q.res.status = st_status[sl];
+      q.res.iters = st_iters[sl];
+      q.res.rnorm = st_r[sl];
+      q.res.bnorm = st_b[sl];
+      cudaError_t ce = cudaSuccess;
+      if (q.in.nnodes > 0)
+        ce = cudaMemcpyAsync(q.in.x_out, q.h.d_x, sizeof(double) * q.in.nnodes, cudaMemcpyDeviceToHost, s->ctx->stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->ctx->stream);
+      if (ce != cudaSuccess) {
+        snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: copying the solution of request %lld", (long long)id);
+        return FE_ECUDA;
+      }
+      q.res.finished_s = now_s(t0);
+      slot_owner[sl] = -1;
+      held -= q.res.bytes;
+      release(s, q);
+      active.erase(active.begin() + k);
+    }
+  }
+  s->run_s = now_s(t0);
+  return FE_OK;
+}
+
+fe_status server_result(const fe_server *h, int64_t id, fe_solve_result *out) {
+  const Server *s = h->s;
+  if (id < 0 || id >= (int64_t)s->reqs.size()) return FE_EINVAL;
+  *out = s->reqs[id].res;
+  return FE_OK;
+}
+
+fe_status server_stats(const fe_server *h, fe_server_stats *out) {
+  const Server *s = h->s;
+  memset(out, 0, sizeof *out);
+  out->peak_bytes = s->peak_bytes;
+  out->live_bytes = s->live_bytes;
+  out->base_bytes = s->base_bytes;
+  out->estimate_misses = s->estimate_misses;
+  out->run_s = s->run_s;
+  for (const Req &q : s->reqs) {
+    out->submitted++;
+    if (q.res.status == FE_SOLVE_CONVERGED) out->converged++;
+    if (q.res.status == FE_SOLVE_REFUSED) out->refused++;
+  }
+  return FE_OK;
+}
+
+void server_destroy(fe_server *h) {
+  server_free(h->s);
+  h->magic = 0xDEADu;
+  h->s = nullptr;
+  delete h;
+}
+
+}  // namespace fe

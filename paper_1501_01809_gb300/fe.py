@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
 import torch
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libfe.so")
@@ -29,7 +30,9 @@ SYMBOLS = [
     "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
     "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
-    "fe_batch_assemble", "fe_batch_destroy",
+    "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
+    "fe_cg_poll", "fe_cg_remove", "fe_cg_destroy", "fe_server_create", "fe_server_submit", "fe_server_run",
+    "fe_server_result", "fe_server_stats_get", "fe_server_destroy",
 ]
 
 
@@ -52,6 +55,32 @@ class fe_batch_item(C.Structure):
     _fields_ = [("kmat", C.c_void_p), ("kvec", C.c_void_p), ("cells", C.c_void_p), ("sp", C.c_void_p),
                 ("coords", C.c_void_p), ("coord_map", C.c_void_p), ("f", fe_arg)]
 
+
+class fe_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("iters_per_tick", C.c_int),
+                ("rtol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int)]
+
+
+class fe_solve_request(C.Structure):
+    _fields_ = [("degree", C.c_int), ("ncell", C.c_int64), ("nnodes", C.c_int64), ("nvert", C.c_int64),
+                ("cell_node", C.c_void_p), ("cell_vertex", C.c_void_p), ("coords", C.c_void_p), ("f", C.c_void_p),
+                ("is_bc", C.c_void_p), ("x_out", C.c_void_p), ("arrival_s", C.c_double)]
+
+
+class fe_solve_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("rnorm", C.c_double), ("bnorm", C.c_double),
+                ("admitted_s", C.c_double), ("finished_s", C.c_double), ("bytes", C.c_size_t),
+                ("estimate", C.c_size_t)]
+
+
+class fe_server_stats(C.Structure):
+    _fields_ = [("peak_bytes", C.c_size_t), ("live_bytes", C.c_size_t), ("base_bytes", C.c_size_t),
+                ("submitted", C.c_int), ("converged", C.c_int), ("refused", C.c_int), ("estimate_misses", C.c_int),
+                ("run_s", C.c_double)]
+
+
+CG_RUNNING, CG_CONVERGED, CG_MAXIT, CG_BREAKDOWN = 0, 1, 2, 3
+SOLVE_PENDING, SOLVE_CONVERGED, SOLVE_MAXIT, SOLVE_BREAKDOWN, SOLVE_REFUSED = 0, 1, 2, 3, 4
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -95,6 +124,14 @@ def load():
         "fe_batch_values": (I, [P, I, PP, C.POINTER(I64), PP, C.POINTER(I64)]),
         "fe_batch_tune": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_float)]),
         "fe_batch_assemble": (I, [P, I]), "fe_batch_destroy": (I, [P]),
+        "fe_dirichlet_apply": (I, [P, P, P, P, P]),
+        "fe_cg_create": (I, [P, I, PP]), "fe_cg_add": (I, [P, P, P, P, C.c_double, I, C.POINTER(I)]),
+        "fe_cg_iterate": (I, [P, I, I]),
+        "fe_cg_poll": (I, [P, I, P, P, P, P]), "fe_cg_remove": (I, [P, I]), "fe_cg_destroy": (I, [P]),
+        "fe_server_create": (I, [P, C.POINTER(fe_server_config), PP]),
+        "fe_server_submit": (I, [P, C.POINTER(fe_solve_request), C.POINTER(I64)]),
+        "fe_server_run": (I, [P]), "fe_server_result": (I, [P, I64, C.POINTER(fe_solve_result)]),
+        "fe_server_stats_get": (I, [P, C.POINTER(fe_server_stats)]), "fe_server_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +222,14 @@ class Kernel(Handle):
 
 class Batch(Handle):
     _destroy = "fe_batch_destroy"
+
+
+class Cg(Handle):
+    _destroy = "fe_cg_destroy"
+
+
+class Server(Handle):
+    _destroy = "fe_server_destroy"
 
 
 def _torch_alloc(nbytes, user):
@@ -434,3 +479,86 @@ def batch_buffers(b: Batch):
     nv = (vl.value - v0.value) // 8 + nnz.value
     nrr = (rl.value - r0.value) // 8 + nr.value
     return _view(v0.value, nv, torch.float64, b, dev), _view(r0.value, nrr, torch.float64, b, dev)
+
+
+# ----------------------------------------------------------------------------------- boundary conditions, CG
+
+def dirichlet_apply(ctx: Ctx, A: Mat, b: Dat, is_bc: torch.Tensor, g: torch.Tensor | None = None) -> None:
+    """fe_dirichlet_apply: is_bc device uint8 [nrows]; g device float64 [nrows] or None (g = 0)."""
+    is_bc = _dev_tensor(is_bc, torch.uint8, "is_bc")
+    gp = None if g is None else _dev_tensor(g, torch.float64, "g").data_ptr()
+    _check(load().fe_dirichlet_apply(ctx.ptr, A.ptr, b.ptr, is_bc.data_ptr(), gp))
+
+
+def cg_create(ctx: Ctx, max_systems: int) -> Cg:
+    out = C.c_void_p()
+    _check(load().fe_cg_create(ctx.ptr, int(max_systems), C.byref(out)))
+    return Cg(out, ctx)
+
+
+def cg_add(cg: Cg, A: Mat, b: Dat, x: Dat, rtol: float = 1e-8, maxit: int = 100000) -> int:
+    slot = C.c_int()
+    _check(load().fe_cg_add(cg.ptr, A.ptr, b.ptr, x.ptr, float(rtol), int(maxit), C.byref(slot)))
+    cg._keep.append((A, b, x))
+    return slot.value
+
+
+def cg_iterate(cg: Cg, iters: int, use_graph: bool = True) -> None:
+    _check(load().fe_cg_iterate(cg.ptr, int(iters), int(bool(use_graph))))
+
+
+def cg_poll(cg: Cg, nslots: int):
+    """(status, iterations, ||r||, ||b||) arrays over slots 0..nslots-1 (synchronises)."""
+    st, it = np.zeros(nslots, np.int32), np.zeros(nslots, np.int32)
+    rn, bn = np.zeros(nslots), np.zeros(nslots)
+    _check(load().fe_cg_poll(cg.ptr, int(nslots), st.ctypes.data, it.ctypes.data, rn.ctypes.data, bn.ctypes.data))
+    return st, it, rn, bn
+
+
+def cg_remove(cg: Cg, slot: int) -> None:
+    _check(load().fe_cg_remove(cg.ptr, int(slot)))
+
+
+# ----------------------------------------------------------------------------------- serving
+
+def server_create(ctx: Ctx, hbm_budget: int, max_active: int = 64, iters_per_tick: int = 16, rtol: float = 1e-8,
+                  maxit: int = 100000, precision: int = PREC_FP64) -> Server:
+    cfg = fe_server_config(int(hbm_budget), int(max_active), int(iters_per_tick), float(rtol), int(maxit),
+                           int(precision))
+    out = C.c_void_p()
+    _check(load().fe_server_create(ctx.ptr, C.byref(cfg), C.byref(out)))
+    return Server(out, ctx, keep=([],))
+
+
+def server_submit(srv: Server, degree: int, cell_node, cell_vertex, coords, f, is_bc, x_out, arrival_s: float) -> int:
+    """Queue one Poisson solve; the host arrays are kept alive by the server handle until it is destroyed."""
+    arrs = [np.ascontiguousarray(cell_node, np.int32), np.ascontiguousarray(cell_vertex, np.int32),
+            np.ascontiguousarray(coords, np.float64), np.ascontiguousarray(f, np.float64),
+            np.ascontiguousarray(is_bc, np.uint8)]
+    if not (isinstance(x_out, np.ndarray) and x_out.dtype == np.float64 and x_out.flags.c_contiguous):
+        raise TypeError("x_out must be a C-contiguous float64 numpy array")
+    if x_out.size != arrs[3].size:
+        raise ValueError("x_out must hold one value per node")
+    req = fe_solve_request(int(degree), arrs[0].shape[0], arrs[3].size, arrs[2].shape[0], arrs[0].ctypes.data,
+                           arrs[1].ctypes.data, arrs[2].ctypes.data, arrs[3].ctypes.data, arrs[4].ctypes.data,
+                           x_out.ctypes.data, float(arrival_s))
+    rid = C.c_int64()
+    _check(load().fe_server_submit(srv.ptr, C.byref(req), C.byref(rid)))
+    srv._keep[0].append((arrs, x_out))
+    return rid.value
+
+
+def server_run(srv: Server) -> None:
+    _check(load().fe_server_run(srv.ptr))
+
+
+def server_result(srv: Server, rid: int) -> dict:
+    r = fe_solve_result()
+    _check(load().fe_server_result(srv.ptr, int(rid), C.byref(r)))
+    return {k: getattr(r, k) for k, _ in fe_solve_result._fields_}
+
+
+def server_stats(srv: Server) -> dict:
+    r = fe_server_stats()
+    _check(load().fe_server_stats_get(srv.ptr, C.byref(r)))
+    return {k: getattr(r, k) for k, _ in fe_server_stats._fields_}
