@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cells/s assembled (sparsity + CSR assembly + matrix-free action per step)"
+METRIC_SERVE = "served Poisson solves/s (assemble + Dirichlet + Jacobi-CG to rtol 1e-8, host to host), p50/p99 latency"
 METRIC_BATCH = "cells/s assembled (CSR + RHS of every mesh of the batch per step, sparsity cached)"
 WORKLOADS = {
     "p2-3d": dict(dim=3, p=2, n=64, jitter=0.2, seed=0,
@@ -42,6 +43,11 @@ WORKLOADS = {
                   name="2048 UnitSquareMesh n x n meshes, n log-uniform in [8,256] (seed 4), each P1 or P2 "
                        "(Bernoulli 1/2), Helmholtz CSR + RHS f v dx (f uniform[-1,1] per node, seed 1000+i), "
                        "one persistent launch under a CUDA graph, tuned tile and grid"),
+    "serve": dict(serve=True, count=64, seed=5, lo=16, hi=512, budget=2 << 30, max_active=64, tick=16,
+                  name="Poisson solve requests on UnitSquareMesh n x n, n log-uniform in [16,512] (seed 5), P1 or P2, "
+                       "f from u = sin(k pi x) sin(m pi y), k, m uniform in 1..4, u = 0 on the boundary; pull assembly, "
+                       "Dirichlet elimination, Jacobi-CG rtol 1e-8 (FP64 dots); Poisson arrivals, admission by a "
+                       "2 GiB device-memory budget"),
 }
 # ncu dram bytes (read + write) per launch of the dominant kernel, with the sha1 of the kernel
 # source they were taken from; reported as null once the source has changed.
@@ -484,6 +490,170 @@ def run_batch(args, wl, rank, world):
     return out, meshes
 
 
+# ------------------------------------------------------------------------------ serving workload
+
+def make_serve_inputs(wl):
+    """Per request (n, p, k, m, cell-node map, mesh, nodes, f, boundary mask); meshes cached by (n, p)."""
+    from paper_1501_01809_gb300 import meshgen as mg
+    reqs = mg.serve_requests(wl["count"], wl["seed"], 1.0, wl["lo"], wl["hi"])
+    cache, out = {}, []
+    for (t, n, p, k, m) in reqs:
+        if (n, p) not in cache:
+            mesh = mg.unit_square_mesh(n)
+            cmap, nn = mg.cell_node_map(mesh, p)
+            cache[(n, p)] = (mesh, cmap, nn, mg.boundary_nodes(mesh, p))
+        mesh, cmap, nn, bc = cache[(n, p)]
+        f, _ = mg.manufactured_sine(mesh, p, k, m)
+        out.append(dict(t1=t, n=n, p=p, k=k, m=m, mesh=mesh, cmap=cmap, nn=nn, f=f, bc=bc))
+    return out
+
+
+def _serve_once(fe, ctx, wl, reqs, rate, max_active):
+    """One run of the request loop; arrival times are the unit-rate draws divided by rate (0: all at once)."""
+    srv = fe.server_create(ctx, wl["budget"], max_active=max_active, iters_per_tick=wl["tick"], rtol=1e-8)
+    ids, xs = [], []
+    for r in reqs:
+        x = np.empty(r["nn"])
+        t = r["t1"] / rate if rate > 0 else 0.0
+        ids.append(fe.server_submit(srv, r["p"], r["cmap"], r["mesh"].cell_vertex, r["mesh"].coords, r["f"], r["bc"],
+                                    x, t))
+        xs.append(x)
+    fe.server_run(srv)
+    res = [fe.server_result(srv, i) for i in ids]
+    st = fe.server_stats(srv)
+    srv.destroy()
+    arr = np.array([r["t1"] / rate if rate > 0 else 0.0 for r in reqs])
+    lat = np.array([q["finished_s"] for q in res]) - arr
+    ok = all(q["status"] == fe.SOLVE_CONVERGED for q in res)
+    return {"rate_req_s": rate, "solves_per_s": len(reqs) / st["run_s"], "run_s": st["run_s"],
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_iters": float(np.mean([q["iters"] for q in res])), "all_converged": ok,
+            "peak_bytes": st["peak_bytes"], "cg_launches": st["cg_launches"]}, xs
+
+
+def run_serve(args, wl, rank, world):
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    reqs = make_serve_inputs(wl)
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    # warm-up: a few small requests through both paths
+    small = [r for r in reqs if r["n"] <= 40][:4] or reqs[:2]
+    for _ in range(args.warmup):
+        _serve_once(fe, ctx, wl, small, 0.0, wl["max_active"])
+        _serve_once(fe, ctx, wl, small, 0.0, 1)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sat, x_mix = _serve_once(fe, ctx, wl, reqs, 0.0, wl["max_active"])
+        b.record(stream)
+        b.synchronize()
+        dev_ms = a.elapsed_time(b)
+        plain_sat, x_one = _serve_once(fe, ctx, wl, reqs, 0.0, 1)
+        identical = all(np.array_equal(u, v) for u, v in zip(x_mix, x_one))
+        sweep = []
+        for frac in (0.25, 0.5, 0.75, 0.9):
+            rate = frac * sat["solves_per_s"]
+            served, _ = _serve_once(fe, ctx, wl, reqs, rate, wl["max_active"])
+            plain, _ = _serve_once(fe, ctx, wl, reqs, rate, 1)
+            sweep.append({"rate_req_s": rate, "served": served, "plain": plain})
+    # CG iteration of the largest system alone: the dominant kernels, timed with CUDA events
+    big = max(reqs, key=lambda r: r["nn"] * (r["p"] ** 2))
+    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+         dict(map=big["cmap"], cv=big["mesh"].cell_vertex, xy=big["mesh"].coords, f=big["f"], bc=big["bc"]).items()}
+    tb, tx = torch.zeros(big["nn"], dtype=torch.float64, device=dev), torch.zeros(big["nn"], dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        cells, nodes, verts = (fe.set_create(ctx, big["mesh"].ncell), fe.set_create(ctx, big["nn"]),
+                               fe.set_create(ctx, big["mesh"].nvert))
+        M, CM = fe.map_create(ctx, cells, nodes, t["map"]), fe.map_create(ctx, cells, verts, t["cv"])
+        XY, F = fe.dat_create(ctx, verts, t["xy"]), fe.dat_create(ctx, nodes, t["f"])
+        B, X = fe.dat_create(ctx, nodes, tb), fe.dat_create(ctx, nodes, tx)
+        sp = fe.sparsity_build(ctx, M, M)
+        A = fe.mat_create(ctx, sp)
+        kl = fe.kernel_create(ctx, fe.FORM_LAPLACE, 2, big["p"], strategy=fe.STRATEGY_PULL)
+        ks = fe.kernel_create(ctx, fe.FORM_SOURCE, 2, big["p"], coeff_degree=big["p"], strategy=fe.STRATEGY_PULL)
+        fe.assemble_mat(ctx, kl, cells, A, XY, CM, zero_first=True)
+        fe.assemble_vec(ctx, ks, cells, B, M, XY, CM, [(F, M)], zero_first=True, sp=sp)
+        fe.dirichlet_apply(ctx, A, B, t["bc"])
+        cg = fe.cg_create(ctx, 1)
+        fe.cg_add(cg, A, B, X, rtol=1e-30, maxit=1 << 30)
+        fe.cg_iterate(cg, 10)
+        fe.sync(ctx)
+        iters = 200
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fe.cg_iterate(cg, iters)
+        e1.record(stream)
+        e1.synchronize()
+    it_ms = e0.elapsed_time(e1) / iters
+    nnz = fe.sparsity_csr(sp)[2]
+    nn = big["nn"]
+    # algorithmic bytes of one iteration (launch A + launch B): CSR values and columns and the row
+    # pointers once, z and p_old read, p_new and q written (A); p_new, q, x, r, diag^-1 read, x, r, z
+    # written (B)
+    it_bytes = nnz * 12 + (nn + 1) * 8 + 4 * nn * 8 + 8 * nn * 8
+    peaks, src = _peaks()
+    gbs = it_bytes / (it_ms / 1e3) / 1e9
+    h2d = sum(r["cmap"].nbytes + r["mesh"].cell_vertex.nbytes + r["mesh"].coords.nbytes + r["f"].nbytes + r["bc"].nbytes
+              for r in reqs)
+    d2h = sum(r["nn"] * 8 for r in reqs)
+    out = {
+        "metric": METRIC_SERVE, "value": world * sat["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * sat["run_s"] / len(reqs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "requests": len(reqs), "hbm_budget_bytes": wl["budget"],
+                   "max_active": wl["max_active"], "iters_per_tick": wl["tick"],
+                   "step": "one solve (ms_per_step = run time / requests at saturation)",
+                   "gpu_launches_counted": "CG engine launches of the saturated served run (set-up, iterations, "
+                                           "polls); each admission adds its sparsity, assembly and elimination "
+                                           "launches",
+                   "saturation": {"served": sat, "plain_one_at_a_time": plain_sat,
+                                  "speedup": sat["solves_per_s"] / plain_sat["solves_per_s"],
+                                  "device_ms_served_run": dev_ms},
+                   "mixed_equals_alone_bitwise": identical, "rate_sweep": sweep,
+                   "parallelism": f"replicas x{world} (independent servers, no collective)",
+                   "l2": "each request's data is written and read within its own solve; no flush"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": f"CG iteration (k_cg_direction_spmv + k_cg_update), largest request alone "
+                               f"(P{big['p']} n={big['n']}, {nn} rows, {nnz} nonzeros): {it_ms * 1e3:.1f} us/iteration",
+                     "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+        "gpu_launches": sat["cg_launches"], "clocks": clk.summary(),
+        "e2e": {"value": world * sat["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": h2d // len(reqs),
+                "d2h_bytes_per_step": d2h // len(reqs),
+                "note": "the served figure is already host to host: meshes copied in, solutions copied out"},
+    }
+    return out, reqs
+
+
+SERVE_CPU_MAX_N = 128
+
+
+def serve_cpu_sample(reqs, budget_s):
+    """Oracle on the requests with n <= SERVE_CPU_MAX_N, in arrival order (sparsity, assembly,
+    elimination, CG), until budget_s seconds (a single larger solve would take minutes on one core)."""
+    import oracle as O
+    done, t0 = 0, time.perf_counter()
+    for r in (q for q in reqs if q["n"] <= SERVE_CPU_MAX_N):
+        rp, ci = O.sparsity(r["cmap"], r["cmap"], r["nn"], r["nn"])
+        v, _ = O.assemble_mat(2, r["p"], O.LAPLACE, r["cmap"], r["mesh"].coords, r["mesh"].cell_vertex, rp, ci)
+        b, _ = O.assemble_vec(2, r["p"], r["p"], r["cmap"], r["nn"], r["mesh"].coords, r["mesh"].cell_vertex, r["f"],
+                              r["cmap"])
+        v, b = O.dirichlet_apply(rp, ci, v, b, r["bc"])
+        O.cg_jacobi(rp, ci, v, b, rtol=1e-8)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
 def batch_cpu_sample(meshes, budget_s):
     """Oracle on the first meshes of the batch (sparsity + CSR + RHS) until budget_s seconds are spent."""
     import oracle as O
@@ -524,6 +694,20 @@ def cpu_baseline(wl, inputs, ncell_sample):
 def run_reference(args, wl):
     import oracle
     oracle.build()
+    if wl.get("serve"):
+        reqs = make_serve_inputs(wl)
+        res = [serve_cpu_sample(reqs, args.ref_seconds) for _ in range(args.steps)]
+        v = sum(c for c, _ in res) / sum(t for _, t in res)
+        ms = 1e3 * sum(t for _, t in res) / max(1, sum(c for c, _ in res))
+        return {"impl": "reference", "metric": METRIC_SERVE, "value": v, "unit": "solves/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "reference": "CPU FP64 oracle (plain C), requests in order, "
+                                                                "bounded time per step"},
+                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"requests with n <= {SERVE_CPU_MAX_N} in arrival order, about "
+                                           f"{args.ref_seconds} s per step"},
+                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if "count" in wl:
         meshes = make_batch_inputs(wl)
         batch_cpu_sample(meshes[:4], 1.0)
@@ -590,12 +774,22 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
-    if "count" in wl:
+    if wl.get("serve"):
+        out, reqs = run_serve(args, wl, rank, world)
+    elif "count" in wl:
         out, meshes = run_batch(args, wl, rank, world)
     else:
         out, inputs = run_ours(args, wl, rank, world)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline and "count" in wl:
+        if world == 1 and not args.no_cpu_baseline and wl.get("serve"):
+            import oracle
+            oracle.build()
+            done, dt = serve_cpu_sample(reqs, 15.0)
+            out["cpu_baseline"] = {"value": done / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"the first {done} requests with n <= {SERVE_CPU_MAX_N} in arrival "
+                                             f"order (sparsity, assembly, elimination, CG), {dt:.1f} s on 1 host "
+                                             f"core; larger requests are left out of the sample"}
+        elif world == 1 and not args.no_cpu_baseline and "count" in wl:
             import oracle
             oracle.build()
             batch_cpu_sample(meshes[:4], 1.0)

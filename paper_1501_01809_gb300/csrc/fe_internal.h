@@ -144,6 +144,7 @@ cudaError_t launch_dirichlet(int64_t nrows, const int64_t *rowptr, const int32_t
                              const uint8_t *is_bc, const double *g, cudaStream_t s);
 fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out);
 bool cg_valid(const fe_cg *h);
+int64_t cg_launches(const fe_cg *h);
 fe_ctx *cg_ctx(const fe_cg *h);
 fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const double *vals, int64_t nrows,
                  const double *b, double *x, double rtol, int maxit, int *slot);

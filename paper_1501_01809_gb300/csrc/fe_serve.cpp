@@ -395,6 +395,7 @@ fe_status server_stats(const fe_server *h, fe_server_stats *out) {
   out->base_bytes = s->base_bytes;
   out->estimate_misses = s->estimate_misses;
   out->run_s = s->run_s;
+  out->cg_launches = s->cg ? cg_launches(s->cg) : 0;
   for (const Req &q : s->reqs) {
     out->submitted++;
     if (q.res.status == FE_SOLVE_CONVERGED) out->converged++;

@@ -325,6 +325,7 @@ struct CgEngine {
   cudaStream_t capture;
   cudaGraphExec_t graph;
   int graph_iters;
+  int64_t launches;  // kernels launched by the engine (graph replays counted per kernel)
 };
 
 }  // namespace fe
@@ -389,6 +390,7 @@ void free_sys_vectors(CgEngine *e, CgSys &S) {
 }  // namespace
 
 bool cg_valid(const fe_cg *h) { return h && h->magic == kMagicCg && h->e; }
+int64_t cg_launches(const fe_cg *h) { return h->e->launches; }
 fe_ctx *cg_ctx(const fe_cg *h) { return h->e->ctx; }
 
 fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out) {
@@ -403,6 +405,7 @@ fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out) {
   e->grid = 152 * 4;
   e->graph = nullptr;
   e->graph_iters = 0;
+  e->launches = 0;
   e->dirty = true;
   e->d_sys = (CgSys *)dev_alloc(c, sizeof(CgSys) * max_systems);
   e->d_stat = (CgStat *)dev_alloc(c, sizeof(CgStat) * max_systems);
@@ -482,6 +485,7 @@ fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const d
   if (err == cudaSuccess && ntiles > 0) {
     k_cg_init<<<(unsigned)ntiles, kCgThreads, 0, st>>>(e->d_sys + s);
     err = cudaGetLastError();
+    e->launches++;
   }
   if (err != cudaSuccess) {
     cudaStreamSynchronize(st);
@@ -522,6 +526,7 @@ fe_status cg_iterate(fe_cg *h, int iters, int use_graph) {
       }
       if (err == cudaSuccess) err = cudaGraphLaunch(e->graph, st);
     }
+    if (err == cudaSuccess) e->launches += 2 * (int64_t)iters;
   }
   if (err != cudaSuccess) {
     snprintf(g_smsg, sizeof g_smsg, "fe_cg_iterate: %s", cudaGetErrorString(err));
@@ -540,6 +545,7 @@ fe_status cg_poll(fe_cg *h, int n, int *status, int *iters, double *rnorm, doubl
   cudaStream_t st = e->ctx->stream;
   k_cg_pack<<<(e->cap + 127) / 128, 128, 0, st>>>(e->d_sys, e->cap, e->d_stat);
   cudaError_t err = cudaGetLastError();
+  e->launches++;
   if (err == cudaSuccess)
     err = cudaMemcpyAsync(e->h_stat, e->d_stat, sizeof(CgStat) * e->cap, cudaMemcpyDeviceToHost, st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(st);
