@@ -271,11 +271,14 @@ fe_status fe_dirichlet_apply(fe_ctx *ctx, fe_mat *A, fe_dat *b, const uint8_t *i
  * Sec. 6.2 solves with CG) for many independent SPD CSR systems at once: every fe_cg_iterate runs
  * `iters` iterations of all added, unfinished systems with two persistent launches per iteration
  * (captured once into a CUDA graph when use_graph != 0, replayed on the context stream).  Dot
- * products are FP64 sums over fixed tiles of 1024 rows added in tile order (Globals with SUM
- * access, Sec. 4.4.2), so a system's iterates are bitwise the same alone or beside others.
- * Stopping test after every iteration: ||r||_2 <= rtol ||b||_2, or maxit iterations.
- * fe_cg_add reads A (values and pattern) and b, and updates x (initial guess on entry, iterate
- * after each call) in place; A, b and x must stay alive until fe_cg_remove.  fe_cg_poll
+ * products are FP64 sums over fixed tiles of 512 rows added in tile order (Globals with SUM
+ * access, Sec. 4.4.2), so a system's iterates are bitwise the same alone or beside others.  The
+ * products q = A p follow from the SpMV w = A z and q = w + beta q_old (algebraically equal to the
+ * textbook order).  Stopping test after every iteration: ||r||_2 <= rtol ||b||_2, or maxit
+ * iterations.  fe_cg_add copies A's values into the engine's sliced layout (SELL-32: slices of 32
+ * rows stored column by column; later changes to A are not seen), reads b, and updates x
+ * (initial guess on entry, iterate after each call) in place; A, b and x must stay alive until
+ * fe_cg_remove.  fe_cg_poll
  * synchronises the context stream and reports, for slots 0..nslots-1: status (FE_CG_* below,
  * -1 for a free slot), iterations, ||r|| and ||b||.  fe_cg_remove synchronises, then frees the
  * slot's vectors.  Errors: FE_EINVAL (no free slot, bad sizes), FE_ENOMEM, FE_ECUDA. */

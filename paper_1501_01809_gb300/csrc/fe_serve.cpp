@@ -125,17 +125,27 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 int nodes_p(int p) { return (p + 1) * (p + 2) / 2; }
 
 // Worst-case device bytes of one request (every allocation it makes, at its largest, while it
-// is built; nnz bounded by the cell-node incidences times the arity).
+// is built; nnz bounded by the cell-node incidences times the arity, a row's length by the
+// node's most frequent incidence times the arity).
 size_t estimate_bytes(const fe_solve_request &r) {
   const size_t nd = nodes_p(r.degree), ncell = r.ncell, nn = r.nnodes, nv = r.nvert;
   const size_t ninc = ncell * nd, nnz = ninc * nd;
+  std::vector<int32_t> inc(nn, 0);
+  int32_t maxinc = 0;
+  for (size_t k = 0; k < ninc; k++) {
+    const int32_t v = r.cell_node[k];
+    if (v >= 0 && (size_t)v < nn) maxinc = std::max(maxinc, ++inc[v]);
+  }
+  const size_t nsl = (nn + 31) / 32, maxlen = std::min(nn, (size_t)maxinc * nd);
+  const size_t sell = std::min(32 * nsl * maxlen, 32 * nsl * nn);
   auto a = [](size_t b) { return (std::max<size_t>(b, 16) + 255) & ~size_t(255); };
   size_t t = 0;
   t += a(4 * ninc) + a(12 * ncell) + a(16 * nv) + a(8 * nn) + a(nn) + a(8 * nn) + a(8 * nn);  // inputs, b, x
   t += 2 * a(8 * (nn + 1)) + a(4 * ninc) + a(4 * nn) + a(4 * ninc * nd) + a(ninc * nd) +
        a(8 * scan_tmp_elems((int64_t)nn)) + a(4) + a(4 * nnz);                                  // sparsity
   t += a(8 * nnz) + a(8 * ncell * nd * (nd + 1) / 2) + a(8 * ncell * nd);                       // Mat, staging
-  t += 6 * a(8 * nn) + a(24 * (nn / 1024 + 1));                                                 // CG vectors
+  t += 5 * a(8 * nn) + a(24 * (nn / 1024 + 1));                                                 // CG vectors
+  t += a(8 * (nsl + 1)) + a(4 * nsl) + a(8 * scan_tmp_elems((int64_t)nsl)) + a(8 * sell) + a(4 * sell);  // SELL
   return t;
 }
 

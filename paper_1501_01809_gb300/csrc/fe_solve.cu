@@ -12,10 +12,13 @@
 // system's arithmetic depends only on its own data and tiling: the iterates are bitwise the same
 // whichever other systems share the launches.
 //
-//   launch A, per tile: p_new = z + beta p_old (rows of the tile, stored), q = A p_new (gathering
-//            z_j + beta p_old_j for the columns), partial p_new.q; last tile: alpha = rz / p.q
-//   launch B, per tile: x += alpha p_new, r -= alpha q, z = r / diag, partials r.z and r.r;
-//            last tile: beta = rz' / rz, convergence test ||r|| <= rtol ||b||, swap p buffers
+//   launch A, per tile: w = A z (one FMA per nonzero), then per row q = w + beta q and
+//            p = z + beta p (q = A p follows from p = z + beta p_old: A p = A z + beta A p_old),
+//            partial p.q; last tile: alpha = rz / p.q
+//   launch B, per tile: x += alpha p, r -= alpha q, z = r / diag, partials r.z and r.r;
+//            last tile: beta = rz' / rz, convergence test ||r|| <= rtol ||b||
+// FP64 arithmetic is the scarce resource on this GPU (about 1/64 of the FP32 rate), so the SpMV
+// runs on z, which needs no per-entry update, instead of gathering z_j + beta p_old_j.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -29,9 +32,19 @@
 namespace fe {
 namespace {
 
+#ifndef FE_CG_TILE_ROWS
+#define FE_CG_TILE_ROWS 512
+#endif
+// (tile rows and SELL batch were swept on GB300 over 256..2048 rows and 4..8 columns: 512 / 4
+// balances large systems against the per-iteration latency of small ones)
 constexpr int kCgThreads = 256;
-constexpr int kCgRowsPerThread = 4;
-constexpr int64_t kCgTileRows = kCgThreads * kCgRowsPerThread;
+constexpr int64_t kCgTileRows = FE_CG_TILE_ROWS;              // rows per tile (a multiple of kCgThreads)
+constexpr int kCgRowsPerThread = FE_CG_TILE_ROWS / kCgThreads;
+#ifndef FE_CG_SELL_BATCH
+#define FE_CG_SELL_BATCH 4
+#endif
+constexpr int kSellBatch = FE_CG_SELL_BATCH;  // SELL columns whose loads are issued together
+static_assert(FE_CG_TILE_ROWS % kCgThreads == 0, "tile rows must be a multiple of the block size");
 
 enum CgStatusCode : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
 
@@ -40,10 +53,15 @@ struct CgSys {
   const int32_t *colidx;
   const double *vals;
   const double *b;
-  double *x, *r, *z, *q, *dinv, *part;
-  double *p[2];
+  double *x, *r, *z, *q, *dinv, *part, *p;
+  // A in slices of 32 consecutive rows stored column by column (SELL-32): slice s holds
+  // (sptr[s+1] - sptr[s]) columns of 32 entries from svals/scols + 32 sptr[s]; a row's entries in
+  // CSR order, then zeros (column = the row itself) up to the slice width
+  const int64_t *sptr;
+  const double *svals;
+  const int32_t *scols;
   int64_t nrows;
-  int ntiles, cur;
+  int ntiles;
   double rz, alpha, beta, bnorm2, rnorm2, rtol;
   int iters, maxit, active, status;
   unsigned cnt;
@@ -92,15 +110,12 @@ __device__ __forceinline__ bool last_tile(unsigned *cnt, int ntiles, int *sh_las
   return *sh_last != 0;
 }
 
-// Sum of part[t * 3 + slot] over t = 0..ntiles-1 in a fixed association (warp 0; lane l takes
-// t = l, l + 32, ... in order, then the xor butterfly).  Result valid in lane 0.
-__device__ __forceinline__ double ordered_tiles_sum(const double *part, int slot, int ntiles) {
-  const int l = threadIdx.x & 31;
+// Sum of part[t * 3 + slot] over t = 0..ntiles-1 in a fixed association: thread k adds tiles
+// k, k + blockDim, ... in order, then block_sum.  Called by the whole block; result in thread 0.
+__device__ __forceinline__ double block_tiles_sum(const double *part, int slot, int ntiles, double *sh) {
   double s = 0.0;
-  for (int t = l; t < ntiles; t += 32) s += __ldcg(part + (int64_t)t * 3 + slot);
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-  return s;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s += __ldcg(part + (int64_t)t * 3 + slot);
+  return block_sum(s, sh);
 }
 
 // ---------------------------------------------------------------------------------- Dirichlet
@@ -126,6 +141,37 @@ __global__ void k_dirichlet(int64_t nrows, const int64_t *__restrict__ rowptr, c
 }
 
 // ---------------------------------------------------------------------------------- CG kernels
+// SELL-32 layout: width of each slice (the longest of its 32 rows).  One warp per slice.
+__global__ void k_sell_width(const int64_t *__restrict__ rowptr, int64_t nrows, int64_t nslices,
+                             int32_t *__restrict__ width) {
+  const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (sl >= nslices) return;  // warp-uniform
+  const int64_t i = sl * 32 + lane;
+  const int len = i < nrows ? (int)(rowptr[i + 1] - rowptr[i]) : 0;
+  const int w = __reduce_max_sync(0xffffffffu, len);
+  if (lane == 0) width[sl] = w;
+}
+
+// SELL-32 layout: copy of the values and columns, padded with zeros on the row's own column.
+__global__ void k_sell_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                            const double *__restrict__ vals, int64_t nrows, int64_t nslices,
+                            const int64_t *__restrict__ sptr, double *__restrict__ svals, int32_t *__restrict__ scols) {
+  const int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (sl >= nslices) return;
+  const int64_t i = sl * 32 + lane;
+  const int64_t e0 = i < nrows ? rowptr[i] : 0;
+  const int len = i < nrows ? (int)(rowptr[i + 1] - e0) : 0;
+  const int32_t pad = i < nrows ? (int32_t)i : 0;
+  const int64_t k0 = sptr[sl], width = sptr[sl + 1] - k0;
+  for (int64_t k = 0; k < width; k++) {
+    const int64_t d = (k0 + k) * 32 + lane;
+    svals[d] = k < len ? vals[e0 + k] : 0.0;
+    scols[d] = k < len ? colidx[e0 + k] : pad;
+  }
+}
+
 // Initial residual of one system (grid = its tiles): r = b - A x, z = r / diag, p_old = 0.
 __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgSys *S) {
   __shared__ double sh[kCgThreads / 32];
@@ -149,7 +195,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgSys *S) {
     S->dinv[i] = di;
     S->r[i] = ri;
     S->z[i] = zi;
-    S->p[0][i] = 0.0;
+    S->p[i] = 0.0;
+    S->q[i] = 0.0;
     rz += ri * zi;
     rr += ri * ri;
     bb += bi * bi;
@@ -163,17 +210,16 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgSys *S) {
     S->part[(int64_t)t * 3 + 1] = rr;
     S->part[(int64_t)t * 3 + 2] = bb;
   }
-  if (last_tile(&S->cnt, S->ntiles, &sh_last) && threadIdx.x < 32) {
-    const double srz = ordered_tiles_sum(S->part, 0, S->ntiles);
-    const double srr = ordered_tiles_sum(S->part, 1, S->ntiles);
-    const double sbb = ordered_tiles_sum(S->part, 2, S->ntiles);
+  if (last_tile(&S->cnt, S->ntiles, &sh_last)) {
+    const double srz = block_tiles_sum(S->part, 0, S->ntiles, sh);
+    const double srr = block_tiles_sum(S->part, 1, S->ntiles, sh);
+    const double sbb = block_tiles_sum(S->part, 2, S->ntiles, sh);
     if (threadIdx.x == 0) {
       S->rz = srz;
       S->rnorm2 = srr;
       S->bnorm2 = sbb;
       S->beta = 0.0;
       S->alpha = 0.0;
-      S->cur = 0;
       S->iters = 0;
       if (atomicOr(&S->bad, 0)) S->status = CG_BREAKDOWN;
       else if (sqrt(srr) <= S->rtol * sqrt(sbb)) S->status = CG_CONVERGED;
@@ -185,43 +231,63 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgSys *S) {
   }
 }
 
-// Launch A: new direction, q = A p, p.q; last tile: alpha.
-__global__ void __launch_bounds__(kCgThreads) k_cg_direction_spmv(CgSys *sys, const CgTile *__restrict__ tiles,
-                                                                  const int *ntiles_p) {
+// Launch A: w = A z, q = w + beta q, p = z + beta p, p.q; last tile: alpha.  A warp takes one
+// SELL-32 slice at a time: lane l owns row 32 s + l, every load of values and columns is one
+// coalesced 256-byte access, kSellBatch columns in flight, and the row sum runs in CSR order.
+__global__ void __launch_bounds__(kCgThreads, 6) k_cg_direction_spmv(CgSys *sys, const CgTile *__restrict__ tiles,
+                                                                     const int *ntiles_p) {
   __shared__ double sh[kCgThreads / 32];
   __shared__ int sh_last;
   const int ntiles = *ntiles_p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const CgTile tl = tiles[t];
     CgSys *S = sys + tl.sys;
     if (!S->active) continue;
     const double beta = S->beta;
-    const int cur = S->cur;
-    const double *__restrict__ pold = S->p[cur];
-    double *__restrict__ pnew = S->p[cur ^ 1];
+    double *__restrict__ p = S->p;
+    double *__restrict__ q = S->q;
     const double *__restrict__ z = S->z;
-    const int64_t *__restrict__ rowptr = S->rowptr;
-    const int32_t *__restrict__ colidx = S->colidx;
-    const double *__restrict__ vals = S->vals;
-    const int64_t r0 = (int64_t)tl.tile * kCgTileRows, nrows = S->nrows;
+    const int64_t *__restrict__ sptr = S->sptr;
+    const double *__restrict__ svals = S->svals;
+    const int32_t *__restrict__ scols = S->scols;
+    const int64_t nrows = S->nrows;
+    const int64_t nsl = (nrows + 31) / 32;
+    const int64_t s0 = (int64_t)tl.tile * (kCgTileRows / 32);
+    const int64_t s1 = s0 + kCgTileRows / 32 < nsl ? s0 + kCgTileRows / 32 : nsl;
     double pq = 0.0;
-    for (int k = 0; k < kCgRowsPerThread; k++) {
-      const int64_t i = r0 + k * kCgThreads + threadIdx.x;
-      if (i >= nrows) break;
-      double acc = 0.0;
-      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
-        const int32_t j = colidx[e];
-        acc += vals[e] * (z[j] + beta * pold[j]);
+    for (int64_t sl = s0 + warp; sl < s1; sl += kCgThreads / 32) {
+      const int64_t k0 = sptr[sl];
+      const int width = (int)(sptr[sl + 1] - k0);
+      const double *__restrict__ vv = svals + k0 * 32 + lane;
+      const int32_t *__restrict__ cc = scols + k0 * 32 + lane;
+      double w = 0.0;
+      int k = 0;
+      for (; k + kSellBatch <= width; k += kSellBatch) {
+        int32_t c[kSellBatch];
+        double v[kSellBatch];
+#pragma unroll
+        for (int u = 0; u < kSellBatch; u++) {
+          c[u] = cc[(int64_t)(k + u) * 32];
+          v[u] = vv[(int64_t)(k + u) * 32];
+        }
+#pragma unroll
+        for (int u = 0; u < kSellBatch; u++) w = fma(v[u], z[c[u]], w);
       }
-      const double pn = z[i] + beta * pold[i];
-      pnew[i] = pn;
-      S->q[i] = acc;
-      pq += pn * acc;
+      for (; k < width; k++) w = fma(vv[(int64_t)k * 32], z[cc[(int64_t)k * 32]], w);
+      const int64_t i = sl * 32 + lane;
+      if (i < nrows) {
+        const double qi = w + beta * q[i];
+        const double pi = z[i] + beta * p[i];
+        q[i] = qi;
+        p[i] = pi;
+        pq += pi * qi;
+      }
     }
     pq = block_sum(pq, sh);
     if (threadIdx.x == 0) S->part[(int64_t)tl.tile * 3] = pq;
-    if (last_tile(&S->cnt, S->ntiles, &sh_last) && threadIdx.x < 32) {
-      const double s = ordered_tiles_sum(S->part, 0, S->ntiles);
+    if (last_tile(&S->cnt, S->ntiles, &sh_last)) {
+      const double s = block_tiles_sum(S->part, 0, S->ntiles, sh);
       if (threadIdx.x == 0) {
         if (!(s > 0.0)) {
           S->status = CG_BREAKDOWN;
@@ -236,8 +302,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_direction_spmv(CgSys *sys, co
   }
 }
 
-// Launch B: x, r, z; r.z and r.r; last tile: beta, convergence, buffer swap.
-__global__ void __launch_bounds__(kCgThreads) k_cg_update(CgSys *sys, const CgTile *__restrict__ tiles,
+// Launch B: x, r, z; r.z and r.r; last tile: beta and the convergence test.
+__global__ void __launch_bounds__(kCgThreads, 6) k_cg_update(CgSys *sys, const CgTile *__restrict__ tiles,
                                                           const int *ntiles_p) {
   __shared__ double sh[kCgThreads / 32];
   __shared__ int sh_last;
@@ -247,19 +313,26 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(CgSys *sys, const CgTi
     CgSys *S = sys + tl.sys;
     if (!S->active) continue;
     const double alpha = S->alpha;
-    const double *__restrict__ pn = S->p[S->cur ^ 1];
+    const double *__restrict__ p = S->p;
+    const double *__restrict__ q = S->q;
+    const double *__restrict__ dinv = S->dinv;
+    double *__restrict__ x = S->x;
+    double *__restrict__ r = S->r;
+    double *__restrict__ z = S->z;
     const int64_t r0 = (int64_t)tl.tile * kCgTileRows, nrows = S->nrows;
     double rz = 0.0, rr = 0.0;
+#pragma unroll 2
     for (int k = 0; k < kCgRowsPerThread; k++) {
       const int64_t i = r0 + k * kCgThreads + threadIdx.x;
-      if (i >= nrows) break;
-      S->x[i] += alpha * pn[i];
-      const double ri = S->r[i] - alpha * S->q[i];
-      const double zi = S->dinv[i] * ri;
-      S->r[i] = ri;
-      S->z[i] = zi;
-      rz += ri * zi;
-      rr += ri * ri;
+      if (i < nrows) {
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        const double zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+      }
     }
     rz = block_sum(rz, sh);
     rr = block_sum(rr, sh);
@@ -267,15 +340,14 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(CgSys *sys, const CgTi
       S->part[(int64_t)tl.tile * 3 + 1] = rz;
       S->part[(int64_t)tl.tile * 3 + 2] = rr;
     }
-    if (last_tile(&S->cnt, S->ntiles, &sh_last) && threadIdx.x < 32) {
-      const double srz = ordered_tiles_sum(S->part, 1, S->ntiles);
-      const double srr = ordered_tiles_sum(S->part, 2, S->ntiles);
+    if (last_tile(&S->cnt, S->ntiles, &sh_last)) {
+      const double srz = block_tiles_sum(S->part, 1, S->ntiles, sh);
+      const double srr = block_tiles_sum(S->part, 2, S->ntiles, sh);
       if (threadIdx.x == 0) {
         S->beta = srz / S->rz;
         S->rz = srz;
         S->rnorm2 = srr;
         S->iters += 1;
-        S->cur ^= 1;
         if (sqrt(srr) <= S->rtol * sqrt(S->bnorm2)) {
           S->status = CG_CONVERGED;
           S->active = 0;
@@ -382,8 +454,10 @@ void free_sys_vectors(CgEngine *e, CgSys &S) {
   dev_free(e->ctx, S.z);
   dev_free(e->ctx, S.q);
   dev_free(e->ctx, S.dinv);
-  dev_free(e->ctx, S.p[0]);
-  dev_free(e->ctx, S.p[1]);
+  dev_free(e->ctx, S.p);
+  dev_free(e->ctx, (void *)S.sptr);
+  dev_free(e->ctx, (void *)S.svals);
+  dev_free(e->ctx, (void *)S.scols);
   dev_free(e->ctx, S.part);
   memset(&S, 0, sizeof S);
 }
@@ -402,7 +476,12 @@ fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out) {
   e->h_sys.assign(max_systems, CgSys{});
   e->used.assign(max_systems, 0);
   e->tile_cap = 1024;
-  e->grid = 152 * 4;
+  int sms = 152, per_a = 4, per_b = 4, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_a, k_cg_direction_spmv, kCgThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, k_cg_update, kCgThreads, 0);
+  e->grid = sms * (per_a < per_b ? per_a : per_b);  // one wave of resident CTAs
+  if (e->grid < 1) e->grid = 152;
   e->graph = nullptr;
   e->graph_iters = 0;
   e->launches = 0;
@@ -471,13 +550,48 @@ fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const d
   S.z = (double *)dev_alloc(e->ctx, vb);
   S.q = (double *)dev_alloc(e->ctx, vb);
   S.dinv = (double *)dev_alloc(e->ctx, vb);
-  S.p[0] = (double *)dev_alloc(e->ctx, vb);
-  S.p[1] = (double *)dev_alloc(e->ctx, vb);
+  S.p = (double *)dev_alloc(e->ctx, vb);
   S.part = (double *)dev_alloc(e->ctx, sizeof(double) * 3 * (ntiles > 0 ? ntiles : 1));
-  if (!S.r || !S.z || !S.q || !S.dinv || !S.p[0] || !S.p[1] || !S.part) {
+  if (!S.r || !S.z || !S.q || !S.dinv || !S.p || !S.part) {
     free_sys_vectors(e, S);
     snprintf(g_smsg, sizeof g_smsg, "fe_cg_add: device allocation failed");
     return FE_ENOMEM;
+  }
+  // SELL-32 copy of A: slice widths, their prefix sums, then the padded values and columns
+  cudaStream_t st0 = e->ctx->stream;
+  const int64_t nsl = (nrows + 31) / 32;
+  int64_t *sptr = (int64_t *)dev_alloc(e->ctx, sizeof(int64_t) * (nsl + 1));
+  int32_t *width = (int32_t *)dev_alloc(e->ctx, sizeof(int32_t) * (nsl > 0 ? nsl : 1));
+  int64_t *tmp = (int64_t *)dev_alloc(e->ctx, sizeof(int64_t) * scan_tmp_elems(nsl));
+  S.sptr = sptr;
+  int64_t ncol = 0;
+  cudaError_t err0 = (sptr && width && tmp) ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (err0 == cudaSuccess && nsl > 0) {
+    k_sell_width<<<(unsigned)((nsl * 32 + 255) / 256), 256, 0, st0>>>(rowptr, nrows, nsl, width);
+    err0 = cudaGetLastError();
+  }
+  if (err0 == cudaSuccess) err0 = exclusive_scan_i32_to_i64(width, sptr, nsl, tmp, st0);
+  if (err0 == cudaSuccess) err0 = cudaMemcpyAsync(&ncol, sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, st0);
+  if (err0 == cudaSuccess) err0 = cudaStreamSynchronize(st0);
+  dev_free(e->ctx, width);
+  dev_free(e->ctx, tmp);
+  if (err0 == cudaSuccess) {
+    S.svals = (double *)dev_alloc(e->ctx, sizeof(double) * 32 * (ncol > 0 ? ncol : 1));
+    S.scols = (int32_t *)dev_alloc(e->ctx, sizeof(int32_t) * 32 * (ncol > 0 ? ncol : 1));
+    if (!S.svals || !S.scols) err0 = cudaErrorMemoryAllocation;
+  }
+  if (err0 == cudaSuccess && nsl > 0) {
+    k_sell_fill<<<(unsigned)((nsl * 32 + 255) / 256), 256, 0, st0>>>(rowptr, colidx, vals, nrows, nsl, sptr,
+                                                                     (double *)S.svals, (int32_t *)S.scols);
+    err0 = cudaGetLastError();
+    e->launches += 5;  // width, three scan passes, fill
+  }
+  if (err0 != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(st0);
+    free_sys_vectors(e, S);
+    snprintf(g_smsg, sizeof g_smsg, "fe_cg_add: sliced copy of A: %s", cudaGetErrorString(err0));
+    return err0 == cudaErrorMemoryAllocation ? FE_ENOMEM : FE_ECUDA;
   }
   if (nrows == 0) S.status = CG_CONVERGED;  // nothing to solve
   cudaStream_t st = e->ctx->stream;
