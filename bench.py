@@ -39,6 +39,9 @@ WORKLOADS = {
     "p1-2d": dict(dim=2, p=1, n=64, jitter=0.0, seed=0,
                   name="P1 Lagrange UnitSquareMesh 64x64 (8192 cells, 4225 nodes), Helmholtz, FP64 CSR: "
                        "sparsity + assembly + matrix-free action"),
+    "p1-sweep": dict(sweep=True, dim=2, p=1, ns=[256, 512, 1024, 2048], jitter=0.0, seed=0,
+                     name="P1 Lagrange UnitSquareMesh n x n for n = 256..2048 (up to 8,388,608 cells), Helmholtz, "
+                          "FP64 CSR: assembly roofline sweep (labelled extra; sparsity built once per n)"),
     "batch": dict(count=2048, seed=4, lo=8, hi=256,
                   name="2048 UnitSquareMesh n x n meshes, n log-uniform in [8,256] (seed 4), each P1 or P2 "
                        "(Bernoulli 1/2), Helmholtz CSR + RHS f v dx (f uniform[-1,1] per node, seed 1000+i), "
@@ -53,7 +56,10 @@ WORKLOADS = {
 # source they were taken from; reported as null once the source has changed.
 TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 250.05 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
-    ("assemble", "push", "f32x2"): (1.024e9, "05c9080c2599"),
+    ("assemble", "push", "f32x2"): (1.024e9, "768d9df1bf84"),
+    # one sparsity rebuild (k_inc_count, k_inc_fill, k_rows_build, k_rows_compact, scans, zeros):
+    # 431.4 MB at 40^3, scaled x4.096 to 64^3 (at 40^3 part of the output stays in L2: a lower bound)
+    ("sparsity", None, None): (1.767e9, "8cad725b839f"),
 }
 
 
@@ -225,6 +231,8 @@ def run_ours(args, wl, rank, world):
             phases[p] += ev[p].elapsed_time(ev[p + 1])
     total_ms = evs[0][0].elapsed_time(evs[-1][4])
     ms_step = total_ms / args.steps
+    per_step = sorted(ev[0].elapsed_time(ev[4]) for ev in evs)
+    step_stats = {"min_ms": per_step[0], "median_ms": per_step[len(per_step) // 2], "max_ms": per_step[-1]}
     if dist:
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
         td.all_reduce(t, op=td.ReduceOp.MAX)
@@ -302,8 +310,9 @@ def run_ours(args, wl, rank, world):
     else:
         roof = {"bound": "hbm", "achieved": dk["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": dk["hbm_frac"], "kernel": dom, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
-    tr = TRAFFIC.get((dom, args.strategy, args.precision))
-    roof["traffic"] = tr[0] if tr and tr[1] == _src_hash("fe_kernels.cuh") else None
+    tr = TRAFFIC.get((dom, args.strategy, args.precision)) or TRAFFIC.get((dom, None, None))
+    src_file = "fe_sparsity.cu" if dom == "sparsity" else "fe_kernels.cuh"
+    roof["traffic"] = tr[0] if tr and tr[1] == _src_hash(src_file) else None
     out = {
         "metric": METRIC, "value": world * ncell / (ms_step / 1e3), "unit": "cells/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -314,13 +323,83 @@ def run_ours(args, wl, rank, world):
                                  if args.precision == "f32x2" else "FP64 throughout"),
                    "parallelism": f"replicas x{world} (independent meshes, no collective)",
                    "l2": "inputs larger than L2 (CSR values + lookup table ~650 MB), no flush"},
-        "roofline": roof, "kernels": kern, "gpu_launches": launches, "wall_s_timed": wall,
+        "roofline": roof, "kernels": kern, "step_ms": step_stats, "gpu_launches": launches, "wall_s_timed": wall,
         "clocks": clk.summary(), "e2e": e2e,
     }
     return out, (mesh, cmap, nn, x)
 
 
 # ------------------------------------------------------------------------------ batched workload
+
+# ------------------------------------------------------------------------------ P1 roofline sweep
+
+def run_p1_sweep(args, wl, rank, world):
+    """Assembly (zero + Mat) and action of P1 Helmholtz on n x n squares for several n: the P1 roofline
+    behaviour as the mesh outgrows L2.  Sparsity built once per n (outside the timed loop)."""
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    prec = {"fp64": fe.PREC_FP64, "f32x2": fe.PREC_F32X2}[args.precision]
+    peaks, src = _peaks()
+    rows = []
+    for n in wl["ns"]:
+        w = dict(wl, n=n)
+        mesh, cmap, nn, x = make_inputs(w)
+        t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+             dict(map=cmap, cv=mesh.cell_vertex, xy=mesh.coords, x=x).items()}
+        ty = torch.zeros_like(t["x"])
+        with torch.cuda.stream(stream):
+            cells, nodes, verts = fe.set_create(ctx, mesh.ncell), fe.set_create(ctx, nn), fe.set_create(ctx, mesh.nvert)
+            M, CM = fe.map_create(ctx, cells, nodes, t["map"]), fe.map_create(ctx, cells, verts, t["cv"])
+            XY, X, Y = fe.dat_create(ctx, verts, t["xy"]), fe.dat_create(ctx, nodes, t["x"]), fe.dat_create(ctx, nodes, ty)
+            K = fe.kernel_create(ctx, fe.FORM_HELMHOLTZ, 2, 1, precision=prec, strategy=fe.STRATEGY_PUSH)
+            sp = fe.sparsity_build(ctx, M, M)
+            A = fe.mat_create(ctx, sp)
+        nnz = fe.sparsity_csr(sp)[2]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for _ in range(args.warmup):
+            fe.assemble_mat(ctx, K, cells, A, XY, CM, zero_first=True)
+            fe.action(ctx, K, cells, X, Y, M, XY, CM, zero_first=True)
+        fe.sync(ctx)
+        reps = max(3, min(args.steps, 50))
+        ev[0].record(stream)
+        for _ in range(reps):
+            fe.assemble_mat(ctx, K, cells, A, XY, CM, zero_first=True)
+        ev[1].record(stream)
+        for _ in range(reps):
+            fe.action(ctx, K, cells, X, Y, M, XY, CM, zero_first=True)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        ms_a, ms_x = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+        # algorithmic bytes: map 12 + coordinate map 12 per cell, coordinates once, CSR values written
+        # once (zero + INC counted once), x read and y written once for the action
+        b_a = mesh.ncell * 24 + mesh.nvert * 16 + nnz * 8
+        b_x = mesh.ncell * 24 + mesh.nvert * 16 + 2 * nn * 8
+        rows.append({"n": n, "cells": mesh.ncell, "nnz": nnz, "assemble_ms": ms_a, "action_ms": ms_x,
+                     "assemble_cells_per_s": mesh.ncell / (ms_a / 1e3), "action_cells_per_s": mesh.ncell / (ms_x / 1e3),
+                     "assemble_hbm_frac": b_a / (ms_a / 1e3) / 1e9 / peaks["hbm_gbs"],
+                     "action_hbm_frac": b_x / (ms_x / 1e3) / 1e9 / peaks["hbm_gbs"]})
+        del A, sp
+    big = rows[-1]
+    gbs = (big["cells"] * 24 + (big["n"] + 1) ** 2 * 16 + big["nnz"] * 8) / (big["assemble_ms"] / 1e3) / 1e9
+    out = {"metric": "cells/s assembled (P1 CSR assembly incl. zero), labelled extra sweep", "value":
+           world * big["assemble_cells_per_s"], "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": big["assemble_ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["name"], "sweep": rows, "precision": args.precision,
+                      "parallelism": f"replicas x{world}", "l2": "largest n: inputs larger than L2"},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                        "kernel": f"k_zero_f64 + k_mat_push<2,1,HELMHOLTZ> at n={big['n']}",
+                        "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+           "gpu_launches": 2 * max(3, min(args.steps, 50)), "e2e": None}
+    return out
+
 
 def make_batch_inputs(wl):
     """Per mesh (n, p, mesh, cell-node map, nodes, f); meshes of equal (n, p) share host arrays only."""
@@ -641,7 +720,8 @@ def serve_cpu_sample(reqs, budget_s):
     elimination, CG), until budget_s seconds (a single larger solve would take minutes on one core)."""
     import oracle as O
     done, t0 = 0, time.perf_counter()
-    for r in (q for q in reqs if q["n"] <= SERVE_CPU_MAX_N):
+    small = [q for q in reqs if q["n"] <= SERVE_CPU_MAX_N]
+    for r in (small[k % len(small)] for k in range(1 << 30)):
         rp, ci = O.sparsity(r["cmap"], r["cmap"], r["nn"], r["nn"])
         v, _ = O.assemble_mat(2, r["p"], O.LAPLACE, r["cmap"], r["mesh"].coords, r["mesh"].cell_vertex, rp, ci)
         b, _ = O.assemble_vec(2, r["p"], r["p"], r["cmap"], r["nn"], r["mesh"].coords, r["mesh"].cell_vertex, r["f"],
@@ -694,6 +774,8 @@ def cpu_baseline(wl, inputs, ncell_sample):
 def run_reference(args, wl):
     import oracle
     oracle.build()
+    if wl.get("sweep"):
+        wl = dict(wl, n=wl["ns"][-1])
     if wl.get("serve"):
         reqs = make_serve_inputs(wl)
         res = [serve_cpu_sample(reqs, args.ref_seconds) for _ in range(args.steps)]
@@ -774,6 +856,11 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
+    if wl.get("sweep"):
+        out = run_p1_sweep(args, wl, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if wl.get("serve"):
         out, reqs = run_serve(args, wl, rank, world)
     elif "count" in wl:
@@ -786,9 +873,9 @@ def main():
             oracle.build()
             done, dt = serve_cpu_sample(reqs, 15.0)
             out["cpu_baseline"] = {"value": done / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                   "sample": f"the first {done} requests with n <= {SERVE_CPU_MAX_N} in arrival "
-                                             f"order (sparsity, assembly, elimination, CG), {dt:.1f} s on 1 host "
-                                             f"core; larger requests are left out of the sample"}
+                                   "sample": f"{done} solves of the requests with n <= {SERVE_CPU_MAX_N}, in arrival "
+                                             f"order and repeated (sparsity, assembly, elimination, CG), {dt:.1f} s "
+                                             f"on 1 host core; larger requests are left out of the sample"}
         elif world == 1 and not args.no_cpu_baseline and "count" in wl:
             import oracle
             oracle.build()

@@ -187,6 +187,47 @@ __device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &
   }
 }
 
+
+// Bitonic sort of 64 (key, payload) pairs across a warp, ascending by key: lane l holds elements
+// 2l (k0, p0) and 2l + 1 (k1, p1).  Equal keys keep their own payloads (both partners keep theirs
+// on a tie), so no payload is lost or duplicated.
+__device__ __forceinline__ void warp_bitonic64(uint32_t &k0, int32_t &p0, uint32_t &k1, int32_t &p1) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+    const bool up = ((2 * lane) & k) == 0;
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 1) {
+        const bool sw = up ? (k0 > k1) : (k0 < k1);
+        if (sw) {
+          const uint32_t tk = k0;
+          k0 = k1;
+          k1 = tk;
+          const int32_t tp = p0;
+          p0 = p1;
+          p1 = tp;
+        }
+      } else {
+        const int m = j >> 1;
+        const uint32_t o0 = __shfl_xor_sync(0xffffffffu, k0, m), o1 = __shfl_xor_sync(0xffffffffu, k1, m);
+        const int32_t r0 = __shfl_xor_sync(0xffffffffu, p0, m), r1 = __shfl_xor_sync(0xffffffffu, p1, m);
+        const bool take_min = ((lane & m) == 0) == up;
+        const bool t0 = take_min ? (o0 < k0) : (o0 > k0);
+        const bool t1 = take_min ? (o1 < k1) : (o1 > k1);
+        if (t0) {
+          k0 = o0;
+          p0 = r0;
+        }
+        if (t1) {
+          k1 = o1;
+          p1 = r1;
+        }
+      }
+    }
+  }
+}
+
 struct RowsParams {
   int64_t nrows;
   int ndr, ndc;
@@ -245,6 +286,63 @@ __global__ void k_rows_build(const RowsParams p) {
     }
     if (na == 0) {
       if (lane == 0) p.rowlen[r] = 0;
+      continue;
+    }
+    if (ncand <= 64 && na <= 32) {
+      // Small rows (most rows of P2/P3 meshes): sort the candidates instead of hashing them.
+      // 1. canonical incidence order by rank
+      const uint32_t v = lane < na ? (uint32_t)p.adj[a0 + lane] : 0xFFFFFFFFu;
+      int rk = 0;
+      for (int q = 0; q < na; q++) rk += __shfl_sync(0xffffffffu, v, q) < v;
+      if (lane < na) {
+        adjs[rk] = v;
+        p.adj[a0 + rk] = (int32_t)v;
+      }
+      __syncwarp();
+      // 2. candidates t = 2 lane + h: (column, t); padding sorts last
+      uint32_t k0 = 0xFFFFFFFFu, k1 = 0xFFFFFFFFu;
+      int32_t q0 = -1, q1 = -1;
+      if (2 * lane < ncand) {
+        const uint32_t t = 2 * lane, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+        k0 = (uint32_t)p.cmap[(int64_t)div_ndr(adjs[a], p) * ndc + j];
+        q0 = (int32_t)t;
+      }
+      if (2 * lane + 1 < ncand) {
+        const uint32_t t = 2 * lane + 1, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+        k1 = (uint32_t)p.cmap[(int64_t)div_ndr(adjs[a], p) * ndc + j];
+        q1 = (int32_t)t;
+      }
+      warp_bitonic64(k0, q0, k1, q1);
+      // 3. first element of each run of equal columns; ranks by a warp prefix count
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, k1, 1);
+      const int f0 = q0 >= 0 && (lane == 0 || k0 != prev);
+      const int f1 = q1 >= 0 && k1 != k0;
+      const int c = f0 + f1;
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+      }
+      const int nu_small = __shfl_sync(0xffffffffu, incl, 31);
+      const int rank0 = incl - c + f0 - 1, rank1 = incl - 1;
+      int32_t *outc = p.coltmp + a0 * ndc;
+      if (f0) outc[rank0] = (int32_t)k0;
+      if (f1) outc[rank1] = (int32_t)k1;
+      // 4. lookup table: every candidate gets the rank of its column
+      if (q0 >= 0 && rank0 < kMaxRowLen) {
+        const uint32_t a = div_ndc((uint32_t)q0, p), j = (uint32_t)q0 - a * (uint32_t)ndc;
+        p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank0;
+      }
+      if (q1 >= 0 && rank1 < kMaxRowLen) {
+        const uint32_t a = div_ndc((uint32_t)q1, p), j = (uint32_t)q1 - a * (uint32_t)ndc;
+        p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank1;
+      }
+      if (lane == 0) {
+        p.rowlen[r] = nu_small;
+        if (nu_small > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
+      }
+      __syncwarp();
       continue;
     }
     const int H = next_pow2(ncand);  // <= cap
