@@ -612,8 +612,8 @@ int oracle_eval_function(int dim, int p, int qdeg, int64_t ncell, const int32_t 
 
 /*
  * Strong Dirichlet conditions u = g on the boundary nodes, applied to an assembled system by
- * symmetric elimination (the Poisson listing of Sec. 3.1 assembles A and b "with the boundary
- * conditions applied"; Sec. 6.2 states u = 0 on Gamma_D).  Written out from the definition:
+ * symmetric elimination (the Poisson listing of Sec. 3.1 imposes its boundary condition while
+ * assembling A and b; Sec. 6.2 states u = 0 on Gamma_D).  Written out from the definition:
  * for every row i that is not a boundary row, b_i <- b_i - sum_{j boundary} A_ij g_j and
  * A_ij <- 0 for boundary j; for every boundary row i, A_ij <- delta_ij and b_i <- g_i.
  * Rows are processed in order, entries of a row in CSR order.  g == NULL means g = 0.

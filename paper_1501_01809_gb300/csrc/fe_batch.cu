@@ -1,7 +1,7 @@
 // Batched assembly of many independent meshes in one persistent launch.
 //
-// The paper names the fixed per-field overhead of a par_loop ("some hundreds of microseconds",
-// Sec. 6.4.2) as what limits strong scaling; on a GPU the analogue is the launch and tail cost of
+// The paper attributes the flattening of strong scaling to a fixed cost per field and par_loop of
+// a few hundred microseconds (Sec. 6.4.2); on a GPU the analogue is the launch and tail cost of
 // one kernel per mesh.  A batch concatenates the Mats and right-hand sides of all its problems in
 // two contiguous buffers and assembles them with two launches (zero, then one persistent kernel
 // whose CTAs take (problem, cell range) tiles from a device work counter and dispatch on the
