@@ -133,6 +133,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# --------------------------------------------------------------------------------------- ranks
+
+def max_over_ranks(x, device=None):
+    """Maximum of x over the ranks of the default process group (x itself when not distributed).
+    Replicas exchange nothing else: this is the only collective of a multi-rank run."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if device is not None else "cpu")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job rate: every rank processes units_per_rank in at most ms_max milliseconds."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 # --------------------------------------------------------------------------------------- workload
 
 def make_inputs(wl):
@@ -234,9 +253,7 @@ def run_ours(args, wl, rank, world):
     per_step = sorted(ev[0].elapsed_time(ev[4]) for ev in evs)
     step_stats = {"min_ms": per_step[0], "median_ms": per_step[len(per_step) // 2], "max_ms": per_step[-1]}
     if dist:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dev)
     phase_ms = phases / args.steps
     # launches of libfe kernels per step: sparsity rebuild 14 (zero, count, zero, max, scan x3, zero, fill,
     # row sort, scan x3, compact); push: mat zero 1, assembly 1, action zero + action 2; pull: assembly 2
@@ -271,10 +288,8 @@ def run_ours(args, wl, rank, world):
         b.synchronize()
         e2e_ms = a.elapsed_time(b) / ksteps
         if dist:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * mesh.ncell / (e2e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+            e2e_ms = max_over_ranks(e2e_ms, dev)
+        e2e = {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
         fe.sync(ctx)
 
@@ -314,7 +329,7 @@ def run_ours(args, wl, rank, world):
     src_file = "fe_sparsity.cu" if dom == "sparsity" else "fe_kernels.cuh"
     roof["traffic"] = tr[0] if tr and tr[1] == _src_hash(src_file) else None
     out = {
-        "metric": METRIC, "value": world * ncell / (ms_step / 1e3), "unit": "cells/s", "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(ncell, world, ms_step), "unit": "cells/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
@@ -494,9 +509,7 @@ def run_batch(args, wl, rank, world):
         wall = time.perf_counter() - t0
     if dist:
         td.barrier()
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dev)
     fe.sync(ctx)
     # the same batch without the graph, and the plain path: one Mat zero + one Mat launch + one RHS
     # launch per mesh (its own Mat and RHS), both on the same stream
@@ -552,7 +565,8 @@ def run_batch(args, wl, rank, world):
             "kernel": "batch step (k_batch_zero + k_batch_assemble, one graph)", "traffic": None,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
     out = {
-        "metric": METRIC_BATCH, "value": world * ncell_tot / (ms_step / 1e3), "unit": "cells/s", "n_gpus": world,
+        "metric": METRIC_BATCH, "value": job_throughput(ncell_tot, world, ms_step), "unit": "cells/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "meshes": len(meshes), "cells_per_gpu": ncell_tot, "nnz": nnz_tot,
@@ -607,7 +621,8 @@ def _serve_once(fe, ctx, wl, reqs, rate, max_active):
     return {"rate_req_s": rate, "solves_per_s": len(reqs) / st["run_s"], "run_s": st["run_s"],
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "mean_iters": float(np.mean([q["iters"] for q in res])), "all_converged": ok,
-            "peak_bytes": st["peak_bytes"], "cg_launches": st["cg_launches"]}, xs
+            "peak_bytes": st["peak_bytes"], "cg_launches": st["cg_launches"],
+            "host_s": {"admit": st["admit_s"], "tick": st["tick_s"], "retire": st["retire_s"]}}, xs
 
 
 def run_serve(args, wl, rank, world):
@@ -683,8 +698,10 @@ def run_serve(args, wl, rank, world):
     h2d = sum(r["cmap"].nbytes + r["mesh"].cell_vertex.nbytes + r["mesh"].coords.nbytes + r["f"].nbytes + r["bc"].nbytes
               for r in reqs)
     d2h = sum(r["nn"] * 8 for r in reqs)
+    run_max = max_over_ranks(sat["run_s"], dev) if world > 1 else sat["run_s"]
     out = {
-        "metric": METRIC_SERVE, "value": world * sat["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "metric": METRIC_SERVE, "value": job_throughput(len(reqs), world, 1e3 * run_max), "unit": "solves/s",
+        "n_gpus": world,
         "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * sat["run_s"] / len(reqs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "requests": len(reqs), "hbm_budget_bytes": wl["budget"],
@@ -705,7 +722,8 @@ def run_serve(args, wl, rank, world):
                                f"(P{big['p']} n={big['n']}, {nn} rows, {nnz} nonzeros): {it_ms * 1e3:.1f} us/iteration",
                      "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": sat["cg_launches"], "clocks": clk.summary(),
-        "e2e": {"value": world * sat["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": h2d // len(reqs),
+        "e2e": {"value": job_throughput(len(reqs), world, 1e3 * run_max), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d // len(reqs),
                 "d2h_bytes_per_step": d2h // len(reqs),
                 "note": "the served figure is already host to host: meshes copied in, solutions copied out"},
     }

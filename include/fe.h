@@ -344,6 +344,7 @@ typedef struct {
   int submitted, converged, refused, estimate_misses;
   double run_s;
   int64_t cg_launches;     /* kernels the CG engine launched (set-up, iterations, polls)                 */
+  double admit_s, tick_s, retire_s;  /* host time spent admitting, iterating (launch + poll), retiring  */
 } fe_server_stats;
 fe_status fe_server_create(fe_ctx *ctx, const fe_server_config *cfg, fe_server **out);
 fe_status fe_server_submit(fe_server *srv, const fe_solve_request *req, int64_t *id);

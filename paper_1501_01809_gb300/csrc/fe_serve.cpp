@@ -69,7 +69,7 @@ struct Server {
   int64_t owner = -1;
   size_t base_bytes = 0, live_bytes = 0, peak_bytes = 0, reserved = 0;
   int estimate_misses = 0;
-  double run_s = 0.0;
+  double run_s = 0.0, admit_s = 0.0, tick_s = 0.0, retire_s = 0.0;
 };
 
 }  // namespace fe
@@ -333,6 +333,7 @@ fe_status server_run(fe_server *h) {
       s->owner = id;
       fe_status st = admit(s, q);
       s->owner = -1;
+      s->admit_s += now_s(t0) - q.res.admitted_s;
       if (st != FE_OK) {
         snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)id, fe_last_error());
         release(s, q);
@@ -353,8 +354,11 @@ fe_status server_run(fe_server *h) {
       continue;
     }
     // 2. one tick of CG for every admitted system, then retire the finished ones
+    const double tt0 = now_s(t0);
     fe_status st = fe_cg_iterate(s->cg, cfg.iters_per_tick, 1);
     if (st == FE_OK) st = fe_cg_poll(s->cg, cfg.max_active, st_status.data(), st_iters.data(), st_r.data(), st_b.data());
+    const double tt1 = now_s(t0);
+    s->tick_s += tt1 - tt0;
     if (st != FE_OK) {
       snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: %s", fe_last_error());
       return st;
@@ -385,6 +389,7 @@ fe_status server_run(fe_server *h) {
       release(s, q);
       active.erase(active.begin() + k);
     }
+    s->retire_s += now_s(t0) - tt1;
   }
   s->run_s = now_s(t0);
   return FE_OK;
@@ -406,6 +411,9 @@ fe_status server_stats(const fe_server *h, fe_server_stats *out) {
   out->estimate_misses = s->estimate_misses;
   out->run_s = s->run_s;
   out->cg_launches = s->cg ? cg_launches(s->cg) : 0;
+  out->admit_s = s->admit_s;
+  out->tick_s = s->tick_s;
+  out->retire_s = s->retire_s;
   for (const Req &q : s->reqs) {
     out->submitted++;
     if (q.res.status == FE_SOLVE_CONVERGED) out->converged++;

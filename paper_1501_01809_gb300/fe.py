@@ -76,7 +76,8 @@ class fe_solve_result(C.Structure):
 class fe_server_stats(C.Structure):
     _fields_ = [("peak_bytes", C.c_size_t), ("live_bytes", C.c_size_t), ("base_bytes", C.c_size_t),
                 ("submitted", C.c_int), ("converged", C.c_int), ("refused", C.c_int), ("estimate_misses", C.c_int),
-                ("run_s", C.c_double), ("cg_launches", C.c_int64)]
+                ("run_s", C.c_double), ("cg_launches", C.c_int64), ("admit_s", C.c_double), ("tick_s", C.c_double),
+                ("retire_s", C.c_double)]
 
 
 CG_RUNNING, CG_CONVERGED, CG_MAXIT, CG_BREAKDOWN = 0, 1, 2, 3
