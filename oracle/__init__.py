@@ -68,6 +68,8 @@ def _load():
                                            np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS"), C.c_void_p]
     lib.oracle_cg_jacobi.argtypes = [C.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p, C.c_double, C.c_int,
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.oracle_wave_steps.argtypes = [C.c_int, C.c_int, C.c_int64, _i32p, _f64p, _i32p, C.c_int64, C.c_void_p,
+                                      _f64p, _f64p, C.c_double, C.c_double, C.c_int]
     _lib = lib
     return lib
 
@@ -230,3 +232,17 @@ def cg_jacobi(rowptr, colidx, vals, b, x0=None, rtol=1e-8, maxit=100000):
     it = _load().oracle_cg_jacobi(b.size, _c(rowptr, np.int64), _c(colidx, np.int32), _c(vals, np.float64), b, x,
                                   float(rtol), int(maxit), C.byref(rn), C.byref(bn))
     return x, it, rn.value, bn.value
+
+
+def wave_steps(dim, p, cmap, coords, coord_map, nnodes, phi, pv, t0, dt, nsteps, is_bc=None):
+    """Explicit lumped-mass wave steps; returns new (phi, p)."""
+    cmap = _c(cmap, np.int32)
+    phi = np.array(phi, dtype=np.float64, copy=True)
+    pv = np.array(pv, dtype=np.float64, copy=True)
+    bc = None if is_bc is None else _c(is_bc, np.uint8)
+    rc = _load().oracle_wave_steps(dim, p, cmap.shape[0], cmap.ravel(), _c(coords, np.float64).ravel(),
+                                   _c(coord_map, np.int32).ravel(), int(nnodes),
+                                   None if bc is None else bc.ctypes.data, phi, pv, float(t0), float(dt), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("oracle_wave_steps failed")
+    return phi, pv

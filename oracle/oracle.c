@@ -6,7 +6,8 @@
  * pair of maps (Sec. 4.4.3), and the forms of the Poisson listing (Sec. 3.1, Listing 1:
  * a = inner(grad u, grad v) dx, L = f v dx) extended by a mass term (Helmholtz) and a
  * P1 coefficient kappa (diffusion); for solves, strong Dirichlet conditions by symmetric
- * elimination (Sec. 3.1) and Jacobi-preconditioned conjugate gradients (Sec. 6.2).
+ * elimination (Sec. 3.1), Jacobi-preconditioned conjugate gradients (Sec. 6.2) and explicit
+ * lumped-mass wave steps (Sec. 6.3).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the benchmark's
  * CPU-baseline leg may load this library.  It shares no code, header, table or constant
@@ -712,4 +713,47 @@ int oracle_cg_jacobi(int64_t n, const int64_t *rowptr, const int32_t *colidx, co
     free(q);
     free(dinv);
     return bad ? -1 : it;
+}
+
+/*
+ * Explicit linear wave steps with lumped mass (Sec. 6.3): the state is (phi, p) on the nodes of a
+ * P_p space; m_i = integral of the i-th basis function (the lumped mass, the linear form v dx); each
+ * step, at time t = t0 + k dt, in the paper's order:
+ *   p_bc = sin(10 pi t); phi -= dt/2 p; p += dt (K phi) / m with K phi the action of
+ *   inner(grad v, grad phi) dx; p_i = p_bc on the flagged nodes; phi -= dt/2 p.
+ * phi and p are updated in place.  Returns 0, or -1 on bad arguments.
+ */
+int oracle_wave_steps(int dim, int p, int64_t ncell, const int32_t *map, const double *coords,
+                      const int32_t *coord_map, int64_t nnodes, const uint8_t *is_bc, double *phi, double *pv,
+                      double t0, double dt, int nsteps) {
+    int nd = oracle_num_nodes(dim, p);
+    if (nd < 0 || nsteps < 0) return -1;
+    double *m = calloc((size_t)(nnodes > 0 ? nnodes : 1), sizeof(double));
+    double *ma = calloc((size_t)(nnodes > 0 ? nnodes : 1), sizeof(double));
+    double *one = malloc(sizeof(double) * (size_t)(nnodes > 0 ? nnodes : 1));
+    double *y = calloc((size_t)(nnodes > 0 ? nnodes : 1), sizeof(double));
+    double *ya = calloc((size_t)(nnodes > 0 ? nnodes : 1), sizeof(double));
+    for (int64_t i = 0; i < nnodes; i++) one[i] = 1.0;
+    int rc = oracle_assemble_vec(dim, p, p, ncell, map, coords, coord_map, one, map, m, ma);
+    for (int k = 0; rc == 0 && k < nsteps; k++) {
+        const double t = t0 + k * dt;
+        const double pbc = sin(10.0 * M_PI * t);
+        const double half = (g_mutation == 11 ? dt : 0.5 * dt); /* planted mistake (11): full step */
+        for (int64_t i = 0; i < nnodes; i++) phi[i] -= half * pv[i];
+        memset(y, 0, sizeof(double) * (size_t)nnodes);
+        memset(ya, 0, sizeof(double) * (size_t)nnodes);
+        rc = oracle_action(dim, p, OR_LAPLACE, ncell, map, coords, coord_map, NULL, phi, y, ya);
+        for (int64_t i = 0; i < nnodes; i++) {
+            if (g_mutation == 10) pv[i] -= dt * y[i] / m[i]; /* planted mistake (10): wrong sign */
+            else pv[i] += dt * y[i] / m[i];
+            if (is_bc && is_bc[i]) pv[i] = pbc;
+        }
+        for (int64_t i = 0; i < nnodes; i++) phi[i] -= half * pv[i];
+    }
+    free(m);
+    free(ma);
+    free(one);
+    free(y);
+    free(ya);
+    return rc;
 }

@@ -37,7 +37,7 @@ import numpy as np
 __all__ = [
     "Mesh", "unit_square_mesh", "unit_cube_mesh", "lagrange_nodes", "cell_node_map",
     "node_coordinates", "uniform_dat", "lognormal_dat", "batch_mesh_sizes", "boundary_nodes",
-    "manufactured_sine", "serve_requests",
+    "manufactured_sine", "serve_requests", "face_nodes",
 ]
 
 
@@ -247,3 +247,11 @@ def serve_requests(count: int, seed: int, rate: float, lo: int = 16, hi: int = 5
     k = rng.integers(1, 5, size=count)
     mm = rng.integers(1, 5, size=count)
     return [(float(t[i]), int(n[i]), int(p[i]), int(k[i]), int(mm[i])) for i in range(count)]
+
+
+def face_nodes(mesh: Mesh, p: int, axis: int, side: int) -> np.ndarray:
+    """uint8 mask over the P_p nodes: 1 on the face x_axis = side (0 or 1) of the unit square/cube."""
+    m = p * mesh.n + 1
+    ids = np.arange(m ** mesh.dim, dtype=np.int64)
+    c = (ids // m ** axis) % m
+    return (c == (0 if side == 0 else m - 1)).astype(np.uint8)

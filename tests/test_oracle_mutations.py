@@ -4,7 +4,7 @@ The oracle has a test-only switch that introduces one plausible mistake at a tim
 mass term, a transposed Jacobian inverse, a signed determinant, two swapped local nodes, a
 dropped Duffy factor in the quadrature, a Dirichlet lift with the wrong sign, boundary columns
 left in place, a CG search direction built from the unpreconditioned residual, a CG step length
-from r.r instead of r.z.  Each must make some pin fail; otherwise the pins
+from r.r instead of r.z, a wave p update with the wrong sign, full phi steps instead of halves.  Each must make some pin fail; otherwise the pins
 would not be strong enough to trust the oracle.
 """
 import pytest
@@ -12,6 +12,7 @@ import pytest
 import oracle as O
 from tests import test_oracle_pins as P
 from tests import test_oracle_solve as S
+from tests import test_oracle_wave as W
 
 PINS = [
     ("reference_elements", lambda: P.pin_reference_elements()),
@@ -25,6 +26,7 @@ PINS = [
     ("harmonic_p2", lambda: S.pin_harmonic_reproduction(2)),
     ("cg_dense_spd", lambda: S.pin_cg_dense_spd()),
     ("cg_diagonal", lambda: S.pin_cg_diagonal()),
+    ("wave_modes", lambda: W.pin_modes()),
 ]
 
 
@@ -32,7 +34,9 @@ PINS = [
                                        (4, "swapped edge nodes"), (5, "dropped Duffy factor"),
                                        (6, "Dirichlet lift with the wrong sign"),
                                        (7, "boundary columns kept"), (8, "CG direction from r, not z"),
-                                       (9, "CG step length from r.r")])
+                                       (9, "CG step length from r.r"),
+                                       (10, "wave: p update with the wrong sign"),
+                                       (11, "wave: full phi steps instead of halves")])
 def test_planted_mistake_is_caught(code, what):
     O.set_mutation(code)
     caught = []
