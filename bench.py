@@ -42,6 +42,10 @@ WORKLOADS = {
     "p1-sweep": dict(sweep=True, dim=2, p=1, ns=[256, 512, 1024, 2048], jitter=0.0, seed=0,
                      name="P1 Lagrange UnitSquareMesh n x n for n = 256..2048 (up to 8,388,608 cells), Helmholtz, "
                           "FP64 CSR: assembly roofline sweep (labelled extra; sparsity built once per n)"),
+    "wave": dict(wave=True, dim=3, p=1, n=64, jitter=0.2, seed=0, dt=0.001,
+                 name="explicit linear wave (lumped mass, Sec. 6.3) on P1 UnitCubeMesh 64^3 (1,572,864 Kuhn tets, "
+                      "+-0.2h jitter seed 0, 274,625 nodes), p = sin(10 pi t) on y = 0, dt = 0.001: one time step = "
+                      "pull action element kernel + fused per-node update"),
     "batch": dict(count=2048, seed=4, lo=8, hi=256,
                   name="2048 UnitSquareMesh n x n meshes, n log-uniform in [8,256] (seed 4), each P1 or P2 "
                        "(Bernoulli 1/2), Helmholtz CSR + RHS f v dx (f uniform[-1,1] per node, seed 1000+i), "
@@ -345,6 +349,106 @@ def run_ours(args, wl, rank, world):
 
 
 # ------------------------------------------------------------------------------ batched workload
+
+# ------------------------------------------------------------------------------ wave steps
+
+def run_wave(args, wl, rank, world):
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mesh, cmap, nn, _ = make_inputs(wl)
+    bc = mg.face_nodes(mesh, 1, 1, 0)
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    prec = {"fp64": fe.PREC_FP64, "f32x2": fe.PREC_F32X2}[args.precision]
+    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+         dict(map=cmap, cv=mesh.cell_vertex, xy=mesh.coords, bc=bc, one=np.ones(nn)).items()}
+    phi = torch.zeros(nn, dtype=torch.float64, device=dev)
+    pv = torch.zeros(nn, dtype=torch.float64, device=dev)
+    mass = torch.zeros(nn, dtype=torch.float64, device=dev)
+    dt = wl["dt"]
+    with torch.cuda.stream(stream):
+        cells, nodes, verts = fe.set_create(ctx, mesh.ncell), fe.set_create(ctx, nn), fe.set_create(ctx, mesh.nvert)
+        M, CM = fe.map_create(ctx, cells, nodes, t["map"]), fe.map_create(ctx, cells, verts, t["cv"])
+        XY = fe.dat_create(ctx, verts, t["xy"])
+        PHI, P = fe.dat_create(ctx, nodes, phi), fe.dat_create(ctx, nodes, pv)
+        ONE, MASS = fe.dat_create(ctx, nodes, t["one"]), fe.dat_create(ctx, nodes, mass)
+        sp = fe.sparsity_build(ctx, M, M)
+        ks = fe.kernel_create(ctx, fe.FORM_SOURCE, wl["dim"], 1, coeff_degree=1, strategy=fe.STRATEGY_PULL)
+        fe.assemble_vec(ctx, ks, cells, MASS, M, XY, CM, [(ONE, M)], zero_first=True, sp=sp)
+        kl = fe.kernel_create(ctx, fe.FORM_LAPLACE, wl["dim"], 1, precision=prec)
+    fe.wave_steps(ctx, kl, cells, PHI, P, mass, t["bc"], M, XY, CM, sp, 0.0, dt, args.warmup)
+    fe.sync(ctx)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        a.record(stream)
+        fe.wave_steps(ctx, kl, cells, PHI, P, mass, t["bc"], M, XY, CM, sp, args.warmup * dt, dt, args.steps)
+        b.record(stream)
+        b.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    if world > 1:
+        ms = max_over_ranks(ms, dev)
+    fe.sync(ctx)
+    # e2e: every time step takes (phi, p) from pinned host memory and returns them
+    h_in = [torch.empty(nn, dtype=torch.float64, pin_memory=True).copy_(x.cpu()) for x in (phi, pv)]
+    h_out = [torch.empty(nn, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    ke = max(3, min(args.steps, 50))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(ke):
+        with torch.cuda.stream(stream):
+            phi.copy_(h_in[0], non_blocking=True)
+            pv.copy_(h_in[1], non_blocking=True)
+            fe.wave_steps(ctx, kl, cells, PHI, P, mass, t["bc"], M, XY, CM, sp, 0.0, dt, 1)
+            h_out[0].copy_(phi, non_blocking=True)
+            h_out[1].copy_(pv, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
+    peaks, src = _peaks()
+    # algorithmic bytes per time step: maps (4 + 4 ints per cell), coordinates and phi gathered once,
+    # p, phi read and written, mass and the boundary flags read once
+    byt = mesh.ncell * 32 + mesh.nvert * 24 + nn * (8 + 16 + 16 + 8 + 1)
+    gbs = byt / (ms / 1e3) / 1e9
+    out = {"metric": "cells/s stepped (explicit wave: action + lumped-mass updates per time step)",
+           "value": job_throughput(mesh.ncell, world, ms), "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["name"], "cells_per_gpu": mesh.ncell, "nodes": nn,
+                      "precision": ("action element tensors in FP32 pairs, FP64 state" if args.precision == "f32x2"
+                                    else "FP64 throughout"),
+                      "step": "one time step", "parallelism": f"replicas x{world}",
+                      "l2": "state and maps larger than L2 in total; no flush"},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                        "kernel": "time step (k_action_elem<3,1,LAPLACE> + k_wave_row)",
+                        "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+           "gpu_launches": 2 * args.steps + 1, "clocks": clk.summary(),
+           "e2e": {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s",
+                   "h2d_bytes_per_step": 16 * nn, "d2h_bytes_per_step": 16 * nn, "ms_per_step": e2e_ms}}
+    return out, (mesh, cmap, nn, bc)
+
+
+def wave_cpu_sample(wl, inputs, budget_s):
+    """Oracle wave steps on the workload mesh, one step at a time, until budget_s seconds."""
+    import oracle as O
+    mesh, cmap, nn, bc = inputs
+    # one call (its lumped mass once, then the steps); the step count from a one-step probe
+    t0 = time.perf_counter()
+    O.wave_steps(wl["dim"], 1, cmap, mesh.coords, mesh.cell_vertex, nn, np.zeros(nn), np.zeros(nn), 0.0, wl["dt"], 1,
+                 is_bc=bc)
+    probe = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(probe, 1e-3)))
+    t0 = time.perf_counter()
+    O.wave_steps(wl["dim"], 1, cmap, mesh.coords, mesh.cell_vertex, nn, np.zeros(nn), np.zeros(nn), 0.0, wl["dt"],
+                 steps, is_bc=bc)
+    return steps * mesh.ncell, time.perf_counter() - t0
+
 
 # ------------------------------------------------------------------------------ P1 roofline sweep
 
@@ -794,6 +898,21 @@ def run_reference(args, wl):
     oracle.build()
     if wl.get("sweep"):
         wl = dict(wl, n=wl["ns"][-1])
+    if wl.get("wave"):
+        mesh, cmap, nn, _ = make_inputs(wl)
+        from paper_1501_01809_gb300 import meshgen as mg
+        inputs = (mesh, cmap, nn, mg.face_nodes(mesh, 1, 1, 0))
+        res = [wave_cpu_sample(wl, inputs, args.ref_seconds) for _ in range(args.steps)]
+        v = sum(c for c, _ in res) / sum(t for _, t in res)
+        ms = 1e3 * sum(t for _, t in res) / max(1, sum(c for c, _ in res) // mesh.ncell)
+        return {"impl": "reference", "metric": "cells/s stepped (explicit wave: action + lumped-mass updates per "
+                                               "time step)", "value": v, "unit": "cells/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "reference": "CPU FP64 oracle (plain C), bounded time per step"},
+                "cpu_baseline": {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"oracle time steps of the workload mesh, about {args.ref_seconds} s each"},
+                "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if wl.get("serve"):
         reqs = make_serve_inputs(wl)
         res = [serve_cpu_sample(reqs, args.ref_seconds) for _ in range(args.steps)]
@@ -877,6 +996,19 @@ def main():
     if wl.get("sweep"):
         out = run_p1_sweep(args, wl, rank, world)
         if rank == 0:
+            print(json.dumps(out))
+        return
+    if wl.get("wave"):
+        out, winputs = run_wave(args, wl, rank, world)
+        if rank == 0:
+            if world == 1 and not args.no_cpu_baseline:
+                import oracle
+                oracle.build()
+                cells, dt_s = wave_cpu_sample(wl, winputs, 15.0)
+                out["cpu_baseline"] = {"value": cells / dt_s, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"{cells // winputs[0].ncell} oracle time steps of the workload "
+                                                 f"mesh in one call (its lumped-mass assembly included), "
+                                                 f"{dt_s:.1f} s on 1 host core"}
             print(json.dumps(out))
         return
     if wl.get("serve"):

@@ -266,6 +266,21 @@ fe_status fe_batch_destroy(fe_batch *b);
  * g = 0.  One thread per row; deterministic.  Enqueued on the context stream. */
 fe_status fe_dirichlet_apply(fe_ctx *ctx, fe_mat *A, fe_dat *b, const uint8_t *is_bc, const double *g);
 
+/* ---------------------------------------------------------------- explicit wave steps
+ * nsteps steps of the linear wave scheme of Sec. 6.3 on a P1 space (triangles or tetrahedra), in
+ * place on phi and p (scalar Dats on map's target): at t = t0 + k dt, phi -= dt/2 p;
+ * p += dt (K phi) / m with K phi the action of k (FE_FORM_LAPLACE, degree 1, FE_PREC_FP64 or
+ * FE_PREC_F32X2) and m the lumped mass (device double[nrows], the linear form v dx, e.g. from
+ * fe_assemble_vec with f = 1); p = sin(10 pi t) on the nodes flagged in is_bc (device uint8[nrows],
+ * or NULL for none); phi -= dt/2 p.  The second half step of one time step and the first of the
+ * next are merged, so a time step is two launches: the pull action's element kernel, then one
+ * thread per node summing its staged contributions in fixed order and applying all pointwise
+ * updates (deterministic).  sp: the sparsity built from (map, map) (its row incidence).
+ * Errors: FE_EUNSUPPORTED (element, form, precision), FE_EINVAL, FE_ENOMEM, FE_ECUDA. */
+fe_status fe_wave_steps(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *phi, fe_dat *p, const double *mass,
+                        const uint8_t *is_bc, fe_map *map, fe_dat *coords, fe_map *coord_map, const fe_sparsity *sp,
+                        double t0, double dt, int nsteps);
+
 /* ---------------------------------------------------------------- batched Jacobi-CG
  * Conjugate gradients with the Jacobi preconditioner M = diag(A) (the Poisson experiment of
  * Sec. 6.2 solves with CG) for many independent SPD CSR systems at once: every fe_cg_iterate runs

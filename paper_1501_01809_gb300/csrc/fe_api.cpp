@@ -1,6 +1,7 @@
 // C ABI of libfe (declared in include/fe.h): handle management, argument validation, the
 // allocator, and the host-side sequencing of the sparsity and assembly kernels.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -707,6 +708,42 @@ fe_status fe_batch_destroy(fe_batch *b) {
   if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_destroy: invalid batch");
   DeviceGuard g(fe::batch_ctx(b)->device);
   fe::batch_destroy(b, batch_release);
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ wave steps
+static double wave_bc_value(double t) {
+  constexpr double kPi = 3.14159265358979323846;
+  return sin(10.0 * kPi * t);
+}
+
+fe_status fe_wave_steps(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *phi, fe_dat *p, const double *mass,
+                        const uint8_t *is_bc, fe_map *map, fe_dat *coords, fe_map *coord_map, const fe_sparsity *sp,
+                        double t0, double dt, int nsteps) {
+  const char *who = "fe_wave_steps";
+  fe::AsmArgs a;
+  fe_status st = common_args(who, c, k, cells, map, coords, coord_map, a);
+  if (st != FE_OK) return st;
+  if (k->d.form != FE_FORM_LAPLACE || k->d.degree != 1 ||
+      (k->d.precision != FE_PREC_FP64 && k->d.precision != FE_PREC_F32X2))
+    return fail(FE_EUNSUPPORTED, "%s: P1 Laplace kernels in FP64 or double-float only", who);
+  if (!valid(phi) || !valid(p) || phi->ctx != c || p->ctx != c || phi->set != map->to || p->set != map->to ||
+      phi->dim != 1 || p->dim != 1 || phi->data == p->data)
+    return fail(FE_EINVAL, "%s: phi and p must be distinct scalar Dats on the map's target", who);
+  if (nsteps < 0 || !(dt == dt) || (map->to->size > 0 && !mass)) return fail(FE_EINVAL, "%s: bad nsteps, dt or mass", who);
+  if (!sp || !valid(sp) || sp->ctx != c || sp->rmap != map || sp->ncell != cells->size)
+    return fail(FE_EINVAL, "%s: sp must be the sparsity built from (map, map)", who);
+  a.x = phi->data;
+  a.y = phi->data;
+  a.adjptr = sp->adjptr;
+  a.adj = sp->adj;
+  DeviceGuard g(c->device);
+  fe_sparsity *msp = const_cast<fe_sparsity *>(sp);
+  st = ensure_stage(c, &msp->vstage, &msp->vstage_bytes, fe::wave_stage_bytes(k->d.dim, k->d.precision, cells->size),
+                    who);
+  if (st != FE_OK) return st;
+  FE_CHECK_CUDA(fe::launch_wave(k->d, a, msp->vstage, mass, is_bc, p->data, t0, dt, nsteps, wave_bc_value, c->stream),
+                who);
   return ok();
 }
 

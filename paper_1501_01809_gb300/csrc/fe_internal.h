@@ -205,4 +205,10 @@ cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStr
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 bool kernel_supported(const fe_form_desc &d);
 
+// ---- explicit wave steps (fe_wave.cu) ----
+size_t wave_stage_bytes(int dim, int precision, int64_t ncell);
+cudaError_t launch_wave(const fe_form_desc &d, const AsmArgs &a, void *stage, const double *mass,
+                        const uint8_t *is_bc, double *p, double t0, double dt, int nsteps,
+                        double (*bc_value)(double), cudaStream_t s);
+
 }  // namespace fe

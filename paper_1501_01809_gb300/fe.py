@@ -32,7 +32,7 @@ SYMBOLS = [
     "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
     "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
     "fe_cg_poll", "fe_cg_remove", "fe_cg_destroy", "fe_server_create", "fe_server_submit", "fe_server_run",
-    "fe_server_result", "fe_server_stats_get", "fe_server_destroy",
+    "fe_server_result", "fe_server_stats_get", "fe_server_destroy", "fe_wave_steps",
 ]
 
 
@@ -126,6 +126,7 @@ def load():
         "fe_batch_tune": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_float)]),
         "fe_batch_assemble": (I, [P, I]), "fe_batch_destroy": (I, [P]),
         "fe_dirichlet_apply": (I, [P, P, P, P, P]),
+        "fe_wave_steps": (I, [P, P, P, P, P, P, P, P, P, P, P, C.c_double, C.c_double, I]),
         "fe_cg_create": (I, [P, I, PP]), "fe_cg_add": (I, [P, P, P, P, C.c_double, I, C.POINTER(I)]),
         "fe_cg_iterate": (I, [P, I, I]),
         "fe_cg_poll": (I, [P, I, P, P, P, P]), "fe_cg_remove": (I, [P, I]), "fe_cg_destroy": (I, [P]),
@@ -563,3 +564,12 @@ def server_stats(srv: Server) -> dict:
     r = fe_server_stats()
     _check(load().fe_server_stats_get(srv.ptr, C.byref(r)))
     return {k: getattr(r, k) for k, _ in fe_server_stats._fields_}
+
+
+def wave_steps(ctx: Ctx, k: Kernel, cells: Set, phi: Dat, p: Dat, mass: torch.Tensor, is_bc, map_: Map,
+               coords: Dat, coord_map: Map, sp: Sparsity, t0: float, dt: float, nsteps: int) -> None:
+    """fe_wave_steps: mass device float64 [nrows]; is_bc device uint8 [nrows] or None."""
+    mass = _dev_tensor(mass, torch.float64, "mass")
+    bc = None if is_bc is None else _dev_tensor(is_bc, torch.uint8, "is_bc").data_ptr()
+    _check(load().fe_wave_steps(ctx.ptr, k.ptr, cells.ptr, phi.ptr, p.ptr, mass.data_ptr(), bc, map_.ptr,
+                                coords.ptr, coord_map.ptr, sp.ptr, float(t0), float(dt), int(nsteps)))
