@@ -46,6 +46,7 @@ WORKLOADS = {
                  name="explicit linear wave (lumped mass, Sec. 6.3) on P1 UnitCubeMesh 64^3 (1,572,864 Kuhn tets, "
                       "+-0.2h jitter seed 0, 274,625 nodes), p = sin(10 pi t) on y = 0, dt = 0.001: one time step = "
                       "pull action element kernel + fused per-node update"),
+    "cg": dict(cg=True, name="Jacobi-CG iteration of the largest serving request alone"),
     "batch": dict(count=2048, seed=4, lo=8, hi=256,
                   name="2048 UnitSquareMesh n x n meshes, n log-uniform in [8,256] (seed 4), each P1 or P2 "
                        "(Bernoulli 1/2), Helmholtz CSR + RHS f v dx (f uniform[-1,1] per node, seed 1000+i), "
@@ -764,39 +765,8 @@ def run_serve(args, wl, rank, world):
             sweep.append({"rate_req_s": rate, "served": served, "plain": plain})
     # CG iteration of the largest system alone: the dominant kernels, timed with CUDA events
     big = max(reqs, key=lambda r: r["nn"] * (r["p"] ** 2))
-    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
-         dict(map=big["cmap"], cv=big["mesh"].cell_vertex, xy=big["mesh"].coords, f=big["f"], bc=big["bc"]).items()}
-    tb, tx = torch.zeros(big["nn"], dtype=torch.float64, device=dev), torch.zeros(big["nn"], dtype=torch.float64, device=dev)
-    with torch.cuda.stream(stream):
-        cells, nodes, verts = (fe.set_create(ctx, big["mesh"].ncell), fe.set_create(ctx, big["nn"]),
-                               fe.set_create(ctx, big["mesh"].nvert))
-        M, CM = fe.map_create(ctx, cells, nodes, t["map"]), fe.map_create(ctx, cells, verts, t["cv"])
-        XY, F = fe.dat_create(ctx, verts, t["xy"]), fe.dat_create(ctx, nodes, t["f"])
-        B, X = fe.dat_create(ctx, nodes, tb), fe.dat_create(ctx, nodes, tx)
-        sp = fe.sparsity_build(ctx, M, M)
-        A = fe.mat_create(ctx, sp)
-        kl = fe.kernel_create(ctx, fe.FORM_LAPLACE, 2, big["p"], strategy=fe.STRATEGY_PULL)
-        ks = fe.kernel_create(ctx, fe.FORM_SOURCE, 2, big["p"], coeff_degree=big["p"], strategy=fe.STRATEGY_PULL)
-        fe.assemble_mat(ctx, kl, cells, A, XY, CM, zero_first=True)
-        fe.assemble_vec(ctx, ks, cells, B, M, XY, CM, [(F, M)], zero_first=True, sp=sp)
-        fe.dirichlet_apply(ctx, A, B, t["bc"])
-        cg = fe.cg_create(ctx, 1)
-        fe.cg_add(cg, A, B, X, rtol=1e-30, maxit=1 << 30)
-        fe.cg_iterate(cg, 10)
-        fe.sync(ctx)
-        iters = 200
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fe.cg_iterate(cg, iters)
-        e1.record(stream)
-        e1.synchronize()
-    it_ms = e0.elapsed_time(e1) / iters
-    nnz = fe.sparsity_csr(sp)[2]
+    it_ms, nnz, it_bytes = cg_single_system(fe, ctx, stream, dev, big, 200)
     nn = big["nn"]
-    # algorithmic bytes of one iteration (launch A + launch B): CSR values and columns and the row
-    # pointers once, z and p_old read, p_new and q written (A); p_new, q, x, r, diag^-1 read, x, r, z
-    # written (B)
-    it_bytes = nnz * 12 + (nn + 1) * 8 + 4 * nn * 8 + 8 * nn * 8
     peaks, src = _peaks()
     gbs = it_bytes / (it_ms / 1e3) / 1e9
     h2d = sum(r["cmap"].nbytes + r["mesh"].cell_vertex.nbytes + r["mesh"].coords.nbytes + r["f"].nbytes + r["bc"].nbytes
@@ -835,6 +805,75 @@ def run_serve(args, wl, rank, world):
 
 
 SERVE_CPU_MAX_N = 128
+
+
+def cg_single_system(fe, ctx, stream, dev, req, iters, warm=10):
+    """Assemble (pull), eliminate and iterate CG on one request's system alone; returns the mean
+    time of one iteration (ms), nnz and the algorithmic bytes of one iteration."""
+    import torch
+    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+         dict(map=req["cmap"], cv=req["mesh"].cell_vertex, xy=req["mesh"].coords, f=req["f"], bc=req["bc"]).items()}
+    nn = req["nn"]
+    tb, tx = torch.zeros(nn, dtype=torch.float64, device=dev), torch.zeros(nn, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        cells, nodes, verts = (fe.set_create(ctx, req["mesh"].ncell), fe.set_create(ctx, nn),
+                               fe.set_create(ctx, req["mesh"].nvert))
+        M, CM = fe.map_create(ctx, cells, nodes, t["map"]), fe.map_create(ctx, cells, verts, t["cv"])
+        XY, F = fe.dat_create(ctx, verts, t["xy"]), fe.dat_create(ctx, nodes, t["f"])
+        B, X = fe.dat_create(ctx, nodes, tb), fe.dat_create(ctx, nodes, tx)
+        sp = fe.sparsity_build(ctx, M, M)
+        A = fe.mat_create(ctx, sp)
+        kl = fe.kernel_create(ctx, fe.FORM_LAPLACE, 2, req["p"], strategy=fe.STRATEGY_PULL)
+        ks = fe.kernel_create(ctx, fe.FORM_SOURCE, 2, req["p"], coeff_degree=req["p"], strategy=fe.STRATEGY_PULL)
+        fe.assemble_mat(ctx, kl, cells, A, XY, CM, zero_first=True)
+        fe.assemble_vec(ctx, ks, cells, B, M, XY, CM, [(F, M)], zero_first=True, sp=sp)
+        fe.dirichlet_apply(ctx, A, B, t["bc"])
+        cg = fe.cg_create(ctx, 1)
+        fe.cg_add(cg, A, B, X, rtol=1e-30, maxit=1 << 30)
+        fe.cg_iterate(cg, warm)
+        fe.sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fe.cg_iterate(cg, iters)
+        e1.record(stream)
+        e1.synchronize()
+    nnz = fe.sparsity_csr(sp)[2]
+    # algorithmic bytes of one iteration (launch A + launch B): values and columns once, slice
+    # offsets, z gathered once, p and q read and written (A); p, q, x, r, diag^-1 read, x, r, z
+    # written (B)
+    it_bytes = nnz * 12 + (nn // 32 + 1) * 8 + nn * 8 + 4 * nn * 8 + 8 * nn * 8
+    return e0.elapsed_time(e1) / iters, nnz, it_bytes
+
+
+def run_cg(args, wl, rank, world):
+    """One CG system alone (the largest request of the serving workload): iterations per second."""
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    reqs = make_serve_inputs(dict(WORKLOADS["serve"]))
+    big = max(reqs, key=lambda r: r["nn"] * (r["p"] ** 2))
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    with ClockSampler(dev.index) as clk:
+        it_ms, nnz, it_bytes = cg_single_system(fe, ctx, stream, dev, big, args.steps, warm=args.warmup)
+    if world > 1:
+        it_ms = max_over_ranks(it_ms, dev)
+    peaks, src = _peaks()
+    gbs = it_bytes / (it_ms / 1e3) / 1e9
+    return {"metric": "CG iterations/s (one system alone)", "value": world * 1e3 / it_ms, "unit": "iterations/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": it_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Jacobi-CG iteration on the largest serving request (P{big['p']} n={big['n']}, "
+                                   f"{big['nn']} rows, {nnz} nonzeros), SELL-32 SpMV", "step": "one CG iteration",
+                       "parallelism": f"replicas x{world}", "l2": "matrix larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "k_cg_direction_spmv + k_cg_update",
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+            "gpu_launches": 2 * args.steps, "clocks": clk.summary(), "e2e": None}
 
 
 def serve_cpu_sample(reqs, budget_s):
@@ -898,6 +937,33 @@ def run_reference(args, wl):
     oracle.build()
     if wl.get("sweep"):
         wl = dict(wl, n=wl["ns"][-1])
+    if wl.get("cg"):
+        import oracle as O
+        reqs = make_serve_inputs(dict(WORKLOADS["serve"]))
+        r = max(reqs, key=lambda q: q["nn"] * (q["p"] ** 2))
+        rp, ci = O.sparsity(r["cmap"], r["cmap"], r["nn"], r["nn"])
+        v, _ = O.assemble_mat(2, r["p"], O.LAPLACE, r["cmap"], r["mesh"].coords, r["mesh"].cell_vertex, rp, ci)
+        b, _ = O.assemble_vec(2, r["p"], r["p"], r["cmap"], r["nn"], r["mesh"].coords, r["mesh"].cell_vertex, r["f"],
+                              r["cmap"])
+        v, b = O.dirichlet_apply(rp, ci, v, b, r["bc"])
+        t0 = time.perf_counter()
+        O.cg_jacobi(rp, ci, v, b, rtol=1e-30, maxit=5)
+        per = max((time.perf_counter() - t0) / 5, 1e-6)
+        iters = max(5, int(args.ref_seconds / per))
+        res = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            O.cg_jacobi(rp, ci, v, b, rtol=1e-30, maxit=iters)
+            res.append(time.perf_counter() - t0)
+        vv = iters * len(res) / sum(res)
+        return {"impl": "reference", "metric": "CG iterations/s (one system alone)", "value": vv,
+                "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 / vv, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["name"], "reference": "CPU FP64 oracle CG (plain C)"},
+                "cpu_baseline": {"value": vv, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{iters} oracle CG iterations per step"},
+                "e2e": {"value": vv, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if wl.get("wave"):
         mesh, cmap, nn, _ = make_inputs(wl)
         from paper_1501_01809_gb300 import meshgen as mg
@@ -995,6 +1061,11 @@ def main():
         td.init_process_group("nccl")
     if wl.get("sweep"):
         out = run_p1_sweep(args, wl, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if wl.get("cg"):
+        out = run_cg(args, wl, rank, world)
         if rank == 0:
             print(json.dumps(out))
         return
