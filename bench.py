@@ -932,9 +932,16 @@ def cpu_baseline(wl, inputs, ncell_sample):
                       f"{dt:.1f} s on 1 host core"}
 
 
+def ref_budget_s(args):
+    """Seconds of oracle work per reference step so that warm-up plus timed steps take about two
+    minutes in total (never more than --ref-seconds per step)."""
+    return min(args.ref_seconds, max(0.05, 120.0 / (args.steps + args.warmup)))
+
+
 def run_reference(args, wl):
     import oracle
     oracle.build()
+    args.ref_seconds = ref_budget_s(args)
     if wl.get("sweep"):
         wl = dict(wl, n=wl["ns"][-1])
     if wl.get("cg"):
@@ -1008,7 +1015,8 @@ def run_reference(args, wl):
                                  "sample": f"first meshes of the batch, about {args.ref_seconds} s per step"},
                 "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     inputs = make_inputs(wl)
-    ns = args.ref_cells
+    probe = max(_oracle_sample(wl, inputs, 512) / 512, 1e-7)
+    ns = int(max(256, min(args.ref_cells, ref_budget_s(args) / probe)))
     for _ in range(args.warmup):
         _oracle_sample(wl, inputs, ns)
     times = [_oracle_sample(wl, inputs, ns) for _ in range(args.steps)]
