@@ -46,6 +46,10 @@ WORKLOADS = {
                  name="explicit linear wave (lumped mass, Sec. 6.3) on P1 UnitCubeMesh 64^3 (1,572,864 Kuhn tets, "
                       "+-0.2h jitter seed 0, 274,625 nodes), p = sin(10 pi t) on y = 0, dt = 0.001: one time step = "
                       "pull action element kernel + fused per-node update"),
+    "p4-kappa": dict(p4=True, dim=2, p=4, n=512, jitter=0.0, seed=0, kappa_seed=3,
+                     name="P4 Lagrange UnitSquareMesh 512x512 (524,288 triangles, 4,198,401 dofs), kappa-diffusion "
+                          "kappa*inner(grad u, grad v) dx with kappa = exp(N(0,1)) per P1 node (seed 3): zero + CSR "
+                          "assembly with element tensors on the tensor cores (three TF32 products), FP64 CSR"),
     "cg": dict(cg=True, name="Jacobi-CG iteration of the largest serving request alone"),
     "batch": dict(count=2048, seed=4, lo=8, hi=256,
                   name="2048 UnitSquareMesh n x n meshes, n log-uniform in [8,256] (seed 4), each P1 or P2 "
@@ -519,6 +523,82 @@ def run_p1_sweep(args, wl, rank, world):
                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
            "gpu_launches": 2 * max(3, min(args.steps, 50)), "e2e": None}
     return out
+
+
+# ------------------------------------------------------------------------------ P4 kappa precision study
+
+def run_p4(args, wl, rank, world):
+    """Zero + assembly of the P4 kappa-diffusion Mat (sparsity built once) for the element-tensor
+    precisions; the step is the tensor-core variant; errors against the FP64 variant."""
+    import torch
+    from paper_1501_01809_gb300 import build as fb
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+    fb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mesh, cmap, nn, _ = make_inputs(wl)
+    kap = mg.lognormal_dat(mesh.nvert, wl["kappa_seed"])
+    stream = torch.cuda.Stream(dev)
+    ctx = fe.ctx_create(dev.index, stream=stream)
+    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+         dict(map=cmap, cv=mesh.cell_vertex, xy=mesh.coords, kap=kap).items()}
+    with torch.cuda.stream(stream):
+        cells, nodes, verts = fe.set_create(ctx, mesh.ncell), fe.set_create(ctx, nn), fe.set_create(ctx, mesh.nvert)
+        M, CM = fe.map_create(ctx, cells, nodes, t["map"]), fe.map_create(ctx, cells, verts, t["cv"])
+        XY, KAP = fe.dat_create(ctx, verts, t["xy"]), fe.dat_create(ctx, verts, t["kap"])
+        sp = fe.sparsity_build(ctx, M, M)
+        A = fe.mat_create(ctx, sp)
+    nnz = fe.sparsity_csr(sp)[2]
+    vals = fe.mat_values(A)
+    res, outs = {}, {}
+    variants = [("tf32x3", fe.PREC_TF32X3), ("fp32", fe.PREC_FP32), ("fp64", fe.PREC_FP64)]
+    clk_summary = None
+    for name, prec in variants:
+        K = fe.kernel_create(ctx, fe.FORM_KAPPA_DIFFUSION, 2, 4, precision=prec)
+        for _ in range(args.warmup):
+            fe.assemble_mat(ctx, K, cells, A, XY, CM, [(KAP, CM)], zero_first=True)
+        fe.sync(ctx)
+        steps = args.steps if name == "tf32x3" else max(3, min(args.steps, 20))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index) as clk:
+            a.record(stream)
+            for _ in range(steps):
+                fe.assemble_mat(ctx, K, cells, A, XY, CM, [(KAP, CM)], zero_first=True)
+            b.record(stream)
+            b.synchronize()
+        if name == "tf32x3":
+            clk_summary = clk.summary()
+        fe.sync(ctx)
+        res[name] = a.elapsed_time(b) / steps
+        with torch.cuda.stream(stream):  # copied before the next variant overwrites the values
+            outs[name] = vals.clone()
+        stream.synchronize()
+    ref = outs["fp64"]
+    err = {k: float((outs[k] - ref).norm() / ref.norm()) for k in ("tf32x3", "fp32")}
+    ms = res["tf32x3"]
+    if world > 1:
+        ms = max_over_ranks(ms, dev)
+    peaks, src = _peaks()
+    # algorithmic bytes: map 60 + coordinate map 12 per cell, coordinates and kappa once, CSR values
+    # written once (zero + INC counted once)
+    byt = mesh.ncell * 72 + mesh.nvert * 24 + nnz * 8
+    gbs = byt / (ms / 1e3) / 1e9
+    tflop = mesh.ncell * 2 * 18 * 120 * 3 / (ms / 1e3) / 1e12  # three TF32 products per cell
+    return {"metric": "cells/s assembled (P4 kappa-diffusion CSR, element tensors on the tensor cores)",
+            "value": job_throughput(mesh.ncell, world, ms), "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "tf32x3", "data": "synthetic",
+            "config": {"workload": wl["name"], "cells_per_gpu": mesh.ncell, "dofs": nn, "nnz": nnz,
+                       "ms_per_assembly": res, "rel_frobenius_vs_fp64": err,
+                       "tensor_tflops_issued": tflop, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (CSR values 789 MB), no flush"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "k_zero_f64 + k_mat_push_tc_kappa_p4 (the scatter of 225 FP64 values per cell binds; "
+                                   "the tensor-core product is a few microseconds)",
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+            "gpu_launches": 2 * args.steps, "clocks": clk_summary, "e2e": None}
 
 
 def make_batch_inputs(wl):
@@ -1069,6 +1149,11 @@ def main():
         td.init_process_group("nccl")
     if wl.get("sweep"):
         out = run_p1_sweep(args, wl, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if wl.get("p4"):
+        out = run_p4(args, wl, rank, world)
         if rank == 0:
             print(json.dumps(out))
         return

@@ -72,6 +72,9 @@ typedef enum {
 typedef enum {
   FE_PREC_FP64 = 0,   /* native IEEE double                                               */
   FE_PREC_F32X2 = 1,  /* pairs of FP32 (error-free transformations), ~2^-46 relative     */
+  FE_PREC_TF32X3 = 3, /* tensor cores (tcgen05): three TF32 products of hi/lo splits, FP32
+                         accumulation in TMEM, FP64 global accumulation; P4 kappa-diffusion Mat on
+                         triangles, push only                                            */
   FE_PREC_FP32 = 2    /* single FP32 (triangles, push): the precision study of high-order
                          elements, ~1e-7 relative element error                           */
 } fe_precision;

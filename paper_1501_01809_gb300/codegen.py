@@ -454,6 +454,36 @@ def emit_kappa(dim: int, p: int) -> str:
     return "\n".join(lines)
 
 
+def emit_kappa_tc(dim: int, p: int) -> str:
+    """Tables of the kappa-diffusion contraction as a dense matrix for the tensor cores:
+    K_upper[n] = sum_k KL[k] C[n][k], n over the upper-triangle pairs (I[n], J[n]), k = kappa node x Lam pair."""
+    C = kappa_tensor(dim, p)
+    pairs = _lam_pairs(dim)
+    nd = len(basis(dim, p))
+    up = _upper(nd)
+    nv = dim + 1
+    nk = nv * len(pairs)
+    tag = f"{dim}{p}"
+    lines = [f"template <> struct KappaTC<{dim}, {p}> {{",
+             f"  static constexpr int N = {len(up)}, K = {nk}, ND = {nd};",
+             "};",
+             "#ifdef FE_GEN_KAPPA_TC_TABLES",
+             f"// row n: upper-triangle pair (I[n], J[n]); column k = kappa node * {len(pairs)} + Lam pair"]
+    lines.append(f"static __constant__ unsigned char kKappaTC{tag}_I[{len(up)}] = {{" + ", ".join(str(i) for i, _ in up) + "};")
+    lines.append(f"static __constant__ unsigned char kKappaTC{tag}_J[{len(up)}] = {{" + ", ".join(str(j) for _, j in up) + "};")
+    rows = []
+    for (i, j) in up:
+        vals = []
+        for k in range(nv):
+            for mn in pairs:
+                c = C[(k,) + mn][i][j]
+                vals.append(repr(float(np.float32(float(c)))) + "f" if c != 0 else "0.0f")
+        rows.append("{" + ", ".join(vals) + "}")
+    lines.append(f"static __device__ const float kKappaTC{tag}_C[{len(up)}][{nk}] = {{" + ",\n    ".join(rows) + "};")
+    lines.append("#endif")
+    return "\n".join(lines)
+
+
 HEADER = """// GENERATED by paper_1501_01809_gb300/codegen.py -- do not edit.
 // Element-tensor contractions for affine simplices (barycentric form); see codegen.py.
 #pragma once
@@ -461,6 +491,7 @@ namespace fe_gen {
 template <int DIM, int P> struct Elem;
 template <int DIM, int P, int Q> struct Source;
 template <int DIM, int P> struct Kappa;
+template <int DIM, int P> struct KappaTC;
 """
 
 
@@ -474,6 +505,7 @@ def generate(check: bool = True) -> str:
         parts.append(emit_source(dim, p, q))
     for dim, p in KAPPA_ELEMENTS:
         parts.append(emit_kappa(dim, p))
+    parts.append(emit_kappa_tc(2, 4))
     parts.append("}  // namespace fe_gen\n")
     return "\n\n".join(parts)
 

@@ -91,6 +91,8 @@ fe_status check_device_flags(fe_ctx *c, const char *where) {
     FE_CHECK_CUDA(cudaStreamSynchronize(c->stream), where);
     if (h[0] & fe::ERR_RANGE) return fail(FE_ERANGE, "%s: a map value lies outside its target set (first index %d)", where, h[1]);
     if (h[0] & fe::ERR_NNZ_CHANGED) return fail(FE_EINVAL, "%s: the rebuilt pattern has a different nnz", where);
+    if (h[0] & fe::ERR_TC_TIMEOUT)
+      return fail(FE_ETIMEOUT, "%s: a tensor-core product did not complete in time (block %d)", where, h[1]);
     if (h[0] & fe::ERR_ROW_TOO_LONG)
       return fail(FE_EUNSUPPORTED, "%s: a row has more than %d columns (row %d)", where, fe::kMaxRowLen, h[1]);
     if (h[0] & fe::ERR_CAND_OVERFLOW)

@@ -26,6 +26,7 @@ LaunchFn pick_vec_pull_dd2(const fe_form_desc &d);
 LaunchFn pick_mat_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_action_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_vec_pull_dd3(const fe_form_desc &d);
+LaunchFn pick_mat_push_tc(const fe_form_desc &d);
 
 namespace {
 
@@ -35,6 +36,7 @@ LaunchFn pick_mat(const fe_form_desc &d, int strategy) {
   const bool pull = strategy == FE_STRATEGY_PULL;
   if (d.precision == FE_PREC_FP64) return pull ? pick_mat_pull_f64(d) : pick_mat_push_f64(d);
   if (d.precision == FE_PREC_FP32) return pull || d.dim != 2 ? nullptr : pick_mat_push_f32(d);
+  if (d.precision == FE_PREC_TF32X3) return pull ? nullptr : pick_mat_push_tc(d);
   if (d.precision == FE_PREC_F32X2) {
     if (d.dim == 2) return pull ? pick_mat_pull_dd2(d) : pick_mat_push_dd2(d);
     return pull ? pick_mat_pull_dd3(d) : pick_mat_push_dd3(d);

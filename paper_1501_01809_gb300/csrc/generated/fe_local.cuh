@@ -5,6 +5,7 @@ namespace fe_gen {
 template <int DIM, int P> struct Elem;
 template <int DIM, int P, int Q> struct Source;
 template <int DIM, int P> struct Kappa;
+template <int DIM, int P> struct KappaTC;
 
 
 // ---- P1 Lagrange on the triangle (3 nodes) ----
@@ -2345,5 +2346,134 @@ template <> struct Kappa<3, 2> {
   }
   static constexpr int TERMS = 544;
 };
+
+template <> struct KappaTC<2, 4> {
+  static constexpr int N = 120, K = 18, ND = 15;
+};
+#ifdef FE_GEN_KAPPA_TC_TABLES
+// row n: upper-triangle pair (I[n], J[n]); column k = kappa node * 6 + Lam pair
+static __constant__ unsigned char kKappaTC24_I[120] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6, 6, 6, 7, 7, 7, 7, 7, 7, 7, 7, 8, 8, 8, 8, 8, 8, 8, 9, 9, 9, 9, 9, 9, 10, 10, 10, 10, 10, 11, 11, 11, 11, 12, 12, 12, 13, 13, 14};
+static __constant__ unsigned char kKappaTC24_J[120] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 6, 7, 8, 9, 10, 11, 12, 13, 14, 7, 8, 9, 10, 11, 12, 13, 14, 8, 9, 10, 11, 12, 13, 14, 9, 10, 11, 12, 13, 14, 10, 11, 12, 13, 14, 11, 12, 13, 14, 12, 13, 14, 13, 14, 14};
+static __device__ const float kKappaTC24_C[120][18] = {{0.5943562388420105f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.07583773881196976f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.07583773881196976f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {0.0f, -0.05149911716580391f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -0.05149911716580391f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -0.010229276493191719f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {0.0f, 0.0f, -0.05149911716580391f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -0.010229276493191719f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -0.05149911716580391f, 0.0f, 0.0f, 0.0f},
+    {0.4021163880825043f, 1.3742504119873047f, 0.0f, 0.0f, 0.0f, 0.0f, -0.09876543283462524f, 0.09171076118946075f, 0.0f, 0.0f, 0.0f, 0.0f, -0.04938271641731262f, 0.09171076118946075f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {-0.1358024626970291f, -0.7343915104866028f, 0.0f, 0.0f, 0.0f, 0.0f, 0.17989417910575867f, -0.051146384328603745f, 0.0f, 0.0f, 0.0f, 0.0f, 0.04056437313556671f, -0.06525573134422302f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {0.035273369401693344f, 0.3075837790966034f, 0.0f, 0.0f, 0.0f, 0.0f, -0.10440917313098907f, 0.0634920671582222f, 0.0f, 0.0f, 0.0f, 0.0f, -0.015520282089710236f, 0.035273369401693344f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {0.4021163880825043f, 0.0f, 1.3742504119873047f, 0.0f, 0.0f, 0.0f, -0.04938271641731262f, 0.0f, 0.09171076118946075f, 0.0f, 0.0f, 0.0f, -0.09876543283462524f, 0.0f, 0.09171076118946075f, 0.0f, 0.0f, 0.0f},
+    {-0.1358024626970291f, 0.0f, -0.7343915104866028f, 0.0f, 0.0f, 0.0f, 0.04056437313556671f, 0.0f, -0.06525573134422302f, 0.0f, 0.0f, 0.0f, 0.17989417910575867f, 0.0f, -0.051146384328603745f, 0.0f, 0.0f, 0.0f},
+    {0.035273369401693344f, 0.0f, 0.3075837790966034f, 0.0f, 0.0f, 0.0f, -0.015520282089710236f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, 0.0f, -0.10440917313098907f, 0.0f, 0.0634920671582222f, 0.0f, 0.0f, 0.0f},
+    {0.0f, 0.035273369401693344f, 0.035273369401693344f, 0.0f, 0.0f, 0.0f, 0.0f, -0.08888889104127884f, -0.10440917313098907f, 0.0f, 0.0f, 0.0f, 0.0f, -0.03104056417942047f, -0.015520282089710236f, 0.0f, 0.0f, 0.0f},
+    {0.0f, 0.019400352612137794f, 0.019400352612137794f, 0.0f, 0.0f, 0.0f, 0.0f, -0.04691357910633087f, -0.05714285746216774f, 0.0f, 0.0f, 0.0f, 0.0f, -0.05714285746216774f, -0.04691357910633087f, 0.0f, 0.0f, 0.0f},
+    {0.0f, 0.035273369401693344f, 0.035273369401693344f, 0.0f, 0.0f, 0.0f, 0.0f, -0.015520282089710236f, -0.03104056417942047f, 0.0f, 0.0f, 0.0f, 0.0f, -0.10440917313098907f, -0.08888889104127884f, 0.0f, 0.0f, 0.0f},
+    {0.07054673880338669f, 0.5925925970077515f, 0.5925925970077515f, 0.0f, 0.0f, 0.0f, 0.1975308656692505f, 0.014109347015619278f, 0.028218694031238556f, 0.0f, 0.0f, 0.0f, 0.1975308656692505f, 0.028218694031238556f, 0.014109347015619278f, 0.0f, 0.0f, 0.0f},
+    {0.014109347015619278f, -0.14109347760677338f, -0.14109347760677338f, 0.0f, 0.0f, 0.0f, -0.15238095819950104f, 0.07054673880338669f, 0.08465608209371567f, 0.0f, 0.0f, 0.0f, -0.0733686089515686f, 0.028218694031238556f, 0.014109347015619278f, 0.0f, 0.0f, 0.0f},
+    {0.014109347015619278f, -0.14109347760677338f, -0.14109347760677338f, 0.0f, 0.0f, 0.0f, -0.0733686089515686f, 0.014109347015619278f, 0.028218694031238556f, 0.0f, 0.0f, 0.0f, -0.15238095819950104f, 0.08465608209371567f, 0.07054673880338669f, 0.0f, 0.0f, 0.0f},
+    {0.0f, 0.0f, 0.0f, 0.07583773881196976f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.5943562388420105f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.07583773881196976f, 0.0f, 0.0f},
+    {0.0f, 0.0f, 0.0f, 0.0f, -0.010229276493191719f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -0.05149911716580391f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, -0.05149911716580391f, 0.0f},
+    {0.0f, 0.0634920671582222f, 0.0f, -0.10440917313098907f, 0.0f, 0.0f, 0.0f, 0.3075837790966034f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, -0.015520282089710236f, 0.0f, 0.0f},
+    {0.0f, -0.051146384328603745f, 0.0f, 0.17989417910575867f, 0.0f, 0.0f, 0.0f, -0.7343915104866028f, 0.0f, -0.1358024626970291f, 0.0f, 0.0f, 0.0f, -0.06525573134422302f, 0.0f, 0.04056437313556671f, 0.0f, 0.0f},
+    {0.0f, 0.09171076118946075f, 0.0f, -0.09876543283462524f, 0.0f, 0.0f, 0.0f, 1.3742504119873047f, 0.0f, 0.4021163880825043f, 0.0f, 0.0f, 0.0f, 0.09171076118946075f, 0.0f, -0.04938271641731262f, 0.0f, 0.0f},
+    {0.0f, -0.08888889104127884f, 0.0f, 0.0f, -0.10440917313098907f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, -0.03104056417942047f, 0.0f, 0.0f, -0.015520282089710236f, 0.0f},
+    {0.0f, -0.04691357910633087f, 0.0f, 0.0f, -0.05714285746216774f, 0.0f, 0.0f, 0.019400352612137794f, 0.0f, 0.0f, 0.019400352612137794f, 0.0f, 0.0f, -0.05714285746216774f, 0.0f, 0.0f, -0.04691357910633087f, 0.0f},
+    {0.0f, -0.015520282089710236f, 0.0f, 0.0f, -0.03104056417942047f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, -0.10440917313098907f, 0.0f, 0.0f, -0.08888889104127884f, 0.0f},
+    {0.0f, 0.0f, 0.0f, -0.04938271641731262f, 0.09171076118946075f, 0.0f, 0.0f, 0.0f, 0.0f, 0.4021163880825043f, 1.3742504119873047f, 0.0f, 0.0f, 0.0f, 0.0f, -0.09876543283462524f, 0.09171076118946075f, 0.0f},
+    {0.0f, 0.0f, 0.0f, 0.04056437313556671f, -0.06525573134422302f, 0.0f, 0.0f, 0.0f, 0.0f, -0.1358024626970291f, -0.7343915104866028f, 0.0f, 0.0f, 0.0f, 0.0f, 0.17989417910575867f, -0.051146384328603745f, 0.0f},
+    {0.0f, 0.0f, 0.0f, -0.015520282089710236f, 0.035273369401693344f, 0.0f, 0.0f, 0.0f, 0.0f, 0.035273369401693344f, 0.3075837790966034f, 0.0f, 0.0f, 0.0f, 0.0f, -0.10440917313098907f, 0.0634920671582222f, 0.0f},
+    {0.0f, 0.07054673880338669f, 0.0f, -0.15238095819950104f, 0.08465608209371567f, 0.0f, 0.0f, -0.14109347760677338f, 0.0f, 0.014109347015619278f, -0.14109347760677338f, 0.0f, 0.0f, 0.028218694031238556f, 0.0f, -0.0733686089515686f, 0.014109347015619278f, 0.0f},
+    {0.0f, 0.014109347015619278f, 0.0f, 0.1975308656692505f, 0.028218694031238556f, 0.0f, 0.0f, 0.5925925970077515f, 0.0f, 0.07054673880338669f, 0.5925925970077515f, 0.0f, 0.0f, 0.028218694031238556f, 0.0f, 0.1975308656692505f, 0.014109347015619278f, 0.0f},
+    {0.0f, 0.014109347015619278f, 0.0f, -0.0733686089515686f, 0.028218694031238556f, 0.0f, 0.0f, -0.14109347760677338f, 0.0f, 0.014109347015619278f, -0.14109347760677338f, 0.0f, 0.0f, 0.08465608209371567f, 0.0f, -0.15238095819950104f, 0.07054673880338669f, 0.0f},
+    {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.07583773881196976f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.07583773881196976f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.5943562388420105f},
+    {0.0f, 0.0f, -0.08888889104127884f, 0.0f, -0.10440917313098907f, 0.0f, 0.0f, 0.0f, -0.03104056417942047f, 0.0f, -0.015520282089710236f, 0.0f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.035273369401693344f, 0.0f},
+    {0.0f, 0.0f, -0.04691357910633087f, 0.0f, -0.05714285746216774f, 0.0f, 0.0f, 0.0f, -0.05714285746216774f, 0.0f, -0.04691357910633087f, 0.0f, 0.0f, 0.0f, 0.019400352612137794f, 0.0f, 0.019400352612137794f, 0.0f},
+    {0.0f, 0.0f, -0.015520282089710236f, 0.0f, -0.03104056417942047f, 0.0f, 0.0f, 0.0f, -0.10440917313098907f, 0.0f, -0.08888889104127884f, 0.0f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.035273369401693344f, 0.0f},
+    {0.0f, 0.0f, 0.0634920671582222f, 0.0f, 0.0f, -0.10440917313098907f, 0.0f, 0.0f, 0.035273369401693344f, 0.0f, 0.0f, -0.015520282089710236f, 0.0f, 0.0f, 0.3075837790966034f, 0.0f, 0.0f, 0.035273369401693344f},
+    {0.0f, 0.0f, -0.051146384328603745f, 0.0f, 0.0f, 0.17989417910575867f, 0.0f, 0.0f, -0.06525573134422302f, 0.0f, 0.0f, 0.04056437313556671f, 0.0f, 0.0f, -0.7343915104866028f, 0.0f, 0.0f, -0.1358024626970291f},
+    {0.0f, 0.0f, 0.09171076118946075f, 0.0f, 0.0f, -0.09876543283462524f, 0.0f, 0.0f, 0.09171076118946075f, 0.0f, 0.0f, -0.04938271641731262f, 0.0f, 0.0f, 1.3742504119873047f, 0.0f, 0.0f, 0.4021163880825043f},
+    {0.0f, 0.0f, 0.0f, 0.0f, 0.035273369401693344f, -0.015520282089710236f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0634920671582222f, -0.10440917313098907f, 0.0f, 0.0f, 0.0f, 0.0f, 0.3075837790966034f, 0.035273369401693344f},
+    {0.0f, 0.0f, 0.0f, 0.0f, -0.06525573134422302f, 0.04056437313556671f, 0.0f, 0.0f, 0.0f, 0.0f, -0.051146384328603745f, 0.17989417910575867f, 0.0f, 0.0f, 0.0f, 0.0f, -0.7343915104866028f, -0.1358024626970291f},
+    {0.0f, 0.0f, 0.0f, 0.0f, 0.09171076118946075f, -0.04938271641731262f, 0.0f, 0.0f, 0.0f, 0.0f, 0.09171076118946075f, -0.09876543283462524f, 0.0f, 0.0f, 0.0f, 0.0f, 1.3742504119873047f, 0.4021163880825043f},
+    {0.0f, 0.0f, 0.07054673880338669f, 0.0f, 0.08465608209371567f, -0.15238095819950104f, 0.0f, 0.0f, 0.028218694031238556f, 0.0f, 0.014109347015619278f, -0.0733686089515686f, 0.0f, 0.0f, -0.14109347760677338f, 0.0f, -0.14109347760677338f, 0.014109347015619278f},
+    {0.0f, 0.0f, 0.014109347015619278f, 0.0f, 0.028218694031238556f, -0.0733686089515686f, 0.0f, 0.0f, 0.08465608209371567f, 0.0f, 0.07054673880338669f, -0.15238095819950104f, 0.0f, 0.0f, -0.14109347760677338f, 0.0f, -0.14109347760677338f, 0.014109347015619278f},
+    {0.0f, 0.0f, 0.014109347015619278f, 0.0f, 0.028218694031238556f, 0.1975308656692505f, 0.0f, 0.0f, 0.028218694031238556f, 0.0f, 0.014109347015619278f, 0.1975308656692505f, 0.0f, 0.0f, 0.5925925970077515f, 0.0f, 0.5925925970077515f, 0.07054673880338669f},
+    {2.0317461490631104f, 3.250793695449829f, 0.0f, 3.566843032836914f, 0.0f, 0.0f, 1.2190476655960083f, 0.6320987939834595f, 0.0f, 0.31604939699172974f, 0.0f, 0.0f, 0.40634921193122864f, 0.31604939699172974f, 0.0f, 0.31604939699172974f, 0.0f, 0.0f},
+    {-0.16931216418743134f, 0.5530864000320435f, 0.0f, -1.388359785079956f, 0.0f, 0.0f, -0.9142857193946838f, 0.4740740656852722f, 0.0f, 0.04514991119503975f, 0.0f, 0.0f, -0.2370370328426361f, 0.022574955597519875f, 0.0f, -0.180599644780159f, 0.0f, 0.0f},
+    {0.0f, -0.31604939699172974f, 0.0f, 0.5869488716125488f, 0.0f, 0.0f, 0.5869488716125488f, -0.31604939699172974f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0902998223900795f, -0.04514991119503975f, 0.0f, 0.0902998223900795f, 0.0f, 0.0f},
+    {1.0158730745315552f, 1.6253968477249146f, 1.6253968477249146f, 0.0f, 3.566843032836914f, 0.0f, 0.40634921193122864f, 0.15802469849586487f, 0.31604939699172974f, 0.0f, 0.31604939699172974f, 0.0f, 0.40634921193122864f, 0.31604939699172974f, 0.15802469849586487f, 0.0f, 0.31604939699172974f, 0.0f},
+    {-0.3216931223869324f, -0.42892417311668396f, -0.7788359522819519f, 0.0f, -1.388359785079956f, 0.0f, -0.16931216418743134f, -0.06208112835884094f, -0.2370370328426361f, 0.0f, -0.180599644780159f, 0.0f, -0.2370370328426361f, -0.10158730298280716f, 0.08465608209371567f, 0.0f, 0.04514991119503975f, 0.0f},
+    {0.06772486865520477f, 0.0902998223900795f, 0.40634921193122864f, 0.0f, 0.5869488716125488f, 0.0f, 0.04514991119503975f, 0.022574955597519875f, 0.13544973731040955f, 0.0f, 0.0902998223900795f, 0.0f, 0.0902998223900795f, 0.0902998223900795f, -0.06772486865520477f, 0.0f, 0.0f, 0.0f},
+    {0.0f, -0.06772486865520477f, 0.0f, 0.0902998223900795f, 0.0902998223900795f, 0.0f, 0.0f, 0.40634921193122864f, 0.5869488716125488f, 0.06772486865520477f, 0.0902998223900795f, 0.0f, 0.0f, 0.13544973731040955f, 0.0902998223900795f, 0.04514991119503975f, 0.022574955597519875f, 0.0f},
+    {0.0f, -0.05079365149140358f, -0.033862434327602386f, 0.022574955597519875f, 0.022574955597519875f, 0.0f, 0.0f, 0.10158730298280716f, 0.16931216418743134f, 0.028218694031238556f, 0.033862434327602386f, 0.0f, 0.0f, 0.16931216418743134f, 0.16931216418743134f, 0.033862434327602386f, 0.028218694031238556f, 0.0f},
+    {0.0f, 0.06772486865520477f, 0.13544973731040955f, 0.0902998223900795f, 0.0902998223900795f, 0.0f, 0.0f, 0.04514991119503975f, 0.13544973731040955f, 0.022574955597519875f, 0.04514991119503975f, 0.0f, 0.0f, 0.0902998223900795f, 0.13544973731040955f, 0.0902998223900795f, 0.06772486865520477f, 0.0f},
+    {0.9481481313705444f, 2.3477954864501953f, 3.521693229675293f, 2.573544979095459f, 2.573544979095459f, 0.0f, -0.40634921193122864f, 0.4514991044998169f, 1.2190476655960083f, 0.22574955224990845f, 0.4514991044998169f, 0.0f, -0.2708994746208191f, 0.4514991044998169f, 0.40634921193122864f, 0.4514991044998169f, 0.22574955224990845f, 0.0f},
+    {-0.13544973731040955f, 0.0902998223900795f, -0.2708994746208191f, -0.49664902687072754f, -0.49664902687072754f, 0.0f, 0.6772486567497253f, 0.0f, -0.40634921193122864f, 0.04514991119503975f, 0.0f, 0.0f, 0.2708994746208191f, -0.0902998223900795f, -0.13544973731040955f, -0.0902998223900795f, -0.04514991119503975f, 0.0f},
+    {-0.13544973731040955f, -0.4514991044998169f, -0.8126984238624573f, -0.49664902687072754f, -0.49664902687072754f, 0.0f, 0.13544973731040955f, -0.0902998223900795f, -0.40634921193122864f, -0.04514991119503975f, -0.0902998223900795f, 0.0f, 0.2708994746208191f, 0.0f, -0.13544973731040955f, 0.0f, 0.04514991119503975f, 0.0f},
+    {1.244444489479065f, 1.7777777910232544f, 0.0f, 3.1576719284057617f, 0.0f, 0.0f, 3.1576719284057617f, 1.7777777910232544f, 0.0f, 1.244444489479065f, 0.0f, 0.0f, 0.49947088956832886f, 0.3301587402820587f, 0.0f, 0.49947088956832886f, 0.0f, 0.0f},
+    {0.04514991119503975f, 0.4740740656852722f, 0.0f, -0.9142857193946838f, 0.0f, 0.0f, -1.388359785079956f, 0.5530864000320435f, 0.0f, -0.16931216418743134f, 0.0f, 0.0f, -0.180599644780159f, 0.022574955597519875f, 0.0f, -0.2370370328426361f, 0.0f, 0.0f},
+    {-0.3216931223869324f, -0.7788359522819519f, -0.42892417311668396f, 0.0f, -1.388359785079956f, 0.0f, -0.2370370328426361f, 0.08465608209371567f, -0.10158730298280716f, 0.0f, 0.04514991119503975f, 0.0f, -0.16931216418743134f, -0.2370370328426361f, -0.06208112835884094f, 0.0f, -0.180599644780159f, 0.0f},
+    {-0.10582010447978973f, -0.1608465611934662f, -0.1608465611934662f, 0.0f, -0.3640211522579193f, 0.0f, -0.09312169253826141f, -0.10582010447978973f, -0.1269841343164444f, 0.0f, -0.21164020895957947f, 0.0f, -0.09312169253826141f, -0.1269841343164444f, -0.10582010447978973f, 0.0f, -0.21164020895957947f, 0.0f},
+    {0.028218694031238556f, 0.033862434327602386f, 0.10158730298280716f, 0.0f, 0.16931216418743134f, 0.0f, 0.033862434327602386f, 0.028218694031238556f, 0.16931216418743134f, 0.0f, 0.16931216418743134f, 0.0f, 0.022574955597519875f, 0.022574955597519875f, -0.05079365149140358f, 0.0f, -0.033862434327602386f, 0.0f},
+    {0.0f, 0.08465608209371567f, 0.04514991119503975f, -0.2370370328426361f, -0.10158730298280716f, 0.0f, 0.0f, -0.7788359522819519f, -1.388359785079956f, -0.3216931223869324f, -0.42892417311668396f, 0.0f, 0.0f, -0.2370370328426361f, -0.180599644780159f, -0.16931216418743134f, -0.06208112835884094f, 0.0f},
+    {0.0f, -0.10582010447978973f, -0.21164020895957947f, -0.09312169253826141f, -0.1269841343164444f, 0.0f, 0.0f, -0.1608465611934662f, -0.3640211522579193f, -0.10582010447978973f, -0.1608465611934662f, 0.0f, 0.0f, -0.1269841343164444f, -0.21164020895957947f, -0.09312169253826141f, -0.10582010447978973f, 0.0f},
+    {0.0f, 0.028218694031238556f, 0.16931216418743134f, 0.033862434327602386f, 0.16931216418743134f, 0.0f, 0.0f, 0.033862434327602386f, 0.16931216418743134f, 0.028218694031238556f, 0.10158730298280716f, 0.0f, 0.0f, 0.022574955597519875f, -0.033862434327602386f, 0.022574955597519875f, -0.05079365149140358f, 0.0f},
+    {0.5079365372657776f, 0.6095238327980042f, 0.6095238327980042f, -1.049735426902771f, 2.4719576835632324f, 0.0f, 1.6592592000961304f, 1.0158730745315552f, 1.1174603700637817f, 0.37248677015304565f, 1.8285714387893677f, 0.0f, 0.4740740656852722f, 0.20317460596561432f, 0.10158730298280716f, -0.33862432837486267f, 0.37248677015304565f, 0.0f},
+    {0.37248677015304565f, 1.0158730745315552f, 1.8285714387893677f, 1.6592592000961304f, 1.1174603700637817f, 0.0f, -1.049735426902771f, 0.6095238327980042f, 2.4719576835632324f, 0.5079365372657776f, 0.6095238327980042f, 0.0f, -0.33862432837486267f, 0.20317460596561432f, 0.37248677015304565f, 0.4740740656852722f, 0.10158730298280716f, 0.0f},
+    {-0.16931216418743134f, -0.33862432837486267f, -0.6095238327980042f, -0.2370370328426361f, -0.7788359522819519f, 0.0f, -0.2370370328426361f, -0.33862432837486267f, -0.7788359522819519f, -0.16931216418743134f, -0.6095238327980042f, 0.0f, -0.20317460596561432f, -0.33862432837486267f, -0.033862434327602386f, -0.20317460596561432f, -0.033862434327602386f, 0.0f},
+    {0.31604939699172974f, 0.6320987939834595f, 0.0f, 1.2190476655960083f, 0.0f, 0.0f, 3.566843032836914f, 3.250793695449829f, 0.0f, 2.0317461490631104f, 0.0f, 0.0f, 0.31604939699172974f, 0.31604939699172974f, 0.0f, 0.40634921193122864f, 0.0f, 0.0f},
+    {0.06772486865520477f, 0.40634921193122864f, 0.0902998223900795f, 0.0f, 0.5869488716125488f, 0.0f, 0.0902998223900795f, -0.06772486865520477f, 0.0902998223900795f, 0.0f, 0.0f, 0.0f, 0.04514991119503975f, 0.13544973731040955f, 0.022574955597519875f, 0.0f, 0.0902998223900795f, 0.0f},
+    {0.028218694031238556f, 0.10158730298280716f, 0.033862434327602386f, 0.0f, 0.16931216418743134f, 0.0f, 0.022574955597519875f, -0.05079365149140358f, 0.022574955597519875f, 0.0f, -0.033862434327602386f, 0.0f, 0.033862434327602386f, 0.16931216418743134f, 0.028218694031238556f, 0.0f, 0.16931216418743134f, 0.0f},
+    {0.022574955597519875f, 0.04514991119503975f, 0.04514991119503975f, 0.0f, 0.13544973731040955f, 0.0f, 0.0902998223900795f, 0.06772486865520477f, 0.0902998223900795f, 0.0f, 0.13544973731040955f, 0.0f, 0.0902998223900795f, 0.0902998223900795f, 0.06772486865520477f, 0.0f, 0.13544973731040955f, 0.0f},
+    {0.0f, 0.15802469849586487f, 0.31604939699172974f, 0.40634921193122864f, 0.31604939699172974f, 0.0f, 0.0f, 1.6253968477249146f, 3.566843032836914f, 1.0158730745315552f, 1.6253968477249146f, 0.0f, 0.0f, 0.31604939699172974f, 0.31604939699172974f, 0.40634921193122864f, 0.15802469849586487f, 0.0f},
+    {0.0f, -0.06208112835884094f, -0.180599644780159f, -0.16931216418743134f, -0.2370370328426361f, 0.0f, 0.0f, -0.42892417311668396f, -1.388359785079956f, -0.3216931223869324f, -0.7788359522819519f, 0.0f, 0.0f, -0.10158730298280716f, 0.04514991119503975f, -0.2370370328426361f, 0.08465608209371567f, 0.0f},
+    {0.0f, 0.022574955597519875f, 0.0902998223900795f, 0.04514991119503975f, 0.13544973731040955f, 0.0f, 0.0f, 0.0902998223900795f, 0.5869488716125488f, 0.06772486865520477f, 0.40634921193122864f, 0.0f, 0.0f, 0.0902998223900795f, 0.0f, 0.0902998223900795f, -0.06772486865520477f, 0.0f},
+    {0.04514991119503975f, 0.0f, 0.0f, 0.6772486567497253f, -0.40634921193122864f, 0.0f, -0.49664902687072754f, 0.0902998223900795f, -0.49664902687072754f, -0.13544973731040955f, -0.2708994746208191f, 0.0f, -0.0902998223900795f, -0.0902998223900795f, -0.04514991119503975f, 0.2708994746208191f, -0.13544973731040955f, 0.0f},
+    {0.22574955224990845f, 0.4514991044998169f, 0.4514991044998169f, -0.40634921193122864f, 1.2190476655960083f, 0.0f, 2.573544979095459f, 2.3477954864501953f, 2.573544979095459f, 0.9481481313705444f, 3.521693229675293f, 0.0f, 0.4514991044998169f, 0.4514991044998169f, 0.22574955224990845f, -0.2708994746208191f, 0.40634921193122864f, 0.0f},
+    {-0.04514991119503975f, -0.0902998223900795f, -0.0902998223900795f, 0.13544973731040955f, -0.40634921193122864f, 0.0f, -0.49664902687072754f, -0.4514991044998169f, -0.49664902687072754f, -0.13544973731040955f, -0.8126984238624573f, 0.0f, 0.0f, 0.0f, 0.04514991119503975f, 0.2708994746208191f, -0.13544973731040955f, 0.0f},
+    {2.0317461490631104f, 0.0f, 3.250793695449829f, 0.0f, 0.0f, 3.566843032836914f, 0.40634921193122864f, 0.0f, 0.31604939699172974f, 0.0f, 0.0f, 0.31604939699172974f, 1.2190476655960083f, 0.0f, 0.6320987939834595f, 0.0f, 0.0f, 0.31604939699172974f},
+    {-0.16931216418743134f, 0.0f, 0.5530864000320435f, 0.0f, 0.0f, -1.388359785079956f, -0.2370370328426361f, 0.0f, 0.022574955597519875f, 0.0f, 0.0f, -0.180599644780159f, -0.9142857193946838f, 0.0f, 0.4740740656852722f, 0.0f, 0.0f, 0.04514991119503975f},
+    {0.0f, 0.0f, -0.31604939699172974f, 0.0f, 0.0f, 0.5869488716125488f, 0.0902998223900795f, 0.0f, -0.04514991119503975f, 0.0f, 0.0f, 0.0902998223900795f, 0.5869488716125488f, 0.0f, -0.31604939699172974f, 0.0f, 0.0f, 0.0f},
+    {0.0f, 0.13544973731040955f, 0.06772486865520477f, 0.0f, 0.0902998223900795f, 0.0902998223900795f, 0.0f, 0.13544973731040955f, 0.0902998223900795f, 0.0f, 0.06772486865520477f, 0.0902998223900795f, 0.0f, 0.13544973731040955f, 0.04514991119503975f, 0.0f, 0.04514991119503975f, 0.022574955597519875f},
+    {0.0f, -0.033862434327602386f, -0.05079365149140358f, 0.0f, 0.022574955597519875f, 0.022574955597519875f, 0.0f, 0.16931216418743134f, 0.16931216418743134f, 0.0f, 0.028218694031238556f, 0.033862434327602386f, 0.0f, 0.16931216418743134f, 0.10158730298280716f, 0.0f, 0.033862434327602386f, 0.028218694031238556f},
+    {0.0f, 0.0f, -0.06772486865520477f, 0.0f, 0.0902998223900795f, 0.0902998223900795f, 0.0f, 0.0902998223900795f, 0.13544973731040955f, 0.0f, 0.022574955597519875f, 0.04514991119503975f, 0.0f, 0.5869488716125488f, 0.40634921193122864f, 0.0f, 0.0902998223900795f, 0.06772486865520477f},
+    {0.9481481313705444f, 3.521693229675293f, 2.3477954864501953f, 0.0f, 2.573544979095459f, 2.573544979095459f, -0.2708994746208191f, 0.40634921193122864f, 0.4514991044998169f, 0.0f, 0.22574955224990845f, 0.4514991044998169f, -0.40634921193122864f, 1.2190476655960083f, 0.4514991044998169f, 0.0f, 0.4514991044998169f, 0.22574955224990845f},
+    {-0.13544973731040955f, -0.8126984238624573f, -0.4514991044998169f, 0.0f, -0.49664902687072754f, -0.49664902687072754f, 0.2708994746208191f, -0.13544973731040955f, 0.0f, 0.0f, 0.04514991119503975f, 0.0f, 0.13544973731040955f, -0.40634921193122864f, -0.0902998223900795f, 0.0f, -0.0902998223900795f, -0.04514991119503975f},
+    {-0.13544973731040955f, -0.2708994746208191f, 0.0902998223900795f, 0.0f, -0.49664902687072754f, -0.49664902687072754f, 0.2708994746208191f, -0.13544973731040955f, -0.0902998223900795f, 0.0f, -0.04514991119503975f, -0.0902998223900795f, 0.6772486567497253f, -0.40634921193122864f, 0.0f, 0.0f, 0.0f, 0.04514991119503975f},
+    {1.244444489479065f, 0.0f, 1.7777777910232544f, 0.0f, 0.0f, 3.1576719284057617f, 0.49947088956832886f, 0.0f, 0.3301587402820587f, 0.0f, 0.0f, 0.49947088956832886f, 3.1576719284057617f, 0.0f, 1.7777777910232544f, 0.0f, 0.0f, 1.244444489479065f},
+    {0.04514991119503975f, 0.0f, 0.4740740656852722f, 0.0f, 0.0f, -0.9142857193946838f, -0.180599644780159f, 0.0f, 0.022574955597519875f, 0.0f, 0.0f, -0.2370370328426361f, -1.388359785079956f, 0.0f, 0.5530864000320435f, 0.0f, 0.0f, -0.16931216418743134f},
+    {0.0f, 0.16931216418743134f, 0.028218694031238556f, 0.0f, 0.16931216418743134f, 0.033862434327602386f, 0.0f, -0.033862434327602386f, 0.022574955597519875f, 0.0f, -0.05079365149140358f, 0.022574955597519875f, 0.0f, 0.16931216418743134f, 0.033862434327602386f, 0.0f, 0.10158730298280716f, 0.028218694031238556f},
+    {0.0f, -0.21164020895957947f, -0.10582010447978973f, 0.0f, -0.1269841343164444f, -0.09312169253826141f, 0.0f, -0.21164020895957947f, -0.1269841343164444f, 0.0f, -0.10582010447978973f, -0.09312169253826141f, 0.0f, -0.3640211522579193f, -0.1608465611934662f, 0.0f, -0.1608465611934662f, -0.10582010447978973f},
+    {0.0f, 0.04514991119503975f, 0.08465608209371567f, 0.0f, -0.10158730298280716f, -0.2370370328426361f, 0.0f, -0.180599644780159f, -0.2370370328426361f, 0.0f, -0.06208112835884094f, -0.16931216418743134f, 0.0f, -1.388359785079956f, -0.7788359522819519f, 0.0f, -0.42892417311668396f, -0.3216931223869324f},
+    {0.5079365372657776f, 0.6095238327980042f, 0.6095238327980042f, 0.0f, 2.4719576835632324f, -1.049735426902771f, 0.4740740656852722f, 0.10158730298280716f, 0.20317460596561432f, 0.0f, 0.37248677015304565f, -0.33862432837486267f, 1.6592592000961304f, 1.1174603700637817f, 1.0158730745315552f, 0.0f, 1.8285714387893677f, 0.37248677015304565f},
+    {-0.16931216418743134f, -0.6095238327980042f, -0.33862432837486267f, 0.0f, -0.7788359522819519f, -0.2370370328426361f, -0.20317460596561432f, -0.033862434327602386f, -0.33862432837486267f, 0.0f, -0.033862434327602386f, -0.20317460596561432f, -0.2370370328426361f, -0.7788359522819519f, -0.33862432837486267f, 0.0f, -0.6095238327980042f, -0.16931216418743134f},
+    {0.37248677015304565f, 1.8285714387893677f, 1.0158730745315552f, 0.0f, 1.1174603700637817f, 1.6592592000961304f, -0.33862432837486267f, 0.37248677015304565f, 0.20317460596561432f, 0.0f, 0.10158730298280716f, 0.4740740656852722f, -1.049735426902771f, 2.4719576835632324f, 0.6095238327980042f, 0.0f, 0.6095238327980042f, 0.5079365372657776f},
+    {0.31604939699172974f, 0.0f, 0.6320987939834595f, 0.0f, 0.0f, 1.2190476655960083f, 0.31604939699172974f, 0.0f, 0.31604939699172974f, 0.0f, 0.0f, 0.40634921193122864f, 3.566843032836914f, 0.0f, 3.250793695449829f, 0.0f, 0.0f, 2.0317461490631104f},
+    {0.0f, 0.0902998223900795f, 0.022574955597519875f, 0.0f, 0.13544973731040955f, 0.04514991119503975f, 0.0f, 0.0f, 0.0902998223900795f, 0.0f, -0.06772486865520477f, 0.0902998223900795f, 0.0f, 0.5869488716125488f, 0.0902998223900795f, 0.0f, 0.40634921193122864f, 0.06772486865520477f},
+    {0.0f, -0.180599644780159f, -0.06208112835884094f, 0.0f, -0.2370370328426361f, -0.16931216418743134f, 0.0f, 0.04514991119503975f, -0.10158730298280716f, 0.0f, 0.08465608209371567f, -0.2370370328426361f, 0.0f, -1.388359785079956f, -0.42892417311668396f, 0.0f, -0.7788359522819519f, -0.3216931223869324f},
+    {0.0f, 0.31604939699172974f, 0.15802469849586487f, 0.0f, 0.31604939699172974f, 0.40634921193122864f, 0.0f, 0.31604939699172974f, 0.31604939699172974f, 0.0f, 0.15802469849586487f, 0.40634921193122864f, 0.0f, 3.566843032836914f, 1.6253968477249146f, 0.0f, 1.6253968477249146f, 1.0158730745315552f},
+    {0.04514991119503975f, 0.0f, 0.0f, 0.0f, -0.40634921193122864f, 0.6772486567497253f, -0.0902998223900795f, -0.04514991119503975f, -0.0902998223900795f, 0.0f, -0.13544973731040955f, 0.2708994746208191f, -0.49664902687072754f, -0.49664902687072754f, 0.0902998223900795f, 0.0f, -0.2708994746208191f, -0.13544973731040955f},
+    {-0.04514991119503975f, -0.0902998223900795f, -0.0902998223900795f, 0.0f, -0.40634921193122864f, 0.13544973731040955f, 0.0f, 0.04514991119503975f, 0.0f, 0.0f, -0.13544973731040955f, 0.2708994746208191f, -0.49664902687072754f, -0.49664902687072754f, -0.4514991044998169f, 0.0f, -0.8126984238624573f, -0.13544973731040955f},
+    {0.22574955224990845f, 0.4514991044998169f, 0.4514991044998169f, 0.0f, 1.2190476655960083f, -0.40634921193122864f, 0.4514991044998169f, 0.22574955224990845f, 0.4514991044998169f, 0.0f, 0.40634921193122864f, -0.2708994746208191f, 2.573544979095459f, 2.573544979095459f, 2.3477954864501953f, 0.0f, 3.521693229675293f, 0.9481481313705444f},
+    {0.0f, 0.0f, 0.0f, 0.40634921193122864f, 0.31604939699172974f, 0.31604939699172974f, 0.0f, 0.0f, 0.0f, 2.0317461490631104f, 3.250793695449829f, 3.566843032836914f, 0.0f, 0.0f, 0.0f, 1.2190476655960083f, 0.6320987939834595f, 0.31604939699172974f},
+    {0.0f, 0.0f, 0.0f, -0.2370370328426361f, 0.022574955597519875f, -0.180599644780159f, 0.0f, 0.0f, 0.0f, -0.16931216418743134f, 0.5530864000320435f, -1.388359785079956f, 0.0f, 0.0f, 0.0f, -0.9142857193946838f, 0.4740740656852722f, 0.04514991119503975f},
+    {0.0f, 0.0f, 0.0f, 0.0902998223900795f, -0.04514991119503975f, 0.0902998223900795f, 0.0f, 0.0f, 0.0f, 0.0f, -0.31604939699172974f, 0.5869488716125488f, 0.0f, 0.0f, 0.0f, 0.5869488716125488f, -0.31604939699172974f, 0.0f},
+    {0.0f, -0.13544973731040955f, 0.04514991119503975f, 0.2708994746208191f, 0.0f, 0.0f, 0.0f, -0.8126984238624573f, -0.49664902687072754f, -0.13544973731040955f, -0.4514991044998169f, -0.49664902687072754f, 0.0f, -0.40634921193122864f, -0.0902998223900795f, 0.13544973731040955f, -0.0902998223900795f, -0.04514991119503975f},
+    {0.0f, 0.40634921193122864f, 0.22574955224990845f, -0.2708994746208191f, 0.4514991044998169f, 0.4514991044998169f, 0.0f, 3.521693229675293f, 2.573544979095459f, 0.9481481313705444f, 2.3477954864501953f, 2.573544979095459f, 0.0f, 1.2190476655960083f, 0.4514991044998169f, -0.40634921193122864f, 0.4514991044998169f, 0.22574955224990845f},
+    {0.0f, -0.13544973731040955f, -0.04514991119503975f, 0.2708994746208191f, -0.0902998223900795f, -0.0902998223900795f, 0.0f, -0.2708994746208191f, -0.49664902687072754f, -0.13544973731040955f, 0.0902998223900795f, -0.49664902687072754f, 0.0f, -0.40634921193122864f, 0.0f, 0.6772486567497253f, 0.0f, 0.04514991119503975f},
+    {0.0f, 0.0f, 0.0f, 0.49947088956832886f, 0.3301587402820587f, 0.49947088956832886f, 0.0f, 0.0f, 0.0f, 1.244444489479065f, 1.7777777910232544f, 3.1576719284057617f, 0.0f, 0.0f, 0.0f, 3.1576719284057617f, 1.7777777910232544f, 1.244444489479065f},
+    {0.0f, 0.0f, 0.0f, -0.180599644780159f, 0.022574955597519875f, -0.2370370328426361f, 0.0f, 0.0f, 0.0f, 0.04514991119503975f, 0.4740740656852722f, -0.9142857193946838f, 0.0f, 0.0f, 0.0f, -1.388359785079956f, 0.5530864000320435f, -0.16931216418743134f},
+    {0.0f, -0.033862434327602386f, -0.033862434327602386f, -0.20317460596561432f, -0.33862432837486267f, -0.20317460596561432f, 0.0f, -0.6095238327980042f, -0.7788359522819519f, -0.16931216418743134f, -0.33862432837486267f, -0.2370370328426361f, 0.0f, -0.7788359522819519f, -0.6095238327980042f, -0.2370370328426361f, -0.33862432837486267f, -0.16931216418743134f},
+    {0.0f, 0.10158730298280716f, 0.37248677015304565f, 0.4740740656852722f, 0.20317460596561432f, -0.33862432837486267f, 0.0f, 0.6095238327980042f, 2.4719576835632324f, 0.5079365372657776f, 0.6095238327980042f, -1.049735426902771f, 0.0f, 1.1174603700637817f, 1.8285714387893677f, 1.6592592000961304f, 1.0158730745315552f, 0.37248677015304565f},
+    {0.0f, 0.37248677015304565f, 0.10158730298280716f, -0.33862432837486267f, 0.20317460596561432f, 0.4740740656852722f, 0.0f, 1.8285714387893677f, 1.1174603700637817f, 0.37248677015304565f, 1.0158730745315552f, 1.6592592000961304f, 0.0f, 2.4719576835632324f, 0.6095238327980042f, -1.049735426902771f, 0.6095238327980042f, 0.5079365372657776f},
+    {0.0f, 0.0f, 0.0f, 0.31604939699172974f, 0.31604939699172974f, 0.40634921193122864f, 0.0f, 0.0f, 0.0f, 0.31604939699172974f, 0.6320987939834595f, 1.2190476655960083f, 0.0f, 0.0f, 0.0f, 3.566843032836914f, 3.250793695449829f, 2.0317461490631104f},
+    {0.0f, 0.04514991119503975f, -0.13544973731040955f, 0.0f, 0.0f, 0.2708994746208191f, 0.0f, -0.0902998223900795f, -0.40634921193122864f, -0.04514991119503975f, -0.0902998223900795f, 0.13544973731040955f, 0.0f, -0.49664902687072754f, -0.8126984238624573f, -0.49664902687072754f, -0.4514991044998169f, -0.13544973731040955f},
+    {0.0f, -0.04514991119503975f, -0.13544973731040955f, -0.0902998223900795f, -0.0902998223900795f, 0.2708994746208191f, 0.0f, 0.0f, -0.40634921193122864f, 0.04514991119503975f, 0.0f, 0.6772486567497253f, 0.0f, -0.49664902687072754f, -0.2708994746208191f, -0.49664902687072754f, 0.0902998223900795f, -0.13544973731040955f},
+    {0.0f, 0.22574955224990845f, 0.40634921193122864f, 0.4514991044998169f, 0.4514991044998169f, -0.2708994746208191f, 0.0f, 0.4514991044998169f, 1.2190476655960083f, 0.22574955224990845f, 0.4514991044998169f, -0.40634921193122864f, 0.0f, 2.573544979095459f, 3.521693229675293f, 2.573544979095459f, 2.3477954864501953f, 0.9481481313705444f},
+    {3.7925925254821777f, 5.9597883224487305f, 5.9597883224487305f, 7.043386459350586f, 7.043386459350586f, 7.043386459350586f, 3.7925925254821777f, 2.1671957969665527f, 3.250793695449829f, 1.0835978984832764f, 2.1671957969665527f, 3.250793695449829f, 3.7925925254821777f, 3.250793695449829f, 2.1671957969665527f, 3.250793695449829f, 2.1671957969665527f, 1.0835978984832764f},
+    {0.2708994746208191f, 1.8962962627410889f, 0.8126984238624573f, -1.0835978984832764f, 0.8126984238624573f, 0.8126984238624573f, -1.0835978984832764f, 1.8962962627410889f, 0.8126984238624573f, 0.2708994746208191f, 0.8126984238624573f, 0.8126984238624573f, -0.8126984238624573f, 1.0835978984832764f, 0.0f, -0.8126984238624573f, 0.0f, 0.0f},
+    {0.2708994746208191f, 0.8126984238624573f, 1.8962962627410889f, 0.8126984238624573f, 0.8126984238624573f, -1.0835978984832764f, -0.8126984238624573f, 0.0f, 1.0835978984832764f, 0.0f, 0.0f, -0.8126984238624573f, -1.0835978984832764f, 0.8126984238624573f, 1.8962962627410889f, 0.8126984238624573f, 0.8126984238624573f, 0.2708994746208191f},
+    {1.0835978984832764f, 2.1671957969665527f, 2.1671957969665527f, 3.7925925254821777f, 3.250793695449829f, 3.250793695449829f, 7.043386459350586f, 5.9597883224487305f, 7.043386459350586f, 3.7925925254821777f, 5.9597883224487305f, 7.043386459350586f, 3.250793695449829f, 3.250793695449829f, 2.1671957969665527f, 3.7925925254821777f, 2.1671957969665527f, 1.0835978984832764f},
+    {0.0f, 0.0f, 0.0f, -0.8126984238624573f, 1.0835978984832764f, -0.8126984238624573f, 0.8126984238624573f, 0.8126984238624573f, 0.8126984238624573f, 0.2708994746208191f, 1.8962962627410889f, -1.0835978984832764f, 0.8126984238624573f, 0.8126984238624573f, 0.8126984238624573f, -1.0835978984832764f, 1.8962962627410889f, 0.2708994746208191f},
+    {1.0835978984832764f, 2.1671957969665527f, 2.1671957969665527f, 3.250793695449829f, 3.250793695449829f, 3.7925925254821777f, 3.250793695449829f, 2.1671957969665527f, 3.250793695449829f, 1.0835978984832764f, 2.1671957969665527f, 3.7925925254821777f, 7.043386459350586f, 7.043386459350586f, 5.9597883224487305f, 7.043386459350586f, 5.9597883224487305f, 3.7925925254821777f}};
+#endif
 
 }  // namespace fe_gen

@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "
 FE_OK, FE_EINVAL, FE_EHANDLE, FE_ERANGE, FE_EARITY, FE_ENOMEM, FE_ECUDA, FE_ETIMEOUT, FE_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 FORM_MASS, FORM_LAPLACE, FORM_HELMHOLTZ, FORM_KAPPA_DIFFUSION, FORM_SOURCE = 1, 2, 3, 4, 5
-PREC_FP64, PREC_F32X2, PREC_FP32 = 0, 1, 2
+PREC_FP64, PREC_F32X2, PREC_FP32, PREC_TF32X3 = 0, 1, 2, 3
 STRATEGY_AUTO, STRATEGY_PUSH, STRATEGY_PULL = 0, 1, 2
 
 SYMBOLS = [

@@ -103,7 +103,8 @@ def test_p1_square_64_full(gpu):
 
 def test_p4_square_512_kappa_fp32_sampled(gpu):
     """P4 UnitSquareMesh 512x512 kappa-diffusion (kappa = exp(N(0,1)) per P1 node, seed 3): FP32
-    element tensors, FP64 accumulation -- relative Frobenius error <= 1e-5 over sampled rows; the
+    element tensors (CUDA cores, and three TF32 tensor-core products), FP64 accumulation -- relative
+    Frobenius error <= 1e-5 over sampled rows; the
     double-float variant of P2 and FP64 P4 stay at 1e-12."""
     from paper_1501_01809_gb300 import fe
     pr = PB.make(2, 4, 512, 0.0, kappa_seed=3)
@@ -114,6 +115,10 @@ def test_p4_square_512_kappa_fp32_sampled(gpu):
     srp, sci, vals, absv, _ = _oracle_rows(pr, rows, O.KAPPA_DIFFUSION, kappa=pr.kappa)
     got32 = g.assemble(fe.FORM_KAPPA_DIFFUSION, precision=fe.PREC_FP32)
     got = np.concatenate([got32[rp[r]:rp[r + 1]] for r in rows])
+    err = np.linalg.norm(got - vals) / np.linalg.norm(vals)
+    assert err <= 1e-5, err
+    gottc = g.assemble(fe.FORM_KAPPA_DIFFUSION, precision=fe.PREC_TF32X3)  # tensor cores
+    got = np.concatenate([gottc[rp[r]:rp[r + 1]] for r in rows])
     err = np.linalg.norm(got - vals) / np.linalg.norm(vals)
     assert err <= 1e-5, err
     got64 = g.assemble(fe.FORM_KAPPA_DIFFUSION, precision=fe.PREC_FP64)

@@ -289,3 +289,30 @@ def test_fp32_element_tensors_frobenius(gpu, dim, p, n, jit, form):
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err <= 1e-5, err
     assert np.max(np.abs(got - want) / np.maximum(scale, 1e-300)) <= 1e-5
+
+
+# ------------------------------------------------------------------ tensor cores (tcgen05, three TF32 products)
+@pytest.mark.parametrize("n,jit", [(17, 0.2), (9, 0.0), (1, 0.0)])
+def test_tensor_core_p4_kappa(gpu, n, jit):
+    """P4 kappa-diffusion element tensors as a [cells x 18] x [18 x 120] product on the tensor cores
+    (hi/lo TF32 splits, three products, FP32 accumulation in TMEM), FP64 CSR accumulation:
+    relative Frobenius <= 1e-5 and per entry <= 1e-5 of the contribution scale.  Cell counts
+    578, 162 and 2 leave full, partial and nearly empty 128-cell tiles."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(2, 4, n, jit, seed=3, kappa_seed=3)
+    g = PB.GpuProblem(pr)
+    rp, ci = g.csr()
+    got = g.assemble(fe.FORM_KAPPA_DIFFUSION, precision=fe.PREC_TF32X3)
+    want, scale = O.assemble_mat(2, 4, 4, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci, kappa=pr.kappa)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= 1e-5, err
+    assert np.max(np.abs(got - want) / np.maximum(scale, 1e-300)) <= 1e-5
+
+
+def test_tensor_core_refuses_other_elements(gpu):
+    from paper_1501_01809_gb300 import fe
+    ctx = fe.ctx_create(0)
+    for form, dim, p in [(fe.FORM_HELMHOLTZ, 2, 4), (fe.FORM_KAPPA_DIFFUSION, 2, 2), (fe.FORM_KAPPA_DIFFUSION, 3, 2)]:
+        with pytest.raises(fe.FeError) as ei:
+            fe.kernel_create(ctx, form, dim, p, precision=fe.PREC_TF32X3)
+        assert ei.value.code == fe.FE_EUNSUPPORTED
