@@ -270,36 +270,79 @@ def run_ours(args, wl, rank, world):
     launches = (14 + (4 if pull else 4)) * args.steps
 
     # ------------------------------------------------------------------- e2e through host buffers
+    # Every step copies its inputs (maps, coordinates, x) from pinned host memory and its outputs
+    # (rowptr, colidx, CSR values, y) back.  The copies of neighbouring steps overlap the compute on
+    # separate streams: two device slots of inputs and outputs, ordered by events.
     e2e = None
     if not args.no_e2e:
         pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t.cpu())
-        h_in = [(pin(t), t) for t in (t_map, t_cv, t_xy, t_x)]
-        h_out = [(torch.empty(t.shape, dtype=t.dtype, pin_memory=True), t) for t in (rowptr, colidx, vals, t_y)]
-        h2d = sum(h.numel() * h.element_size() for h, _ in h_in)
-        d2h = sum(h.numel() * h.element_size() for h, _ in h_out)
-        ksteps = max(3, min(args.steps, 20))
-
-        def e2e_step():
+        host_in = [pin(t) for t in (t_map, t_cv, t_xy, t_x)]
+        slots = []
+        for sidx in range(2):
+            d_in = [torch.empty_like(t) for t in (t_map, t_cv, t_xy, t_x)]
+            for d, h in zip(d_in, host_in):
+                d.copy_(h)
+            d_y = torch.zeros_like(t_x)
+            torch.cuda.synchronize()  # the slot's inputs are on the device before the library reads them
             with torch.cuda.stream(stream):
-                for h, d in h_in:
-                    d.copy_(h, non_blocking=True)
-                step()
-                for h, d in h_out:
-                    h.copy_(d, non_blocking=True)
+                Ms = fe.map_create(ctx, cells, nodes, d_in[0])
+                CMs = fe.map_create(ctx, cells, verts, d_in[1])
+                XYs = fe.dat_create(ctx, verts, d_in[2])
+                Xs, Ys = fe.dat_create(ctx, nodes, d_in[3]), fe.dat_create(ctx, nodes, d_y)
+                sps = fe.sparsity_build(ctx, Ms, Ms)
+                As = fe.mat_create(ctx, sps)
+            _, _, _, rps, cis = fe.sparsity_csr(sps)
+            outs = [rps, cis, fe.mat_values(As), d_y]
+            h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+            ev = {k: torch.cuda.Event() for k in ("in", "comp", "out")}
+            slots.append(dict(d_in=d_in, M=Ms, CM=CMs, XY=XYs, X=Xs, Y=Ys, sp=sps, A=As, outs=outs, h_out=h_out, ev=ev,
+                              used=False))
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        h2d = sum(h.numel() * h.element_size() for h in host_in)
+        d2h = sum(h.numel() * h.element_size() for h in slots[0]["h_out"])
 
-        e2e_step()
-        stream.synchronize()
+        def e2e_step(k):
+            sl = slots[k % 2]
+            ev = sl["ev"]
+            if sl["used"]:
+                s_in.wait_event(ev["comp"])      # the slot's previous compute has read its inputs
+            with torch.cuda.stream(s_in):
+                for d, h in zip(sl["d_in"], host_in):
+                    d.copy_(h, non_blocking=True)
+                ev["in"].record(s_in)
+            stream.wait_event(ev["in"])
+            if sl["used"]:
+                stream.wait_event(ev["out"])     # the slot's previous outputs have been read back
+            with torch.cuda.stream(stream):
+                fe.sparsity_rebuild(sl["sp"])
+                if not pull:
+                    fe.mat_zero(sl["A"])
+                fe.assemble_mat(ctx, K, cells, sl["A"], sl["XY"], sl["CM"], zero_first=pull)
+                fe.action(ctx, K, cells, sl["X"], sl["Y"], sl["M"], sl["XY"], sl["CM"], zero_first=True, sp=sl["sp"])
+                ev["comp"].record(stream)
+            s_out.wait_event(ev["comp"])
+            with torch.cuda.stream(s_out):
+                for h, d in zip(sl["h_out"], sl["outs"]):
+                    h.copy_(d, non_blocking=True)
+                ev["out"].record(s_out)
+            sl["used"] = True
+
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        ksteps = max(3, min(args.steps, 20))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(ksteps):
-            e2e_step()
-        b.record(stream)
+        a.record(s_in)
+        for k in range(ksteps):
+            e2e_step(k)
+        b.record(s_out)
         b.synchronize()
         e2e_ms = a.elapsed_time(b) / ksteps
         if dist:
             e2e_ms = max_over_ranks(e2e_ms, dev)
         e2e = {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "pipelining": "copies of neighbouring steps overlap the compute (two device slots, three streams)"}
         fe.sync(ctx)
 
     # ------------------------------------------------------------------- roofline of the dominant kernel
