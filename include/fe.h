@@ -323,7 +323,8 @@ fe_status fe_cg_destroy(fe_cg *cg);
  * x_out and all its device memory is freed at once.  A request whose footprint alone exceeds the
  * budget is refused.  max_active = 1 gives the plain one-request-at-a-time path with the same
  * kernels.  Host arrays of a request must stay valid until fe_server_run returns.  Device memory
- * is drawn from the context's allocator and counted exactly (fe_server_stats). */
+ * comes from the server's own stream-ordered CUDA memory pool on the context's device (kept up to
+ * hbm_budget bytes between requests) and is counted exactly (fe_server_stats). */
 #define FE_SOLVE_PENDING 0
 #define FE_SOLVE_CONVERGED 1
 #define FE_SOLVE_MAXIT 2

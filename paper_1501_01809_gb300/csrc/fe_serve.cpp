@@ -16,8 +16,9 @@
 //      (a captured graph), then a status poll; converged systems copy their solution to the host
 //      and free everything they held;
 //   3. otherwise sleep until the next arrival.
-// Memory is accounted exactly: the server routes its allocations through a counting allocator
-// that forwards to the context's own allocator.
+// Memory is accounted exactly: the server routes its allocations through a counting allocator that
+// draws from its own stream-ordered CUDA memory pool (requests come and go too often for a
+// synchronous allocator).
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -59,6 +60,7 @@ thread_local char g_vmsg[512];
 struct Server {
   fe_ctx *parent;
   fe_ctx *ctx;  // same device and stream as the parent, counting allocator
+  cudaMemPool_t pool = nullptr;  // the server's own stream-ordered pool (requests come and go often)
   fe_server_config cfg;
   fe_kernel *klap[3] = {nullptr, nullptr, nullptr}, *ksrc[3] = {nullptr, nullptr, nullptr};
   fe_cg *cg = nullptr;
@@ -85,11 +87,8 @@ constexpr uint32_t kMagicServer = 0xFE05E2E5u;
 
 void *count_alloc(size_t bytes, void *user) {
   Server *s = static_cast<Server *>(user);
-  fe_ctx *p = s->parent;
   void *ptr = nullptr;
-  if (p->alloc) {
-    ptr = p->alloc(bytes, p->user);
-  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(&ptr, bytes, s->pool, s->ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     ptr = nullptr;
   }
@@ -113,9 +112,7 @@ void count_free(void *ptr, void *user) {
     else s->base_bytes -= b;
     s->live.erase(it);
   }
-  fe_ctx *p = s->parent;
-  if (p->free_fn) p->free_fn(ptr, p->user);
-  else cudaFree(ptr);
+  cudaFreeAsync(ptr, s->ctx->stream);
 }
 
 double now_s(std::chrono::steady_clock::time_point t0) {
@@ -235,7 +232,11 @@ void server_free(Server *s) {
     if (s->klap[p]) fe_kernel_destroy(s->klap[p]);
     if (s->ksrc[p]) fe_kernel_destroy(s->ksrc[p]);
   }
-  if (s->ctx) fe_ctx_destroy(s->ctx);
+  if (s->ctx) {
+    cudaStreamSynchronize(s->ctx->stream);
+    fe_ctx_destroy(s->ctx);
+  }
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
 }
 }  // namespace
@@ -253,6 +254,22 @@ fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server *
   if (!s) return FE_ENOMEM;
   s->parent = parent;
   s->cfg = *cfg;
+  // a private pool on the device: allocations are stream-ordered and cached across requests (the
+  // budget is enforced by the server's own accounting, not by the pool)
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = parent->device;
+  if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_vmsg, sizeof g_vmsg, "fe_server_create: cannot create a memory pool");
+    delete s;
+    return FE_ECUDA;
+  }
+  uint64_t keep = cfg->hbm_budget;
+  cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   fe_status st = fe_ctx_create(parent->device, parent->stream, &s->ctx);
   if (st == FE_OK) st = fe_ctx_set_allocator(s->ctx, count_alloc, count_free, s);
   for (int p = 1; p <= 2 && st == FE_OK; p++) {
