@@ -188,40 +188,35 @@ __device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &
 }
 
 
-// Bitonic sort of 64 (key, payload) pairs across a warp, ascending by key: lane l holds elements
-// 2l (k0, p0) and 2l + 1 (k1, p1).  Equal keys keep their own payloads (both partners keep theirs
-// on a tie), so no payload is lost or duplicated.
-__device__ __forceinline__ void warp_bitonic64(uint32_t &k0, int32_t &p0, uint32_t &k1, int32_t &p1) {
+// Bitonic sort of 32 E packed 32-bit values across a warp, ascending: lane l holds elements
+// E l .. E l + E - 1 in v[0..E).  Stages with j < E are within a lane, the others exchange with
+// lane l ^ (j / E) (same h).
+template <int E>
+__device__ __forceinline__ void warp_bitonic_packed(uint32_t (&v)[E]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 2; k <= 64; k <<= 1) {
-    const bool up = ((2 * lane) & k) == 0;
+  for (int k = 2; k <= 32 * E; k <<= 1) {
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j == 1) {
-        const bool sw = up ? (k0 > k1) : (k0 < k1);
-        if (sw) {
-          const uint32_t tk = k0;
-          k0 = k1;
-          k1 = tk;
-          const int32_t tp = p0;
-          p0 = p1;
-          p1 = tp;
+      if (j < E) {
+#pragma unroll
+        for (int h = 0; h < E; h++) {
+          if ((h & j) == 0) {
+            const bool up = (((E * lane) + h) & k) == 0;
+            const uint32_t a = v[h], b = v[h | j];
+            const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+            v[h] = up ? lo : hi;
+            v[h | j] = up ? hi : lo;
+          }
         }
       } else {
-        const int m = j >> 1;
-        const uint32_t o0 = __shfl_xor_sync(0xffffffffu, k0, m), o1 = __shfl_xor_sync(0xffffffffu, k1, m);
-        const int32_t r0 = __shfl_xor_sync(0xffffffffu, p0, m), r1 = __shfl_xor_sync(0xffffffffu, p1, m);
+        const int m = j / E;
+        const bool up = ((E * lane) & k) == 0;
         const bool take_min = ((lane & m) == 0) == up;
-        const bool t0 = take_min ? (o0 < k0) : (o0 > k0);
-        const bool t1 = take_min ? (o1 < k1) : (o1 > k1);
-        if (t0) {
-          k0 = o0;
-          p0 = r0;
-        }
-        if (t1) {
-          k1 = o1;
-          p1 = r1;
+#pragma unroll
+        for (int h = 0; h < E; h++) {
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, v[h], m);
+          v[h] = take_min ? (o < v[h] ? o : v[h]) : (o > v[h] ? o : v[h]);
         }
       }
     }
@@ -240,6 +235,8 @@ struct RowsParams {
   int cap, acap;      // candidate capacity per row (power of two), incidence capacity (multiple of 4)
   uint64_t mdiv_ndr;  // floor(2^64 / ndr) + 1: exact k / ndr = __umul64hi(k, mdiv_ndr) for k < 2^32
   uint32_t mdiv_ndc;  // floor(2^32 / ndc) + 1: exact t / ndc = __umulhi(t, mdiv_ndc) for t < 2^26
+  int packed_ok;      // ncols < 2^24 - 1: (column << 8 | candidate) fits 32 bits below the padding value
+  int sort_only;      // every row takes the sort path: shared memory holds only the incidence lists
   int *err;
 };
 
@@ -248,6 +245,68 @@ __device__ __forceinline__ uint32_t div_ndr(uint32_t k, const RowsParams &p) {
 }
 __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
   return p.ndc == 1 ? t : __umulhi(t, p.mdiv_ndc);
+}
+
+
+// One row by sorting packed (column << SH | candidate) values, E per lane (32 E >= ncand, na <= 32):
+// canonical incidence order, candidates, sort, first element of each run of equal columns, ranks
+// by a warp prefix count, unique columns (ascending) to coltmp and every candidate's rank to the
+// lookup table.  Returns the number of unique columns (valid in every lane).
+template <int E, int SH>
+__device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t a0, int na, int ncand, uint32_t *adjs) {
+  const int lane = threadIdx.x & 31;
+  const int ndc = p.ndc;
+  const uint32_t tmask = (1u << SH) - 1u;
+  // 1. canonical incidence order by rank
+  const uint32_t v = lane < na ? (uint32_t)p.adj[a0 + lane] : 0xFFFFFFFFu;
+  int rk = 0;
+  for (int q = 0; q < na; q++) rk += __shfl_sync(0xffffffffu, v, q) < v;
+  if (lane < na) {
+    adjs[rk] = v;
+    p.adj[a0 + rk] = (int32_t)v;
+  }
+  __syncwarp();
+  // 2. candidates t = E lane + h, packed (column << SH | t); padding sorts last
+  uint32_t key[E];
+#pragma unroll
+  for (int h = 0; h < E; h++) {
+    const uint32_t t = (uint32_t)(E * lane + h);
+    key[h] = 0xFFFFFFFFu;
+    if ((int)t < ncand) {
+      const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+      key[h] = ((uint32_t)p.cmap[(int64_t)div_ndr(adjs[a], p) * ndc + j] << SH) | t;
+    }
+  }
+  warp_bitonic_packed<E>(key);
+  // 3. first element of each run of equal columns, ranks by a warp prefix count
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, key[E - 1], 1);
+  int f[E], c = 0;
+#pragma unroll
+  for (int h = 0; h < E; h++) {
+    const uint32_t before = h == 0 ? prev : key[h - 1];
+    f[h] = key[h] != 0xFFFFFFFFu && ((h == 0 && lane == 0) || (key[h] >> SH) != (before >> SH));
+    c += f[h];
+  }
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  const int nu = __shfl_sync(0xffffffffu, incl, 31);
+  int32_t *outc = p.coltmp + a0 * ndc;
+  int rank = incl - c - 1;  // rank of the run before this lane's first element
+#pragma unroll
+  for (int h = 0; h < E; h++) {
+    rank += f[h];
+    if (key[h] == 0xFFFFFFFFu) continue;
+    if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
+    if (rank < kMaxRowLen) {
+      const uint32_t t = key[h] & tmask, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+      p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank;
+    }
+  }
+  return nu;
 }
 
 // One warp per row r of the pattern (rows = target set of the row map):
@@ -261,16 +320,17 @@ __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
 //  4. lut[(e*ndr + i)*ndc + j] = rank of the candidate's slot; rowlen[r] = number of unique columns.
 // Shared memory per warp (32-bit words): hkey[cap], hrank[cap], ucol[cap], uslot[cap], cslot[cap],
 // adju[acap], adjs[acap].
-__global__ void k_rows_build(const RowsParams p) {
+__global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
   extern __shared__ __align__(16) int32_t smem_i[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int cap = p.cap;
-  int32_t *hkey = smem_i + (size_t)wid * (5 * cap + 2 * p.acap);
+  // per warp: hash tables (5 cap words) unless every row is sorted, then the incidence lists
+  int32_t *hkey = smem_i + (size_t)wid * ((p.sort_only ? 0 : 5 * cap) + 2 * p.acap);
   int32_t *hrank = hkey + cap;
   uint32_t *ucol = reinterpret_cast<uint32_t *>(hrank + cap);
   int32_t *uslot = reinterpret_cast<int32_t *>(ucol + cap);
   int32_t *cslot = uslot + cap;
-  uint32_t *adju = reinterpret_cast<uint32_t *>(cslot + cap);
+  uint32_t *adju = p.sort_only ? reinterpret_cast<uint32_t *>(hkey) : reinterpret_cast<uint32_t *>(cslot + cap);
   uint32_t *adjs = adju + p.acap;
   const int ndc = p.ndc;
   for (int64_t r = (int64_t)blockIdx.x * wpb + wid; r < p.nrows; r += (int64_t)gridDim.x * wpb) {
@@ -288,59 +348,12 @@ __global__ void k_rows_build(const RowsParams p) {
       if (lane == 0) p.rowlen[r] = 0;
       continue;
     }
-    if (ncand <= 64 && na <= 32) {
-      // Small rows (most rows of P2/P3 meshes): sort the candidates instead of hashing them.
-      // 1. canonical incidence order by rank
-      const uint32_t v = lane < na ? (uint32_t)p.adj[a0 + lane] : 0xFFFFFFFFu;
-      int rk = 0;
-      for (int q = 0; q < na; q++) rk += __shfl_sync(0xffffffffu, v, q) < v;
-      if (lane < na) {
-        adjs[rk] = v;
-        p.adj[a0 + rk] = (int32_t)v;
-      }
-      __syncwarp();
-      // 2. candidates t = 2 lane + h: (column, t); padding sorts last
-      uint32_t k0 = 0xFFFFFFFFu, k1 = 0xFFFFFFFFu;
-      int32_t q0 = -1, q1 = -1;
-      if (2 * lane < ncand) {
-        const uint32_t t = 2 * lane, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
-        k0 = (uint32_t)p.cmap[(int64_t)div_ndr(adjs[a], p) * ndc + j];
-        q0 = (int32_t)t;
-      }
-      if (2 * lane + 1 < ncand) {
-        const uint32_t t = 2 * lane + 1, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
-        k1 = (uint32_t)p.cmap[(int64_t)div_ndr(adjs[a], p) * ndc + j];
-        q1 = (int32_t)t;
-      }
-      warp_bitonic64(k0, q0, k1, q1);
-      // 3. first element of each run of equal columns; ranks by a warp prefix count
-      const uint32_t prev = __shfl_up_sync(0xffffffffu, k1, 1);
-      const int f0 = q0 >= 0 && (lane == 0 || k0 != prev);
-      const int f1 = q1 >= 0 && k1 != k0;
-      const int c = f0 + f1;
-      int incl = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += n;
-      }
-      const int nu_small = __shfl_sync(0xffffffffu, incl, 31);
-      const int rank0 = incl - c + f0 - 1, rank1 = incl - 1;
-      int32_t *outc = p.coltmp + a0 * ndc;
-      if (f0) outc[rank0] = (int32_t)k0;
-      if (f1) outc[rank1] = (int32_t)k1;
-      // 4. lookup table: every candidate gets the rank of its column
-      if (q0 >= 0 && rank0 < kMaxRowLen) {
-        const uint32_t a = div_ndc((uint32_t)q0, p), j = (uint32_t)q0 - a * (uint32_t)ndc;
-        p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank0;
-      }
-      if (q1 >= 0 && rank1 < kMaxRowLen) {
-        const uint32_t a = div_ndc((uint32_t)q1, p), j = (uint32_t)q1 - a * (uint32_t)ndc;
-        p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank1;
-      }
+    if (p.packed_ok && na <= 32 && ncand <= 256) {
+      // rows of up to 256 candidates (all rows of P1-P3 meshes): sort packed values
+      const int nu = ncand <= 64 ? row_by_sort<2, 6>(p, a0, na, ncand, adjs) : row_by_sort<8, 8>(p, a0, na, ncand, adjs);
       if (lane == 0) {
-        p.rowlen[r] = nu_small;
-        if (nu_small > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
+        p.rowlen[r] = nu;
+        if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
       }
       __syncwarp();
       continue;
@@ -506,8 +519,11 @@ cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err) {
   p.acap = sp->acap;
   p.mdiv_ndr = sp->ndr > 1 ? (~0ull / (uint64_t)sp->ndr) + 1 : 0;
   p.mdiv_ndc = sp->ndc > 1 ? (uint32_t)((0xFFFFFFFFull / (uint64_t)sp->ndc) + 1) : 0;
+  p.packed_ok = sp->ncols < (int64_t)(1 << 24) - 1;
   p.err = err;
-  const size_t per_warp = (size_t)(5 * sp->cap + 2 * sp->acap) * sizeof(int32_t);
+  // rows of at most 256 candidates and 32 incidences are sorted (no hash tables needed)
+  p.sort_only = p.packed_ok && sp->cap <= 256 && sp->acap <= 32;
+  const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
   const size_t smem = warps * per_warp;
