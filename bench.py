@@ -66,9 +66,9 @@ WORKLOADS = {
 TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 250.05 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
     ("assemble", "push", "f32x2"): (1.024e9, "768d9df1bf84"),
-    # one sparsity rebuild (k_inc_count, k_inc_fill, k_rows_build, k_rows_compact, scans, zeros):
-    # 431.4 MB at 40^3, scaled x4.096 to 64^3 (at 40^3 part of the output stays in L2: a lower bound)
-    ("sparsity", None, None): (1.767e9, "8cad725b839f"),
+    # one sparsity rebuild (zeros, k_inc_count, scans, k_inc_fill, the in-place k_rows_build pass and the
+    # gated launches that return at once): 206.4 MB at 40^3, scaled x4.096 to 64^3
+    ("sparsity", None, None): (0.8456e9, "d5a04742d59a"),
 }
 
 
@@ -264,10 +264,11 @@ def run_ours(args, wl, rank, world):
     if dist:
         ms_step = max_over_ranks(ms_step, dev)
     phase_ms = phases / args.steps
-    # launches of libfe kernels per step: sparsity rebuild 14 (zero, count, zero, max, scan x3, zero, fill,
-    # row sort, scan x3, compact); push: mat zero 1, assembly 1, action zero + action 2; pull: assembly 2
+    # launches of libfe kernels per step: sparsity rebuild 13 (zero, count, scan x3, zero, fill, in-place
+    # row pass, then the gated full row pass, scan x3 and compact, which return at once when no row
+    # changed length); push: mat zero 1, assembly 1, action zero + action 2; pull: assembly 2
     # (element, row), action 2 (element, row)
-    launches = (14 + (4 if pull else 4)) * args.steps
+    launches = (13 + 4) * args.steps
 
     # ------------------------------------------------------------------- e2e through host buffers
     # Every step copies its inputs (maps, coordinates, x) from pinned host memory and its outputs

@@ -257,6 +257,7 @@ static void sparsity_free(fe_sparsity *sp) {
   dev_free(c, sp->coltmp);
   dev_free(c, sp->scan_tmp);
   dev_free(c, sp->d_maxcnt);
+  dev_free(c, sp->d_changed);
   dev_free(c, sp->vstage);
 }
 
@@ -292,7 +293,9 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
   sp->lut = (uint8_t *)dev_alloc(c, (size_t)ninc * sp->ndc);
   sp->scan_tmp = (int64_t *)dev_alloc(c, sizeof(int64_t) * sp->scan_tmp_elems);
   sp->d_maxcnt = (int *)dev_alloc(c, sizeof(int));
-  if (!sp->rowptr || !sp->adjptr || !sp->adj || !sp->rowcnt || !sp->coltmp || !sp->lut || !sp->scan_tmp || !sp->d_maxcnt) {
+  sp->d_changed = (int *)dev_alloc(c, sizeof(int));
+  if (!sp->rowptr || !sp->adjptr || !sp->adj || !sp->rowcnt || !sp->coltmp || !sp->lut || !sp->scan_tmp || !sp->d_maxcnt ||
+      !sp->d_changed) {
     sparsity_free(sp);
     delete sp;
     return fail(FE_ENOMEM, "fe_sparsity_build: device allocation failed");
@@ -383,9 +386,13 @@ fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
   fe_ctx *c = sp->ctx;
   DeviceGuard g(c->device);
   if (!sp->coltmp) return fail(FE_EINVAL, "fe_sparsity_rebuild: the pattern's build scratch was released");
-  FE_CHECK_CUDA(fe::sparsity_incidence(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
-  FE_CHECK_CUDA(fe::sparsity_rows(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
-  FE_CHECK_CUDA(fe::sparsity_compact(sp, c->stream, c->d_err, 1), "fe_sparsity_rebuild");
+  // In-place pass first: rows that keep their lengths go straight to colidx.  Only when a row's
+  // length changed do the full row pass, its scan and the compaction run (gated on the device).
+  FE_CHECK_CUDA(cudaMemsetAsync(sp->d_changed, 0, sizeof(int), c->stream), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_incidence(sp, c->stream, c->d_err, 0), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_rows_inplace(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_rows(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_compact(sp, c->stream, c->d_err, 1, sp->d_changed), "fe_sparsity_rebuild");
   return ok();
 }
 

@@ -73,6 +73,7 @@ struct fe_sparsity {
   int64_t *scan_tmp; // scan block sums
   int64_t scan_tmp_elems;
   int *d_maxcnt;     // [1] max incidence count
+  int *d_changed;    // [1] rebuild: some row changed its length (the in-place pass is not enough)
   int maxrow;        // longest row (entries), known after build
   void *vstage;      // staging of element vectors for pull action / linear form (lazily allocated)
   size_t vstage_bytes;
@@ -100,18 +101,27 @@ namespace fe {
 // ---- scan ----
 int64_t scan_tmp_elems(int64_t n);
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.  tmp: scan_tmp_elems(n) int64.
+// gate: NULL, or a device flag; when it holds 0 the launches return without work.
 cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp,
-                                      cudaStream_t s);
+                                      cudaStream_t s, const int *gate = nullptr);
 
 // ---- maps / sparsity ----
 cudaError_t launch_map_validate(const int32_t *v, int64_t n, int64_t limit, int *err, cudaStream_t s);
-// incidence: counts -> adjptr (scan) -> adj fill; also the max count
-cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err);
-// sort rows, write lut, unique columns (coltmp), row lengths -> rowptr (scan) -> compact colidx.
-// capacity_check: flags ERR_NNZ_CHANGED if rowptr[nrows] != sp->nnz (rebuild); when nnz_known == 0
-// the colidx compaction is skipped (build: host learns nnz first, then calls sparsity_compact).
-cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err);
-cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz);
+// incidence: counts -> adjptr (scan) -> adj fill; with_max: also the longest incidence list
+// (d_maxcnt, needed to size the row kernel at build time only)
+cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int with_max = 1);
+// sort rows, write lut, unique columns (coltmp at incidence-based offsets), row lengths -> rowptr
+// (scan).  gate as for the scan.
+cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err, const int *gate = nullptr);
+// rebuild fast pass: as sparsity_rows, but every row whose length equals its length in rowptr
+// writes its columns straight to colidx; rowptr is not rewritten.  *changed = 1 when a row's
+// length differs or rowptr[nrows] != nnz (then sparsity_rows, its scan and the compaction must
+// run, gated on changed).
+cudaError_t sparsity_rows_inplace(fe_sparsity *sp, cudaStream_t s, int *err, int *changed);
+// colidx[rowptr[r] + k] = coltmp[adjptr[r] ndc + k]; check_nnz: flags ERR_NNZ_CHANGED if
+// rowptr[nrows] != nnz.  gate as for the scan.
+cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz,
+                             const int *gate = nullptr);
 cudaError_t launch_max_i32(const int32_t *v, int64_t n, int *out, cudaStream_t s);
 
 // ---- fills ----

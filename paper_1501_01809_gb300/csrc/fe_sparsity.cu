@@ -53,7 +53,8 @@ __device__ __forceinline__ int64_t block_scan_incl(int64_t v, int64_t *total) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__restrict__ in, int64_t n,
-                                                               int64_t *__restrict__ bsum) {
+                                                               int64_t *__restrict__ bsum, const int *gate) {
+  if (gate && *gate == 0) return;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int64_t s = 0;
 #pragma unroll
@@ -65,7 +66,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__r
 }
 
 // single block: exclusive scan of the block sums in place (any count, chunked)
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t *bsum, int64_t nb) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t *bsum, int64_t nb, const int *gate) {
+  if (gate && *gate == 0) return;
   int64_t carry = 0;
   for (int64_t c = 0; c < nb; c += kScanThreads) {
     int64_t i = c + threadIdx.x;
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t *bsum, int64
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int32_t *__restrict__ in, int64_t n,
                                                               const int64_t *__restrict__ bsum,
-                                                              int64_t *__restrict__ out) {
+                                                              int64_t *__restrict__ out, const int *gate) {
+  if (gate && *gate == 0) return;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int32_t v[kScanItems];
   int64_t s = 0;
@@ -238,7 +241,25 @@ struct RowsParams {
   int packed_ok;      // ncols < 2^24 - 1: (column << 8 | candidate) fits 32 bits below the padding value
   int sort_only;      // every row takes the sort path: shared memory holds only the incidence lists
   int *err;
+  // in-place rebuild pass (colidx != NULL): a row whose length equals rowptr[r+1] - rowptr[r]
+  // writes its columns to colidx + rowptr[r]; any other row sets *changed
+  int32_t *colidx;
+  const int64_t *rowptr;
+  int64_t nnz;
+  int *changed;
+  const int *gate;  // NULL, or a device flag: 0 = return without work
 };
+
+// Where row r's nu unique columns go: colidx in place when the in-place pass applies and the
+// row's length is unchanged (and inside the nnz entries), else coltmp at the incidence offset.
+__device__ __forceinline__ int32_t *row_out(const RowsParams &p, int64_t r, int64_t a0, int nu) {
+  if (p.colidx) {
+    const int64_t b = p.rowptr[r];
+    if (p.rowptr[r + 1] - b == nu && b >= 0 && b + nu <= p.nnz) return p.colidx + b;
+    if ((threadIdx.x & 31) == 0) *p.changed = 1;
+  }
+  return p.coltmp + a0 * p.ndc;
+}
 
 __device__ __forceinline__ uint32_t div_ndr(uint32_t k, const RowsParams &p) {
   return p.ndr == 1 ? k : (uint32_t)__umul64hi((uint64_t)k, p.mdiv_ndr);
@@ -253,7 +274,8 @@ __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
 // by a warp prefix count, unique columns (ascending) to coltmp and every candidate's rank to the
 // lookup table.  Returns the number of unique columns (valid in every lane).
 template <int E, int SH>
-__device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t a0, int na, int ncand, uint32_t *adjs) {
+__device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
+                                           uint32_t *adjs) {
   const int lane = threadIdx.x & 31;
   const int ndc = p.ndc;
   const uint32_t tmask = (1u << SH) - 1u;
@@ -294,7 +316,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t a0, int 
     if (lane >= o) incl += n;
   }
   const int nu = __shfl_sync(0xffffffffu, incl, 31);
-  int32_t *outc = p.coltmp + a0 * ndc;
+  int32_t *outc = row_out(p, r, a0, nu);
   int rank = incl - c - 1;  // rank of the run before this lane's first element
 #pragma unroll
   for (int h = 0; h < E; h++) {
@@ -322,8 +344,10 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t a0, int 
 // adju[acap], adjs[acap].
 __global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
   extern __shared__ __align__(16) int32_t smem_i[];
+  if (p.gate && *p.gate == 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int cap = p.cap;
+  if (p.colidx && blockIdx.x == 0 && threadIdx.x == 0 && p.rowptr[p.nrows] != p.nnz) *p.changed = 1;
   // per warp: hash tables (5 cap words) unless every row is sorted, then the incidence lists
   int32_t *hkey = smem_i + (size_t)wid * ((p.sort_only ? 0 : 5 * cap) + 2 * p.acap);
   int32_t *hrank = hkey + cap;
@@ -350,7 +374,8 @@ __global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
     }
     if (p.packed_ok && na <= 32 && ncand <= 256) {
       // rows of up to 256 candidates (all rows of P1-P3 meshes): sort packed values
-      const int nu = ncand <= 64 ? row_by_sort<2, 6>(p, a0, na, ncand, adjs) : row_by_sort<8, 8>(p, a0, na, ncand, adjs);
+      const int nu = ncand <= 64 ? row_by_sort<2, 6>(p, r, a0, na, ncand, adjs)
+                                : row_by_sort<8, 8>(p, r, a0, na, ncand, adjs);
       if (lane == 0) {
         p.rowlen[r] = nu;
         if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
@@ -396,7 +421,7 @@ __global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
       nu += __popc(m);
     }
     __syncwarp();
-    int32_t *outc = p.coltmp + a0 * ndc;
+    int32_t *outc = row_out(p, r, a0, nu);
     warp_rank_distinct(ucol, nu, [&](int q, int rk) {
       hrank[uslot[q]] = rk;
       outc[rk] = (int32_t)ucol[q];
@@ -421,7 +446,9 @@ __global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
 // against a pattern that grew beyond the allocated nnz (rebuild with different maps).
 __global__ void k_rows_compact(int64_t nrows, int ndc, const int64_t *__restrict__ adjptr,
                                const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coltmp,
-                               int32_t *__restrict__ colidx, int64_t nnz_cap, int check_nnz, int *err) {
+                               int32_t *__restrict__ colidx, int64_t nnz_cap, int check_nnz, int *err,
+                               const int *gate) {
+  if (gate && *gate == 0) return;
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   if (check_nnz && blockIdx.x == 0 && threadIdx.x == 0 && rowptr[nrows] != nnz_cap) flag(err, ERR_NNZ_CHANGED, nrows);
   for (int64_t r0 = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; r0 < nrows;
@@ -454,15 +481,16 @@ int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
 
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
+cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s,
+                                      const int *gate) {
   int64_t nb = (n + kScanTile - 1) / kScanTile;
-  if (nb == 0) {  // n == 0: out[0] = 0
-    k_zero_i64<<<1, 32, 0, s>>>(out, 1);
+  if (nb == 0) {  // n == 0: out[0] = 0 (already so when gated: an empty scan never changes)
+    if (!gate) k_zero_i64<<<1, 32, 0, s>>>(out, 1);
     return cudaGetLastError();
   }
-  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nb);
-  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, out);
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, gate);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nb, gate);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, out, gate);
   return cudaGetLastError();
 }
 
@@ -490,12 +518,15 @@ cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err) {
+cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int with_max) {
   const int64_t n = sp->ncell * sp->ndr;
   k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows);
   if (n > 0) k_inc_count<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->rowcnt, err);
-  k_zero_i32<<<1, 32, 0, s>>>(sp->d_maxcnt, 1);
-  if (sp->nrows > 0) k_max_count<<<grid_for(sp->nrows, 256, 152 * 4), 256, 0, s>>>(sp->rowcnt, sp->nrows, sp->d_maxcnt);
+  if (with_max) {
+    k_zero_i32<<<1, 32, 0, s>>>(sp->d_maxcnt, 1);
+    if (sp->nrows > 0)
+      k_max_count<<<grid_for(sp->nrows, 256, 152 * 4), 256, 0, s>>>(sp->rowcnt, sp->nrows, sp->d_maxcnt);
+  }
   cudaError_t e = exclusive_scan_i32_to_i64(sp->rowcnt, sp->adjptr, sp->nrows, sp->scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows);
@@ -504,7 +535,8 @@ cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err) {
   return cudaGetLastError();
 }
 
-cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err) {
+namespace {
+cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed, const int *gate) {
   RowsParams p;
   p.nrows = sp->nrows;
   p.ndr = sp->ndr;
@@ -523,6 +555,11 @@ cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err) {
   p.err = err;
   // rows of at most 256 candidates and 32 incidences are sorted (no hash tables needed)
   p.sort_only = p.packed_ok && sp->cap <= 256 && sp->acap <= 32;
+  p.colidx = changed ? sp->colidx : nullptr;
+  p.rowptr = sp->rowptr;
+  p.nnz = sp->nnz;
+  p.changed = changed;
+  p.gate = gate;
   const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
@@ -532,14 +569,25 @@ cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err) {
     if (e != cudaSuccess) return e;
   }
   if (sp->nrows > 0) k_rows_build<<<grid_for(sp->nrows, warps, 152 * 32), warps * 32, smem, s>>>(p);
-  return exclusive_scan_i32_to_i64(sp->rowcnt, sp->rowptr, sp->nrows, sp->scan_tmp, s);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err, const int *gate) {
+  cudaError_t e = launch_rows(sp, s, err, nullptr, gate);
+  if (e != cudaSuccess) return e;
+  return exclusive_scan_i32_to_i64(sp->rowcnt, sp->rowptr, sp->nrows, sp->scan_tmp, s, gate);
 }
 
-cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz) {
+cudaError_t sparsity_rows_inplace(fe_sparsity *sp, cudaStream_t s, int *err, int *changed) {
+  return launch_rows(sp, s, err, changed, nullptr);
+}
+
+cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz, const int *gate) {
   const int warps = 8;
   if (sp->nrows > 0)
     k_rows_compact<<<grid_for((sp->nrows + 31) / 32, warps, 152 * 16), warps * 32, 0, s>>>(
-        sp->nrows, sp->ndc, sp->adjptr, sp->rowptr, sp->coltmp, sp->colidx, sp->nnz, check_nnz, err);
+        sp->nrows, sp->ndc, sp->adjptr, sp->rowptr, sp->coltmp, sp->colidx, sp->nnz, check_nnz, err, gate);
   return cudaGetLastError();
 }
 

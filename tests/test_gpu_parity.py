@@ -104,6 +104,89 @@ def test_rebuild_is_bitwise_stable(gpu):
         np.testing.assert_array_equal(lut0, g.fe.sparsity_lut(g.sparsity(), pr.mesh.ncell, 10, 10).cpu().numpy())
 
 
+def _check_pattern(g, cmap, nnodes):
+    """CSR bitwise equal to the oracle's for cmap, and every lookup-table entry points at its column."""
+    rp, ci = g.csr()
+    orp, oci = O.sparsity(cmap, cmap, nnodes, nnodes)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(ci, oci)
+    nd = cmap.shape[1]
+    lut = g.fe.sparsity_lut(g.sparsity(), cmap.shape[0], nd, nd).cpu().numpy().reshape(-1, nd, nd).astype(np.int64)
+    pos = orp[cmap][:, :, None] + lut
+    np.testing.assert_array_equal(oci[pos], np.broadcast_to(cmap[:, None, :], pos.shape))
+
+
+def _rewrite_map(g, cmap):
+    g.t_map.copy_(g.torch.from_numpy(np.ascontiguousarray(cmap)))
+
+
+def test_rebuild_same_row_lengths_in_place(gpu):
+    """Local node order permuted within each cell: the pattern is unchanged (rows keep their
+    lengths, the in-place pass writes colidx directly) while the lookup table changes."""
+    pr = PB.make(3, 2, 5, 0.2, seed=0)
+    g = PB.GpuProblem(pr)
+    g.sparsity()
+    rng = np.random.default_rng(11)
+    perm = np.argsort(rng.random(pr.cmap.shape), axis=1)
+    m2 = np.take_along_axis(pr.cmap, perm, axis=1)
+    _rewrite_map(g, m2)
+    g.fe.sparsity_rebuild(g.sparsity())
+    g.fe.sync(g.ctx)
+    _check_pattern(g, m2, pr.nnodes)
+
+
+def test_rebuild_changed_row_lengths(gpu):
+    """Nodes relabelled: the same nnz, but rows change length, so the full row pass, the scan and
+    the compaction must run after the in-place pass."""
+    pr = PB.make(3, 2, 5, 0.2, seed=0)
+    g = PB.GpuProblem(pr)
+    g.sparsity()
+    relabel = np.random.default_rng(12).permutation(pr.nnodes).astype(np.int32)
+    m2 = relabel[pr.cmap]
+    rp0, _ = g.csr()
+    orp2, _ = O.sparsity(m2, m2, pr.nnodes, pr.nnodes)
+    assert orp2[-1] == rp0[-1] and np.any(np.diff(orp2) != np.diff(rp0))
+    _rewrite_map(g, m2)
+    g.fe.sparsity_rebuild(g.sparsity())
+    g.fe.sync(g.ctx)
+    _check_pattern(g, m2, pr.nnodes)
+    # and back: rebuilding with the original map restores the original pattern
+    _rewrite_map(g, pr.cmap)
+    g.fe.sparsity_rebuild(g.sparsity())
+    g.fe.sync(g.ctx)
+    _check_pattern(g, pr.cmap, pr.nnodes)
+
+
+def test_rebuild_changed_nnz_is_reported(gpu):
+    """A map whose pattern has another nnz is reported at the next sync, every time it is rebuilt
+    (also when the previous failed rebuild left rowptr at that map's lengths); rebuilding with the
+    original map then gives the original pattern."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(3, 2, 5, 0.2, seed=0)
+    g = PB.GpuProblem(pr)
+    g.sparsity()
+    counts = np.bincount(pr.cmap.ravel(), minlength=pr.nnodes)
+    # cell 0 takes the nodes of a cell whose nodes all have fewer incidences than the longest list,
+    # so the row kernel's capacities still hold
+    donor = next(e for e in range(1, pr.cmap.shape[0])
+                 if counts[pr.cmap[e]].max() < counts.max() and not np.intersect1d(pr.cmap[e], pr.cmap[0]).size)
+    m2 = pr.cmap.copy()
+    m2[0] = pr.cmap[donor]
+    orp2, _ = O.sparsity(m2, m2, pr.nnodes, pr.nnodes)
+    rp0, _ = g.csr()
+    assert orp2[-1] != rp0[-1]
+    _rewrite_map(g, m2)
+    for _ in range(2):
+        g.fe.sparsity_rebuild(g.sparsity())
+        with pytest.raises(fe.FeError) as ei:
+            g.fe.sync(g.ctx)
+        assert ei.value.code == fe.FE_EINVAL
+    _rewrite_map(g, pr.cmap)
+    g.fe.sparsity_rebuild(g.sparsity())
+    g.fe.sync(g.ctx)
+    _check_pattern(g, pr.cmap, pr.nnodes)
+
+
 def test_rectangular_sparsity(gpu):
     """Rows from P2 nodes, columns from P1 nodes (Sec. 4.4.3: two different maps)."""
     from paper_1501_01809_gb300 import meshgen as mg
