@@ -217,23 +217,60 @@ def run_ours(args, wl, rank, world):
     vals = fe.mat_values(A)
 
     pull = args.strategy in ("pull", "auto")
+    # The Mat zero and the push action depend on neither the rebuilt pattern nor the assembly, so with
+    # --overlap they run on a second stream, concurrently with the sparsity rebuild (the pull action
+    # reads the rebuilt incidence and stays on the main stream).
+    side = None
+    if args.overlap != "off" and not pull:
+        side = torch.cuda.Stream(dev, priority=-1 if args.overlap == "hi" else 0)
 
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        fe.sparsity_rebuild(sp)
+    def compute(sp_, A_, X_, Y_, M_, XY_, CM_, ev=None, sev=None):
+        """One pass of the hot path: sparsity rebuild, Mat zero, assembly, action.  ev: 5 events on the
+        main stream (start, after the rebuild, before the assembly, after it, end); sev: 2 events on the
+        side stream (after the zero, after the action)."""
+        e0 = ev[0] if ev is not None else torch.cuda.Event()
+        e0.record(stream)
+        if side is None:
+            fe.sparsity_rebuild(sp_)
+            if ev is not None:
+                ev[1].record(stream)
+            if not pull:  # the pull row owners overwrite (zero_first) instead: no separate zero pass
+                fe.mat_zero(A_)
+            if ev is not None:
+                ev[2].record(stream)
+            fe.assemble_mat(ctx, K, cells, A_, XY_, CM_, zero_first=pull)
+            if ev is not None:
+                ev[3].record(stream)
+            fe.action(ctx, K, cells, X_, Y_, M_, XY_, CM_, zero_first=True, sp=sp_)
+            if ev is not None:
+                ev[4].record(stream)
+            return
+        ez = sev[0] if sev is not None else torch.cuda.Event()
+        ea = sev[1] if sev is not None else torch.cuda.Event()
+        side.wait_event(e0)
+        fe.ctx_set_stream(ctx, side)
+        try:
+            fe.mat_zero(A_)
+            ez.record(side)
+            fe.action(ctx, K, cells, X_, Y_, M_, XY_, CM_, zero_first=True, sp=sp_)
+            ea.record(side)
+        finally:
+            fe.ctx_set_stream(ctx, stream)
+        fe.sparsity_rebuild(sp_)
         if ev is not None:
             ev[1].record(stream)
-        if not pull:  # the pull row owners overwrite (zero_first) instead: no separate zero pass
-            fe.mat_zero(A)
+        stream.wait_event(ez)
         if ev is not None:
             ev[2].record(stream)
-        fe.assemble_mat(ctx, K, cells, A, XY, CM, zero_first=pull)
+        fe.assemble_mat(ctx, K, cells, A_, XY_, CM_, zero_first=False)
         if ev is not None:
             ev[3].record(stream)
-        fe.action(ctx, K, cells, X, Y, M, XY, CM, zero_first=True, sp=sp)
+        stream.wait_event(ea)
         if ev is not None:
             ev[4].record(stream)
+
+    def step(ev=None, sev=None):
+        compute(sp, A, X, Y, M, XY, CM, ev, sev)
 
     for _ in range(args.warmup):
         step()
@@ -244,19 +281,24 @@ def run_ours(args, wl, rank, world):
         td.barrier()
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sevs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     with ClockSampler(dev.index) as clk:
         t0 = time.perf_counter()
         for k in range(args.steps):
-            step(evs[k])
+            step(evs[k], sevs[k])
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if dist:
         td.barrier()
     fe.sync(ctx)
     phases = np.zeros(4)
-    for ev in evs:
-        for p in range(4):
-            phases[p] += ev[p].elapsed_time(ev[p + 1])
+    for ev, sev in zip(evs, sevs):
+        if side is None:
+            for p in range(4):
+                phases[p] += ev[p].elapsed_time(ev[p + 1])
+        else:  # live durations of the concurrent phases (sparsity on the main stream, zero and action beside it)
+            phases += [ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(sev[0]), ev[2].elapsed_time(ev[3]),
+                       sev[0].elapsed_time(sev[1])]
     total_ms = evs[0][0].elapsed_time(evs[-1][4])
     ms_step = total_ms / args.steps
     per_step = sorted(ev[0].elapsed_time(ev[4]) for ev in evs)
@@ -315,11 +357,7 @@ def run_ours(args, wl, rank, world):
             if sl["used"]:
                 stream.wait_event(ev["out"])     # the slot's previous outputs have been read back
             with torch.cuda.stream(stream):
-                fe.sparsity_rebuild(sl["sp"])
-                if not pull:
-                    fe.mat_zero(sl["A"])
-                fe.assemble_mat(ctx, K, cells, sl["A"], sl["XY"], sl["CM"], zero_first=pull)
-                fe.action(ctx, K, cells, sl["X"], sl["Y"], sl["M"], sl["XY"], sl["CM"], zero_first=True, sp=sl["sp"])
+                compute(sl["sp"], sl["A"], sl["X"], sl["Y"], sl["M"], sl["XY"], sl["CM"])
                 ev["comp"].record(stream)
             s_out.wait_event(ev["comp"])
             with torch.cuda.stream(s_out):
@@ -387,6 +425,8 @@ def run_ours(args, wl, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
                    "strategy": args.strategy,
+                   "schedule": ("Mat zero and action on a second stream, concurrent with the sparsity rebuild"
+                                if side is not None else "serial on one stream"),
                    "precision": ("element tensors in FP32 pairs (double-float), FP64 global accumulation"
                                  if args.precision == "f32x2" else "FP64 throughout"),
                    "parallelism": f"replicas x{world} (independent meshes, no collective)",
@@ -1169,6 +1209,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle seconds per step (batch workload)")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size (profiling on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--overlap", default="off", choices=["off", "on", "hi"],
+                    help="p2-3d push: Mat zero and action on a second stream beside the sparsity rebuild "
+                         "(hi: that stream at high priority)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
