@@ -192,34 +192,54 @@ __device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &
 
 
 // Bitonic sort of 32 E packed 32-bit values across a warp, ascending: lane l holds elements
-// E l .. E l + E - 1 in v[0..E).  Stages with j < E are within a lane, the others exchange with
-// lane l ^ (j / E) (same h).
+// E l .. E l + E - 1 in v[0..E).  Each merge of size k starts with a mirror stage (element i against
+// i ^ (k - 1)), after which every half-cleaner stage sorts ascending, so compare-exchanges inside a
+// lane need no direction select.  Stages between lanes exchange with lane l ^ (stride / E); the lane
+// holding the lower index keeps the minimum.
 template <int E>
 __device__ __forceinline__ void warp_bitonic_packed(uint32_t (&v)[E]) {
   const int lane = threadIdx.x & 31;
+  constexpr int LG = E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : -1;
+  static_assert(LG >= 0, "E must be a power of two up to 16");
 #pragma unroll
   for (int k = 2; k <= 32 * E; k <<= 1) {
+    if (k <= E) {  // mirror stage inside the lane
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int h = 0; h < E; h++) {
+        const int ph = h ^ (k - 1);
+        if (h < ph) {
+          const uint32_t a = v[h], b = v[ph];
+          v[h] = umin(a, b);
+          v[ph] = umax(a, b);
+        }
+      }
+    } else {  // mirror stage between lanes: element h meets the partner lane's element E - 1 - h
+      const int m = (k >> LG) - 1;
+      const bool lower = (lane & (k >> (LG + 1))) == 0;
+      uint32_t o[E];
+#pragma unroll
+      for (int h = 0; h < E; h++) o[h] = __shfl_xor_sync(0xffffffffu, v[E - 1 - h], m);
+#pragma unroll
+      for (int h = 0; h < E; h++) v[h] = lower ? umin(v[h], o[h]) : umax(v[h], o[h]);
+    }
+#pragma unroll
+    for (int j = k >> 2; j > 0; j >>= 1) {
       if (j < E) {
 #pragma unroll
         for (int h = 0; h < E; h++) {
           if ((h & j) == 0) {
-            const bool up = (((E * lane) + h) & k) == 0;
             const uint32_t a = v[h], b = v[h | j];
-            const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
-            v[h] = up ? lo : hi;
-            v[h | j] = up ? hi : lo;
+            v[h] = umin(a, b);
+            v[h | j] = umax(a, b);
           }
         }
       } else {
-        const int m = j / E;
-        const bool up = ((E * lane) & k) == 0;
-        const bool take_min = ((lane & m) == 0) == up;
+        const int m = j >> LG;
+        const bool lower = (lane & m) == 0;
 #pragma unroll
         for (int h = 0; h < E; h++) {
           const uint32_t o = __shfl_xor_sync(0xffffffffu, v[h], m);
-          v[h] = take_min ? (o < v[h] ? o : v[h]) : (o > v[h] ? o : v[h]);
+          v[h] = lower ? umin(v[h], o) : umax(v[h], o);
         }
       }
     }
@@ -342,7 +362,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
 //  4. lut[(e*ndr + i)*ndc + j] = rank of the candidate's slot; rowlen[r] = number of unique columns.
 // Shared memory per warp (32-bit words): hkey[cap], hrank[cap], ucol[cap], uslot[cap], cslot[cap],
 // adju[acap], adjs[acap].
-__global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
+__global__ void __launch_bounds__(256, 6) k_rows_build(const RowsParams p) {
   extern __shared__ __align__(16) int32_t smem_i[];
   if (p.gate && *p.gate == 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -373,9 +393,10 @@ __global__ void __launch_bounds__(256, 4) k_rows_build(const RowsParams p) {
       continue;
     }
     if (p.packed_ok && na <= 32 && ncand <= 256) {
-      // rows of up to 256 candidates (all rows of P1-P3 meshes): sort packed values
-      const int nu = ncand <= 64 ? row_by_sort<2, 6>(p, r, a0, na, ncand, adjs)
-                                : row_by_sort<8, 8>(p, r, a0, na, ncand, adjs);
+      // rows of up to 256 candidates (every row of P1 and P2 meshes and of P3 triangles): sort packed values
+      const int nu = ncand <= 64    ? row_by_sort<2, 6>(p, r, a0, na, ncand, adjs)
+                     : ncand <= 128 ? row_by_sort<4, 7>(p, r, a0, na, ncand, adjs)
+                                    : row_by_sort<8, 8>(p, r, a0, na, ncand, adjs);
       if (lane == 0) {
         p.rowlen[r] = nu;
         if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
