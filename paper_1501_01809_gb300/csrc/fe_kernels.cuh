@@ -126,15 +126,41 @@ __device__ __forceinline__ void mat_push_cell(const AsmArgs &a, int64_t e) {
   }
 }
 
+// Blocks per SM the push Mat kernel is compiled for.  The FP64 atomics bind it, so more resident
+// warps keep more of them in flight: double-float builds fit 128 registers (four 128-thread blocks
+// per SM instead of three at 167 registers, a few words spilled), which measured 6% faster for P2
+// tetrahedra.  FP64 and FP32 builds keep the compiler's choice (P3/P4 would spill hundreds of bytes).
+template <class Ops>
+struct MatOcc {
+  static constexpr int kMinBlocks = 1;
+};
+template <>
+struct MatOcc<OpsF32x2> {
+  static constexpr int kMinBlocks = 4;
+};
+
 template <int DIM, int P, int FORM, class Ops>
-__global__ void __launch_bounds__(kPushThreads) k_mat_push(const AsmArgs a) {
+__global__ void __launch_bounds__(kPushThreads, MatOcc<Ops>::kMinBlocks) k_mat_push(const AsmArgs a) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e < a.ncell) mat_push_cell<DIM, P, FORM, Ops>(a, e);
 }
 
 // ---------------------------------------------------------------------------- action, push
+// Blocks per SM the push action is compiled for.  Double-float element arithmetic fits 96
+// registers (five 128-thread blocks per SM) with at most a few words spilled, which measured 3%
+// faster than 128 registers at four blocks; FP64 and FP32 builds keep the compiler's choice (the
+// FP64 ones would spill hundreds of bytes).
+template <class Ops>
+struct ActionOcc {
+  static constexpr int kMinBlocks = 1;
+};
+template <>
+struct ActionOcc<OpsF32x2> {
+  static constexpr int kMinBlocks = 5;
+};
+
 template <int DIM, int P, int FORM, class Ops>
-__global__ void __launch_bounds__(kPushThreads) k_action_push(const AsmArgs a) {
+__global__ void __launch_bounds__(kPushThreads, ActionOcc<Ops>::kMinBlocks) k_action_push(const AsmArgs a) {
   using T = typename Ops::T;
   using E = fe_gen::Elem<DIM, P>;
   constexpr int ND = E::ND;

@@ -308,11 +308,12 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
     p.adj[a0 + rk] = (int32_t)v;
   }
   __syncwarp();
-  // 2. candidates t = E lane + h, packed (column << SH | t); padding sorts last
+  // 2. candidates t = 32 h + lane (consecutive lanes read consecutive map entries), packed
+  //    (column << SH | t); padding sorts last.  The sort does not depend on the starting slots.
   uint32_t key[E];
 #pragma unroll
   for (int h = 0; h < E; h++) {
-    const uint32_t t = (uint32_t)(E * lane + h);
+    const uint32_t t = (uint32_t)(32 * h + lane);
     key[h] = 0xFFFFFFFFu;
     if ((int)t < ncand) {
       const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
