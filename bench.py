@@ -228,8 +228,8 @@ def run_ours(args, wl, rank, world):
         """One pass of the hot path: sparsity rebuild, Mat zero, assembly, action.  ev: 5 events on the
         main stream (start, after the rebuild, before the assembly, after it, end); sev: 2 events on the
         side stream (after the zero, after the action)."""
-        e0 = ev[0] if ev is not None else torch.cuda.Event()
-        e0.record(stream)
+        if ev is not None:
+            ev[0].record(stream)
         if side is None:
             fe.sparsity_rebuild(sp_)
             if ev is not None:
@@ -245,6 +245,9 @@ def run_ours(args, wl, rank, world):
             if ev is not None:
                 ev[4].record(stream)
             return
+        e0 = ev[0] if ev is not None else torch.cuda.Event()
+        if ev is None:
+            e0.record(stream)
         ez = sev[0] if sev is not None else torch.cuda.Event()
         ea = sev[1] if sev is not None else torch.cuda.Event()
         side.wait_event(e0)
@@ -275,6 +278,20 @@ def run_ours(args, wl, rank, world):
     for _ in range(args.warmup):
         step()
     fe.sync(ctx)
+    # --graph: the whole step (rebuild, zero, assembly, action) captured once as a CUDA graph and
+    # replayed, so the launch latency of its 17 kernels is paid once per graph instead of per kernel
+    graph = None
+    use_graph = args.graph == "on" or (args.graph == "auto" and side is None and not pull)
+    if use_graph:
+        if side is not None or pull:
+            raise SystemExit("--graph on: one stream and the push strategy only")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream, capture_error_mode="thread_local"):
+            step()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                graph.replay()
+        fe.sync(ctx)
     dist = world > 1
     if dist:
         import torch.distributed as td
@@ -282,9 +299,19 @@ def run_ours(args, wl, rank, world):
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     sevs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    # Workloads that fit in L2 (the 8192-cell P1 case) overwrite a 256 MB buffer between steps, outside
+    # the timed intervals, so every step starts cold; the large ones have inputs beyond L2.
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if mesh.ncell < 200_000 else None
+
+    def flush_l2():
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+
     with ClockSampler(dev.index) as clk:
         t0 = time.perf_counter()
         for k in range(args.steps):
+            flush_l2()
             step(evs[k], sevs[k])
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -299,10 +326,31 @@ def run_ours(args, wl, rank, world):
         else:  # live durations of the concurrent phases (sparsity on the main stream, zero and action beside it)
             phases += [ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(sev[0]), ev[2].elapsed_time(ev[3]),
                        sev[0].elapsed_time(sev[1])]
-    total_ms = evs[0][0].elapsed_time(evs[-1][4])
-    ms_step = total_ms / args.steps
     per_step = sorted(ev[0].elapsed_time(ev[4]) for ev in evs)
+    # back to back, the span of all steps; with flushes in between, the sum of the steps
+    total_ms = evs[0][0].elapsed_time(evs[-1][4]) if flush is None else sum(per_step)
+    ms_step = total_ms / args.steps
     step_stats = {"min_ms": per_step[0], "median_ms": per_step[len(per_step) // 2], "max_ms": per_step[-1]}
+    if graph is not None:  # the step time of record is the graph's; the phases above come from launches
+        step_stats["eager_ms"] = ms_step
+        gev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev.index) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                flush_l2()
+                with torch.cuda.stream(stream):
+                    gev[k][0].record(stream)
+                    graph.replay()
+                    gev[k][1].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        fe.sync(ctx)
+        per_step = sorted(a.elapsed_time(b) for a, b in gev)
+        ms_step = (gev[0][0].elapsed_time(gev[-1][1]) if flush is None else sum(per_step)) / args.steps
+        step_stats.update({"min_ms": per_step[0], "median_ms": per_step[len(per_step) // 2], "max_ms": per_step[-1]})
     if dist:
         ms_step = max_over_ranks(ms_step, dev)
     phase_ms = phases / args.steps
@@ -426,11 +474,14 @@ def run_ours(args, wl, rank, world):
         "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
                    "strategy": args.strategy,
                    "schedule": ("Mat zero and action on a second stream, concurrent with the sparsity rebuild"
-                                if side is not None else "serial on one stream"),
+                                if side is not None else
+                                "one CUDA graph per step (phases from a launch-by-launch pass)" if graph is not None
+                                else "serial on one stream"),
                    "precision": ("element tensors in FP32 pairs (double-float), FP64 global accumulation"
                                  if args.precision == "f32x2" else "FP64 throughout"),
                    "parallelism": f"replicas x{world} (independent meshes, no collective)",
-                   "l2": "inputs larger than L2 (CSR values + lookup table ~650 MB), no flush"},
+                   "l2": ("inputs larger than L2 (CSR values + lookup table ~650 MB), no flush" if flush is None else
+                          "L2 flushed between steps (256 MB written outside the timed intervals)")},
         "roofline": roof, "kernels": kern, "step_ms": step_stats, "gpu_launches": launches, "wall_s_timed": wall,
         "clocks": clk.summary(), "e2e": e2e,
     }
@@ -1209,6 +1260,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle seconds per step (batch workload)")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size (profiling on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
+                    help="p2-3d/p1-2d: replay the step as one captured CUDA graph (auto: push strategy on one "
+                         "stream)")
     ap.add_argument("--overlap", default="off", choices=["off", "on", "hi"],
                     help="p2-3d push: Mat zero and action on a second stream beside the sparsity rebuild "
                          "(hi: that stream at high priority)")
