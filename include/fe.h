@@ -293,8 +293,10 @@ fe_status fe_wave_steps(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *phi, f
  * Sec. 6.2 solves with CG) for many independent SPD CSR systems at once: every fe_cg_iterate runs
  * `iters` iterations of all added, unfinished systems with two persistent launches per iteration
  * (captured once into a CUDA graph when use_graph != 0, replayed on the context stream).  Dot
- * products are FP64 sums over fixed tiles of 512 rows added in tile order (Globals with SUM
- * access, Sec. 4.4.2), so a system's iterates are bitwise the same alone or beside others.  The
+ * products are FP64 sums over fixed tiles added in tile order (Globals with SUM access,
+ * Sec. 4.4.2).  A tile is 512 rows, or for a system larger than 512 rows per resident block its
+ * rows split evenly over those blocks; the tiling depends only on the system and the device, so a
+ * system's iterates are bitwise the same alone or beside others.  The
  * products q = A p follow from the SpMV w = A z and q = w + beta q_old (algebraically equal to the
  * textbook order).  Stopping test after every iteration: ||r||_2 <= rtol ||b||_2, or maxit
  * iterations.  fe_cg_add copies A's values into the engine's sliced layout (SELL-32: slices of 32

@@ -8,14 +8,15 @@
 // itself is host code that decides what to launch.
 //
 // Loop, until every submitted request has finished or been refused:
-//   1. admit, in arrival order, requests that have arrived while a slot is free and the
+//   1. if systems are iterating: launch one tick of `iters_per_tick` CG iterations for all of
+//      them (a captured graph) on the server's stream, without waiting for it;
+//   2. meanwhile admit, in arrival order, requests that have arrived while a slot is free and the
 //      request's worst-case device footprint fits in the budget beside what is held (a request
 //      larger than the whole budget is refused; a request that does not fit yet waits, and so do
-//      the ones behind it);
-//   2. if systems are iterating: one tick of `iters_per_tick` CG iterations for all of them
-//      (a captured graph), then a status poll; converged systems copy their solution to the host
-//      and free everything they held;
-//   3. otherwise sleep until the next arrival.
+//      the ones behind it).  Admission runs on a second stream, so the systems already iterating
+//      are not paused by it; the server's stream waits for it before the next tick;
+//   3. poll the tick: converged systems copy their solution to the host and free everything they
+//      held.  With nothing iterating and nothing admitted, sleep until the next arrival.
 // Memory is accounted exactly: the server routes its allocations through a counting allocator that
 // draws from its own stream-ordered CUDA memory pool (requests come and go too often for a
 // synchronous allocator).
@@ -60,6 +61,9 @@ thread_local char g_vmsg[512];
 struct Server {
   fe_ctx *parent;
   fe_ctx *ctx;  // same device and stream as the parent, counting allocator
+  cudaStream_t main_stream = nullptr;  // the parent's stream: CG ticks, polls, retirement
+  cudaStream_t adm = nullptr;          // admission (copies, sparsity, assembly, elimination, CG set-up)
+  cudaEvent_t adm_done = nullptr;      // end of the last admissions, waited for by main_stream
   cudaMemPool_t pool = nullptr;  // the server's own stream-ordered pool (requests come and go often)
   fe_server_config cfg;
   fe_kernel *klap[3] = {nullptr, nullptr, nullptr}, *ksrc[3] = {nullptr, nullptr, nullptr};
@@ -232,10 +236,14 @@ void server_free(Server *s) {
     if (s->klap[p]) fe_kernel_destroy(s->klap[p]);
     if (s->ksrc[p]) fe_kernel_destroy(s->ksrc[p]);
   }
+  if (s->adm) cudaStreamSynchronize(s->adm);
   if (s->ctx) {
+    s->ctx->stream = s->main_stream ? s->main_stream : s->ctx->stream;
     cudaStreamSynchronize(s->ctx->stream);
     fe_ctx_destroy(s->ctx);
   }
+  if (s->adm_done) cudaEventDestroy(s->adm_done);
+  if (s->adm) cudaStreamDestroy(s->adm);
   if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
 }
@@ -271,6 +279,14 @@ fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server *
   uint64_t keep = cfg->hbm_budget;
   cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   fe_status st = fe_ctx_create(parent->device, parent->stream, &s->ctx);
+  if (st == FE_OK) {
+    s->main_stream = s->ctx->stream;
+    if (cudaStreamCreateWithFlags(&s->adm, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->adm_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      st = FE_ECUDA;
+    }
+  }
   if (st == FE_OK) st = fe_ctx_set_allocator(s->ctx, count_alloc, count_free, s);
   for (int p = 1; p <= 2 && st == FE_OK; p++) {
     fe_form_desc d{FE_FORM_LAPLACE, 2, p, 0, cfg->precision, FE_STRATEGY_PULL};
@@ -334,7 +350,20 @@ fe_status server_run(fe_server *h) {
   const auto t0 = std::chrono::steady_clock::now();
   size_t held = 0;  // sum of charges of the admitted requests
   while (next < order.size() || !active.empty()) {
-    // 1. admission, in arrival order
+    // 1. one tick of CG for every admitted system, launched without waiting
+    const double tt0 = now_s(t0);
+    const bool ticked = !active.empty();
+    if (ticked) {
+      fe_status st = fe_cg_iterate(s->cg, cfg.iters_per_tick, 1);
+      if (st != FE_OK) {
+        snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: %s", fe_last_error());
+        return st;
+      }
+    }
+    s->tick_s += now_s(t0) - tt0;
+    // 2. admission, in arrival order, on the admission stream while the tick runs
+    bool admitted = false;
+    s->ctx->stream = s->adm;
     while (next < order.size() && (int)active.size() < cfg.max_active) {
       Req &q = s->reqs[order[next]];
       if (q.in.arrival_s > now_s(t0)) break;
@@ -353,6 +382,7 @@ fe_status server_run(fe_server *h) {
       s->admit_s += now_s(t0) - q.res.admitted_s;
       if (st != FE_OK) {
         snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)id, fe_last_error());
+        s->ctx->stream = s->main_stream;
         release(s, q);
         return st;
       }
@@ -361,21 +391,27 @@ fe_status server_run(fe_server *h) {
       held += q.res.bytes;
       slot_owner[q.h.slot] = id;
       active.push_back(id);
+      admitted = true;
       next++;
     }
-    if (active.empty()) {
-      if (next < order.size()) {
+    s->ctx->stream = s->main_stream;
+    if (admitted && (cudaEventRecord(s->adm_done, s->adm) != cudaSuccess ||
+                     cudaStreamWaitEvent(s->main_stream, s->adm_done, 0) != cudaSuccess)) {
+      snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: ordering admission before the next tick");
+      return FE_ECUDA;
+    }
+    if (!ticked) {
+      if (!admitted && next < order.size()) {
         const double wait = s->reqs[order[next]].in.arrival_s - now_s(t0);
         if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 0.01)));
       }
       continue;
     }
-    // 2. one tick of CG for every admitted system, then retire the finished ones
-    const double tt0 = now_s(t0);
-    fe_status st = fe_cg_iterate(s->cg, cfg.iters_per_tick, 1);
-    if (st == FE_OK) st = fe_cg_poll(s->cg, cfg.max_active, st_status.data(), st_iters.data(), st_r.data(), st_b.data());
+    // 3. poll the tick, then retire the finished systems
+    const double tp0 = now_s(t0);
+    fe_status st = fe_cg_poll(s->cg, cfg.max_active, st_status.data(), st_iters.data(), st_r.data(), st_b.data());
     const double tt1 = now_s(t0);
-    s->tick_s += tt1 - tt0;
+    s->tick_s += tt1 - tp0;
     if (st != FE_OK) {
       snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: %s", fe_last_error());
       return st;

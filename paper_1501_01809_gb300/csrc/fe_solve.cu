@@ -6,7 +6,8 @@
 //
 // CG (Hestenes-Stiefel with M = diag(A), the solver of the Poisson experiment, Sec. 6.2): many
 // independent systems advance together, two persistent launches per iteration for all of them.
-// A system is cut into fixed tiles of kCgTileRows rows.  Dot products are Globals with SUM access
+// A system is cut into fixed tiles: 512 rows, or for a large system its rows split evenly over
+// the resident blocks (one wave, no tail).  Dot products are Globals with SUM access
 // (Sec. 4.4.2): every tile writes its partial sum to its own slot, and the tile that finishes
 // last for that system (a device counter, no waiting) adds the slots in tile order.  So every
 // system's arithmetic depends only on its own data and tiling: the iterates are bitwise the same
@@ -38,13 +39,21 @@ namespace {
 // (tile rows and SELL batch were swept on GB300 over 256..2048 rows and 4..8 columns: 512 / 4
 // balances large systems against the per-iteration latency of small ones)
 constexpr int kCgThreads = 256;
-constexpr int64_t kCgTileRows = FE_CG_TILE_ROWS;              // rows per tile (a multiple of kCgThreads)
-constexpr int kCgRowsPerThread = FE_CG_TILE_ROWS / kCgThreads;
+constexpr int64_t kCgTileRows = FE_CG_TILE_ROWS;  // smallest tile (a multiple of 32 rows)
 #ifndef FE_CG_SELL_BATCH
 #define FE_CG_SELL_BATCH 4
 #endif
 constexpr int kSellBatch = FE_CG_SELL_BATCH;  // SELL columns whose loads are issued together
-static_assert(FE_CG_TILE_ROWS % kCgThreads == 0, "tile rows must be a multiple of the block size");
+static_assert(FE_CG_TILE_ROWS % 32 == 0, "tiles are whole SELL-32 slices");
+
+// Rows per tile of a system: 512, or for a system of more than 512 rows per resident block, its
+// rows split evenly over the resident blocks (rounded up to whole 32-row slices), so that it runs
+// as one wave with no tail.  Depends only on the system and the grid, never on the other systems
+// in a launch, so a system's sums are the same alone and in a mix.
+int64_t cg_tile_rows(int64_t nrows, int grid) {
+  if (nrows <= kCgTileRows * (int64_t)grid) return kCgTileRows;
+  return ((nrows + grid - 1) / grid + 31) / 32 * 32;
+}
 
 enum CgStatusCode : int { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXIT = 2, CG_BREAKDOWN = 3 };
 
@@ -61,6 +70,7 @@ struct CgSys {
   const double *svals;
   const int32_t *scols;
   int64_t nrows;
+  int64_t tile_rows;  // rows per tile (whole SELL-32 slices)
   int ntiles;
   double rz, alpha, beta, bnorm2, rnorm2, rtol;
   int iters, maxit, active, status;
@@ -177,12 +187,11 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_init(CgSys *S) {
   __shared__ double sh[kCgThreads / 32];
   __shared__ int sh_last;
   const int t = blockIdx.x;
-  const int64_t r0 = (int64_t)t * kCgTileRows;
+  const int64_t r0 = (int64_t)t * S->tile_rows;
+  const int64_t r1 = r0 + S->tile_rows < S->nrows ? r0 + S->tile_rows : S->nrows;
   double rz = 0.0, rr = 0.0, bb = 0.0;
   int bad = 0;
-  for (int k = 0; k < kCgRowsPerThread; k++) {
-    const int64_t i = r0 + k * kCgThreads + threadIdx.x;
-    if (i >= S->nrows) break;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kCgThreads) {
     double d = 0.0, ax = 0.0;
     for (int64_t e = S->rowptr[i]; e < S->rowptr[i + 1]; e++) {
       const int32_t j = S->colidx[e];
@@ -253,8 +262,9 @@ __global__ void __launch_bounds__(kCgThreads, 6) k_cg_direction_spmv(CgSys *sys,
     const int32_t *__restrict__ scols = S->scols;
     const int64_t nrows = S->nrows;
     const int64_t nsl = (nrows + 31) / 32;
-    const int64_t s0 = (int64_t)tl.tile * (kCgTileRows / 32);
-    const int64_t s1 = s0 + kCgTileRows / 32 < nsl ? s0 + kCgTileRows / 32 : nsl;
+    const int64_t tsl = S->tile_rows / 32;
+    const int64_t s0 = (int64_t)tl.tile * tsl;
+    const int64_t s1 = s0 + tsl < nsl ? s0 + tsl : nsl;
     double pq = 0.0;
     for (int64_t sl = s0 + warp; sl < s1; sl += kCgThreads / 32) {
       const int64_t k0 = sptr[sl];
@@ -319,20 +329,18 @@ __global__ void __launch_bounds__(kCgThreads, 6) k_cg_update(CgSys *sys, const C
     double *__restrict__ x = S->x;
     double *__restrict__ r = S->r;
     double *__restrict__ z = S->z;
-    const int64_t r0 = (int64_t)tl.tile * kCgTileRows, nrows = S->nrows;
+    const int64_t r0 = (int64_t)tl.tile * S->tile_rows;
+    const int64_t r1 = r0 + S->tile_rows < S->nrows ? r0 + S->tile_rows : S->nrows;
     double rz = 0.0, rr = 0.0;
 #pragma unroll 2
-    for (int k = 0; k < kCgRowsPerThread; k++) {
-      const int64_t i = r0 + k * kCgThreads + threadIdx.x;
-      if (i < nrows) {
-        x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
-        const double zi = dinv[i] * ri;
-        r[i] = ri;
-        z[i] = zi;
-        rz += ri * zi;
-        rr += ri * ri;
-      }
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += kCgThreads) {
+      x[i] += alpha * p[i];
+      const double ri = r[i] - alpha * q[i];
+      const double zi = dinv[i] * ri;
+      r[i] = ri;
+      z[i] = zi;
+      rz += ri * zi;
+      rr += ri * ri;
     }
     rz = block_sum(rz, sh);
     rr = block_sum(rr, sh);
@@ -529,7 +537,8 @@ fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const d
     snprintf(g_smsg, sizeof g_smsg, "fe_cg_add: all %d slots are in use", e->cap);
     return FE_EINVAL;
   }
-  const int64_t ntiles = nrows > 0 ? (nrows + kCgTileRows - 1) / kCgTileRows : 0;
+  const int64_t tile_rows = cg_tile_rows(nrows, e->grid);
+  const int64_t ntiles = nrows > 0 ? (nrows + tile_rows - 1) / tile_rows : 0;
   if (ntiles > INT32_MAX / 2) {
     snprintf(g_smsg, sizeof g_smsg, "fe_cg_add: %lld rows is too many", (long long)nrows);
     return FE_EUNSUPPORTED;
@@ -542,6 +551,7 @@ fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const d
   S.b = b;
   S.x = x;
   S.nrows = nrows;
+  S.tile_rows = tile_rows;
   S.ntiles = (int)ntiles;
   S.rtol = rtol;
   S.maxit = maxit;
