@@ -155,6 +155,12 @@ cudaError_t launch_dirichlet(int64_t nrows, const int64_t *rowptr, const int32_t
 fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out);
 bool cg_valid(const fe_cg *h);
 int64_t cg_launches(const fe_cg *h);
+// Rows above which a system is cut into one tile per resident block (one wave of the launch).
+int64_t cg_one_wave_rows(const fe_cg *h);
+// Blocks the engine launches (one wave of resident blocks by default); cg_limit_grid lowers it,
+// before any system is added (the tiling of a system depends on it).
+int cg_grid(const fe_cg *h);
+fe_status cg_limit_grid(fe_cg *h, int grid);
 fe_ctx *cg_ctx(const fe_cg *h);
 fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const double *vals, int64_t nrows,
                  const double *b, double *x, double rtol, int maxit, int *slot);

@@ -9,7 +9,12 @@
 //
 // Loop, until every submitted request has finished or been refused:
 //   1. if systems are iterating: launch one tick of `iters_per_tick` CG iterations for all of
-//      them (a captured graph) on the server's stream, without waiting for it;
+//      them (a captured graph), without waiting for it.  Systems too large for one wave of
+//      512-row tiles iterate in a second engine on a high-priority stream whose launches use
+//      15/16 of the resident blocks: their blocks take the SMs first, and the smaller systems'
+//      blocks run in the sixteenth kept free (sharing one launch instead, the small tiles would
+//      add a second round on some blocks and slow the large system down; with all blocks taken
+//      at high priority, the small systems would only run in the gaps between its launches);
 //   2. meanwhile admit, in arrival order, requests that have arrived while a slot is free and the
 //      request's worst-case device footprint fits in the budget beside what is held (a request
 //      larger than the whole budget is refused; a request that does not fit yet waits, and so do
@@ -45,6 +50,7 @@ struct Holding {  // device objects of one admitted request
   void *d_map = nullptr, *d_cv = nullptr, *d_xy = nullptr, *d_f = nullptr, *d_bc = nullptr, *d_b = nullptr,
        *d_x = nullptr;
   int slot = -1;
+  bool big = false;  // iterating in the large-system engine (high-priority stream)
 };
 
 struct Req {
@@ -63,7 +69,9 @@ struct Server {
   fe_ctx *ctx;  // same device and stream as the parent, counting allocator
   cudaStream_t main_stream = nullptr;  // the parent's stream: CG ticks, polls, retirement
   cudaStream_t adm = nullptr;          // admission (copies, sparsity, assembly, elimination, CG set-up)
-  cudaEvent_t adm_done = nullptr;      // end of the last admissions, waited for by main_stream
+  cudaEvent_t adm_done = nullptr;      // end of the last admissions, waited for by main_stream and hi
+  cudaStream_t hi = nullptr;           // high priority: CG of the systems of more than one wave
+  fe_cg *cgb = nullptr;                // engine of those systems
   cudaMemPool_t pool = nullptr;  // the server's own stream-ordered pool (requests come and go often)
   fe_server_config cfg;
   fe_kernel *klap[3] = {nullptr, nullptr, nullptr}, *ksrc[3] = {nullptr, nullptr, nullptr};
@@ -145,7 +153,7 @@ size_t estimate_bytes(const fe_solve_request &r) {
   t += 2 * a(8 * (nn + 1)) + a(4 * ninc) + a(4 * nn) + a(4 * ninc * nd) + a(ninc * nd) +
        a(8 * scan_tmp_elems((int64_t)nn)) + a(4) + a(4 * nnz);                                  // sparsity
   t += a(8 * nnz) + a(8 * ncell * nd * (nd + 1) / 2) + a(8 * ncell * nd);                       // Mat, staging
-  t += 5 * a(8 * nn) + a(24 * (nn / 1024 + 1));                                                 // CG vectors
+  t += 5 * a(8 * nn) + a(24 * (nn / 512 + 1));  // CG vectors, tile partials (tiles of at least 512 rows)
   t += a(8 * (nsl + 1)) + a(4 * nsl) + a(8 * scan_tmp_elems((int64_t)nsl)) + a(8 * sell) + a(4 * sell);  // SELL
   return t;
 }
@@ -167,7 +175,7 @@ void release(Server *s, Req &q) {
   Holding &h = q.h;
   const int64_t saved = s->owner;
   s->owner = &q - s->reqs.data();
-  if (h.slot >= 0) fe_cg_remove(s->cg, h.slot);
+  if (h.slot >= 0) fe_cg_remove(h.big ? s->cgb : s->cg, h.slot);
   cudaStreamSynchronize(s->ctx->stream);
   if (h.A) fe_mat_destroy(h.A);
   if (h.sp) fe_sparsity_destroy(h.sp);
@@ -224,19 +232,31 @@ fe_status admit(Server *s, Req &q) {
   h.sp->vstage_bytes = 0;
   dev_free(c, h.sp->coltmp);
   h.sp->coltmp = nullptr;
-  SV_TRY(fe_cg_add(s->cg, h.A, h.B, h.X, s->cfg.rtol, s->cfg.maxit, &h.slot));
+  h.big = r.nnodes > cg_one_wave_rows(s->cg);
+  SV_TRY(fe_cg_add(h.big ? s->cgb : s->cg, h.A, h.B, h.X, s->cfg.rtol, s->cfg.maxit, &h.slot));
   return FE_OK;
 }
 
 void server_free(Server *s) {
   if (!s) return;
+  // nothing may be in flight on any of the server's streams while its objects are freed
+  if (s->adm) cudaStreamSynchronize(s->adm);
+  if (s->hi) cudaStreamSynchronize(s->hi);
+  if (s->ctx) {
+    if (s->main_stream) s->ctx->stream = s->main_stream;
+    cudaStreamSynchronize(s->ctx->stream);
+  }
   for (Req &q : s->reqs) release(s, q);
   if (s->cg) fe_cg_destroy(s->cg);
+  if (s->cgb) {
+    if (s->ctx) s->ctx->stream = s->hi;
+    fe_cg_destroy(s->cgb);
+  }
   for (int p = 1; p <= 2; p++) {
     if (s->klap[p]) fe_kernel_destroy(s->klap[p]);
     if (s->ksrc[p]) fe_kernel_destroy(s->ksrc[p]);
   }
-  if (s->adm) cudaStreamSynchronize(s->adm);
+  if (s->hi) cudaStreamSynchronize(s->hi);
   if (s->ctx) {
     s->ctx->stream = s->main_stream ? s->main_stream : s->ctx->stream;
     cudaStreamSynchronize(s->ctx->stream);
@@ -244,6 +264,7 @@ void server_free(Server *s) {
   }
   if (s->adm_done) cudaEventDestroy(s->adm_done);
   if (s->adm) cudaStreamDestroy(s->adm);
+  if (s->hi) cudaStreamDestroy(s->hi);
   if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
 }
@@ -281,7 +302,10 @@ fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server *
   fe_status st = fe_ctx_create(parent->device, parent->stream, &s->ctx);
   if (st == FE_OK) {
     s->main_stream = s->ctx->stream;
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
     if (cudaStreamCreateWithFlags(&s->adm, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->hi, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->adm_done, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       st = FE_ECUDA;
@@ -295,6 +319,15 @@ fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server *
     if (st == FE_OK) st = fe_kernel_create(s->ctx, &v, &s->ksrc[p]);
   }
   if (st == FE_OK) st = fe_cg_create(s->ctx, cfg->max_active, &s->cg);
+  if (st == FE_OK) {
+    s->ctx->stream = s->hi;
+    st = fe_cg_create(s->ctx, cfg->max_active, &s->cgb);
+    s->ctx->stream = s->main_stream;
+  }
+  if (st == FE_OK) {
+    const int g = cg_grid(s->cgb);
+    st = cg_limit_grid(s->cgb, g - g / 16);
+  }
   if (st != FE_OK) {
     snprintf(g_vmsg, sizeof g_vmsg, "fe_server_create: %s", fe_last_error());
     server_free(s);
@@ -344,17 +377,34 @@ fe_status server_run(fe_server *h) {
                    [&](int64_t a, int64_t b) { return s->reqs[a].in.arrival_s < s->reqs[b].in.arrival_s; });
   size_t next = 0;
   std::vector<int64_t> active;            // request ids iterating
-  std::vector<int64_t> slot_owner(cfg.max_active, -1);
-  std::vector<int> st_status(cfg.max_active), st_iters(cfg.max_active);
-  std::vector<double> st_r(cfg.max_active), st_b(cfg.max_active);
+  // per engine (0: the systems of one wave or less, 1: the larger ones): status of every slot
+  std::vector<int> st_status[2], st_iters[2];
+  std::vector<double> st_r[2], st_b[2];
+  for (int k = 0; k < 2; k++) {
+    st_status[k].assign(cfg.max_active, 0);
+    st_iters[k].assign(cfg.max_active, 0);
+    st_r[k].assign(cfg.max_active, 0.0);
+    st_b[k].assign(cfg.max_active, 0.0);
+  }
+  fe_cg *engines[2] = {s->cg, s->cgb};
+  cudaStream_t streams[2] = {s->main_stream, s->hi};
+  auto has = [&](int k) {
+    for (int64_t id : active)
+      if ((int)s->reqs[id].h.big == k) return true;
+    return false;
+  };
   const auto t0 = std::chrono::steady_clock::now();
   size_t held = 0;  // sum of charges of the admitted requests
   while (next < order.size() || !active.empty()) {
     // 1. one tick of CG for every admitted system, launched without waiting
     const double tt0 = now_s(t0);
     const bool ticked = !active.empty();
-    if (ticked) {
-      fe_status st = fe_cg_iterate(s->cg, cfg.iters_per_tick, 1);
+    const bool ran[2] = {has(0), has(1)};
+    for (int k = 1; k >= 0; k--) {  // the large systems' tick first, on the high-priority stream
+      if (!ran[k]) continue;
+      s->ctx->stream = streams[k];
+      fe_status st = fe_cg_iterate(engines[k], cfg.iters_per_tick, 1);
+      s->ctx->stream = s->main_stream;
       if (st != FE_OK) {
         snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: %s", fe_last_error());
         return st;
@@ -389,14 +439,14 @@ fe_status server_run(fe_server *h) {
       if (s->owner_bytes[id] > q.estimate) s->estimate_misses++;
       q.res.bytes = s->owner_bytes[id];
       held += q.res.bytes;
-      slot_owner[q.h.slot] = id;
       active.push_back(id);
       admitted = true;
       next++;
     }
     s->ctx->stream = s->main_stream;
     if (admitted && (cudaEventRecord(s->adm_done, s->adm) != cudaSuccess ||
-                     cudaStreamWaitEvent(s->main_stream, s->adm_done, 0) != cudaSuccess)) {
+                     cudaStreamWaitEvent(s->main_stream, s->adm_done, 0) != cudaSuccess ||
+                     cudaStreamWaitEvent(s->hi, s->adm_done, 0) != cudaSuccess)) {
       snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: ordering admission before the next tick");
       return FE_ECUDA;
     }
@@ -409,7 +459,14 @@ fe_status server_run(fe_server *h) {
     }
     // 3. poll the tick, then retire the finished systems
     const double tp0 = now_s(t0);
-    fe_status st = fe_cg_poll(s->cg, cfg.max_active, st_status.data(), st_iters.data(), st_r.data(), st_b.data());
+    fe_status st = FE_OK;
+    for (int k = 0; k < 2 && st == FE_OK; k++) {
+      if (!ran[k] && !has(k)) continue;  // nothing of this engine iterating or just admitted
+      s->ctx->stream = streams[k];
+      st = fe_cg_poll(engines[k], cfg.max_active, st_status[k].data(), st_iters[k].data(), st_r[k].data(),
+                      st_b[k].data());
+      s->ctx->stream = s->main_stream;
+    }
     const double tt1 = now_s(t0);
     s->tick_s += tt1 - tp0;
     if (st != FE_OK) {
@@ -419,27 +476,30 @@ fe_status server_run(fe_server *h) {
     for (size_t k = 0; k < active.size();) {
       const int64_t id = active[k];
       Req &q = s->reqs[id];
-      const int sl = q.h.slot;
-      if (st_status[sl] == 0) {
+      const int sl = q.h.slot, e = q.h.big ? 1 : 0;
+      if (st_status[e][sl] == 0) {
         k++;
         continue;
       }
-      q.res.status = st_status[sl];
-      q.res.iters = st_iters[sl];
-      q.res.rnorm = st_r[sl];
-      q.res.bnorm = st_b[sl];
+      q.res.status = st_status[e][sl];
+      q.res.iters = st_iters[e][sl];
+      q.res.rnorm = st_r[e][sl];
+      q.res.bnorm = st_b[e][sl];
+      // the solution and the frees are ordered on the stream the system iterated on
+      s->ctx->stream = streams[e];
       cudaError_t ce = cudaSuccess;
       if (q.in.nnodes > 0)
         ce = cudaMemcpyAsync(q.in.x_out, q.h.d_x, sizeof(double) * q.in.nnodes, cudaMemcpyDeviceToHost, s->ctx->stream);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->ctx->stream);
       if (ce != cudaSuccess) {
+        s->ctx->stream = s->main_stream;
         snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: copying the solution of request %lld", (long long)id);
         return FE_ECUDA;
       }
       q.res.finished_s = now_s(t0);
-      slot_owner[sl] = -1;
       held -= q.res.bytes;
       release(s, q);
+      s->ctx->stream = s->main_stream;
       active.erase(active.begin() + k);
     }
     s->retire_s += now_s(t0) - tt1;
@@ -463,7 +523,7 @@ fe_status server_stats(const fe_server *h, fe_server_stats *out) {
   out->base_bytes = s->base_bytes;
   out->estimate_misses = s->estimate_misses;
   out->run_s = s->run_s;
-  out->cg_launches = s->cg ? cg_launches(s->cg) : 0;
+  out->cg_launches = (s->cg ? cg_launches(s->cg) : 0) + (s->cgb ? cg_launches(s->cgb) : 0);
   out->admit_s = s->admit_s;
   out->tick_s = s->tick_s;
   out->retire_s = s->retire_s;

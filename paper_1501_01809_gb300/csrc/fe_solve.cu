@@ -473,6 +473,22 @@ void free_sys_vectors(CgEngine *e, CgSys &S) {
 
 bool cg_valid(const fe_cg *h) { return h && h->magic == kMagicCg && h->e; }
 int64_t cg_launches(const fe_cg *h) { return h->e->launches; }
+int64_t cg_one_wave_rows(const fe_cg *h) { return kCgTileRows * (int64_t)h->e->grid; }
+int cg_grid(const fe_cg *h) { return h->e->grid; }
+
+fe_status cg_limit_grid(fe_cg *h, int grid) {
+  CgEngine *e = h->e;
+  for (int s = 0; s < e->cap; s++)
+    if (e->used[s]) {
+      snprintf(g_smsg, sizeof g_smsg, "cg_limit_grid: systems are already tiled for %d blocks", e->grid);
+      return FE_EINVAL;
+    }
+  if (grid >= 1 && grid < e->grid) {
+    e->grid = grid;
+    drop_graph(e);
+  }
+  return FE_OK;
+}
 fe_ctx *cg_ctx(const fe_cg *h) { return h->e->ctx; }
 
 fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out) {

@@ -107,10 +107,12 @@ def _run_engine(cg, slots, tick=8, use_graph=True, maxticks=100000):
     raise AssertionError("CG did not finish")
 
 
-@pytest.mark.parametrize("n,p", [(12, 1), (31, 1), (9, 2), (24, 2)])
+@pytest.mark.parametrize("n,p", [(12, 1), (31, 1), (9, 2), (24, 2), (90, 2)])
 def test_cg_matches_oracle(gpu, n, p):
     from paper_1501_01809_gb300 import fe
     sp = pytest.importorskip("scipy.sparse")
+    if n > 40:
+        pytest.importorskip("scipy.sparse.linalg")
     ctx = _ctx()
     s = System(ctx, n, p, k=2, m=3, jitter=0.15, seed=1)
     fe.dirichlet_apply(ctx, s.A, s.B, s.t["bc"])
@@ -127,7 +129,11 @@ def test_cg_matches_oracle(gpu, n, p):
     bnorm = np.linalg.norm(b)
     assert abs(bn[slot] - bnorm) <= 1e-12 * bnorm and rn[slot] <= 1e-8 * bn[slot]
     assert np.linalg.norm(b - A @ x) <= 2e-8 * bnorm
-    lam_min = np.linalg.eigvalsh(A.toarray())[0]
+    if n > 40:  # smallest eigenvalue by shift-invert Lanczos (the dense matrix would be 33k x 33k)
+        from scipy.sparse.linalg import eigsh
+        lam_min = eigsh(A.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+    else:
+        lam_min = np.linalg.eigvalsh(A.toarray())[0]
     assert np.linalg.norm(x - xo) <= 2 * 2e-8 * bnorm / lam_min, (np.linalg.norm(x - xo), bnorm / lam_min)
 
 
@@ -252,3 +258,29 @@ def test_server_budget_binds_and_refuses(gpu):
     assert res[3]["admitted_s"] >= res[2]["admitted_s"]
     for r in res[:4]:
         assert r["bytes"] <= r["estimate"]
+
+
+def test_server_large_system_beside_small_ones(gpu):
+    """A system above one wave of 512-row tiles (P1 720 x 720: 519,841 rows, over 512 rows per
+    resident block on this GPU) iterates in the large-system engine on the high-priority stream,
+    beside small ones in the other engine: every solution is bitwise the same as alone, and the large
+    one meets the residual bound against the oracle's own system."""
+    from paper_1501_01809_gb300 import fe
+    sp = pytest.importorskip("scipy.sparse")
+    specs = [(0.0, 720, 1, 1, 1), (0.0, 20, 2, 2, 1), (0.0005, 30, 1, 3, 2), (0.001, 64, 2, 1, 3),
+             (0.002, 9, 1, 2, 2)]
+    reqs = _requests(specs)
+    res_mix, x_mix, stats = _serve(reqs, 1 << 34, 8)
+    res_one, x_one, _ = _serve(reqs, 1 << 34, 1)
+    assert stats["converged"] == len(reqs) and stats["estimate_misses"] == 0
+    for i in range(len(reqs)):
+        assert res_mix[i]["status"] == fe.SOLVE_CONVERGED and res_one[i]["status"] == fe.SOLVE_CONVERGED
+        assert res_mix[i]["iters"] == res_one[i]["iters"], i
+        np.testing.assert_array_equal(x_mix[i], x_one[i], err_msg=f"request {i}: mixed vs alone")
+    r = reqs[0]
+    rp, ci = O.sparsity(r["cmap"], r["cmap"], r["nn"], r["nn"])
+    v, _ = O.assemble_mat(2, 1, O.LAPLACE, r["cmap"], r["mesh"].coords, r["mesh"].cell_vertex, rp, ci)
+    b, _ = O.assemble_vec(2, 1, 1, r["cmap"], r["nn"], r["mesh"].coords, r["mesh"].cell_vertex, r["f"], r["cmap"])
+    v, b = O.dirichlet_apply(rp, ci, v, b, r["bc"])
+    A = sp.csr_matrix((v, ci, rp), shape=(r["nn"], r["nn"]))
+    assert np.linalg.norm(b - A @ x_mix[0]) <= 1.5e-8 * np.linalg.norm(b)
