@@ -153,7 +153,9 @@ fe_status fe_dat_destroy(fe_dat *dat);
  * {(rmap(e)[i], cmap(e)[j])}: rows = rmap target set, columns = cmap target set, columns
  * sorted ascending, no duplicates (bitwise deterministic).  Also builds the per-cell lookup
  * table giving, for each (e, i, j), the position of cmap(e)[j] within row rmap(e)[i], and the
- * row -> (cell, local index) incidence used by the row-owner (pull) kernels.  rmap and cmap
+ * row -> (cell, local index) incidence used by the row-owner (pull) kernels (put into ascending
+ * order by the first pull or wave call after each build, which is what makes their sums
+ * bitwise reproducible; push calls never need it).  rmap and cmap
  * must share their source set (the cells).  Owned buffers.  Synchronises the stream once to
  * learn nnz.  Errors: FE_EINVAL (different source sets), FE_ERANGE (map value out of range),
  * FE_EUNSUPPORTED (a row with more than 256 columns or more than 4096 candidate entries). */

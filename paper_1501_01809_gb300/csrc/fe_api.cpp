@@ -577,6 +577,7 @@ fe_status fe_assemble_mat(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_mat *A, int
   DeviceGuard g(c->device);
   const bool pull = fe::resolve_strategy(k->d, true) == FE_STRATEGY_PULL;
   if (pull) {
+    FE_CHECK_CUDA(fe::sparsity_canonical(A->sp, c->stream), who);  // row owners sum in incidence order
     st = ensure_stage(c, &A->stage, &A->stage_bytes, fe::stage_bytes_mat(k->d, cells->size), who);
     if (st != FE_OK) return st;
     a.stage = A->stage;
@@ -600,6 +601,8 @@ static fe_status pull_incidence(const char *who, fe_ctx *c, fe_kernel *k, fe_set
   if (!have) return fail(FE_EINVAL, "%s: the pull strategy needs the sparsity built from (map, map)", who);
   a.adjptr = sp->adjptr;
   a.adj = sp->adj;
+  DeviceGuard g(c->device);  // the row owners sum in incidence order: canonical, once per build
+  FE_CHECK_CUDA(fe::sparsity_canonical(const_cast<fe_sparsity *>(sp), c->stream), who);
   return FE_OK;
 }
 
@@ -748,6 +751,7 @@ fe_status fe_wave_steps(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *phi, fe_
   a.adj = sp->adj;
   DeviceGuard g(c->device);
   fe_sparsity *msp = const_cast<fe_sparsity *>(sp);
+  FE_CHECK_CUDA(fe::sparsity_canonical(msp, c->stream), who);  // rows sum in incidence order
   st = ensure_stage(c, &msp->vstage, &msp->vstage_bytes, fe::wave_stage_bytes(k->d.dim, k->d.precision, cells->size),
                     who);
   if (st != FE_OK) return st;

@@ -74,6 +74,7 @@ struct fe_sparsity {
   int64_t scan_tmp_elems;
   int *d_maxcnt;     // [1] max incidence count
   int *d_changed;    // [1] rebuild: some row changed its length (the in-place pass is not enough)
+  int adj_canonical; // each row's incidence list is in ascending order (sparsity_canonical)
   int maxrow;        // longest row (entries), known after build
   void *vstage;      // staging of element vectors for pull action / linear form (lazily allocated)
   size_t vstage_bytes;
@@ -118,6 +119,10 @@ cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err, const int *
 // length differs or rowptr[nrows] != nnz (then sparsity_rows, its scan and the compaction must
 // run, gated on changed).
 cudaError_t sparsity_rows_inplace(fe_sparsity *sp, cudaStream_t s, int *err, int *changed);
+// Each row's incidence list in ascending order, once per build: the order the row-owner (pull)
+// kernels and the wave step sum in.  The row kernel leaves the lists in the fill kernel's order
+// (its atomics make that order run-dependent); no-op when already done.
+cudaError_t sparsity_canonical(fe_sparsity *sp, cudaStream_t s);
 // colidx[rowptr[r] + k] = coltmp[adjptr[r] ndc + k]; check_nnz: flags ERR_NNZ_CHANGED if
 // rowptr[nrows] != nnz.  gate as for the scan.
 cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz,

@@ -268,6 +268,7 @@ struct RowsParams {
   int64_t nnz;
   int *changed;
   const int *gate;  // NULL, or a device flag: 0 = return without work
+  int canon;        // also put every row's incidence list in ascending order (else it stays in fill order)
 };
 
 // Where row r's nu unique columns go: colidx in place when the in-place pass applies and the
@@ -299,13 +300,16 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   const int lane = threadIdx.x & 31;
   const int ndc = p.ndc;
   const uint32_t tmask = (1u << SH) - 1u;
-  // 1. canonical incidence order by rank
+  // 1. the row's incidences (in ascending order by rank when canonicalising)
   const uint32_t v = lane < na ? (uint32_t)p.adj[a0 + lane] : 0xFFFFFFFFu;
-  int rk = 0;
-  for (int q = 0; q < na; q++) rk += __shfl_sync(0xffffffffu, v, q) < v;
+  int rk = lane;
+  if (p.canon) {
+    rk = 0;
+    for (int q = 0; q < na; q++) rk += __shfl_sync(0xffffffffu, v, q) < v;
+  }
   if (lane < na) {
     adjs[rk] = v;
-    p.adj[a0 + rk] = (int32_t)v;
+    if (p.canon) p.adj[a0 + rk] = (int32_t)v;
   }
   __syncwarp();
   // 2. candidates t = 32 h + lane (consecutive lanes read consecutive map entries), packed
@@ -352,9 +356,10 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   return nu;
 }
 
-// One warp per row r of the pattern (rows = target set of the row map):
-//  1. rank the row's incidence list {e*ndr + i : rmap(e)[i] = r} (all distinct) and store it in
-//     ascending order, in shared memory and back to adj (canonical order);
+// One warp per row r of the pattern (rows = target set of the row map).  Rows of at most 256
+// candidates and 32 incidences go through row_by_sort; the others:
+//  1. load the row's incidence list {e*ndr + i : rmap(e)[i] = r} (all distinct) into shared
+//     memory (ranked into ascending order and written back when p.canon is set);
 //  2. insert every candidate column cmap(e)[j] of every incident cell into a shared-memory hash
 //     table sized to the row (deduplication), remembering each candidate's slot;
 //  3. compact the unique columns (remembering their slots) and rank them by counting;
@@ -408,13 +413,17 @@ __global__ void __launch_bounds__(256, 6) k_rows_build(const RowsParams p) {
     const int H = next_pow2(ncand);  // <= cap
     int logH = 5;
     while ((1 << logH) < H) logH++;
-    // 1. canonical incidence order
+    // 1. the row's incidences (in ascending order when canonicalising)
     for (int t = lane; t < na; t += 32) adju[t] = (uint32_t)p.adj[a0 + t];
     for (int t = lane; t < H; t += 32) hkey[t] = -1;
     __syncwarp();
-    warp_rank_distinct(adju, na, [&](int q, int rk) { adjs[rk] = adju[q]; });
-    __syncwarp();
-    for (int t = lane; t < na; t += 32) p.adj[a0 + t] = (int32_t)adjs[t];
+    if (p.canon) {
+      warp_rank_distinct(adju, na, [&](int q, int rk) { adjs[rk] = adju[q]; });
+      __syncwarp();
+      for (int t = lane; t < na; t += 32) p.adj[a0 + t] = (int32_t)adjs[t];
+    } else {
+      for (int t = lane; t < na; t += 32) adjs[t] = adju[t];
+    }
     // 2. insert candidates, remember their slots
     for (int t = lane; t < ncand; t += 32) {
       const uint32_t a = div_ndc((uint32_t)t, p);
@@ -492,6 +501,33 @@ __global__ void k_rows_compact(int64_t nrows, int ndc, const int64_t *__restrict
   }
 }
 
+// One warp per row: the row's incidence list (distinct values e*ndr+i) in ascending order, in place.
+// Rows of at most 32 incidences rank in registers, longer ones through shared memory (acap words
+// twice per warp; no row is longer than acap, which the row kernel has checked).
+__global__ void k_adj_canon(int64_t nrows, const int64_t *__restrict__ adjptr, int32_t *__restrict__ adj, int acap) {
+  extern __shared__ __align__(16) uint32_t sm_canon[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  uint32_t *u = sm_canon + (size_t)wid * 2 * acap, *o = u + acap;
+  for (int64_t r = (int64_t)blockIdx.x * wpb + wid; r < nrows; r += (int64_t)gridDim.x * wpb) {
+    const int64_t a0 = adjptr[r];
+    const int na = (int)(adjptr[r + 1] - a0);
+    if (na <= 32) {
+      const uint32_t v = lane < na ? (uint32_t)adj[a0 + lane] : 0xFFFFFFFFu;
+      int rk = 0;
+      for (int q = 0; q < na; q++) rk += __shfl_sync(0xffffffffu, v, q) < v;
+      __syncwarp();
+      if (lane < na) adj[a0 + rk] = (int32_t)v;
+    } else if (na <= acap) {
+      for (int t = lane; t < na; t += 32) u[t] = (uint32_t)adj[a0 + t];
+      __syncwarp();
+      warp_rank_distinct(u, na, [&](int q, int rk) { o[rk] = u[q]; });
+      __syncwarp();
+      for (int t = lane; t < na; t += 32) adj[a0 + t] = (int32_t)o[t];
+    }
+    __syncwarp();
+  }
+}
+
 int grid_for(int64_t n, int threads, int max_blocks = 152 * 16) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -559,6 +595,7 @@ cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int wi
 
 namespace {
 cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed, const int *gate) {
+  sp->adj_canonical = 0;  // the row kernel leaves each incidence list in fill order
   RowsParams p;
   p.nrows = sp->nrows;
   p.ndr = sp->ndr;
@@ -582,6 +619,7 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
   p.nnz = sp->nnz;
   p.changed = changed;
   p.gate = gate;
+  p.canon = 0;
   const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
@@ -603,6 +641,21 @@ cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err, const int *
 
 cudaError_t sparsity_rows_inplace(fe_sparsity *sp, cudaStream_t s, int *err, int *changed) {
   return launch_rows(sp, s, err, changed, nullptr);
+}
+
+cudaError_t sparsity_canonical(fe_sparsity *sp, cudaStream_t s) {
+  if (sp->adj_canonical) return cudaSuccess;
+  const int warps = 8;
+  const size_t smem = (size_t)warps * 2 * sp->acap * sizeof(uint32_t);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_canon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (sp->nrows > 0)
+    k_adj_canon<<<grid_for(sp->nrows, warps, 152 * 16), warps * 32, smem, s>>>(sp->nrows, sp->adjptr, sp->adj, sp->acap);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) sp->adj_canonical = 1;
+  return e;
 }
 
 cudaError_t sparsity_compact(fe_sparsity *sp, cudaStream_t s, int *err, int check_nnz, const int *gate) {

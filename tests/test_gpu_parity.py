@@ -342,6 +342,14 @@ def test_pull_is_bitwise_reproducible(gpu):
         y1 = g.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL)
         y2 = g.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL)
         np.testing.assert_array_equal(y1, y2)
+        # after a rebuild (incidence lists refilled by atomics, in a run-dependent order) and from a
+        # fresh build in another context, the sums run in the same order again
+        g.fe.sparsity_rebuild(g.sparsity())
+        np.testing.assert_array_equal(g.assemble(3, precision=prec, strategy=fe.STRATEGY_PULL), a1)
+        np.testing.assert_array_equal(g.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL), y1)
+        g2 = PB.GpuProblem(pr)
+        np.testing.assert_array_equal(g2.assemble(3, precision=prec, strategy=fe.STRATEGY_PULL), a1)
+        np.testing.assert_array_equal(g2.action(3, x, precision=prec, strategy=fe.STRATEGY_PULL), y1)
 
 
 def test_pull_inc_semantics(gpu):
