@@ -37,7 +37,7 @@ static_assert(KT::N <= kTcN && KT::K <= kTcK, "tile too small for the contractio
 
 // 256 threads: threads 0..127 build the A rows (cells), threads 128..255 the B rows; after the
 // products, warps w and w + 4 read the same TMEM lanes (cells 32 (w % 4) ..) and split the 120
-// columns between them for the scatter.
+// columns between them into shared memory; then each warp scatters whole cells.
 __global__ void __launch_bounds__(kTcThreads) k_mat_push_tc_kappa_p4(const AsmArgs a) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   float *Ahi = reinterpret_cast<float *>(dsm);
@@ -137,21 +137,31 @@ __global__ void __launch_bounds__(kTcThreads) k_mat_push_tc_kappa_p4(const AsmAr
   }
   __syncthreads();
   if (!timeout) {
-    // 2. scatter in CSR row order: two threads per cell, rows 0..7 and 8..14 of the element
-    const int m = t & (kTcM - 1), hrow = t >> 7;
-    const int64_t e = blockIdx.x * (int64_t)kTcM + m;
-    int32_t rows[ND];
-    if (e < a.ncell && gather_rows<ND>(a, e, rows)) {
+    // 2. scatter, one warp per cell: lane l takes entries q = l, l + 32, ... of the element matrix
+    //    in row-major order, so a warp's lookup-table loads are 32 consecutive bytes and its
+    //    atomics of one instruction fall in two or three CSR rows of the cell
+    for (int m = w; m < kTcM; m += kTcThreads / 32) {
+      const int64_t e = blockIdx.x * (int64_t)kTcM + m;
+      if (e >= a.ncell) break;  // warp-uniform
+      int64_t rp = 0;
+      bool ok = true;
+      if (lane < ND) {
+        const int32_t r = a.map[e * ND + lane];
+        ok = !a.checks || (r >= 0 && r < a.nrows);  // a bad value was flagged when the cell was built
+        if (ok) rp = a.rowptr[r];
+      }
+      if (!__all_sync(0xffffffffu, ok)) continue;
       const uint8_t *L = a.lut + e * (ND * ND);
       const float *Sm = S + (size_t)m * kTcStride;
-#pragma unroll 1
-      for (int i = hrow ? 8 : 0; i < (hrow ? ND : 8); i++) {
-        double *rowv = a.vals + a.rowptr[rows[i]];
 #pragma unroll
-        for (int j = 0; j < ND; j++) {
+      for (int k = 0; k < (ND * ND + 31) / 32; k++) {
+        const int q = 32 * k + lane;
+        const int i = q / ND, j = q - (q / ND) * ND;
+        const int64_t base = __shfl_sync(0xffffffffu, rp, i < ND ? i : 0);
+        if (q < ND * ND) {
           const int lo = i < j ? i : j, hi = i < j ? j : i;
           const int n = lo * ND - lo * (lo - 1) / 2 + (hi - lo);  // upper-triangle index of (lo, hi)
-          red_add_f64(rowv + L[i * ND + j], f32_to_f64_exact(Sm[n]));
+          red_add_f64(a.vals + base + L[q], f32_to_f64_exact(Sm[n]));
         }
       }
     }
