@@ -67,8 +67,8 @@ TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 249.0 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
     ("assemble", "push", "f32x2"): (1.020e9, "3f520f948604"),
     # one sparsity rebuild (zeros, k_inc_count, scans, k_inc_fill, the in-place k_rows_build pass and the
-    # gated launches that return at once): 208.1 MB at 40^3, scaled x4.096 to 64^3
-    ("sparsity", None, None): (0.8525e9, "319132c960c7"),
+    # gated launches that return at once): 195.4 MB at 40^3, scaled x4.096 to 64^3
+    ("sparsity", None, None): (0.8002e9, "cab8903aa51d"),
 }
 
 
