@@ -464,7 +464,10 @@ def run_ours(args, wl, rank, world):
     else:
         roof = {"bound": "hbm", "achieved": dk["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": dk["hbm_frac"], "kernel": dom, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    # the captured traffic is that of the P2 64^3 workload; other meshes report none
     tr = TRAFFIC.get((dom, args.strategy, args.precision)) or TRAFFIC.get((dom, None, None))
+    if args.workload != "p2-3d" or args.n:
+        tr = None
     src_file = "fe_sparsity.cu" if dom == "sparsity" else "fe_kernels.cuh"
     roof["traffic"] = tr[0] if tr and tr[1] == _src_hash(src_file) else None
     out = {
@@ -606,6 +609,8 @@ def run_p1_sweep(args, wl, rank, world):
     prec = {"fp64": fe.PREC_FP64, "f32x2": fe.PREC_F32X2}[args.precision]
     peaks, src = _peaks()
     rows = []
+    clk = ClockSampler(dev.index)
+    clk.__enter__()
     for n in wl["ns"]:
         w = dict(wl, n=n)
         mesh, cmap, nn, x = make_inputs(w)
@@ -644,6 +649,7 @@ def run_p1_sweep(args, wl, rank, world):
                      "assemble_hbm_frac": b_a / (ms_a / 1e3) / 1e9 / peaks["hbm_gbs"],
                      "action_hbm_frac": b_x / (ms_x / 1e3) / 1e9 / peaks["hbm_gbs"]})
         del A, sp
+    clk.__exit__(None, None, None)
     big = rows[-1]
     gbs = (big["cells"] * 24 + (big["n"] + 1) ** 2 * 16 + big["nnz"] * 8) / (big["assemble_ms"] / 1e3) / 1e9
     out = {"metric": "cells/s assembled (P1 CSR assembly incl. zero), labelled extra sweep", "value":
@@ -656,7 +662,7 @@ def run_p1_sweep(args, wl, rank, world):
                         "frac": gbs / peaks["hbm_gbs"], "traffic": None,
                         "kernel": f"k_zero_f64 + k_mat_push<2,1,HELMHOLTZ> at n={big['n']}",
                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
-           "gpu_launches": 2 * max(3, min(args.steps, 50)), "e2e": None}
+           "gpu_launches": 2 * max(3, min(args.steps, 50)), "clocks": clk.summary(), "e2e": None}
     return out
 
 
