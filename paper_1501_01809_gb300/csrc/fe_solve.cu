@@ -278,13 +278,13 @@ __global__ void __launch_bounds__(kCgThreads, 6) k_cg_direction_spmv(CgSys *sys,
         double v[kSellBatch];
 #pragma unroll
         for (int u = 0; u < kSellBatch; u++) {
-          c[u] = cc[(int64_t)(k + u) * 32];
-          v[u] = vv[(int64_t)(k + u) * 32];
+          c[u] = __ldcs(cc + (int64_t)(k + u) * 32);  // streamed once per iteration: evict first, so
+          v[u] = __ldcs(vv + (int64_t)(k + u) * 32);  // the vectors stay in L2 across the launches
         }
 #pragma unroll
         for (int u = 0; u < kSellBatch; u++) w = fma(v[u], z[c[u]], w);
       }
-      for (; k < width; k++) w = fma(vv[(int64_t)k * 32], z[cc[(int64_t)k * 32]], w);
+      for (; k < width; k++) w = fma(__ldcs(vv + (int64_t)k * 32), z[__ldcs(cc + (int64_t)k * 32)], w);
       const int64_t i = sl * 32 + lane;
       if (i < nrows) {
         const double qi = w + beta * q[i];
