@@ -62,13 +62,16 @@ WORKLOADS = {
                        "2 GiB device-memory budget"),
 }
 # ncu dram bytes (read + write) per launch of the dominant kernel, with the sha1 of the kernel
-# source they were taken from; reported as null once the source has changed.
+# source they were taken from and what ncu showed binds it; reported as null once the source has
+# changed.
 TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 249.0 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
-    ("assemble", "push", "f32x2"): (1.020e9, "3f520f948604"),
+    ("assemble", "push", "f32x2"): (1.020e9, "3f520f948604",
+                                    "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
     # one sparsity rebuild (zeros, k_inc_count, scans, k_inc_fill, the in-place k_rows_build pass and the
     # gated launches that return at once): 195.4 MB at 40^3, scaled x4.096 to 64^3
-    ("sparsity", None, None): (0.8002e9, "cab8903aa51d"),
+    ("sparsity", None, None): (0.8002e9, "cab8903aa51d",
+                               "integer instruction issue (ncu at 40^3, row pass: issue active 71%, ALU pipe 71%)"),
 }
 
 
@@ -469,7 +472,9 @@ def run_ours(args, wl, rank, world):
     if args.workload != "p2-3d" or args.n:
         tr = None
     src_file = "fe_sparsity.cu" if dom == "sparsity" else "fe_kernels.cuh"
-    roof["traffic"] = tr[0] if tr and tr[1] == _src_hash(src_file) else None
+    fresh = bool(tr) and tr[1] == _src_hash(src_file)
+    roof["traffic"] = tr[0] if fresh else None
+    roof["binding"] = tr[2] if fresh else None
     out = {
         "metric": METRIC, "value": job_throughput(ncell, world, ms_step), "unit": "cells/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
