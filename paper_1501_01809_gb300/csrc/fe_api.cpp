@@ -9,6 +9,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fe_internal.h"
 
 namespace fe {
@@ -79,6 +81,13 @@ struct DeviceGuard {
   }
 };
 
+
+// An NVTX range around one compute call of the C ABI, so that profilers can group its launches by
+// call (header-only NVTX; without an attached tool a call costs a pointer test).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // Reads and clears the device error flags (synchronises the stream).
 fe_status check_device_flags(fe_ctx *c, const char *where) {
@@ -262,6 +271,7 @@ static void sparsity_free(fe_sparsity *sp) {
 }
 
 fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out) {
+  Range nvtx_range("fe_sparsity_build");
   if (!valid(c)) return fail(FE_EHANDLE, "fe_sparsity_build: invalid context");
   if (!valid(rmap) || !valid(cmap) || rmap->ctx != c || cmap->ctx != c)
     return fail(FE_EHANDLE, "fe_sparsity_build: maps belong to another context");
@@ -382,6 +392,7 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
 }
 
 fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
+  Range nvtx_range("fe_sparsity_rebuild");
   if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_rebuild: invalid sparsity");
   fe_ctx *c = sp->ctx;
   DeviceGuard g(c->device);
@@ -399,6 +410,7 @@ fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
 fe_status fe_sparsity_build_noalloc(const int32_t *rmap, int arity_r, const int32_t *cmap, int arity_c, int64_t ncell,
                                     int64_t nrows, int64_t ncols, int64_t *rowptr, int32_t *colidx,
                                     int64_t colidx_capacity, uint8_t *lut, int64_t *nnz, void *cuda_stream) {
+  Range nvtx_range("fe_sparsity_build_noalloc");
   fe_status st = fe::sparsity_build_noalloc(rmap, arity_r, cmap, arity_c, ncell, nrows, ncols, rowptr, colidx,
                                             colidx_capacity, lut, nnz, (cudaStream_t)cuda_stream);
   if (st != FE_OK) return fail(st, "%s", fe::noalloc_message());
@@ -457,6 +469,7 @@ fe_status fe_mat_values(const fe_mat *m, double **values) {
 }
 
 fe_status fe_mat_zero(fe_mat *m) {
+  Range nvtx_range("fe_mat_zero");
   if (!valid(m)) return fail(FE_EHANDLE, "fe_mat_zero: invalid mat");
   DeviceGuard g(m->ctx->device);
   FE_CHECK_CUDA(fe::launch_zero_f64(m->values, m->sp->nnz, m->ctx->stream), "fe_mat_zero");
@@ -558,6 +571,7 @@ static fe_status ensure_stage(fe_ctx *c, void **buf, size_t *have, size_t need, 
 
 fe_status fe_assemble_mat(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_mat *A, int zero_first, fe_dat *coords,
                           fe_map *coord_map, const fe_arg *coeffs, int ncoeffs) {
+  Range nvtx_range("fe_assemble_mat");
   const char *who = "fe_assemble_mat";
   if (!valid(A) || A->ctx != c) return fail(FE_EHANDLE, "%s: invalid mat", who);
   fe::AsmArgs a;
@@ -608,6 +622,7 @@ static fe_status pull_incidence(const char *who, fe_ctx *c, fe_kernel *k, fe_set
 
 fe_status fe_assemble_vec(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *b, fe_map *test_map, int zero_first,
                           fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs, int ncoeffs, const fe_sparsity *sp) {
+  Range nvtx_range("fe_assemble_vec");
   const char *who = "fe_assemble_vec";
   fe::AsmArgs a;
   fe_status st = common_args(who, c, k, cells, test_map, coords, coord_map, a);
@@ -642,6 +657,7 @@ fe_status fe_assemble_vec(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *b, fe_
 
 fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y, fe_map *map, int zero_first,
                     fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs, int ncoeffs, const fe_sparsity *sp) {
+  Range nvtx_range("fe_action");
   const char *who = "fe_action";
   fe::AsmArgs a;
   fe_status st = common_args(who, c, k, cells, map, coords, coord_map, a);
@@ -701,6 +717,7 @@ fe_status fe_batch_values(const fe_batch *b, int item, double **values, int64_t 
 }
 
 fe_status fe_batch_tune(fe_batch *b, int reps, int *tile_cells, int *grid, float *ms) {
+  Range nvtx_range("fe_batch_tune");
   if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_tune: invalid batch");
   DeviceGuard g(fe::batch_ctx(b)->device);
   fe_status st = fe::batch_tune(b, reps, tile_cells, grid, ms);
@@ -709,6 +726,7 @@ fe_status fe_batch_tune(fe_batch *b, int reps, int *tile_cells, int *grid, float
 }
 
 fe_status fe_batch_assemble(fe_batch *b, int use_graph) {
+  Range nvtx_range("fe_batch_assemble");
   if (!fe::batch_valid(b)) return fail(FE_EHANDLE, "fe_batch_assemble: invalid batch");
   DeviceGuard g(fe::batch_ctx(b)->device);
   fe_status st = fe::batch_assemble(b, use_graph);
@@ -732,6 +750,7 @@ static double wave_bc_value(double t) {
 fe_status fe_wave_steps(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *phi, fe_dat *p, const double *mass,
                         const uint8_t *is_bc, fe_map *map, fe_dat *coords, fe_map *coord_map, const fe_sparsity *sp,
                         double t0, double dt, int nsteps) {
+  Range nvtx_range("fe_wave_steps");
   const char *who = "fe_wave_steps";
   fe::AsmArgs a;
   fe_status st = common_args(who, c, k, cells, map, coords, coord_map, a);
@@ -762,6 +781,7 @@ fe_status fe_wave_steps(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *phi, fe_
 
 // ------------------------------------------------------------------------------------ Dirichlet
 fe_status fe_dirichlet_apply(fe_ctx *c, fe_mat *A, fe_dat *b, const uint8_t *is_bc, const double *g) {
+  Range nvtx_range("fe_dirichlet_apply");
   const char *who = "fe_dirichlet_apply";
   if (!valid(c)) return fail(FE_EHANDLE, "%s: invalid context", who);
   if (!valid(A) || A->ctx != c || !valid(b) || b->ctx != c) return fail(FE_EHANDLE, "%s: invalid mat or dat", who);
@@ -785,6 +805,7 @@ fe_status fe_cg_create(fe_ctx *c, int max_systems, fe_cg **out) {
 }
 
 fe_status fe_cg_add(fe_cg *cg, fe_mat *A, fe_dat *b, fe_dat *x, double rtol, int maxit, int *slot) {
+  Range nvtx_range("fe_cg_add");
   const char *who = "fe_cg_add";
   if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "%s: invalid engine", who);
   fe_ctx *c = fe::cg_ctx(cg);
@@ -802,6 +823,7 @@ fe_status fe_cg_add(fe_cg *cg, fe_mat *A, fe_dat *b, fe_dat *x, double rtol, int
 }
 
 fe_status fe_cg_iterate(fe_cg *cg, int iters, int use_graph) {
+  Range nvtx_range("fe_cg_iterate");
   if (!fe::cg_valid(cg)) return fail(FE_EHANDLE, "fe_cg_iterate: invalid engine");
   if (iters < 0) return fail(FE_EINVAL, "fe_cg_iterate: iters < 0");
   DeviceGuard g(fe::cg_ctx(cg)->device);
@@ -852,6 +874,7 @@ fe_status fe_server_submit(fe_server *srv, const fe_solve_request *req, int64_t 
 }
 
 fe_status fe_server_run(fe_server *srv) {
+  Range nvtx_range("fe_server_run");
   if (!fe::server_valid(srv)) return fail(FE_EHANDLE, "fe_server_run: invalid server");
   DeviceGuard g(fe::server_ctx(srv)->device);
   fe_status st = fe::server_run(srv);
