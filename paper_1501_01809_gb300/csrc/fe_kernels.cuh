@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
 // Deterministic INC without atomics, in two kernels.  (1) One thread per cell stores its element
 // tensor (the upper triangle of K_e for a Mat, the element vector for the action and the linear
 // form) with plain stores to a staging buffer.  (2) One thread per row, the row's owner, walks the
-// row's incidence list {(e, i)} -- ascending, fixed by the sparsity build -- and adds the
+// row's incidence list {(e, i)} -- ascending (sparsity_canonical, before the launch) -- and adds the
 // contributions in that order; a Mat row accumulates in shared memory (slots given by the lookup
 // table) and is written once.  The summation order is the same on every run: results are bitwise
 // reproducible.

@@ -3,11 +3,12 @@
 // table that replaces the column search of MatSetValues, the row -> (cell, local index)
 // incidence used by the row-owner kernels, a device-wide scan and small fill kernels.
 //
-// Everything is row-centric and deterministic: each row's incidence list is put in ascending
-// order, its candidate columns are deduplicated in a shared-memory hash table, the unique
-// columns are ranked by counting, and the ranks go to the lookup table.  The CSR result is
-// bitwise identical to a sort-unique of the pair set whatever the ordering of the atomics in
-// the incidence fill.
+// Everything is row-centric and deterministic: each row's candidate columns are deduplicated by a
+// warp sort of packed keys (or, for rows of more than 256 candidates, in a shared-memory hash
+// table), the unique columns are ranked, and the ranks go to the lookup table.  The CSR result is
+// bitwise identical to a sort-unique of the pair set whatever the ordering of the atomics in the
+// incidence fill.  The incidence lists themselves stay in fill order until a row-owner kernel
+// needs a fixed order (sparsity_canonical).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -153,7 +154,7 @@ __global__ void k_max_count(const int32_t *__restrict__ cnt, int64_t n, int *out
 }
 
 // incidence fill: adj[adjptr[r] + slot] = k (k = e*ndr + i); slot order is arbitrary here and
-// made canonical by the row kernel.
+// made canonical by sparsity_canonical when an order-sensitive kernel needs it.
 __global__ void k_inc_fill(const int32_t *__restrict__ rmap, int64_t n, int64_t nrows,
                            const int64_t *__restrict__ adjptr, int32_t *cursor, int32_t *__restrict__ adj) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -291,7 +292,8 @@ __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
 
 
 // One row by sorting packed (column << SH | candidate) values, E per lane (32 E >= ncand, na <= 32):
-// canonical incidence order, candidates, sort, first element of each run of equal columns, ranks
+// the incidence list (ranked into ascending order when p.canon), candidates, sort, first element
+// of each run of equal columns, ranks
 // by a warp prefix count, unique columns (ascending) to coltmp and every candidate's rank to the
 // lookup table.  Returns the number of unique columns (valid in every lane).
 template <int E, int SH>
