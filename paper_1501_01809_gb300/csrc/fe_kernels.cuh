@@ -250,19 +250,27 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
 // table) and is written once.  The summation order is the same on every run: results are bitwise
 // reproducible.
 
+
+// Staging of element tensors through shared memory: used while a block's tensors fit in 64 KB.
+template <class T, int NUP>
+struct ElemStaging {
+  static constexpr size_t kSmem = (size_t)NUP * sizeof(T) * 128;  // dynamic shared memory per block
+  static constexpr bool kTransposed = kSmem <= 64 * 1024;
+};
+
+// One cell's element tensor (upper triangle) to the staging buffer, or (transposed staging) to the
+// block's shared memory; false (the error flagged) on a bad map value.
 template <int DIM, int P, int FORM, class Ops>
-__global__ void __launch_bounds__(kPushThreads) k_mat_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+__device__ __forceinline__ bool mat_elem_cell(const AsmArgs &a, typename Ops::T *__restrict__ stage, int64_t e) {
   using T = typename Ops::T;
   using E = fe_gen::Elem<DIM, P>;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
   double x[DIM + 1][DIM], kap[DIM + 1];
   int32_t v[DIM + 1];
   bool ok = gather_coords<DIM>(a, e, x, v);
   if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) ok &= gather_kappa<DIM>(a, e, kap);
   if (!ok) {
     flag(a.err, ERR_RANGE, e);
-    return;
+    return false;
   }
   T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
   Geo<DIM>::template compute<Ops>(x, Lam, vol);
@@ -270,10 +278,49 @@ __global__ void __launch_bounds__(kPushThreads) k_mat_elem(const AsmArgs a, type
   for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
   T K[E::NUP];
   element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
-  T *out = stage + e * E::NUP;
+  if constexpr (ElemStaging<T, E::NUP>::kTransposed) {
+    // the block's element tensors are one contiguous range of the staging buffer: through shared
+    // memory, every store instruction of the block writes consecutive addresses
+    extern __shared__ __align__(16) unsigned char smem_elem[];
+    T *sK = reinterpret_cast<T *>(smem_elem);
 #pragma unroll
-  for (int u = 0; u < E::NUP; u++) out[u] = K[u];
+    for (int u = 0; u < E::NUP; u++) sK[(size_t)threadIdx.x * E::NUP + u] = K[u];
+  } else {
+    T *out = stage + e * E::NUP;
+#pragma unroll
+    for (int u = 0; u < E::NUP; u++) out[u] = K[u];
+  }
+  return true;
 }
+
+// The same kernel's block epilogue (transposed staging): the cells of the block that were built
+// (flagged cells leave their slots as they were) copied to the staging buffer in address order.
+template <class T, int NUP>
+__device__ __forceinline__ void copy_elem_block(T *__restrict__ stage, int64_t e0, int64_t ncell, const unsigned char *ok) {
+  extern __shared__ __align__(16) unsigned char smem_elem[];
+  const T *sK = reinterpret_cast<const T *>(smem_elem);
+  const int64_t left = ncell - e0;
+  const int n = (left < (int64_t)blockDim.x ? (int)left : (int)blockDim.x) * NUP;
+  T *out = stage + e0 * NUP;
+  for (int q = threadIdx.x; q < n; q += blockDim.x)
+    if (ok[q / NUP]) out[q] = sK[q];
+}
+
+template <int DIM, int P, int FORM, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_mat_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+  using T = typename Ops::T;
+  using E = fe_gen::Elem<DIM, P>;
+  const int64_t e0 = blockIdx.x * (int64_t)blockDim.x, e = e0 + threadIdx.x;
+  if constexpr (ElemStaging<T, E::NUP>::kTransposed) {
+    __shared__ unsigned char ok[kPushThreads];
+    ok[threadIdx.x] = e < a.ncell && mat_elem_cell<DIM, P, FORM, Ops>(a, stage, e);
+    __syncthreads();
+    copy_elem_block<T, E::NUP>(stage, e0, a.ncell, ok);
+  } else {
+    if (e < a.ncell) mat_elem_cell<DIM, P, FORM, Ops>(a, stage, e);
+  }
+}
+
 
 template <int DIM, int P, int FORM, class Ops>
 __global__ void __launch_bounds__(kPushThreads) k_action_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
@@ -432,7 +479,20 @@ cudaError_t mat_pull(const AsmArgs &a, cudaStream_t s) {
   using E = fe_gen::Elem<DIM, P>;
   using T = typename Ops::T;
   T *stage = static_cast<T *>(a.stage);
-  if (a.ncell > 0) k_mat_elem<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a, stage);
+  constexpr size_t esm = ElemStaging<T, E::NUP>::kTransposed ? ElemStaging<T, E::NUP>::kSmem : 0;
+  if (esm > 48 * 1024) {  // opt in once per kernel and device (the first call is never inside a capture)
+    static bool opted[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !opted[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(k_mat_elem<DIM, P, FORM, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)esm);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) opted[dev] = true;
+    }
+  }
+  if (a.ncell > 0)
+    k_mat_elem<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, esm, s>>>(a, stage);
   const int TB = 64;
   const size_t smem = (size_t)a.rowcap * TB * sizeof(T);
   if (smem > 48 * 1024) {
