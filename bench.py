@@ -66,7 +66,7 @@ WORKLOADS = {
 # changed.
 TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 249.0 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
-    ("assemble", "push", "f32x2"): (1.020e9, "b9ac77459240",
+    ("assemble", "push", "f32x2"): (1.020e9, "c827e6c081c1",
                                     "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
     # one sparsity rebuild (zeros, k_inc_count, scans, k_inc_fill, the in-place k_rows_build pass and the
     # gated launches that return at once): 195.4 MB at 40^3, scaled x4.096 to 64^3

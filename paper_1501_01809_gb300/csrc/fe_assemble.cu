@@ -81,7 +81,7 @@ size_t stage_bytes_mat(const fe_form_desc &d, int64_t ncell) {
   // (the FP32 element tensors have no pull kernels; sizes below are for FP64 and FP32 pairs)
   const int nd = nodes_of(d.dim, d.degree);
   const size_t elem = d.precision == FE_PREC_F32X2 ? 2 * sizeof(float) : sizeof(double);
-  return (size_t)ncell * (size_t)(nd * (nd + 1) / 2) * elem;
+  return (size_t)ncell * (size_t)(nd * nd) * elem;  // full element rows
 }
 
 size_t stage_bytes_vec(const fe_form_desc &d, int64_t ncell, int nd) {

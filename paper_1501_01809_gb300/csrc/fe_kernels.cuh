@@ -243,8 +243,8 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_push(const AsmArgs a) {
 
 // ---------------------------------------------------------------------------- staged pull
 // Deterministic INC without atomics, in two kernels.  (1) One thread per cell stores its element
-// tensor (the upper triangle of K_e for a Mat, the element vector for the action and the linear
-// form) with plain stores to a staging buffer.  (2) One thread per row, the row's owner, walks the
+// tensor (K_e for a Mat, as full rows so that a row owner reads each incidence's row contiguously;
+// the element vector for the action and the linear form) with plain stores to a staging buffer.  (2) One thread per row, the row's owner, walks the
 // row's incidence list {(e, i)} -- ascending (sparsity_canonical, before the launch) -- and adds the
 // contributions in that order; a Mat row accumulates in shared memory (slots given by the lookup
 // table) and is written once.  The summation order is the same on every run: results are bitwise
@@ -286,24 +286,31 @@ __device__ __forceinline__ bool mat_elem_cell(const AsmArgs &a, typename Ops::T 
 #pragma unroll
     for (int u = 0; u < E::NUP; u++) sK[(size_t)threadIdx.x * E::NUP + u] = K[u];
   } else {
-    T *out = stage + e * E::NUP;
+    T *out = stage + e * (E::ND * E::ND);  // full rows, expanded from the upper triangle
 #pragma unroll
-    for (int u = 0; u < E::NUP; u++) out[u] = K[u];
+    for (int i = 0; i < E::ND; i++)
+#pragma unroll
+      for (int j = 0; j < E::ND; j++) out[i * E::ND + j] = K[E::upper_index(i, j)];
   }
   return true;
 }
 
 // The same kernel's block epilogue (transposed staging): the cells of the block that were built
-// (flagged cells leave their slots as they were) copied to the staging buffer in address order.
-template <class T, int NUP>
+// (flagged cells leave their slots as they were) copied to the staging buffer in address order,
+// each as its full ND x ND matrix (row i of cell e at (e ND + i) ND: the rows the row owners read).
+template <class T, int ND>
 __device__ __forceinline__ void copy_elem_block(T *__restrict__ stage, int64_t e0, int64_t ncell, const unsigned char *ok) {
+  constexpr int NUP = ND * (ND + 1) / 2, NN = ND * ND;
   extern __shared__ __align__(16) unsigned char smem_elem[];
   const T *sK = reinterpret_cast<const T *>(smem_elem);
   const int64_t left = ncell - e0;
-  const int n = (left < (int64_t)blockDim.x ? (int)left : (int)blockDim.x) * NUP;
-  T *out = stage + e0 * NUP;
-  for (int q = threadIdx.x; q < n; q += blockDim.x)
-    if (ok[q / NUP]) out[q] = sK[q];
+  const int n = (left < (int64_t)blockDim.x ? (int)left : (int)blockDim.x) * NN;
+  T *out = stage + e0 * NN;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int m = q / NN, idx = q - m * NN, i = idx / ND, j = idx - (idx / ND) * ND;
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    if (ok[m]) out[q] = sK[m * NUP + lo * ND - lo * (lo - 1) / 2 + (hi - lo)];
+  }
 }
 
 template <int DIM, int P, int FORM, class Ops>
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(kPushThreads) k_mat_elem(const AsmArgs a, type
     __shared__ unsigned char ok[kPushThreads];
     ok[threadIdx.x] = e < a.ncell && mat_elem_cell<DIM, P, FORM, Ops>(a, stage, e);
     __syncthreads();
-    copy_elem_block<T, E::NUP>(stage, e0, a.ncell, ok);
+    copy_elem_block<T, E::ND>(stage, e0, a.ncell, ok);
   } else {
     if (e < a.ncell) mat_elem_cell<DIM, P, FORM, Ops>(a, stage, e);
   }
@@ -409,7 +416,6 @@ __global__ void k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr, co
                            const typename Ops::T *__restrict__ stage, double *__restrict__ vals, int rowcap,
                            int zero_first, int *err) {
   using T = typename Ops::T;
-  constexpr int NUP = ND * (ND + 1) / 2;
   extern __shared__ __align__(16) unsigned char smp[];
   T *acc = reinterpret_cast<T *>(smp) + threadIdx.x;
   const int TB = blockDim.x;
@@ -423,15 +429,13 @@ __global__ void k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr, co
     for (int q = 0; q < len; q++) acc[q * TB] = Ops::zero();
     const int64_t a0 = adjptr[r], a1 = adjptr[r + 1];
     for (int64_t ai = a0; ai < a1; ai++) {
-      const int32_t k = adj[ai];
-      const int32_t e = k / ND, i = k - e * ND;
-      const T *Ke = stage + (int64_t)e * NUP;
+      const int32_t k = adj[ai];  // incidence (e, i) = e ND + i
+      const T *Krow = stage + (int64_t)k * ND;  // row i of cell e's element matrix, contiguous
       const uint8_t *L = lut + (int64_t)k * ND;
 #pragma unroll
       for (int j = 0; j < ND; j++) {
-        const int u = i <= j ? i * ND - (i * (i - 1)) / 2 + (j - i) : j * ND - (j * (j - 1)) / 2 + (i - j);
         const int q = L[j];
-        acc[q * TB] = Ops::add(acc[q * TB], Ke[u]);
+        acc[q * TB] = Ops::add(acc[q * TB], Krow[j]);
       }
     }
     double *out = vals + b;
@@ -467,8 +471,9 @@ cudaError_t action_push(const AsmArgs &a, cudaStream_t s) {
   if (a.ncell > 0) k_action_push<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
-// The staging buffer (a.stage) holds ncell * NUP (Mat) or ncell * ND (action, vector) values of
-// the arithmetic type; AsmArgs.zero_first selects overwrite instead of INC in the row kernels.
+// The staging buffer (a.stage) holds ncell * ND * ND (Mat: full element rows) or ncell * ND (action,
+// vector) values of the arithmetic type; AsmArgs.zero_first selects overwrite instead of INC in the
+// row kernels.
 inline int pull_blocks(int64_t n, int t) {
   int64_t b = (n + t - 1) / t;
   return (int)(b < 1 ? 1 : b > 152 * 32 ? 152 * 32 : b);

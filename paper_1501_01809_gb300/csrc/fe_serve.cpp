@@ -152,7 +152,7 @@ size_t estimate_bytes(const fe_solve_request &r) {
   t += a(4 * ninc) + a(12 * ncell) + a(16 * nv) + a(8 * nn) + a(nn) + a(8 * nn) + a(8 * nn);  // inputs, b, x
   t += 2 * a(8 * (nn + 1)) + a(4 * ninc) + a(4 * nn) + a(4 * ninc * nd) + a(ninc * nd) +
        a(8 * scan_tmp_elems((int64_t)nn)) + a(4) + a(4 * nnz);                                  // sparsity
-  t += a(8 * nnz) + a(8 * ncell * nd * (nd + 1) / 2) + a(8 * ncell * nd);                       // Mat, staging
+  t += a(8 * nnz) + a(8 * ncell * nd * nd) + a(8 * ncell * nd);                                 // Mat, staging
   t += 5 * a(8 * nn) + a(24 * (nn / 512 + 1));  // CG vectors, tile partials (tiles of at least 512 rows)
   t += a(8 * (nsl + 1)) + a(4 * nsl) + a(8 * scan_tmp_elems((int64_t)nsl)) + a(8 * sell) + a(4 * sell);  // SELL
   return t;
