@@ -159,6 +159,32 @@ def max_over_ranks(x, device=None):
     return float(t.item())
 
 
+def bind_to_gpu_cpus(dev_index):
+    """Restrict this process to the CPUs local to the GPU (sysfs local_cpulist of its PCI function),
+    so that pinned host buffers are allocated on the GPU's own socket and host copies do not cross
+    the link between sockets.  Returns the CPU list, or None where sysfs does not say (no change)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev_index)
+        addr = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{addr}/local_cpulist") as fh:
+            spec = fh.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return f"{addr}: CPUs {spec}"
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
 def job_throughput(units_per_rank, world, ms_max):
     """Whole-job rate: every rank processes units_per_rank in at most ms_max milliseconds."""
     return world * units_per_rank / (ms_max / 1e3)
@@ -369,6 +395,7 @@ def run_ours(args, wl, rank, world):
     # separate streams: two device slots of inputs and outputs, ordered by events.
     e2e = None
     if not args.no_e2e:
+        host_cpus = bind_to_gpu_cpus(dev.index)  # pinned buffers on the GPU's own socket
         pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t.cpu())
         host_in = [pin(t) for t in (t_map, t_cv, t_xy, t_x)]
         slots = []
@@ -432,7 +459,8 @@ def run_ours(args, wl, rank, world):
             e2e_ms = max_over_ranks(e2e_ms, dev)
         e2e = {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "pipelining": "copies of neighbouring steps overlap the compute (two device slots, three streams)"}
+               "pipelining": "copies of neighbouring steps overlap the compute (two device slots, three streams)",
+               "host_cpus": host_cpus or "unchanged (no local CPU list in sysfs)"}
         fe.sync(ctx)
 
     # ------------------------------------------------------------------- roofline of the dominant kernel
