@@ -86,6 +86,22 @@ struct Server {
   double run_s = 0.0, admit_s = 0.0, tick_s = 0.0, retire_s = 0.0;
 };
 
+// The server context's stream for the duration of a scope: the engines and the library calls it
+// makes run on the context's stream, which the loop points at the admission, main or high-priority
+// stream; restored on every exit from the scope.
+struct OnStream {
+  fe_ctx *c;
+  cudaStream_t prev;
+  OnStream(Server *s, cudaStream_t st) : c(s->ctx), prev(s->ctx ? s->ctx->stream : nullptr) {
+    if (c) c->stream = st;
+  }
+  ~OnStream() {
+    if (c) c->stream = prev;
+  }
+  OnStream(const OnStream &) = delete;
+  OnStream &operator=(const OnStream &) = delete;
+};
+
 }  // namespace fe
 
 struct fe_server {
@@ -249,7 +265,7 @@ void server_free(Server *s) {
   for (Req &q : s->reqs) release(s, q);
   if (s->cg) fe_cg_destroy(s->cg);
   if (s->cgb) {
-    if (s->ctx) s->ctx->stream = s->hi;
+    OnStream on(s, s->hi);
     fe_cg_destroy(s->cgb);
   }
   for (int p = 1; p <= 2; p++) {
@@ -320,9 +336,8 @@ fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server *
   }
   if (st == FE_OK) st = fe_cg_create(s->ctx, cfg->max_active, &s->cg);
   if (st == FE_OK) {
-    s->ctx->stream = s->hi;
+    OnStream on(s, s->hi);
     st = fe_cg_create(s->ctx, cfg->max_active, &s->cgb);
-    s->ctx->stream = s->main_stream;
   }
   if (st == FE_OK) {
     const int g = cg_grid(s->cgb);
@@ -402,9 +417,11 @@ fe_status server_run(fe_server *h) {
     const bool ran[2] = {has(0), has(1)};
     for (int k = 1; k >= 0; k--) {  // the large systems' tick first, on the high-priority stream
       if (!ran[k]) continue;
-      s->ctx->stream = streams[k];
-      fe_status st = fe_cg_iterate(engines[k], cfg.iters_per_tick, 1);
-      s->ctx->stream = s->main_stream;
+      fe_status st;
+      {
+        OnStream on(s, streams[k]);
+        st = fe_cg_iterate(engines[k], cfg.iters_per_tick, 1);
+      }
       if (st != FE_OK) {
         snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: %s", fe_last_error());
         return st;
@@ -413,37 +430,45 @@ fe_status server_run(fe_server *h) {
     s->tick_s += now_s(t0) - tt0;
     // 2. admission, in arrival order, on the admission stream while the tick runs
     bool admitted = false;
-    s->ctx->stream = s->adm;
-    while (next < order.size() && (int)active.size() < cfg.max_active) {
-      Req &q = s->reqs[order[next]];
-      if (q.in.arrival_s > now_s(t0)) break;
-      if (s->base_bytes + q.estimate > cfg.hbm_budget) {
-        q.res.status = FE_SOLVE_REFUSED;
-        q.res.admitted_s = q.res.finished_s = now_s(t0);
+    fe_status adm_st = FE_OK;
+    int64_t adm_failed = -1;
+    {
+      OnStream on(s, s->adm);
+      while (next < order.size() && (int)active.size() < cfg.max_active) {
+        Req &q = s->reqs[order[next]];
+        if (q.in.arrival_s > now_s(t0)) break;
+        if (s->base_bytes + q.estimate > cfg.hbm_budget) {
+          q.res.status = FE_SOLVE_REFUSED;
+          q.res.admitted_s = q.res.finished_s = now_s(t0);
+          next++;
+          continue;
+        }
+        if (s->base_bytes + held + q.estimate > cfg.hbm_budget) break;  // wait for memory
+        const int64_t id = order[next];
+        q.res.admitted_s = now_s(t0);
+        s->owner = id;
+        fe_status st = admit(s, q);
+        s->owner = -1;
+        s->admit_s += now_s(t0) - q.res.admitted_s;
+        if (st != FE_OK) {
+          snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)id, fe_last_error());
+          adm_st = st;
+          adm_failed = id;
+          break;
+        }
+        if (s->owner_bytes[id] > q.estimate) s->estimate_misses++;
+        q.res.bytes = s->owner_bytes[id];
+        held += q.res.bytes;
+        active.push_back(id);
+        admitted = true;
         next++;
-        continue;
       }
-      if (s->base_bytes + held + q.estimate > cfg.hbm_budget) break;  // wait for memory
-      const int64_t id = order[next];
-      q.res.admitted_s = now_s(t0);
-      s->owner = id;
-      fe_status st = admit(s, q);
-      s->owner = -1;
-      s->admit_s += now_s(t0) - q.res.admitted_s;
-      if (st != FE_OK) {
-        snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)id, fe_last_error());
-        s->ctx->stream = s->main_stream;
-        release(s, q);
-        return st;
-      }
-      if (s->owner_bytes[id] > q.estimate) s->estimate_misses++;
-      q.res.bytes = s->owner_bytes[id];
-      held += q.res.bytes;
-      active.push_back(id);
-      admitted = true;
-      next++;
     }
-    s->ctx->stream = s->main_stream;
+    if (adm_st != FE_OK) {
+      cudaStreamSynchronize(s->adm);  // the failed request's work on the admission stream has ended
+      release(s, s->reqs[adm_failed]);
+      return adm_st;
+    }
     if (admitted && (cudaEventRecord(s->adm_done, s->adm) != cudaSuccess ||
                      cudaStreamWaitEvent(s->main_stream, s->adm_done, 0) != cudaSuccess ||
                      cudaStreamWaitEvent(s->hi, s->adm_done, 0) != cudaSuccess)) {
@@ -462,10 +487,9 @@ fe_status server_run(fe_server *h) {
     fe_status st = FE_OK;
     for (int k = 0; k < 2 && st == FE_OK; k++) {
       if (!ran[k] && !has(k)) continue;  // nothing of this engine iterating or just admitted
-      s->ctx->stream = streams[k];
+      OnStream on(s, streams[k]);
       st = fe_cg_poll(engines[k], cfg.max_active, st_status[k].data(), st_iters[k].data(), st_r[k].data(),
                       st_b[k].data());
-      s->ctx->stream = s->main_stream;
     }
     const double tt1 = now_s(t0);
     s->tick_s += tt1 - tp0;
@@ -485,21 +509,22 @@ fe_status server_run(fe_server *h) {
       q.res.iters = st_iters[e][sl];
       q.res.rnorm = st_r[e][sl];
       q.res.bnorm = st_b[e][sl];
-      // the solution and the frees are ordered on the stream the system iterated on
-      s->ctx->stream = streams[e];
-      cudaError_t ce = cudaSuccess;
-      if (q.in.nnodes > 0)
-        ce = cudaMemcpyAsync(q.in.x_out, q.h.d_x, sizeof(double) * q.in.nnodes, cudaMemcpyDeviceToHost, s->ctx->stream);
-      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->ctx->stream);
-      if (ce != cudaSuccess) {
-        s->ctx->stream = s->main_stream;
-        snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: copying the solution of request %lld", (long long)id);
-        return FE_ECUDA;
+      {
+        // the solution and the frees are ordered on the stream the system iterated on
+        OnStream on(s, streams[e]);
+        cudaError_t ce = cudaSuccess;
+        if (q.in.nnodes > 0)
+          ce = cudaMemcpyAsync(q.in.x_out, q.h.d_x, sizeof(double) * q.in.nnodes, cudaMemcpyDeviceToHost,
+                               s->ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->ctx->stream);
+        if (ce != cudaSuccess) {
+          snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: copying the solution of request %lld", (long long)id);
+          return FE_ECUDA;
+        }
+        q.res.finished_s = now_s(t0);
+        held -= q.res.bytes;
+        release(s, q);
       }
-      q.res.finished_s = now_s(t0);
-      held -= q.res.bytes;
-      release(s, q);
-      s->ctx->stream = s->main_stream;
       active.erase(active.begin() + k);
     }
     s->retire_s += now_s(t0) - tt1;
