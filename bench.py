@@ -181,7 +181,7 @@ def bind_to_gpu_cpus(dev_index):
             return None
         os.sched_setaffinity(0, cpus)
         return f"{addr}: CPUs {spec}"
-    except (OSError, ValueError, AttributeError):
+    except Exception:  # no sysfs entry, no PCI fields, no permission: leave the affinity alone
         return None
 
 
