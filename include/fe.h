@@ -328,7 +328,11 @@ fe_status fe_cg_destroy(fe_cg *cg);
  * starts) while fewer than max_active are iterating and the request's worst-case device footprint
  * fits beside what is held within hbm_budget; it advances all admitted systems together
  * (iters_per_tick CG iterations between status polls); a converged system's solution is copied to
- * x_out and all its device memory is freed at once.  A request whose footprint alone exceeds the
+ * x_out and all its device memory is freed at once.  Each tick is launched without waiting, and
+ * requests that arrived meanwhile are admitted on a second stream while it runs.  Systems too large
+ * for one wave of 512-row CG tiles iterate in a second engine on a high-priority stream that uses
+ * 15/16 of the resident blocks, so the smaller systems run beside them.  The server creates its
+ * own streams; the context's stream orders nothing inside fe_server_run.  A request whose footprint alone exceeds the
  * budget is refused.  max_active = 1 gives the plain one-request-at-a-time path with the same
  * kernels.  Host arrays of a request must stay valid until fe_server_run returns.  Device memory
  * comes from the server's own stream-ordered CUDA memory pool on the context's device (kept up to
