@@ -463,6 +463,42 @@ def run_ours(args, wl, rank, world):
                "host_cpus": host_cpus or "unchanged (no local CPU list in sysfs)"}
         fe.sync(ctx)
 
+    # ------------------------------------------------------------------- stored element matrices
+    # The stored-matrix alternative to the matrix-free action, timed after the steps and outside them:
+    # fe_elem_matrices once (every cell's upper triangle in FP64, entry-major), then fe_action_stored
+    # per application.  Its result is checked against the step's matrix-free action (in Y).
+    stored = None
+    if not pull:
+        nd_s = counts_per_cell(wl["dim"], wl["p"])[0]
+        nup = nd_s * (nd_s + 1) // 2
+        t_ke = torch.empty((nup, mesh.ncell), dtype=torch.float64, device=dev)
+        t_y2 = torch.zeros_like(t_x)
+        Y2 = fe.dat_create(ctx, nodes, t_y2)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fe.elem_matrices(ctx, K, cells, t_ke, XY, CM)
+                fe.action_stored(ctx, K, cells, t_ke, X, Y2, M, zero_first=True)
+        fe.sync(ctx)
+        reps = 20
+        se = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            se[0].record(stream)
+            fe.elem_matrices(ctx, K, cells, t_ke, XY, CM)
+            se[1].record(stream)
+            for _ in range(reps):
+                fe.action_stored(ctx, K, cells, t_ke, X, Y2, M, zero_first=True)
+            se[2].record(stream)
+        fe.sync(ctx)
+        st_ms, sa_ms = se[0].elapsed_time(se[1]), se[1].elapsed_time(se[2]) / reps
+        ke_bytes = nup * 8 * mesh.ncell
+        sa_bytes = ke_bytes + mesh.ncell * nd_s * 4 + 2 * nn * 8
+        ymax = float(t_y.abs().max())
+        stored = {"elem_matrices_ms": st_ms, "action_ms": sa_ms, "action_reps": reps, "stored_bytes": ke_bytes,
+                  "action_bytes": sa_bytes, "action_gbs": sa_bytes / (sa_ms / 1e3) / 1e9,
+                  "max_diff_vs_matrix_free": float((t_y2 - t_y).abs().max()) / (ymax if ymax > 0 else 1.0),
+                  "note": "not part of the step: stored matrices trade HBM for the element arithmetic of each action"}
+        del t_ke
+
     # ------------------------------------------------------------------- roofline of the dominant kernel
     peaks, src = _peaks()
     nd, fl_mat, fl_act = counts_per_cell(wl["dim"], wl["p"])
@@ -519,7 +555,7 @@ def run_ours(args, wl, rank, world):
                    "l2": ("inputs larger than L2 (CSR values + lookup table ~650 MB), no flush" if flush is None else
                           "L2 flushed between steps (256 MB written outside the timed intervals)")},
         "roofline": roof, "kernels": kern, "step_ms": step_stats, "gpu_launches": launches, "wall_s_timed": wall,
-        "clocks": clk.summary(), "e2e": e2e,
+        "clocks": clk.summary(), "e2e": e2e, "stored_action": stored,
     }
     return out, (mesh, cmap, nn, x)
 

@@ -238,6 +238,29 @@ fe_status fe_action(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat 
                     int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
                     int ncoeffs, const fe_sparsity *sp);
 
+/* ---------------------------------------------------------------- stored element matrices
+ * The stored-matrix alternative to fe_action, which recomputes every element matrix at each
+ * application.  fe_elem_matrices runs the local kernel of a bilinear form once per cell (the
+ * gather of coordinates and coefficients, geometry and element tensor of fe_assemble_mat,
+ * Sec. 4.4 and 5.2) and stores the matrices; fe_action_stored applies them,
+ * y[map(e)[i]] (INC) += sum_j K_e[i][j] x[map(e)[j]], x READ through map, without the element
+ * arithmetic.  The trade: nd(nd+1)/2 FP64 values of device memory per cell (440 bytes for P2
+ * tetrahedra) against that arithmetic at every application.
+ * Ke: caller-owned device buffer of nd(nd+1)/2 * ncell doubles, entry-major: entry u of the upper
+ *     triangle of cell e, u counting the pairs (i, j), i <= j, row by row, is Ke[u * ncell + e].
+ *     Ke must not change between the two calls' use of it (stream order).
+ * Kernels: bilinear forms in FE_PREC_FP64 (every compiled element) or FE_PREC_F32X2 (P1, P2; the
+ *     element tensor and the product in FP32 pairs); stored values and the INC are FP64 in both;
+ *     the INC is by FP64 atomics (push; the kernel's strategy field is not used).
+ * fe_action_stored: zero_first != 0 clears y first.  With checks on, map values outside the
+ *     target set are reported by fe_sync as FE_ERANGE.
+ * Errors: FE_EHANDLE, FE_EINVAL (NULL Ke with cells, sets or Dats that do not match, x aliasing
+ * y), FE_EARITY, FE_EUNSUPPORTED (linear form, other precisions or elements). */
+fe_status fe_elem_matrices(fe_ctx *ctx, fe_kernel *k, fe_set *cells, double *Ke, fe_dat *coords,
+                           fe_map *coord_map, const fe_arg *coeffs, int ncoeffs);
+fe_status fe_action_stored(fe_ctx *ctx, fe_kernel *k, fe_set *cells, const double *Ke, fe_dat *x,
+                           fe_dat *y, fe_map *map, int zero_first);
+
 /* ---------------------------------------------------------------- batches of meshes
  * Many independent problems assembled together (the fixed per-par_loop overhead the paper
  * identifies as the limit of strong scaling, Sec. 6.4.2, paid once for the whole batch).  Each

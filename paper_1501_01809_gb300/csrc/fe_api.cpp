@@ -689,6 +689,72 @@ fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y
   return ok();
 }
 
+// ------------------------------------------------------------------------------------ stored element matrices
+fe_status fe_elem_matrices(fe_ctx *c, fe_kernel *k, fe_set *cells, double *Ke, fe_dat *coords, fe_map *coord_map,
+                           const fe_arg *coeffs, int ncoeffs) {
+  Range nvtx_range("fe_elem_matrices");
+  const char *who = "fe_elem_matrices";
+  if (!valid(c)) return fail(FE_EHANDLE, "%s: invalid context", who);
+  if (!valid(k) || k->ctx != c) return fail(FE_EHANDLE, "%s: invalid kernel", who);
+  if (!valid(cells) || cells->ctx != c) return fail(FE_EHANDLE, "%s: invalid cell set", who);
+  if (!valid(coords) || coords->ctx != c) return fail(FE_EHANDLE, "%s: invalid coordinate dat", who);
+  if (!valid(coord_map) || coord_map->ctx != c) return fail(FE_EHANDLE, "%s: invalid coordinate map", who);
+  if (coord_map->from != cells) return fail(FE_EINVAL, "%s: the coordinate map must start from the iteration set", who);
+  if (coord_map->arity != k->d.dim + 1) return fail(FE_EARITY, "%s: coordinate map arity %d", who, coord_map->arity);
+  if (coords->dim != k->d.dim || coords->set != coord_map->to)
+    return fail(FE_EINVAL, "%s: coordinates must be a dim-%d Dat on the coordinate map's target", who, k->d.dim);
+  if (k->d.form == FE_FORM_SOURCE) return fail(FE_EUNSUPPORTED, "%s: element matrices need a bilinear form", who);
+  if (!Ke && cells->size > 0) return fail(FE_EINVAL, "%s: Ke is NULL", who);
+  fe::AsmArgs a;
+  memset(&a, 0, sizeof a);
+  a.ncell = cells->size;
+  a.coords = coords->data;
+  a.cmapv = coord_map->values;
+  a.nvert = coords->set->size;
+  a.err = c->d_err;
+  a.checks = c->checks;
+  fe_status st = kappa_arg(who, c, k, cells, coeffs, ncoeffs, a);
+  if (st != FE_OK) return st;
+  DeviceGuard g(c->device);
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_elem_store(k->d, a, Ke, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no stored-matrix kernel for this form/element/precision", who);
+  return ok();
+}
+
+fe_status fe_action_stored(fe_ctx *c, fe_kernel *k, fe_set *cells, const double *Ke, fe_dat *x, fe_dat *y, fe_map *map,
+                           int zero_first) {
+  Range nvtx_range("fe_action_stored");
+  const char *who = "fe_action_stored";
+  if (!valid(c)) return fail(FE_EHANDLE, "%s: invalid context", who);
+  if (!valid(k) || k->ctx != c) return fail(FE_EHANDLE, "%s: invalid kernel", who);
+  if (!valid(cells) || cells->ctx != c) return fail(FE_EHANDLE, "%s: invalid cell set", who);
+  if (!valid(map) || map->ctx != c) return fail(FE_EHANDLE, "%s: invalid map", who);
+  if (map->from != cells) return fail(FE_EINVAL, "%s: the map must start from the iteration set", who);
+  if (map->arity != k->nd) return fail(FE_EARITY, "%s: map arity %d, element has %d nodes", who, map->arity, k->nd);
+  if (k->d.form == FE_FORM_SOURCE) return fail(FE_EUNSUPPORTED, "%s: the action needs a bilinear form", who);
+  if (!valid(x) || !valid(y) || x->ctx != c || y->ctx != c || x->set != map->to || y->set != map->to || x->dim != 1 ||
+      y->dim != 1)
+    return fail(FE_EINVAL, "%s: x and y must be scalar Dats on the map's target", who);
+  if (x->data == y->data) return fail(FE_EINVAL, "%s: x and y must not alias", who);
+  if (!Ke && cells->size > 0) return fail(FE_EINVAL, "%s: Ke is NULL", who);
+  fe::AsmArgs a;
+  memset(&a, 0, sizeof a);
+  a.ncell = cells->size;
+  a.map = map->values;
+  a.nrows = map->to->size;
+  a.x = x->data;
+  a.y = y->data;
+  a.err = c->d_err;
+  a.checks = c->checks;
+  DeviceGuard g(c->device);
+  if (zero_first) FE_CHECK_CUDA(fe::launch_zero_f64(y->data, y->set->size, c->stream), who);
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_action_stored(k->d, k->nd, a, Ke, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no stored-matrix kernel for this form/element/precision", who);
+  return ok();
+}
+
 // ------------------------------------------------------------------------------------ batches
 static void *batch_alloc(fe_ctx *c, size_t n) { return dev_alloc(c, n); }
 static void batch_release(fe_ctx *c, void *p) { dev_free(c, p); }

@@ -27,6 +27,10 @@ LaunchFn pick_mat_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_action_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_vec_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_mat_push_tc(const fe_form_desc &d);
+StoreFn pick_elem_store_f64(const fe_form_desc &d);
+StoreFn pick_elem_store_dd(const fe_form_desc &d);
+StoredActionFn pick_action_stored_f64(int nd);
+StoredActionFn pick_action_stored_dd(int nd);
 
 namespace {
 
@@ -110,6 +114,28 @@ cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStr
   LaunchFn f = pick_vec(d, resolve_strategy(d, a.adj != nullptr));
   *unsupported = f == nullptr;
   return f ? f(a, s) : cudaSuccess;
+}
+
+// Stored element matrices: FP64 and double-float element arithmetic, bilinear forms.
+static StoreFn pick_elem_store(const fe_form_desc &d) {
+  if (d.form == FE_FORM_SOURCE) return nullptr;
+  if (d.precision == FE_PREC_FP64) return pick_elem_store_f64(d);
+  if (d.precision == FE_PREC_F32X2) return pick_elem_store_dd(d);
+  return nullptr;
+}
+
+cudaError_t launch_elem_store(const fe_form_desc &d, const AsmArgs &a, double *Ke, cudaStream_t s, int *unsupported) {
+  StoreFn f = pick_elem_store(d);
+  *unsupported = f == nullptr;
+  return f ? f(a, Ke, s) : cudaSuccess;
+}
+
+cudaError_t launch_action_stored(const fe_form_desc &d, int nd, const AsmArgs &a, const double *Ke, cudaStream_t s,
+                                 int *unsupported) {
+  StoredActionFn f = nullptr;
+  if (pick_elem_store(d)) f = d.precision == FE_PREC_FP64 ? pick_action_stored_f64(nd) : pick_action_stored_dd(nd);
+  *unsupported = f == nullptr;
+  return f ? f(a, Ke, s) : cudaSuccess;
 }
 
 }  // namespace fe

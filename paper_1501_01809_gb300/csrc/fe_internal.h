@@ -226,6 +226,14 @@ cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStr
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 bool kernel_supported(const fe_form_desc &d);
 
+// ---- stored element matrices (fe_stored_f64.cu, fe_stored_dd.cu) ----
+// Ke: [nd(nd+1)/2][ncell] FP64, entry-major (see fe_stored.cuh)
+using StoreFn = cudaError_t (*)(const AsmArgs &, double *, cudaStream_t);
+using StoredActionFn = cudaError_t (*)(const AsmArgs &, const double *, cudaStream_t);
+cudaError_t launch_elem_store(const fe_form_desc &d, const AsmArgs &a, double *Ke, cudaStream_t s, int *unsupported);
+cudaError_t launch_action_stored(const fe_form_desc &d, int nd, const AsmArgs &a, const double *Ke, cudaStream_t s,
+                                 int *unsupported);
+
 // ---- explicit wave steps (fe_wave.cu) ----
 size_t wave_stage_bytes(int dim, int precision, int64_t ncell);
 cudaError_t launch_wave(const fe_form_desc &d, const AsmArgs &a, void *stage, const double *mass,

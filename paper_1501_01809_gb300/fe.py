@@ -29,7 +29,7 @@ SYMBOLS = [
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
     "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
-    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
+    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_elem_matrices", "fe_action_stored", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
     "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
     "fe_cg_poll", "fe_cg_remove", "fe_cg_destroy", "fe_server_create", "fe_server_submit", "fe_server_run",
     "fe_server_result", "fe_server_stats_get", "fe_server_destroy", "fe_wave_steps",
@@ -121,6 +121,8 @@ def load():
         "fe_assemble_mat": (I, [P, P, P, P, I, P, P, C.POINTER(fe_arg), I]),
         "fe_assemble_vec": (I, [P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
         "fe_action": (I, [P, P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
+        "fe_elem_matrices": (I, [P, P, P, P, P, P, C.POINTER(fe_arg), I]),
+        "fe_action_stored": (I, [P, P, P, P, P, P, P, I]),
         "fe_batch_create": (I, [P, I, C.POINTER(fe_batch_item), PP]),
         "fe_batch_values": (I, [P, I, PP, C.POINTER(I64), PP, C.POINTER(I64)]),
         "fe_batch_tune": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(C.c_float)]),
@@ -398,7 +400,9 @@ def kernel_create(ctx: Ctx, form: int, dim: int, degree: int, coeff_degree: int 
     d = fe_form_desc(form, dim, degree, coeff_degree, precision, strategy)
     out = C.c_void_p()
     _check(load().fe_kernel_create(ctx.ptr, C.byref(d), C.byref(out)))
-    return Kernel(out, ctx)
+    k = Kernel(out, ctx)
+    k.nd = (degree + 1) * (degree + 2) // 2 if dim == 2 else (degree + 1) * (degree + 2) * (degree + 3) // 6
+    return k
 
 
 def _args(coeffs):
@@ -429,6 +433,31 @@ def action(ctx: Ctx, k: Kernel, cells: Set, x: Dat, y: Dat, map_: Map, coords: D
     arr, n = _args(coeffs)
     _check(load().fe_action(ctx.ptr, k.ptr, cells.ptr, x.ptr, y.ptr, map_.ptr, int(bool(zero_first)),
                             coords.ptr, coord_map.ptr, arr, n, sp.ptr if sp is not None else None))
+
+
+
+def _stored_tensor(Ke, k: Kernel, cells: Set):
+    Ke = _dev_tensor(Ke, torch.float64, "Ke")
+    nup, ncell = k.nd * (k.nd + 1) // 2, set_size(cells)
+    if Ke.numel() != nup * ncell:
+        raise ValueError(f"Ke must hold nd(nd+1)/2 * ncell = {nup} * {ncell} values")
+    return Ke
+
+
+def elem_matrices(ctx: Ctx, k: Kernel, cells: Set, Ke: torch.Tensor, coords: Dat, coord_map: Map, coeffs=()) -> None:
+    """fe_elem_matrices: each cell's element matrix, upper triangle in FP64, entry-major (Ke[u, e])."""
+    Ke = _stored_tensor(Ke, k, cells)
+    arr, n = _args(coeffs)
+    _check(load().fe_elem_matrices(ctx.ptr, k.ptr, cells.ptr, C.c_void_p(Ke.data_ptr()), coords.ptr, coord_map.ptr,
+                                   arr, n))
+
+
+def action_stored(ctx: Ctx, k: Kernel, cells: Set, Ke: torch.Tensor, x: Dat, y: Dat, map_: Map,
+                  zero_first: bool = True) -> None:
+    """fe_action_stored: y(INC) += K_e x_e cell by cell from matrices stored by elem_matrices."""
+    Ke = _stored_tensor(Ke, k, cells)
+    _check(load().fe_action_stored(ctx.ptr, k.ptr, cells.ptr, C.c_void_p(Ke.data_ptr()), x.ptr, y.ptr, map_.ptr,
+                                   int(bool(zero_first))))
 
 
 def batch_create(ctx: Ctx, items) -> Batch:
