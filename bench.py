@@ -1222,6 +1222,61 @@ def cpu_baseline(wl, inputs, ncell_sample):
                       f"{dt:.1f} s on 1 host core"}
 
 
+def _oracle_block_worker(task):
+    """One process of the all-cores oracle sample: sparsity + assembly + action on its own block of
+    cells, inputs memory-mapped from the files the parent wrote.  Returns its seconds of work."""
+    d, lo, hi = task
+    import oracle as O
+    with open(os.path.join(d, "meta.json")) as fh:
+        meta = json.load(fh)
+    c = np.ascontiguousarray(np.load(os.path.join(d, "cmap.npy"), mmap_mode="r")[lo:hi])
+    cv = np.ascontiguousarray(np.load(os.path.join(d, "cv.npy"), mmap_mode="r")[lo:hi])
+    coords = np.load(os.path.join(d, "coords.npy"))
+    x = np.load(os.path.join(d, "x.npy"))
+    t0 = time.perf_counter()
+    rp, ci = O.sparsity(c, c, meta["nn"], meta["nn"])
+    O.assemble_mat(meta["dim"], meta["p"], O.HELMHOLTZ, c, coords, cv, rp, ci)
+    O.action(meta["dim"], meta["p"], O.HELMHOLTZ, c, coords, cv, x)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(wl, inputs, ncell_per_proc, timeout_s=180.0):
+    """The oracle sample on every host core this process may use: one spawned process per core, each
+    on its own block of ncell_per_proc cells (the blocks' matrices are not merged).  Value = cells of
+    all blocks / wall time of the parallel pass."""
+    import multiprocessing as mp
+    import shutil
+    import tempfile
+    import oracle
+    oracle.build()
+    mesh, cmap, nn, x = inputs
+    ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    k = max(1, min(ncpu, mesh.ncell // max(1, ncell_per_proc)))
+    b = min(ncell_per_proc, mesh.ncell // k)
+    d = tempfile.mkdtemp(prefix="oracle_blocks_")
+    try:
+        np.save(os.path.join(d, "cmap.npy"), np.ascontiguousarray(cmap))
+        np.save(os.path.join(d, "cv.npy"), np.ascontiguousarray(mesh.cell_vertex))
+        np.save(os.path.join(d, "coords.npy"), np.ascontiguousarray(mesh.coords))
+        np.save(os.path.join(d, "x.npy"), np.ascontiguousarray(x))
+        with open(os.path.join(d, "meta.json"), "w") as fh:
+            json.dump({"nn": int(nn), "dim": int(wl["dim"]), "p": int(wl["p"])}, fh)
+        with mp.get_context("spawn").Pool(k) as pool:
+            warm = min(b, 256)  # imports and library load in every process, outside the timing
+            pool.map_async(_oracle_block_worker, [(d, i * warm, (i + 1) * warm) for i in range(k)],
+                           chunksize=1).get(timeout_s)
+            t0 = time.perf_counter()
+            secs = pool.map_async(_oracle_block_worker, [(d, i * b, (i + 1) * b) for i in range(k)],
+                                  chunksize=1).get(timeout_s)
+            wall = time.perf_counter() - t0
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    return {"value": k * b / wall, "unit": "cells/s", "cores": k, "kind": "oracle",
+            "sample": f"{k} processes (one per host core), each on its own block of {b} cells of the workload mesh "
+                      f"(sparsity + assembly + action per block, the blocks' matrices not merged), {wall:.1f} s wall, "
+                      f"{max(secs):.1f} s for the slowest block"}
+
+
 def ref_budget_s(args):
     """Seconds of oracle work per reference step so that warm-up plus timed steps take about two
     minutes in total (never more than --ref-seconds per step)."""
@@ -1416,6 +1471,11 @@ def main():
                                              f"{dt:.1f} s on 1 host core"}
         elif world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(wl, inputs, min(args.cpu_cells, inputs[0].ncell))
+            try:  # the same oracle on all host cores: reported beside the one-core figure
+                out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(wl, inputs, min(args.cpu_cells,
+                                                                                          inputs[0].ncell))
+            except Exception as exc:  # a failed side measurement must not lose the bench line
+                out["cpu_baseline"]["all_cores"] = {"error": f"{type(exc).__name__}: {exc}"}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as td

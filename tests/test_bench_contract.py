@@ -32,3 +32,15 @@ def test_reference_arm_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_all_cores_oracle_sample():
+    """The all-cores oracle sample (spawned processes, one block of cells each) reports its cores and a
+    positive rate on a small mesh."""
+    sys.path.insert(0, ROOT)
+    import bench
+    wl = dict(bench.WORKLOADS["p2-3d"], n=6)
+    out = bench.cpu_baseline_all_cores(wl, bench.make_inputs(wl), 64)
+    assert out["kind"] == "oracle" and out["unit"] == "cells/s"
+    assert 1 <= out["cores"] <= (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+    assert out["value"] > 0 and "processes" in out["sample"]
