@@ -59,6 +59,8 @@ __device__ __forceinline__ f2 f2_from_f64(double x) {
 // conversion-unit instructions): the FP64 significand of hi plus lo expressed in units of
 // hi's FP64 ulp, renormalised when the sum crosses a binade.  Error <= 1 ulp of FP64.
 // hi == 0 gives +-0; subnormal hi (|hi| < 2^-126) is flushed to zero.
+// Requires a normalised pair (|lo| <= ulp(hi)/2), which every pair operation returns: a pair
+// straight from f2_from_f64 (truncated hi, lo up to one ulp of hi) must pass through one first.
 __device__ __forceinline__ double f2_to_f64(float hi, float lo) {
   const uint32_t hb = __float_as_uint(hi);
   const int eh = (int)((hb >> 23) & 0xFF);
