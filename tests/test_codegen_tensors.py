@@ -80,3 +80,39 @@ def test_source_tensor(dim, p, q):
         fe = rng.uniform(-1, 1, Mx.shape[1])
         want = O.element_vector(dim, p, q, xv, fe)
         np.testing.assert_allclose(vol * Mx @ fe, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def _generated_array(name):
+    """A float table as emitted into the generated header (the bytes the tensor-core kernel loads)."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(cg.__file__), "csrc", "generated", "fe_local.cuh")).read()
+    m = re.search(name + r"\[(\d+)\]\[(\d+)\] = \{(.*?)\};", src, re.S)
+    assert m, name
+    rows, cols = int(m.group(1)), int(m.group(2))
+    vals = [float(v.rstrip("f")) for v in re.findall(r"-?[0-9.]+(?:e-?[0-9]+)?f", m.group(3))]
+    assert len(vals) == rows * cols
+    return np.array(vals).reshape(rows, cols)
+
+
+def test_tensor_core_kappa_table_layout():
+    """The P4 kappa-diffusion table of the tensor-core kernel: row n is the upper-triangle pair
+    (i <= j, row by row), column k = kappa node * 6 + Lam pair (m <= n).  Its FP32 entries,
+    contracted with kappa_k Lam_mn in FP64, give the oracle's element matrix to the table's own
+    rounding (relative Frobenius below 1e-6, well inside the 1e-5 bound of the tensor-core path)."""
+    Ctab = _generated_array("kKappaTC24_C")
+    nd = 15
+    iu, ju = np.triu_indices(nd)
+    assert Ctab.shape == (len(iu), 3 * 6)
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        xv = _cell(2, rng)
+        kv = np.exp(rng.standard_normal(3))
+        _, lam = _geometry(xv)
+        pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+        a = np.array([kv[k] * lam[mn] for k in range(3) for mn in pairs])
+        K = np.zeros((nd, nd))
+        K[iu, ju] = Ctab @ a
+        K[ju, iu] = K[iu, ju]
+        want = O.element_matrix(2, 4, O.KAPPA_DIFFUSION, xv, kv)
+        assert np.linalg.norm(K - want) <= 1e-6 * np.linalg.norm(want)
