@@ -468,7 +468,7 @@ def run_ours(args, wl, rank, world):
     # fe_elem_matrices once (every cell's upper triangle in FP64, entry-major), then fe_action_stored
     # per application.  Its result is checked against the step's matrix-free action (in Y).
     stored = None
-    if not pull:
+    if not pull and not args.no_stored:
         nd_s = counts_per_cell(wl["dim"], wl["p"])[0]
         nup = nd_s * (nd_s + 1) // 2
         t_ke = torch.empty((nup, mesh.ncell), dtype=torch.float64, device=dev)
@@ -1397,6 +1397,7 @@ def main():
                     help="p2-3d push: Mat zero and action on a second stream beside the sparsity rebuild "
                          "(hi: that stream at high priority)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stored", action="store_true", help="skip the stored-matrix action measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
