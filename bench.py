@@ -1240,7 +1240,7 @@ def _oracle_block_worker(task):
     return time.perf_counter() - t0
 
 
-def cpu_baseline_all_cores(wl, inputs, ncell_per_proc, timeout_s=180.0):
+def cpu_baseline_all_cores(wl, inputs, ncell_per_proc, timeout_s=90.0):
     """The oracle sample on every host core this process may use: one spawned process per core, each
     on its own block of ncell_per_proc cells (the blocks' matrices are not merged).  Value = cells of
     all blocks / wall time of the parallel pass."""
