@@ -53,3 +53,23 @@ def test_generated_local_kernels_are_current():
     from paper_1501_01809_gb300 import build, codegen
     with open(build.GEN) as fh:
         assert fh.read() == codegen.generate(check=False)
+
+
+def test_no_cpu_fallback(lib):
+    """Without a CUDA device the product path fails loudly: the binding refuses to make a context,
+    the C ABI reports a CUDA error for one, and buffers on the host are refused before any call."""
+    import torch
+    from paper_1501_01809_gb300 import fe
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        fe.ctx_create(0)
+    import ctypes as C
+    out = C.c_void_p()
+    assert lib.fe_ctx_create(0, None, C.byref(out)) == fe.FE_ECUDA and not out.value
+    host = torch.zeros((4, 3), dtype=torch.int32)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        fe.map_create(None, None, None, host)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        fe.sparsity_build_noalloc(host, host, 4, 4, torch.zeros(5, dtype=torch.int64), None,
+                                  torch.zeros(36, dtype=torch.uint8))
