@@ -1376,6 +1376,17 @@ def run_reference(args, wl):
             "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def emit(out, args):
+    """Prints the run's one JSON line; with --log also appends it, with the time and the command
+    line, to a JSONL file (one record per run)."""
+    line = json.dumps(out)
+    print(line)
+    if getattr(args, "log", None):
+        rec = dict(out, logged_at=time.strftime("%Y-%m-%dT%H:%M:%S%z"), argv=sys.argv[1:])
+        with open(args.log, "a") as fh:
+            fh.write(json.dumps(rec) + "\n")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1398,6 +1409,7 @@ def main():
                          "(hi: that stream at high priority)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stored", action="store_true", help="skip the stored-matrix action measurement")
+    ap.add_argument("--log", default=None, help="also append the JSON line to this JSONL file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1412,7 +1424,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args, wl)))
+            emit(run_reference(args, wl), args)
         return
     if world > 1:
         import torch
@@ -1422,17 +1434,17 @@ def main():
     if wl.get("sweep"):
         out = run_p1_sweep(args, wl, rank, world)
         if rank == 0:
-            print(json.dumps(out))
+            emit(out, args)
         return
     if wl.get("p4"):
         out = run_p4(args, wl, rank, world)
         if rank == 0:
-            print(json.dumps(out))
+            emit(out, args)
         return
     if wl.get("cg"):
         out = run_cg(args, wl, rank, world)
         if rank == 0:
-            print(json.dumps(out))
+            emit(out, args)
         return
     if wl.get("wave"):
         out, winputs = run_wave(args, wl, rank, world)
@@ -1445,7 +1457,7 @@ def main():
                                        "sample": f"{cells // winputs[0].ncell} oracle time steps of the workload "
                                                  f"mesh in one call (its lumped-mass assembly included), "
                                                  f"{dt_s:.1f} s on 1 host core"}
-            print(json.dumps(out))
+            emit(out, args)
         return
     if wl.get("serve"):
         out, reqs = run_serve(args, wl, rank, world)
@@ -1477,7 +1489,7 @@ def main():
                                                                                           inputs[0].ncell))
             except Exception as exc:  # a failed side measurement must not lose the bench line
                 out["cpu_baseline"]["all_cores"] = {"error": f"{type(exc).__name__}: {exc}"}
-        print(json.dumps(out))
+        emit(out, args)
     if world > 1:
         import torch.distributed as td
         td.barrier()

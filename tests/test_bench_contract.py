@@ -44,3 +44,11 @@ def test_all_cores_oracle_sample():
     assert out["kind"] == "oracle" and out["unit"] == "cells/s"
     assert 1 <= out["cores"] <= (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
     assert out["value"] > 0 and "processes" in out["sample"]
+
+
+def test_log_appends_one_record_per_run(tmp_path):
+    log = tmp_path / "runs.jsonl"
+    for _ in range(2):
+        d = _run("--log", str(log))
+    recs = [json.loads(ln) for ln in log.read_text().splitlines()]
+    assert len(recs) == 2 and all(r["metric"] == d["metric"] and "logged_at" in r and "--log" in r["argv"] for r in recs)
