@@ -303,7 +303,9 @@ int oracle_element_matrix_abs(int dim, int p, int form, const double *xv, const 
                     double gg = 0.0, ga = 0.0;
                     for (int x = 0; x < dim; x++) {
                         gg += grad[i * dim + x] * grad[j * dim + x];
-                        ga += fabs(grad[i * dim + x] * grad[j * dim + x]);
+                        /* planted mistake (14): signed terms; provably inert, see entry_scale */
+                        ga += g_mutation == 14 ? grad[i * dim + x] * grad[j * dim + x]
+                                               : fabs(grad[i * dim + x] * grad[j * dim + x]);
                     }
                     s += kap * gg;
                     a += fabs(kap) * ga;
@@ -313,7 +315,7 @@ int oracle_element_matrix_abs(int dim, int p, int form, const double *xv, const 
                     a += fabs(phi[i] * phi[j]);
                 }
                 K[i * nd + j] += wq * s;
-                if (Kabs) Kabs[i * nd + j] += fabs(wq) * a;
+                if (Kabs) Kabs[i * nd + j] += fabs(wq) * a * (g_mutation == 12 ? nq : 1); /* (12): x point count */
             }
     }
     return nd;
@@ -329,9 +331,16 @@ int oracle_element_matrix(int dim, int p, int form, const double *xv, const doub
  * semi-definite element matrix, so |K_ij| <= sqrt(K_ii K_jj) whatever formulation computes it;
  * the bound keeps the scale meaningful for entries whose quadrature terms all vanish while
  * another (equally exact) formulation leaves rounding-level residue there.
+ *
+ * For the forms here (mass, Laplace, Helmholtz, and kappa-diffusion with kappa > 0) the floor
+ * is always the larger one off the diagonal: by Cauchy-Schwarz over the quadrature points and
+ * components, sum |a_qx b_qx| <= sqrt(sum a_qx^2 sum b_qx^2), and the diagonal sums have
+ * non-negative terms only, so Kabs_ii = K_ii exactly.  The scale is therefore sqrt(K_ii K_jj)
+ * of the element matrix itself, independent of the quadrature rule.
  */
 static double entry_scale(const double *Ka, int nd, int i, int j) {
-    double cs = sqrt(Ka[i * nd + i] * Ka[j * nd + j]);
+    int jj = g_mutation == 13 ? i : j; /* planted mistake (13): the floor from row i's diagonal twice */
+    double cs = sqrt(Ka[i * nd + i] * Ka[jj * nd + jj]);
     return Ka[i * nd + j] > cs ? Ka[i * nd + j] : cs;
 }
 
@@ -364,7 +373,7 @@ int oracle_element_vector_abs(int dim, int p, int pf, const double *xv, const do
         double f = 0.0, fa = 0.0;
         for (int k = 0; k < nf; k++) {
             f += fe[k] * psi[k];
-            fa += fabs(fe[k] * psi[k]);
+            fa += g_mutation == 15 ? fe[k] * psi[k] : fabs(fe[k] * psi[k]); /* (15): signed terms */
         }
         for (int i = 0; i < nd; i++) {
             b[i] += wts[q] * adet * f * phi[i];
