@@ -197,6 +197,8 @@ fe_status fe_sparsity_destroy(fe_sparsity *sp);
  * FE_ERANGE (a map value outside its target set), FE_EUNSUPPORTED, FE_ECUDA.
  * Synchronises cuda_stream (it reads nnz).  The first call on a device looks up the array's
  * device address with that device current; make it before any stream capture on that device.
+ * The address is kept for the life of the process: after cudaDeviceReset on that device (which
+ * unloads the module and its array) this entry point must not be called again.
  * All calls share the array and it keeps the last call's contents (each call clears what must
  * start at zero); calls that overlap on the GPU race on it, so serialise them. */
 fe_status fe_sparsity_build_noalloc(const int32_t *rmap, int arity_r, const int32_t *cmap, int arity_c, int64_t ncell,

@@ -9,9 +9,11 @@
 // The array (kScratchBytes, about 23 MB) is part of the module and stays resident on every device
 // that loads the library until the process exits.  Its device address is looked up once per
 // device, with that device current, on the first call made on that device; make that first call
-// before any stream capture.  All calls share the array and it keeps the last call's contents:
-// everything that must start at zero is cleared by each call, and calls that overlap on the GPU
-// (on different streams, or from several host threads) race on it.
+// before any stream capture.  The address is kept until the process exits, so a cudaDeviceReset
+// (which unloads the module and the array with it) ends this entry point's use on that device.
+// All calls share the array and it keeps the last call's contents: everything that must start at
+// zero is cleared by each call, and calls that overlap on the GPU (on different streams, or from
+// several host threads) race on it.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>

@@ -346,6 +346,15 @@ def sparsity_build_noalloc(rmap: torch.Tensor, cmap: torch.Tensor, nrows: int, n
     cmap = _dev_tensor(cmap, torch.int32, "cmap")
     rowptr = _dev_tensor(rowptr, torch.int64, "rowptr")
     lut = _dev_tensor(lut, torch.uint8, "lut")
+    # the C entry point sees raw pointers only: every buffer's extent is checked here
+    if rmap.dim() != 2 or cmap.dim() != 2 or rmap.shape[0] != cmap.shape[0]:
+        raise ValueError(f"rmap and cmap must be [ncell][arity] with equal ncell, got {tuple(rmap.shape)} "
+                         f"and {tuple(cmap.shape)}")
+    if rowptr.numel() < int(nrows) + 1:
+        raise ValueError(f"rowptr holds {rowptr.numel()} entries, needs nrows + 1 = {int(nrows) + 1}")
+    need = rmap.shape[0] * rmap.shape[1] * cmap.shape[1]
+    if lut.numel() < need:
+        raise ValueError(f"lut holds {lut.numel()} bytes, needs ncell * arity_r * arity_c = {need}")
     cap = 0
     cptr = None
     if colidx is not None:

@@ -73,3 +73,13 @@ def test_no_cpu_fallback(lib):
     with pytest.raises(TypeError, match="CUDA tensor"):
         fe.sparsity_build_noalloc(host, host, 4, 4, torch.zeros(5, dtype=torch.int64), None,
                                   torch.zeros(36, dtype=torch.uint8))
+
+
+def test_noalloc_sources_name_no_allocator():
+    """fe_sparsity_build_noalloc and the sparsity launchers it calls (fe_sparsity.cu) name no
+    device allocation or free routine: their scratch is the static array only."""
+    csrc = os.path.join(ROOT, "paper_1501_01809_gb300", "csrc")
+    pat = re.compile(r"\b(cudaMalloc\w*|cudaFree\w*|cuMemAlloc\w*|cuMemFree\w*|dev_alloc|dev_free|malloc|free)\s*\(")
+    for name in ("fe_noalloc.cu", "fe_sparsity.cu"):
+        src = re.sub(r"//[^\n]*|/\*.*?\*/", "", open(os.path.join(csrc, name)).read(), flags=re.S)
+        assert not pat.findall(src), (name, pat.findall(src))

@@ -4,7 +4,8 @@ Such callers (code whose device memory is a budget owned by another runtime, or 
 afford cudaMalloc's latency and device-wide synchronisation) pass every buffer in; the kernels'
 scratch is a fixed static device array.  This checks, through the C ABI, that two calls in a row
 (different meshes, so the shared scratch is reused) give exactly the pattern and lookup table of
-fe_sparsity_build, and that the size query and the size limits behave as documented.  The file
+fe_sparsity_build, that calls after the first allocate nothing, and that the size query, the
+size limits and the buffer-extent checks behave as documented.  The file
 is named to be collected last; it also runs alone in a fresh process.
 """
 import numpy as np
@@ -59,6 +60,28 @@ def test_two_calls_match_the_allocating_build(env):
             np.testing.assert_array_equal(a, b)
 
 
+def test_second_call_allocates_nothing(env):
+    """After the first call (module loaded, scratch address looked up), a further build changes
+    neither torch's allocator statistics nor the device's free memory."""
+    torch, fe = env
+    pr = PB.make(3, 2, 5, 0.2, seed=4)
+    dev = torch.device("cuda", 0)
+    m = torch.from_numpy(np.ascontiguousarray(pr.cmap)).to(dev)
+    nd = pr.cmap.shape[1]
+    rowptr = torch.empty(pr.nnodes + 1, dtype=torch.int64, device=dev)
+    lut = torch.empty(pr.mesh.ncell * nd * nd, dtype=torch.uint8, device=dev)
+    nnz = fe.sparsity_build_noalloc(m, m, pr.nnodes, pr.nnodes, rowptr, None, lut)
+    colidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+    fe.sparsity_build_noalloc(m, m, pr.nnodes, pr.nnodes, rowptr, colidx, lut)
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(dev), torch.cuda.memory_reserved(dev), torch.cuda.mem_get_info(dev)[0])
+    for _ in range(2):
+        assert fe.sparsity_build_noalloc(m, m, pr.nnodes, pr.nnodes, rowptr, colidx, lut) == nnz
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(dev), torch.cuda.memory_reserved(dev), torch.cuda.mem_get_info(dev)[0])
+    assert after == before, (before, after)
+
+
 def test_small_colidx_and_limits_are_rejected(env):
     torch, fe = env
     pr = PB.make(2, 1, 8, 0.0)
@@ -75,3 +98,10 @@ def test_small_colidx_and_limits_are_rejected(env):
     with pytest.raises(fe.FeError) as ei:
         fe.sparsity_build_noalloc(m, m, big_rows, big_rows, rp_big, None, lut)
     assert ei.value.code == fe.FE_EUNSUPPORTED and "static scratch" in str(ei.value)
+    # buffers too small for the stated sizes are refused before any device work
+    with pytest.raises(ValueError, match="rowptr holds"):
+        fe.sparsity_build_noalloc(m, m, pr.nnodes + 5, pr.nnodes + 5, rowptr, None, lut)
+    with pytest.raises(ValueError, match="lut holds"):
+        fe.sparsity_build_noalloc(m, m, pr.nnodes, pr.nnodes, rowptr, None, lut[:-1])
+    with pytest.raises(ValueError, match="equal ncell"):
+        fe.sparsity_build_noalloc(m, m[:-1], pr.nnodes, pr.nnodes, rowptr, None, lut)
