@@ -174,6 +174,13 @@ fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols,
                           const int64_t **rowptr, const int32_t **colidx);
 /* Device pointer to the uint8 lookup table [ncell][arity_r][arity_c] (rank within the row). */
 fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut);
+/* Caps the row pass of later builds and rebuilds of sp (the per-row sort of Sec. 4.4.3's pattern
+ * construction) at blocks_per_sm resident blocks of 256 threads per SM, as a persistent grid; 0
+ * (the default) launches as many as fit.  The row pass is bound by integer instruction issue and
+ * fills every SM's registers; a cap of 4 leaves room on each SM for a kernel launched on another
+ * stream at the same time, e.g. the FP64 matrix-free action, whose FP64 pipe the row pass does not
+ * use.  The result is the same for every cap.  Errors: FE_EHANDLE, FE_EINVAL (negative). */
+fe_status fe_sparsity_set_row_blocks(fe_sparsity *sp, int blocks_per_sm);
 fe_status fe_sparsity_destroy(fe_sparsity *sp);
 
 /* ---------------------------------------------------------------- Sparsity without allocation

@@ -337,6 +337,108 @@ def _upper(nd):
     return [(i, j) for i in range(nd) for j in range(i, nd)]
 
 
+# ------------------------------------------------------------------ common subexpressions
+# The stiffness entries are linear forms in the Lam_mn with rational coefficients, and many share
+# a pair of terms in the same ratio (K_ij = c (Lam_a + r Lam_b) + ...).  In the spirit of COFFEE's
+# expression rewriting (Sec. 4.5: fewer floating-point operations), the generator extracts such
+# pairs greedily, most frequent first: w = Lam_a + r Lam_b costs one multiply-add and saves one in
+# every entry that uses it.  The rewriting is exact in rational arithmetic (eval_plan checks it);
+# in floating point it reorders the sums of the same terms, with no coefficient larger than the
+# original ones.
+
+def cse_plan(forms):
+    """forms: list of dicts {var: Fraction} (var = int index of Lam).  Returns (temps, reduced):
+    temps[n] = (a, b, r) defines w_n = a + r b (a, b an int Lam index or ('w', k), k < n);
+    reduced[u] = list of (var, coefficient) over Lam indices and temps, in a fixed order."""
+    fs = [dict(f) for f in forms]
+    temps = []
+
+    def key(v):
+        return (0, v) if isinstance(v, int) else (1, v[1])
+
+    while True:
+        cnt = {}
+        for f in fs:
+            ks = sorted(f, key=key)
+            for ia in range(len(ks)):
+                for ib in range(ia + 1, len(ks)):
+                    a, b = ks[ia], ks[ib]
+                    t = (a, b, f[b] / f[a])
+                    cnt[t] = cnt.get(t, 0) + 1
+        if not cnt:
+            break
+        best = max(cnt.items(), key=lambda kv: (kv[1], [-x for x in key(kv[0][0])], [-x for x in key(kv[0][1])]))
+        (a, b, r), n = best
+        if n < 2:
+            break
+        w = ("w", len(temps))
+        temps.append((a, b, r))
+        for f in fs:
+            if a in f and b in f and f[b] / f[a] == r:
+                f[w] = f.pop(a)
+                f.pop(b)
+    return temps, [sorted(f.items(), key=lambda kv: key(kv[0])) for f in fs]
+
+
+def eval_plan(temps, reduced, lam):
+    """The plan evaluated in exact arithmetic for values lam[k] (a test of the rewriting)."""
+    w = []
+    val = lambda v: lam[v] if isinstance(v, int) else w[v[1]]
+    for a, b, r in temps:
+        w.append(val(a) + r * val(b))
+    return [sum((c * val(v) for v, c in terms), F(0)) for terms in reduced]
+
+
+def _var(v, arr="Lam"):
+    return f"{arr}[{v}]" if isinstance(v, int) else f"w{v[1]}"
+
+
+def _chain(terms, addend=None, arr="Lam"):
+    """Multiply-add chain for sum_k c_k v_k (+ addend): c = +-1 folded into moves and negations
+    when there is no addend; with an addend every term is one multiply-add."""
+    if addend is not None:
+        expr = addend
+        for v, c in terms:
+            expr = f"Ops::fmac({_var(v, arr)}, {_num(c)}, {expr})"
+        return expr
+    (v0, c0), rest = terms[0], terms[1:]
+    if c0 == 1:
+        expr = _var(v0, arr)
+    elif c0 == -1:
+        expr = f"Ops::neg({_var(v0, arr)})"
+    else:
+        expr = f"Ops::mulc({_var(v0, arr)}, {_num(c0)})"
+    for v, c in rest:
+        expr = f"Ops::fmac({_var(v, arr)}, {_num(c)}, {expr})"
+    return expr
+
+
+def _emit_temps(temps, indent="    "):
+    out = []
+    for n, (a, b, r) in enumerate(temps):
+        rhs = f"Ops::add({_var(a)}, {_var(b)})" if r == 1 else f"Ops::fmac({_var(b)}, {_num(r)}, {_var(a)})"
+        out.append(f"{indent}const typename Ops::T w{n} = {rhs};")
+    return out
+
+
+def stiffness_forms(dim: int, p: int):
+    """Each upper-triangle stiffness entry as {Lam index: coefficient}."""
+    B = stiffness_tensor(dim, p)
+    pairs = _lam_pairs(dim)
+    nd = len(B[pairs[0]])
+    return [{k: B[mn][i][j] for k, mn in enumerate(pairs) if B[mn][i][j] != 0} for (i, j) in _upper(nd)]
+
+
+def mass_values(dim: int, p: int):
+    """The distinct nonzero entries of the upper-triangle mass tensor, in first-use order."""
+    M = mass_tensor(dim, p)
+    vals = []
+    for (i, j) in _upper(len(M)):
+        if M[i][j] != 0 and M[i][j] not in vals:
+            vals.append(M[i][j])
+    return vals
+
+
 def emit_element(dim: int, p: int) -> str:
     B = stiffness_tensor(dim, p)
     M = mass_tensor(dim, p)
@@ -354,50 +456,72 @@ def emit_element(dim: int, p: int) -> str:
     lines.append(f"  static constexpr int STIFF_TERMS = {nterms};")
     # upper-triangle index tables (host+device constexpr helper via switch-free arrays are avoided)
     lines.append("  // K[u] for u over the upper triangle (i <= j), row-major; Lam[k] over pairs (m <= n)")
+    temps, reduced = cse_plan(stiffness_forms(dim, p))
+    mvals = mass_values(dim, p)
+    lines.append(f"  static constexpr int STIFF_OPS = {len(temps) + sum(len(t) for t in reduced)};  // after rewriting")
     # stiffness
     lines.append("  template <class Ops> __device__ __forceinline__ static void stiffness_upper("
                  "const typename Ops::T* Lam, typename Ops::T* K) {")
-    for u, (i, j) in enumerate(up):
-        terms = [(k, B[mn][i][j]) for k, mn in enumerate(pairs) if B[mn][i][j] != 0]
-        if not terms:
-            lines.append(f"    K[{u}] = Ops::zero();")
-            continue
-        lines.append(f"    K[{u}] = {_term_chain(terms, 'Lam')};")
+    lines += _emit_temps(temps)
+    for u, terms in enumerate(reduced):
+        lines.append(f"    K[{u}] = {_chain(terms) if terms else 'Ops::zero()'};")
     lines.append("  }")
-    # mass added
-    lines.append("  template <class Ops> __device__ __forceinline__ static void mass_upper_add("
-                 "const typename Ops::T& vol, typename Ops::T* K) {")
-    for u, (i, j) in enumerate(up):
-        if M[i][j] != 0:
-            lines.append(f"    K[{u}] = Ops::fmac(vol, {_num(M[i][j])}, K[{u}]);")
+    # Helmholtz: the distinct mass products |T| M first, each entry's chain starting from its own
+    lines.append("  template <class Ops> __device__ __forceinline__ static void helmholtz_upper("
+                 "const typename Ops::T* Lam, const typename Ops::T& vol, typename Ops::T* K) {")
+    lines += _emit_temps(temps)
+    for q, c in enumerate(mvals):
+        lines.append(f"    const typename Ops::T m{q} = Ops::mulc(vol, {_num(c)});")
+    for u, ((i, j), terms) in enumerate(zip(up, reduced)):
+        mq = f"m{mvals.index(M[i][j])}" if M[i][j] != 0 else None
+        if terms:
+            lines.append(f"    K[{u}] = {_chain(terms, mq)};")
+        else:
+            lines.append(f"    K[{u}] = {mq or 'Ops::zero()'};")
     lines.append("  }")
     lines.append("  template <class Ops> __device__ __forceinline__ static void mass_upper("
                  "const typename Ops::T& vol, typename Ops::T* K) {")
+    for q, c in enumerate(mvals):
+        lines.append(f"    const typename Ops::T m{q} = Ops::mulc(vol, {_num(c)});")
     for u, (i, j) in enumerate(up):
-        lines.append(f"    K[{u}] = Ops::mulc(vol, {_num(M[i][j])});")
+        lines.append(f"    K[{u}] = {'m' + str(mvals.index(M[i][j])) if M[i][j] != 0 else 'Ops::zero()'};")
     lines.append("  }")
     # fused action: each K_ij is formed and consumed at once (y_i += K_ij x_j, y_j += K_ij x_i), so the
-    # element matrix is never live as a whole
+    # element matrix is never live as a whole; y is written, not incremented (the first contribution
+    # to each y_i is a product)
     lines.append("  template <class Ops, bool STIFF, bool MASS> __device__ __forceinline__ static void action_upper("
                  "const typename Ops::T* Lam, const typename Ops::T& vol, const typename Ops::T* x, typename Ops::T* y) {")
     lines.append("    typename Ops::T k;")
-    for u, (i, j) in enumerate(up):
-        terms = [(kk, B[mn][i][j]) for kk, mn in enumerate(pairs) if B[mn][i][j] != 0]
-        m = M[i][j]
-        parts = []
-        if terms:
-            parts.append(f"if constexpr (STIFF) {{ k = {_term_chain(terms, 'Lam')}; }} else {{ k = Ops::zero(); }}")
-        else:
-            parts.append("k = Ops::zero();")
-        if m != 0:
-            parts.append(f"if constexpr (MASS) {{ k = Ops::fmac(vol, {_num(m)}, k); }}")
-        if not terms and m == 0:
-            continue
-        guard = "" if terms and m != 0 else ("if constexpr (STIFF) " if terms else "if constexpr (MASS) ")
-        body = " ".join(parts) + f" y[{i}] = Ops::fma3(k, x[{j}], y[{i}]);"
-        if i != j:
-            body += f" y[{j}] = Ops::fma3(k, x[{i}], y[{j}]);"
-        lines.append(f"    {guard}{{ {body} }}")
+    for cond, st, ms in [("STIFF && MASS", True, True), ("STIFF", True, False), ("MASS", False, True)]:
+        lines.append(f"    {'if' if st and ms else 'else if'} constexpr ({cond}) {{")
+        if st:
+            lines += _emit_temps(temps, "      ")
+        if ms:
+            for q, c in enumerate(mvals):
+                lines.append(f"      const typename Ops::T m{q} = Ops::mulc(vol, {_num(c)});")
+        touched = set()
+
+        def acc(i, j):
+            if i in touched:
+                return f"y[{i}] = Ops::fma3(k, x[{j}], y[{i}]);"
+            touched.add(i)
+            return f"y[{i}] = Ops::mul(k, x[{j}]);"
+
+        for u, ((i, j), terms) in enumerate(zip(up, reduced)):
+            m = M[i][j]
+            mq = f"m{mvals.index(m)}" if (ms and m != 0) else None
+            terms = terms if st else []
+            if not terms and not mq:
+                continue
+            kk = _chain(terms, mq) if terms else mq
+            body = f"k = {kk}; " + acc(i, j)
+            if i != j:
+                body += " " + acc(j, i)
+            lines.append(f"      {{ {body} }}")
+        for i in range(nd):
+            if i not in touched:
+                lines.append(f"      y[{i}] = Ops::zero();")
+        lines.append("    }")
     lines.append("  }")
     # upper index maps as constexpr functions
     lines.append("  __host__ __device__ static constexpr int upper_index(int i, int j) {")

@@ -99,6 +99,9 @@ fe_status check_device_flags(fe_ctx *c, const char *where) {
     FE_CHECK_CUDA(cudaMemcpyAsync(c->d_err, z, sizeof z, cudaMemcpyHostToDevice, c->stream), where);
     FE_CHECK_CUDA(cudaStreamSynchronize(c->stream), where);
     if (h[0] & fe::ERR_RANGE) return fail(FE_ERANGE, "%s: a map value lies outside its target set (first index %d)", where, h[1]);
+    if (h[0] & fe::ERR_LUT)
+      return fail(FE_ERANGE, "%s: a lookup-table entry lies beyond its CSR row (cell %d); the entry was skipped", where,
+                  h[1]);
     if (h[0] & fe::ERR_NNZ_CHANGED) return fail(FE_EINVAL, "%s: the rebuilt pattern has a different nnz", where);
     if (h[0] & fe::ERR_TC_TIMEOUT)
       return fail(FE_ETIMEOUT, "%s: a tensor-core product did not complete in time (block %d)", where, h[1]);
@@ -431,6 +434,13 @@ fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols,
 fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut) {
   if (!valid(sp) || !lut) return fail(FE_EHANDLE, "fe_sparsity_lut: invalid sparsity");
   *lut = sp->lut;
+  return ok();
+}
+
+fe_status fe_sparsity_set_row_blocks(fe_sparsity *sp, int blocks_per_sm) {
+  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_set_row_blocks: invalid sparsity");
+  if (blocks_per_sm < 0) return fail(FE_EINVAL, "fe_sparsity_set_row_blocks: negative blocks per SM");
+  sp->row_blocks_per_sm = blocks_per_sm;
   return ok();
 }
 

@@ -143,12 +143,13 @@ __global__ void __launch_bounds__(kTcThreads) k_mat_push_tc_kappa_p4(const AsmAr
     for (int m = w; m < kTcM; m += kTcThreads / 32) {
       const int64_t e = blockIdx.x * (int64_t)kTcM + m;
       if (e >= a.ncell) break;  // warp-uniform
-      int64_t rp = 0;
+      int64_t rp = 0, rl = 0;
       bool ok = true;
       if (lane < ND) {
         const int32_t r = a.map[e * ND + lane];
         ok = !a.checks || (r >= 0 && r < a.nrows);  // a bad value was flagged when the cell was built
         if (ok) rp = a.rowptr[r];
+        if (ok && a.checks) rl = a.rowptr[r + 1] - rp;
       }
       if (!__all_sync(0xffffffffu, ok)) continue;
       const uint8_t *L = a.lut + e * (ND * ND);
@@ -158,10 +159,14 @@ __global__ void __launch_bounds__(kTcThreads) k_mat_push_tc_kappa_p4(const AsmAr
         const int q = 32 * k + lane;
         const int i = q / ND, j = q - (q / ND) * ND;
         const int64_t base = __shfl_sync(0xffffffffu, rp, i < ND ? i : 0);
+        const int64_t len = __shfl_sync(0xffffffffu, rl, i < ND ? i : 0);
         if (q < ND * ND) {
           const int lo = i < j ? i : j, hi = i < j ? j : i;
           const int n = lo * ND - lo * (lo - 1) / 2 + (hi - lo);  // upper-triangle index of (lo, hi)
-          red_add_f64(a.vals + base + L[q], f32_to_f64_exact(Sm[n]));
+          if (a.checks && L[q] >= len)  // check mode: a lookup-table entry beyond its row is skipped
+            flag(a.err, ERR_LUT, e);
+          else
+            red_add_f64(a.vals + base + L[q], f32_to_f64_exact(Sm[n]));
         }
       }
     }

@@ -12,7 +12,8 @@ constexpr uint32_t kMagicCtx = 0xFE0C7A11u, kMagicSet = 0xFE05E7u, kMagicMap = 0
                    kMagicKer = 0xFE0CE2u, kDead = 0xDEADu;
 
 // device error-flag bits (ctx->d_err[0]); d_err[1] keeps the first offending index (low 32 bits)
-enum : int { ERR_RANGE = 1, ERR_ROW_TOO_LONG = 2, ERR_NNZ_CHANGED = 4, ERR_CAND_OVERFLOW = 8, ERR_TC_TIMEOUT = 16 };
+enum : int { ERR_RANGE = 1, ERR_ROW_TOO_LONG = 2, ERR_NNZ_CHANGED = 4, ERR_CAND_OVERFLOW = 8, ERR_TC_TIMEOUT = 16,
+              ERR_LUT = 32 };
 
 // Rows of the CSR pattern are limited to 256 entries so the lookup table fits a byte.
 constexpr int kMaxRowLen = 256;
@@ -78,6 +79,7 @@ struct fe_sparsity {
   int maxrow;        // longest row (entries), known after build
   void *vstage;      // staging of element vectors for pull action / linear form (lazily allocated)
   size_t vstage_bytes;
+  int row_blocks_per_sm;  // 0: the row pass launches as many blocks as fit; else a persistent grid
 };
 
 struct fe_mat {

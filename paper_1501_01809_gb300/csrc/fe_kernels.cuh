@@ -33,8 +33,7 @@ __device__ __forceinline__ void element_upper(const typename Ops::T *Lam, const 
   } else if constexpr (FORM == FE_FORM_LAPLACE) {
     E::template stiffness_upper<Ops>(Lam, K);
   } else if constexpr (FORM == FE_FORM_HELMHOLTZ) {
-    E::template stiffness_upper<Ops>(Lam, K);
-    E::template mass_upper_add<Ops>(vol, K);
+    E::template helmholtz_upper<Ops>(Lam, vol, K);
   } else {
     constexpr int NL = Geo<DIM>::NLAM;
     typename Ops::T KL[(DIM + 1) * NL];
@@ -118,6 +117,19 @@ __device__ __forceinline__ void mat_push_cell(const AsmArgs &a, int64_t e) {
 #pragma unroll
   for (int u = 0; u < E::NUP; u++) Kd[u] = Ops::to_f64(K[u]);
   const uint8_t *L = a.lut + e * (ND * ND);
+  if (a.checks) {  // check mode: every lookup-table entry must lie inside its row (Sec. 4.4.1, INC)
+#pragma unroll
+    for (int i = 0; i < ND; i++) {
+      const int64_t b = a.rowptr[rows[i]], len = a.rowptr[rows[i] + 1] - b;
+#pragma unroll
+      for (int j = 0; j < ND; j++) {
+        const int q = L[i * ND + j];
+        if (q < len) red_add_f64(a.vals + b + q, Kd[E::upper_index(i, j)]);
+        else flag(a.err, ERR_LUT, e);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < ND; i++) {
     double *rowv = a.vals + a.rowptr[rows[i]];
@@ -193,8 +205,6 @@ __global__ void __launch_bounds__(kPushThreads, ActionOcc<Ops>::kMinBlocks) k_ac
       for (int j = 1; j < ND; j++) ye[i] = Ops::fma3(K[E::upper_index(i, j)], xe[j], ye[i]);
     }
   } else {
-#pragma unroll
-    for (int i = 0; i < ND; i++) ye[i] = Ops::zero();
     E::template action_upper<Ops, FORM != FE_FORM_MASS, FORM != FE_FORM_LAPLACE>(Lam, vol, xe, ye);
   }
 #pragma unroll
@@ -363,8 +373,6 @@ __global__ void __launch_bounds__(kPushThreads) k_action_elem(const AsmArgs a, t
       for (int j = 1; j < ND; j++) ye[i] = Ops::fma3(K[E::upper_index(i, j)], xe[j], ye[i]);
     }
   } else {
-#pragma unroll
-    for (int i = 0; i < ND; i++) ye[i] = Ops::zero();
     E::template action_upper<Ops, FORM != FE_FORM_MASS, FORM != FE_FORM_LAPLACE>(Lam, vol, xe, ye);
   }
   T *out = stage + e * ND;
@@ -414,7 +422,7 @@ template <int ND, class Ops>
 __global__ void k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr, const int32_t *__restrict__ adj,
                            const int64_t *__restrict__ rowptr, const uint8_t *__restrict__ lut,
                            const typename Ops::T *__restrict__ stage, double *__restrict__ vals, int rowcap,
-                           int zero_first, int *err) {
+                           int zero_first, int *err, int checks) {
   using T = typename Ops::T;
   extern __shared__ __align__(16) unsigned char smp[];
   T *acc = reinterpret_cast<T *>(smp) + threadIdx.x;
@@ -435,6 +443,10 @@ __global__ void k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr, co
 #pragma unroll
       for (int j = 0; j < ND; j++) {
         const int q = L[j];
+        if (checks && q >= len) {  // check mode: a lookup-table entry beyond the row is skipped
+          flag(err, ERR_LUT, k / ND);
+          continue;
+        }
         acc[q * TB] = Ops::add(acc[q * TB], Krow[j]);
       }
     }
@@ -506,7 +518,8 @@ cudaError_t mat_pull(const AsmArgs &a, cudaStream_t s) {
   }
   if (a.nrows > 0)
     k_mat_pull<E::ND, Ops><<<pull_blocks(a.nrows, TB), TB, smem, s>>>(a.nrows, a.adjptr, a.adj, a.rowptr, a.lut, stage,
-                                                                       a.vals, a.rowcap, a.zero_first, a.err);
+                                                                       a.vals, a.rowcap, a.zero_first, a.err,
+                                                                       a.checks);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ SYMBOLS = [
     "fe_last_error", "fe_version", "fe_ctx_create", "fe_ctx_set_stream", "fe_ctx_set_allocator",
     "fe_ctx_set_checks", "fe_sync", "fe_ctx_destroy", "fe_set_create", "fe_set_size", "fe_set_destroy",
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
-    "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
+    "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_set_row_blocks", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
     "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_elem_matrices", "fe_action_stored", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
     "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
@@ -114,7 +114,7 @@ def load():
         "fe_sparsity_build": (I, [P, P, P, PP]), "fe_sparsity_rebuild": (I, [P]),
         "fe_sparsity_build_noalloc": (I, [P, I, P, I, I64, I64, I64, P, P, I64, P, C.POINTER(I64), P]),
         "fe_sparsity_csr": (I, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), PP, PP]),
-        "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_destroy": (I, [P]),
+        "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_set_row_blocks": (I, [P, I]), "fe_sparsity_destroy": (I, [P]),
         "fe_mat_create": (I, [P, P, PP]), "fe_mat_values": (I, [P, PP]), "fe_mat_zero": (I, [P]),
         "fe_mat_destroy": (I, [P]),
         "fe_kernel_create": (I, [P, C.POINTER(fe_form_desc), PP]), "fe_kernel_destroy": (I, [P]),
@@ -369,6 +369,11 @@ def sparsity_build_noalloc(rmap: torch.Tensor, cmap: torch.Tensor, nrows: int, n
                                             C.c_void_p(rowptr.data_ptr()), cptr, int(cap), C.c_void_p(lut.data_ptr()),
                                             C.byref(nnz), C.c_void_p(stream.cuda_stream)))
     return nnz.value
+
+
+def sparsity_set_row_blocks(sp: Sparsity, blocks_per_sm: int) -> None:
+    """fe_sparsity_set_row_blocks: persistent row pass of at most blocks_per_sm blocks per SM."""
+    _check(load().fe_sparsity_set_row_blocks(sp.ptr, int(blocks_per_sm)))
 
 
 def sparsity_csr(sp: Sparsity):

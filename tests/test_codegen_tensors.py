@@ -116,3 +116,28 @@ def test_tensor_core_kappa_table_layout():
         K[ju, iu] = K[iu, ju]
         want = O.element_matrix(2, 4, O.KAPPA_DIFFUSION, xv, kv)
         assert np.linalg.norm(K - want) <= 1e-6 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("dim,p", ELEMENTS)
+def test_rewritten_stiffness_is_exact(dim, p):
+    """The generator's common-subexpression rewriting of the stiffness entries (pairs of Lam terms
+    extracted into temporaries) gives exactly the original linear forms: evaluated in rational
+    arithmetic at random rational Lam it equals sum_k B_k Lam_k for every entry, and it uses no
+    more multiply-adds than the direct chains."""
+    from fractions import Fraction as F
+    forms = cg.stiffness_forms(dim, p)
+    temps, reduced = cg.cse_plan(forms)
+    rng = np.random.default_rng(7 * dim + p)
+    nlam = len(cg._lam_pairs(dim))
+    for _ in range(3):
+        lam = [F(int(rng.integers(-50, 51)), int(rng.integers(1, 17))) for _ in range(nlam)]
+        got = cg.eval_plan(temps, reduced, lam)
+        want = [sum((c * lam[k] for k, c in f.items()), F(0)) for f in forms]
+        assert got == want
+    assert len(temps) + sum(len(t) for t in reduced) <= sum(len(f) for f in forms)
+    # regrouping only: with every coefficient and ratio replaced by its absolute value, the plan
+    # gives sum_k |B_k| Lam_k at positive Lam, so no rounding error larger than the original
+    # terms' can arise (the parity tolerance scales with those terms)
+    absp = [(a, b, abs(r)) for a, b, r in temps], [[(v, abs(c)) for v, c in t] for t in reduced]
+    lam = [F(int(rng.integers(1, 51)), int(rng.integers(1, 17))) for _ in range(nlam)]
+    assert cg.eval_plan(*absp, lam) == [sum((abs(c) * lam[k] for k, c in f.items()), F(0)) for f in forms]
