@@ -93,6 +93,60 @@ def _peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+class _NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (ctypes) by a thread every few
+    milliseconds, so that even a timed region of tens of milliseconds gets tens of samples.
+    Read-only: it changes no setting of the GPU."""
+    # nvmlClocksEventReason bits
+    BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
+
+    def __init__(self, device_index, period_s=0.005):
+        import ctypes
+        import threading
+        self.ct, self.period = ctypes, period_s
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        rc = -1
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(device_index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h))
+        except Exception:
+            rc = -1
+        if rc != 0 and self.lib.nvmlDeviceGetHandleByIndex_v2(device_index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 else None
+        self.samples, self.stop = [], threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct = self.ct
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0 and \
+                    self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            self.stop.wait(self.period)
+
+    def start(self):
+        self.thread.start()
+
+    def finish(self):
+        self.stop.set()
+        self.thread.join(timeout=2)
+        sm = [c for c, _ in self.samples]
+        reasons = sorted({name for _, r in self.samples for bit, name in self.BITS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "sm_mhz_min": min(sm) if sm else None, "reasons": reasons, "samples": len(sm),
+                "source": f"NVML every {self.period * 1e3:.0f} ms during the timed region"}
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -104,6 +158,13 @@ class ClockSampler:
         self.path = os.path.join("/tmp", f"fe_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
+        self.nvml = None
+        try:
+            self.nvml = _NvmlSampler(self.dev)
+            self.nvml.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
@@ -114,6 +175,9 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
+        if self.nvml is not None:
+            self.result = self.nvml.finish()
+            return
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -123,6 +187,8 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        if self.nvml is not None:
+            return self.result
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         rows = []
@@ -142,7 +208,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi every 100 ms"}
 
 
 # --------------------------------------------------------------------------------------- ranks
@@ -239,6 +305,7 @@ def run_ours(args, wl, rank, world):
     strat = {"push": fe.STRATEGY_PUSH, "pull": fe.STRATEGY_PULL, "auto": fe.STRATEGY_AUTO}[args.strategy]
     prec = {"fp64": fe.PREC_FP64, "f32x2": fe.PREC_F32X2}[args.precision]
     K = fe.kernel_create(ctx, fe.FORM_HELMHOLTZ, wl["dim"], wl["p"], precision=prec, strategy=strat)
+    kcur = [K]  # the kernel the step uses (the labelled double-float extra swaps it)
     with torch.cuda.stream(stream):
         sp = fe.sparsity_build(ctx, M, M)
         A = fe.mat_create(ctx, sp)
@@ -246,6 +313,10 @@ def run_ours(args, wl, rank, world):
     vals = fe.mat_values(A)
 
     pull = args.strategy in ("pull", "auto")
+    # --row-blocks: the sparsity row pass as a persistent grid of that many blocks per SM (auto: 4
+    # when the action runs beside it, so that an action block fits on every SM next to it)
+    row_blocks = args.row_blocks if args.row_blocks >= 0 else (4 if args.overlap != "off" and not pull else 0)
+    fe.sparsity_set_row_blocks(sp, row_blocks)
     # The Mat zero and the push action depend on neither the rebuilt pattern nor the assembly, so with
     # --overlap they run on a second stream, concurrently with the sparsity rebuild (the pull action
     # reads the rebuilt incidence and stays on the main stream).
@@ -267,10 +338,10 @@ def run_ours(args, wl, rank, world):
                 fe.mat_zero(A_)
             if ev is not None:
                 ev[2].record(stream)
-            fe.assemble_mat(ctx, K, cells, A_, XY_, CM_, zero_first=pull)
+            fe.assemble_mat(ctx, kcur[0], cells, A_, XY_, CM_, zero_first=pull)
             if ev is not None:
                 ev[3].record(stream)
-            fe.action(ctx, K, cells, X_, Y_, M_, XY_, CM_, zero_first=True, sp=sp_)
+            fe.action(ctx, kcur[0], cells, X_, Y_, M_, XY_, CM_, zero_first=True, sp=sp_)
             if ev is not None:
                 ev[4].record(stream)
             return
@@ -310,10 +381,10 @@ def run_ours(args, wl, rank, world):
     # --graph: the whole step (rebuild, zero, assembly, action) captured once as a CUDA graph and
     # replayed, so the launch latency of its 17 kernels is paid once per graph instead of per kernel
     graph = None
-    use_graph = args.graph == "on" or (args.graph == "auto" and side is None and not pull)
+    use_graph = args.graph == "on" or (args.graph == "auto" and not pull)
     if use_graph:
-        if side is not None or pull:
-            raise SystemExit("--graph on: one stream and the push strategy only")
+        if pull:
+            raise SystemExit("--graph on: the push strategy only")
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=stream, capture_error_mode="thread_local"):
             step()
@@ -347,14 +418,18 @@ def run_ours(args, wl, rank, world):
     if dist:
         td.barrier()
     fe.sync(ctx)
-    phases = np.zeros(4)
-    for ev, sev in zip(evs, sevs):
-        if side is None:
-            for p in range(4):
-                phases[p] += ev[p].elapsed_time(ev[p + 1])
-        else:  # live durations of the concurrent phases (sparsity on the main stream, zero and action beside it)
-            phases += [ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(sev[0]), ev[2].elapsed_time(ev[3]),
-                       sev[0].elapsed_time(sev[1])]
+    def phase_sums(evs_, sevs_):
+        out = np.zeros(4)
+        for ev, sev in zip(evs_, sevs_):
+            if side is None:
+                for q in range(4):
+                    out[q] += ev[q].elapsed_time(ev[q + 1])
+            else:  # live durations of the concurrent phases (sparsity on the main stream, zero and action beside it)
+                out += [ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(sev[0]), ev[2].elapsed_time(ev[3]),
+                        sev[0].elapsed_time(sev[1])]
+        return out
+
+    phases = phase_sums(evs, sevs)
     per_step = sorted(ev[0].elapsed_time(ev[4]) for ev in evs)
     # back to back, the span of all steps; with flushes in between, the sum of the steps
     total_ms = evs[0][0].elapsed_time(evs[-1][4]) if flush is None else sum(per_step)
@@ -383,6 +458,58 @@ def run_ours(args, wl, rank, world):
     if dist:
         ms_step = max_over_ranks(ms_step, dev)
     phase_ms = phases / args.steps
+
+    # ------------------------------------------------------------------- labelled extra: double-float
+    # The same step with element tensors in FP32 pairs (double-float, about 2^-46 relative per
+    # operation) and FP64 global accumulation: a narrower arithmetic than the FP64 step of record,
+    # reported beside it with its own dtype, never as the headline.
+    f32x2 = None
+    if args.precision == "fp64" and graph is not None and not args.no_f32x2:
+        K32 = fe.kernel_create(ctx, fe.FORM_HELMHOLTZ, wl["dim"], wl["p"], precision=fe.PREC_F32X2, strategy=strat)
+        kcur[0] = K32
+        for _ in range(args.warmup):
+            step()
+        fe.sync(ctx)
+        torch.cuda.synchronize()
+        ph32 = np.zeros(4)
+        for k in range(args.steps):
+            flush_l2()
+            step(evs[k], sevs[k])
+        torch.cuda.synchronize()
+        ph32 = phase_sums(evs, sevs)
+        g32 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g32, stream=stream, capture_error_mode="thread_local"):
+            step()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g32.replay()
+        fe.sync(ctx)
+        torch.cuda.synchronize()
+        gev32 = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush_l2()
+            with torch.cuda.stream(stream):
+                gev32[k][0].record(stream)
+                g32.replay()
+                gev32[k][1].record(stream)
+        torch.cuda.synchronize()
+        fe.sync(ctx)
+        ms32 = (gev32[0][0].elapsed_time(gev32[-1][1]) if flush is None else
+                sum(a.elapsed_time(b) for a, b in gev32)) / args.steps
+        if dist:
+            ms32 = max_over_ranks(ms32, dev)
+        ph32 /= args.steps
+        f32x2 = {"value": job_throughput(mesh.ncell, world, ms32), "unit": "cells/s", "ms_per_step": ms32,
+                 "dtype": "f32x2 element / f64 accumulate",
+                 "precision": "element tensors in FP32 pairs (double-float, about 2^-46 relative), FP64 CSR and y",
+                 "phases_ms": {"sparsity": ph32[0], "zero": ph32[1], "assemble": ph32[2], "action": ph32[3]},
+                 "note": "labelled extra, not the step of record: same step and graph schedule, narrower element "
+                         "arithmetic"}
+        kcur[0] = K
+        del g32
+        # the step of record leaves A and y in FP64: restore them for the checks below
+        step()
+        fe.sync(ctx)
     # launches of libfe kernels per step: sparsity rebuild 13 (zero, count, scan x3, zero, fill, in-place
     # row pass, then the gated full row pass, scan x3 and compact, which return at once when no row
     # changed length); push: mat zero 1, assembly 1, action zero + action 2; pull: assembly 2
@@ -411,6 +538,7 @@ def run_ours(args, wl, rank, world):
                 XYs = fe.dat_create(ctx, verts, d_in[2])
                 Xs, Ys = fe.dat_create(ctx, nodes, d_in[3]), fe.dat_create(ctx, nodes, d_y)
                 sps = fe.sparsity_build(ctx, Ms, Ms)
+                fe.sparsity_set_row_blocks(sps, row_blocks)
                 As = fe.mat_create(ctx, sps)
             _, _, _, rps, cis = fe.sparsity_csr(sps)
             outs = [rps, cis, fe.mat_values(As), d_y]
@@ -505,8 +633,9 @@ def run_ours(args, wl, rank, world):
     ncell = mesh.ncell
     bytes_mat = ncell * (nd * 4 + (wl["dim"] + 1) * 4) + mesh.nvert * wl["dim"] * 8 + nnz * 8
     bytes_act = ncell * (nd * 4 + (wl["dim"] + 1) * 4) + mesh.nvert * wl["dim"] * 8 + 2 * nn * 8
-    # sparsity build: maps read once, incidence written/read once, pattern and lookup table written once
-    bytes_sp = (ncell * nd * 4 * 2 + (nn + 1) * 8 * 2 + ncell * nd * 4 * 2 + nnz * 4 + ncell * nd * nd)
+    # sparsity build, the method's own bytes: the map read once, rowptr, colidx and the lookup table
+    # written once (the incidence lists the design builds on the way are overhead, not counted)
+    bytes_sp = ncell * nd * 4 + (nn + 1) * 8 + nnz * 4 + ncell * nd * nd
     kern = {
         "sparsity": {"ms": phase_ms[0], "bytes": bytes_sp},
         "zero": {"ms": phase_ms[1], "bytes": nnz * 8 if not pull else 0},
@@ -539,24 +668,33 @@ def run_ours(args, wl, rank, world):
     fresh = bool(tr) and tr[1] == _src_hash(src_file)
     roof["traffic"] = tr[0] if fresh else None
     roof["binding"] = tr[2] if fresh else None
+    # every phase against its own binding roofline, beside the dominant one
+    roof["per_kernel"] = {k: ({"bound": "alu", "frac": v["fp64_frac"], "unit": "FP64 TFLOP/s"}
+                              if "fp64_frac" in v and v["flops"] / (FP64_PEAK_TFLOPS * 1e12) >
+                              v["bytes"] / (peaks["hbm_gbs"] * 1e9) else
+                              {"bound": "hbm", "frac": v.get("hbm_frac")}) for k, v in kern.items()}
     out = {
         "metric": METRIC, "value": job_throughput(ncell, world, ms_step), "unit": "cells/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32x2 element / f64 accumulate", "data": "synthetic",
         "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
                    "strategy": args.strategy,
-                   "schedule": ("Mat zero and action on a second stream, concurrent with the sparsity rebuild"
-                                if side is not None else
-                                "one CUDA graph per step (phases from a launch-by-launch pass)" if graph is not None
-                                else "serial on one stream"),
+                   "schedule": (("Mat zero and action on a second stream, concurrent with the sparsity rebuild "
+                                 f"(row pass capped at {row_blocks} blocks per SM)" if side is not None else
+                                 "serial on one stream") +
+                                (", one CUDA graph per step (phases from a launch-by-launch pass)"
+                                 if graph is not None else "")),
                    "precision": ("element tensors in FP32 pairs (double-float), FP64 global accumulation"
                                  if args.precision == "f32x2" else "FP64 throughout"),
                    "parallelism": f"replicas x{world} (independent meshes, no collective)",
                    "l2": ("inputs larger than L2 (CSR values + lookup table ~650 MB), no flush" if flush is None else
                           "L2 flushed between steps (256 MB written outside the timed intervals)")},
         "roofline": roof, "kernels": kern, "step_ms": step_stats, "gpu_launches": launches, "wall_s_timed": wall,
-        "clocks": clk.summary(), "e2e": e2e, "stored_action": stored,
+        "clocks": clk.summary(), "e2e": e2e, "stored_action": stored, "f32x2_step": f32x2,
     }
+    if out["clocks"].get("sm_mhz"):
+        out["clocks"]["ms_x_mhz"] = ms_step * out["clocks"]["sm_mhz"]
     return out, (mesh, cmap, nn, x)
 
 
@@ -630,7 +768,7 @@ def run_wave(args, wl, rank, world):
     out = {"metric": "cells/s stepped (explicit wave: action + lumped-mass updates per time step)",
            "value": job_throughput(mesh.ncell, world, ms), "unit": "cells/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2 element / f64 accumulate", "data": "synthetic",
            "config": {"workload": wl["name"], "cells_per_gpu": mesh.ncell, "nodes": nn,
                       "precision": ("action element tensors in FP32 pairs, FP64 state" if args.precision == "f32x2"
                                     else "FP64 throughout"),
@@ -724,7 +862,7 @@ def run_p1_sweep(args, wl, rank, world):
     out = {"metric": "cells/s assembled (P1 CSR assembly incl. zero), labelled extra sweep", "value":
            world * big["assemble_cells_per_s"], "unit": "cells/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": big["assemble_ms"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2 element / f64 accumulate", "data": "synthetic",
            "config": {"workload": wl["name"], "sweep": rows, "precision": args.precision,
                       "parallelism": f"replicas x{world}", "l2": "largest n: inputs larger than L2"},
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -963,7 +1101,7 @@ def run_batch(args, wl, rank, world):
         "metric": METRIC_BATCH, "value": job_throughput(ncell_tot, world, ms_step), "unit": "cells/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2 element / f64 accumulate", "data": "synthetic",
         "config": {"workload": wl["name"], "meshes": len(meshes), "cells_per_gpu": ncell_tot, "nnz": nnz_tot,
                    "precision": ("element tensors in FP32 pairs (double-float), FP64 global accumulation"
                                  if args.precision == "f32x2" else "FP64 throughout"),
@@ -1395,7 +1533,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="p2-3d", choices=sorted(WORKLOADS))
     ap.add_argument("--strategy", default="push", choices=["push", "pull", "auto"])
-    ap.add_argument("--precision", default="f32x2", choices=["fp64", "f32x2"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "f32x2"],
+                    help="element arithmetic: fp64 (the step of record) or f32x2 (double-float element tensors)")
+    ap.add_argument("--no-f32x2", action="store_true", help="skip the labelled double-float extra of the fp64 step")
     ap.add_argument("--cpu-cells", type=int, default=65536, help="oracle sample size for cpu_baseline")
     ap.add_argument("--ref-cells", type=int, default=8192, help="oracle sample per step for --impl reference")
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle seconds per step (batch workload)")
@@ -1407,6 +1547,9 @@ def main():
     ap.add_argument("--overlap", default="off", choices=["off", "on", "hi"],
                     help="p2-3d push: Mat zero and action on a second stream beside the sparsity rebuild "
                          "(hi: that stream at high priority)")
+    ap.add_argument("--row-blocks", type=int, default=-1,
+                    help="sparsity row pass: persistent grid of this many blocks per SM (0: as many as fit; "
+                         "-1: 4 with --overlap, else 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stored", action="store_true", help="skip the stored-matrix action measurement")
     ap.add_argument("--log", default=None, help="also append the JSON line to this JSONL file")

@@ -83,3 +83,38 @@ def test_push_inc_semantics(gpu, prec):
     fe.sync(g.ctx)
     y2 = ty.cpu().numpy()
     assert np.abs(y2 - 2 * y1).max() <= 1e-14 * np.abs(y1).max()
+
+
+@pytest.mark.parametrize("dim,p,form,prec,strategy", [  # push FP64, push double-float, pull, tensor cores
+    (3, 2, 3, 0, 1), (3, 2, 3, 1, 1), (3, 2, 3, 0, 2), (2, 4, 4, 3, 1)])
+def test_lookup_table_beyond_row_is_flagged(gpu, dim, p, form, prec, strategy):
+    """Check mode (fe_ctx_set_checks): a lookup-table entry that points beyond its CSR row is
+    reported as FE_ERANGE at fe_sync and its write is skipped, so no other row changes (the INC of
+    Sec. 4.4.1 stays inside the row the map names).  One byte of the library's table is poked from
+    the host side; this is a bounds check in the kernels, not a fault."""
+    from paper_1501_01809_gb300 import fe
+    pr = PB.make(dim, p, 4 if dim == 3 else 3, 0.2, seed=6, kappa_seed=3 if form == 4 else None)
+    g = PB.GpuProblem(pr, checks=True)
+    k = fe.kernel_create(g.ctx, form, dim, p, precision=prec, strategy=strategy)
+    A = fe.mat_create(g.ctx, g.sparsity())
+    fe.assemble_mat(g.ctx, k, g.cells, A, g.coords, g.coord_map, g.coeffs(form), zero_first=True)
+    fe.sync(g.ctx)
+    clean = fe.mat_values(A).cpu().numpy().copy()
+    nd = pr.cmap.shape[1]
+    lut = fe.sparsity_lut(g.sparsity(), pr.mesh.ncell, nd, nd)
+    e, i, j = pr.mesh.ncell // 2, 1, nd - 2
+    r = int(pr.cmap[e, i])
+    rp, _ = g.csr()
+    assert rp[r + 1] - rp[r] < 255
+    lut[e * nd * nd + i * nd + j] = 255
+    fe.assemble_mat(g.ctx, k, g.cells, A, g.coords, g.coord_map, g.coeffs(form), zero_first=True)
+    with pytest.raises(fe.FeError) as ei:
+        fe.sync(g.ctx)
+    assert ei.value.code == fe.FE_ERANGE and "lookup-table entry" in str(ei.value)
+    got = fe.mat_values(A).cpu().numpy()
+    outside = np.ones(len(clean), dtype=bool)
+    outside[rp[r]:rp[r + 1]] = False
+    tol = 0 if strategy == fe.STRATEGY_PULL else 1e-13 * np.abs(clean).max()
+    assert np.abs(got[outside] - clean[outside]).max() <= tol
+    # the skipped contribution is the only difference inside the row
+    assert np.count_nonzero(np.abs(got[~outside] - clean[~outside]) > 1e-13 * np.abs(clean).max()) <= 1
