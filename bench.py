@@ -313,10 +313,6 @@ def run_ours(args, wl, rank, world):
     vals = fe.mat_values(A)
 
     pull = args.strategy in ("pull", "auto")
-    # --row-blocks: the sparsity row pass as a persistent grid of that many blocks per SM (auto: 4
-    # when the action runs beside it, so that an action block fits on every SM next to it)
-    row_blocks = args.row_blocks if args.row_blocks >= 0 else (4 if args.overlap != "off" and not pull else 0)
-    fe.sparsity_set_row_blocks(sp, row_blocks)
     # The Mat zero and the push action depend on neither the rebuilt pattern nor the assembly, so with
     # --overlap they run on a second stream, concurrently with the sparsity rebuild (the pull action
     # reads the rebuilt incidence and stays on the main stream).
@@ -538,7 +534,6 @@ def run_ours(args, wl, rank, world):
                 XYs = fe.dat_create(ctx, verts, d_in[2])
                 Xs, Ys = fe.dat_create(ctx, nodes, d_in[3]), fe.dat_create(ctx, nodes, d_y)
                 sps = fe.sparsity_build(ctx, Ms, Ms)
-                fe.sparsity_set_row_blocks(sps, row_blocks)
                 As = fe.mat_create(ctx, sps)
             _, _, _, rps, cis = fe.sparsity_csr(sps)
             outs = [rps, cis, fe.mat_values(As), d_y]
@@ -680,8 +675,8 @@ def run_ours(args, wl, rank, world):
         "dtype": "f64" if args.precision == "fp64" else "f32x2 element / f64 accumulate", "data": "synthetic",
         "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
                    "strategy": args.strategy,
-                   "schedule": (("Mat zero and action on a second stream, concurrent with the sparsity rebuild "
-                                 f"(row pass capped at {row_blocks} blocks per SM)" if side is not None else
+                   "schedule": (("Mat zero and action on a second stream, concurrent with the sparsity rebuild"
+                                 if side is not None else
                                  "serial on one stream") +
                                 (", one CUDA graph per step (phases from a launch-by-launch pass)"
                                  if graph is not None else "")),
@@ -1134,15 +1129,20 @@ def make_serve_inputs(wl):
     return out
 
 
-def _serve_once(fe, ctx, wl, reqs, rate, max_active):
-    """One run of the request loop; arrival times are the unit-rate draws divided by rate (0: all at once)."""
+def _serve_once(fe, ctx, wl, reqs, rate, max_active, keyed=None):
+    """One run of the request loop; arrival times are the unit-rate draws divided by rate (0: all at once).
+    keyed (default: the served configuration, max_active > 1): requests name their mesh by (n, p), so
+    that requests on the same mesh share its device copy and sparsity; the plain path builds each
+    request's mesh for that request alone."""
+    keyed = max_active > 1 if keyed is None else keyed
     srv = fe.server_create(ctx, wl["budget"], max_active=max_active, iters_per_tick=wl["tick"], rtol=1e-8)
     ids, xs = [], []
     for r in reqs:
         x = np.empty(r["nn"])
         t = r["t1"] / rate if rate > 0 else 0.0
+        key = (r["n"] << 4 | r["p"]) if keyed else 0
         ids.append(fe.server_submit(srv, r["p"], r["cmap"], r["mesh"].cell_vertex, r["mesh"].coords, r["f"], r["bc"],
-                                    x, t))
+                                    x, t, mesh_key=key))
         xs.append(x)
     fe.server_run(srv)
     res = [fe.server_result(srv, i) for i in ids]
@@ -1155,6 +1155,8 @@ def _serve_once(fe, ctx, wl, reqs, rate, max_active):
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "mean_iters": float(np.mean([q["iters"] for q in res])), "all_converged": ok,
             "peak_bytes": st["peak_bytes"], "cg_launches": st["cg_launches"],
+            "mesh_cache": {"hits": st["cache_hits"], "misses": st["cache_misses"], "evictions": st["cache_evictions"],
+                           "sparsity_builds": st["sparsity_builds"]},
             "host_s": {"admit": st["admit_s"], "tick": st["tick_s"], "retire": st["retire_s"]}}, xs
 
 
@@ -1547,9 +1549,6 @@ def main():
     ap.add_argument("--overlap", default="off", choices=["off", "on", "hi"],
                     help="p2-3d push: Mat zero and action on a second stream beside the sparsity rebuild "
                          "(hi: that stream at high priority)")
-    ap.add_argument("--row-blocks", type=int, default=-1,
-                    help="sparsity row pass: persistent grid of this many blocks per SM (0: as many as fit; "
-                         "-1: 4 with --overlap, else 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stored", action="store_true", help="skip the stored-matrix action measurement")
     ap.add_argument("--log", default=None, help="also append the JSON line to this JSONL file")

@@ -174,13 +174,6 @@ fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols,
                           const int64_t **rowptr, const int32_t **colidx);
 /* Device pointer to the uint8 lookup table [ncell][arity_r][arity_c] (rank within the row). */
 fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut);
-/* Caps the row pass of later builds and rebuilds of sp (the per-row sort of Sec. 4.4.3's pattern
- * construction) at blocks_per_sm resident blocks of 256 threads per SM, as a persistent grid; 0
- * (the default) launches as many as fit.  The row pass is bound by integer instruction issue and
- * fills every SM's registers; a cap of 4 leaves room on each SM for a kernel launched on another
- * stream at the same time, e.g. the FP64 matrix-free action, whose FP64 pipe the row pass does not
- * use.  The result is the same for every cap.  Errors: FE_EHANDLE, FE_EINVAL (negative). */
-fe_status fe_sparsity_set_row_blocks(fe_sparsity *sp, int blocks_per_sm);
 fe_status fe_sparsity_destroy(fe_sparsity *sp);
 
 /* ---------------------------------------------------------------- Sparsity without allocation
@@ -393,6 +386,10 @@ typedef struct {
   const uint8_t *is_bc;       /* host [nnodes], non-zero on the Dirichlet boundary                      */
   double *x_out;              /* host [nnodes], the solution on completion                              */
   double arrival_s;           /* seconds after fe_server_run starts                                     */
+  uint64_t mesh_key;          /* 0, or a key the caller gives every request on the same mesh (same maps,
+                                 coordinates, degree and boundary flags): such requests share one device
+                                 copy of the mesh and its sparsity, kept across requests and evicted,
+                                 least recently used first, when admission needs the memory          */
 } fe_solve_request;
 typedef struct {
   int status;              /* FE_SOLVE_*                                                                */
@@ -408,6 +405,10 @@ typedef struct {
   double run_s;
   int64_t cg_launches;     /* kernels the CG engine launched (set-up, iterations, polls)                 */
   double admit_s, tick_s, retire_s;  /* host time spent admitting, iterating (launch + poll), retiring  */
+  int cache_hits, cache_misses, cache_evictions;  /* requests whose mesh was cached / built and cached;
+                                                      cached meshes freed to make room            */
+  int sparsity_builds;     /* sparsity builds run (one per mesh built, none on a cache hit)              */
+  size_t cache_bytes;      /* device bytes held by cached meshes at the end of the run                  */
 } fe_server_stats;
 fe_status fe_server_create(fe_ctx *ctx, const fe_server_config *cfg, fe_server **out);
 fe_status fe_server_submit(fe_server *srv, const fe_solve_request *req, int64_t *id);

@@ -437,13 +437,6 @@ fe_status fe_sparsity_lut(const fe_sparsity *sp, const uint8_t **lut) {
   return ok();
 }
 
-fe_status fe_sparsity_set_row_blocks(fe_sparsity *sp, int blocks_per_sm) {
-  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_set_row_blocks: invalid sparsity");
-  if (blocks_per_sm < 0) return fail(FE_EINVAL, "fe_sparsity_set_row_blocks: negative blocks per SM");
-  sp->row_blocks_per_sm = blocks_per_sm;
-  return ok();
-}
-
 fe_status fe_sparsity_destroy(fe_sparsity *sp) {
   if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_destroy: invalid sparsity");
   DeviceGuard g(sp->ctx->device);

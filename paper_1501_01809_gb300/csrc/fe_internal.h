@@ -79,7 +79,6 @@ struct fe_sparsity {
   int maxrow;        // longest row (entries), known after build
   void *vstage;      // staging of element vectors for pull action / linear form (lazily allocated)
   size_t vstage_bytes;
-  int row_blocks_per_sm;  // 0: the row pass launches as many blocks as fit; else a persistent grid
 };
 
 struct fe_mat {

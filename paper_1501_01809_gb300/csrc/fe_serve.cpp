@@ -41,14 +41,27 @@
 namespace fe {
 namespace {
 
-struct Holding {  // device objects of one admitted request
+// Device objects of one mesh: the inputs that define it (cell-node and cell-vertex maps,
+// coordinates, boundary flags) and its sparsity (pattern, lookup table, incidence).  Requests that
+// carry the same non-zero mesh_key share one (the cache, kept across requests until evicted under
+// the budget); a request without a key has a private one.
+struct MeshEntry {
+  uint64_t key = 0;
   fe_set *cells = nullptr, *nodes = nullptr, *verts = nullptr;
   fe_map *M = nullptr, *CM = nullptr;
-  fe_dat *XY = nullptr, *F = nullptr, *B = nullptr, *X = nullptr;
+  fe_dat *XY = nullptr;
   fe_sparsity *sp = nullptr;
+  void *d_map = nullptr, *d_cv = nullptr, *d_xy = nullptr, *d_bc = nullptr;
+  int refs = 0;           // admitted requests using it
+  uint64_t last_use = 0;  // admission counter at the last use (least recently used is evicted first)
+};
+
+struct Holding {  // device objects of one admitted request
+  MeshEntry *mesh = nullptr;
+  bool private_mesh = false;  // built for this request alone (no key): freed with it
+  fe_dat *F = nullptr, *B = nullptr, *X = nullptr;
   fe_mat *A = nullptr;
-  void *d_map = nullptr, *d_cv = nullptr, *d_xy = nullptr, *d_f = nullptr, *d_bc = nullptr, *d_b = nullptr,
-       *d_x = nullptr;
+  void *d_f = nullptr, *d_b = nullptr, *d_x = nullptr;
   int slot = -1;
   bool big = false;  // iterating in the large-system engine (high-priority stream)
 };
@@ -56,7 +69,8 @@ struct Holding {  // device objects of one admitted request
 struct Req {
   fe_solve_request in;
   fe_solve_result res;
-  size_t estimate;
+  size_t estimate;       // worst-case footprint, mesh included
+  size_t mesh_estimate;  // its mesh part (maps, coordinates, flags, sparsity)
   Holding h;
 };
 
@@ -77,11 +91,15 @@ struct Server {
   fe_kernel *klap[3] = {nullptr, nullptr, nullptr}, *ksrc[3] = {nullptr, nullptr, nullptr};
   fe_cg *cg = nullptr;
   std::vector<Req> reqs;
+  std::vector<MeshEntry *> meshes;  // the cache: entries with a key (private ones are not listed)
+  uint64_t admissions = 0;
+  int cache_hits = 0, cache_misses = 0, cache_evictions = 0, sparsity_builds = 0;
   // accounting
-  std::unordered_map<void *, std::pair<size_t, int64_t>> live;  // pointer -> (bytes, owner; -1 = server)
+  // pointer -> (bytes, owner; kOwnerServer = server tables, kOwnerCache = cached meshes, else request)
+  std::unordered_map<void *, std::pair<size_t, int64_t>> live;
   std::vector<size_t> owner_bytes;
   int64_t owner = -1;
-  size_t base_bytes = 0, live_bytes = 0, peak_bytes = 0, reserved = 0;
+  size_t base_bytes = 0, cache_bytes = 0, live_bytes = 0, peak_bytes = 0, reserved = 0;
   int estimate_misses = 0;
   double run_s = 0.0, admit_s = 0.0, tick_s = 0.0, retire_s = 0.0;
 };
@@ -112,6 +130,7 @@ struct fe_server {
 namespace fe {
 namespace {
 constexpr uint32_t kMagicServer = 0xFE05E2E5u;
+constexpr int64_t kOwnerServer = -1, kOwnerCache = -2;
 
 void *count_alloc(size_t bytes, void *user) {
   Server *s = static_cast<Server *>(user);
@@ -125,6 +144,7 @@ void *count_alloc(size_t bytes, void *user) {
   s->live_bytes += bytes;
   s->peak_bytes = std::max(s->peak_bytes, s->live_bytes);
   if (s->owner >= 0) s->owner_bytes[s->owner] += bytes;
+  else if (s->owner == kOwnerCache) s->cache_bytes += bytes;
   else s->base_bytes += bytes;
   return ptr;
 }
@@ -137,6 +157,7 @@ void count_free(void *ptr, void *user) {
     const int64_t o = it->second.second;
     s->live_bytes -= b;
     if (o >= 0) s->owner_bytes[o] -= b;
+    else if (o == kOwnerCache) s->cache_bytes -= b;
     else s->base_bytes -= b;
     s->live.erase(it);
   }
@@ -152,7 +173,7 @@ int nodes_p(int p) { return (p + 1) * (p + 2) / 2; }
 // Worst-case device bytes of one request (every allocation it makes, at its largest, while it
 // is built; nnz bounded by the cell-node incidences times the arity, a row's length by the
 // node's most frequent incidence times the arity).
-size_t estimate_bytes(const fe_solve_request &r) {
+size_t estimate_bytes(const fe_solve_request &r, size_t *mesh_part = nullptr) {
   const size_t nd = nodes_p(r.degree), ncell = r.ncell, nn = r.nnodes, nv = r.nvert;
   const size_t ninc = ncell * nd, nnz = ninc * nd;
   std::vector<int32_t> inc(nn, 0);
@@ -164,10 +185,12 @@ size_t estimate_bytes(const fe_solve_request &r) {
   const size_t nsl = (nn + 31) / 32, maxlen = std::min(nn, (size_t)maxinc * nd);
   const size_t sell = std::min(32 * nsl * maxlen, 32 * nsl * nn);
   auto a = [](size_t b) { return (std::max<size_t>(b, 16) + 255) & ~size_t(255); };
-  size_t t = 0;
-  t += a(4 * ninc) + a(12 * ncell) + a(16 * nv) + a(8 * nn) + a(nn) + a(8 * nn) + a(8 * nn);  // inputs, b, x
-  t += 2 * a(8 * (nn + 1)) + a(4 * ninc) + a(4 * nn) + a(4 * ninc * nd) + a(ninc * nd) +
+  size_t m = 0, t = 0;
+  m += a(4 * ninc) + a(12 * ncell) + a(16 * nv) + a(nn);                                        // mesh inputs
+  m += 2 * a(8 * (nn + 1)) + a(4 * ninc) + a(4 * nn) + a(4 * ninc * nd) + a(ninc * nd) +
        a(8 * scan_tmp_elems((int64_t)nn)) + a(4) + a(4 * nnz);                                  // sparsity
+  if (mesh_part) *mesh_part = m;
+  t += m + a(8 * nn) + a(8 * nn) + a(8 * nn);                                                   // f, b, x
   t += a(8 * nnz) + a(8 * ncell * nd * nd) + a(8 * ncell * nd);                                 // Mat, staging
   t += 5 * a(8 * nn) + a(24 * (nn / 512 + 1));  // CG vectors, tile partials (tiles of at least 512 rows)
   t += a(8 * (nsl + 1)) + a(4 * nsl) + a(8 * scan_tmp_elems((int64_t)nsl)) + a(8 * sell) + a(4 * sell);  // SELL
@@ -187,6 +210,19 @@ fe_status copy_in(Server *s, void **dst, const void *src, size_t bytes) {
   return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s->ctx->stream) == cudaSuccess ? FE_OK : FE_ECUDA;
 }
 
+// Frees a mesh entry's device objects (the caller has synchronised the streams that used them).
+void mesh_free(Server *s, MeshEntry *m) {
+  if (!m) return;
+  if (m->sp) fe_sparsity_destroy(m->sp);
+  if (m->XY) fe_dat_destroy(m->XY);
+  for (fe_map *x : {m->M, m->CM})
+    if (x) fe_map_destroy(x);
+  for (fe_set *t : {m->cells, m->nodes, m->verts})
+    if (t) fe_set_destroy(t);
+  for (void *p : {m->d_map, m->d_cv, m->d_xy, m->d_bc}) dev_free(s->ctx, p);
+  delete m;
+}
+
 void release(Server *s, Req &q) {
   Holding &h = q.h;
   const int64_t saved = s->owner;
@@ -194,60 +230,130 @@ void release(Server *s, Req &q) {
   if (h.slot >= 0) fe_cg_remove(h.big ? s->cgb : s->cg, h.slot);
   cudaStreamSynchronize(s->ctx->stream);
   if (h.A) fe_mat_destroy(h.A);
-  if (h.sp) fe_sparsity_destroy(h.sp);
-  for (fe_dat *d : {h.XY, h.F, h.B, h.X})
+  for (fe_dat *d : {h.F, h.B, h.X})
     if (d) fe_dat_destroy(d);
-  for (fe_map *m : {h.M, h.CM})
-    if (m) fe_map_destroy(m);
-  for (fe_set *t : {h.cells, h.nodes, h.verts})
-    if (t) fe_set_destroy(t);
-  for (void *p : {h.d_map, h.d_cv, h.d_xy, h.d_f, h.d_bc, h.d_b, h.d_x}) dev_free(s->ctx, p);
+  for (void *p : {h.d_f, h.d_b, h.d_x}) dev_free(s->ctx, p);
+  if (h.mesh) {
+    if (h.private_mesh) mesh_free(s, h.mesh);
+    else h.mesh->refs--;  // a cached mesh stays until evicted
+  }
   h = Holding();
   s->owner = saved;
 }
 
-// Build one request's system on the device and hand it to the CG engine.
+// Evicts unused cached meshes, least recently used first, until `need` more bytes fit in the
+// budget beside what is held; returns whether they fit.
+bool make_room(Server *s, size_t held, size_t need) {
+  auto fits = [&]() { return s->base_bytes + s->cache_bytes + held + need <= s->cfg.hbm_budget; };
+  while (!fits()) {
+    MeshEntry *victim = nullptr;
+    for (MeshEntry *m : s->meshes)
+      if (m->refs == 0 && (!victim || m->last_use < victim->last_use)) victim = m;
+    if (!victim) return false;
+    cudaStreamSynchronize(s->adm);
+    cudaStreamSynchronize(s->main_stream);
+    cudaStreamSynchronize(s->hi);
+    s->meshes.erase(std::find(s->meshes.begin(), s->meshes.end(), victim));
+    const int64_t saved = s->owner;
+    s->owner = kOwnerCache;
+    mesh_free(s, victim);
+    s->owner = saved;
+    s->cache_evictions++;
+  }
+  return true;
+}
+
+MeshEntry *find_mesh(Server *s, const fe_solve_request &r) {
+  if (r.mesh_key == 0) return nullptr;
+  for (MeshEntry *m : s->meshes)
+    if (m->key == r.mesh_key) return m;
+  return nullptr;
+}
+
+// Builds a mesh entry on the device: copies of the maps, coordinates and boundary flags, and the
+// sparsity (incidence, pattern, lookup table; its scratch columns are freed at once).
+fe_status mesh_build(Server *s, const fe_solve_request &r, MeshEntry *m) {
+  fe_ctx *c = s->ctx;
+  const int nd = nodes_p(r.degree);
+  SV_TRY(copy_in(s, &m->d_map, r.cell_node, sizeof(int32_t) * r.ncell * nd));
+  SV_TRY(copy_in(s, &m->d_cv, r.cell_vertex, sizeof(int32_t) * r.ncell * 3));
+  SV_TRY(copy_in(s, &m->d_xy, r.coords, sizeof(double) * r.nvert * 2));
+  SV_TRY(copy_in(s, &m->d_bc, r.is_bc, r.nnodes));
+  SV_TRY(fe_set_create(c, r.ncell, &m->cells));
+  SV_TRY(fe_set_create(c, r.nnodes, &m->nodes));
+  SV_TRY(fe_set_create(c, r.nvert, &m->verts));
+  SV_TRY(fe_map_create(c, m->cells, m->nodes, nd, (const int32_t *)m->d_map, 1, &m->M));
+  SV_TRY(fe_map_create(c, m->cells, m->verts, 3, (const int32_t *)m->d_cv, 1, &m->CM));
+  SV_TRY(fe_dat_create(c, m->verts, 2, (double *)m->d_xy, &m->XY));
+  SV_TRY(fe_sparsity_build(c, m->M, m->M, &m->sp));
+  s->sparsity_builds++;
+  dev_free(c, m->sp->coltmp);  // the build's scratch columns
+  m->sp->coltmp = nullptr;
+  return FE_OK;
+}
+
+// Build one request's system on the device and hand it to the CG engine.  Its mesh comes from
+// the cache when an entry with its key is there (no copies of the mesh, no sparsity build);
+// otherwise it is built, and kept in the cache when the request has a key.
 fe_status admit(Server *s, Req &q) {
   const fe_solve_request &r = q.in;
   Holding &h = q.h;
   fe_ctx *c = s->ctx;
-  const int nd = nodes_p(r.degree);
   cudaStream_t st = c->stream;
-  SV_TRY(copy_in(s, &h.d_map, r.cell_node, sizeof(int32_t) * r.ncell * nd));
-  SV_TRY(copy_in(s, &h.d_cv, r.cell_vertex, sizeof(int32_t) * r.ncell * 3));
-  SV_TRY(copy_in(s, &h.d_xy, r.coords, sizeof(double) * r.nvert * 2));
+  const int64_t self = s->owner;
+  MeshEntry *m = find_mesh(s, r);
+  if (m) {
+    s->cache_hits++;
+  } else {
+    m = new (std::nothrow) MeshEntry();
+    if (!m) return FE_ENOMEM;
+    m->key = r.mesh_key;
+    if (r.mesh_key != 0) {
+      s->cache_misses++;
+      s->meshes.push_back(m);
+      s->owner = kOwnerCache;  // its memory is the cache's from here on
+    } else {
+      h.private_mesh = true;
+    }
+    h.mesh = m;  // released with the request if the build fails
+    m->refs++;
+    const fe_status bs = mesh_build(s, r, m);
+    s->owner = self;
+    if (bs != FE_OK) {  // a partly built entry never stays in the cache: freed with the request
+      if (!h.private_mesh) {
+        s->meshes.erase(std::find(s->meshes.begin(), s->meshes.end(), m));
+        h.private_mesh = true;
+      }
+      return bs;
+    }
+    m->refs--;
+  }
+  h.mesh = m;
+  m->refs++;
+  m->last_use = ++s->admissions;
   SV_TRY(copy_in(s, &h.d_f, r.f, sizeof(double) * r.nnodes));
-  SV_TRY(copy_in(s, &h.d_bc, r.is_bc, r.nnodes));
   h.d_b = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
   h.d_x = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
   if (!h.d_b || !h.d_x) return FE_ENOMEM;
   if (cudaMemsetAsync(h.d_x, 0, sizeof(double) * r.nnodes, st) != cudaSuccess) return FE_ECUDA;
-  SV_TRY(fe_set_create(c, r.ncell, &h.cells));
-  SV_TRY(fe_set_create(c, r.nnodes, &h.nodes));
-  SV_TRY(fe_set_create(c, r.nvert, &h.verts));
-  SV_TRY(fe_map_create(c, h.cells, h.nodes, nd, (const int32_t *)h.d_map, 1, &h.M));
-  SV_TRY(fe_map_create(c, h.cells, h.verts, 3, (const int32_t *)h.d_cv, 1, &h.CM));
-  SV_TRY(fe_dat_create(c, h.verts, 2, (double *)h.d_xy, &h.XY));
-  SV_TRY(fe_dat_create(c, h.nodes, 1, (double *)h.d_f, &h.F));
-  SV_TRY(fe_dat_create(c, h.nodes, 1, (double *)h.d_b, &h.B));
-  SV_TRY(fe_dat_create(c, h.nodes, 1, (double *)h.d_x, &h.X));
-  SV_TRY(fe_sparsity_build(c, h.M, h.M, &h.sp));
-  SV_TRY(fe_mat_create(c, h.sp, &h.A));
-  SV_TRY(fe_assemble_mat(c, s->klap[r.degree], h.cells, h.A, 1, h.XY, h.CM, nullptr, 0));
-  fe_arg fa{h.F, h.M};
-  SV_TRY(fe_assemble_vec(c, s->ksrc[r.degree], h.cells, h.B, h.M, 1, h.XY, h.CM, &fa, 1, h.sp));
-  if (launch_dirichlet(r.nnodes, h.sp->rowptr, h.sp->colidx, h.A->values, (double *)h.d_b,
-                       (const uint8_t *)h.d_bc, nullptr, st) != cudaSuccess)
+  SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_f, &h.F));
+  SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_b, &h.B));
+  SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_x, &h.X));
+  SV_TRY(fe_mat_create(c, m->sp, &h.A));
+  SV_TRY(fe_assemble_mat(c, s->klap[r.degree], m->cells, h.A, 1, m->XY, m->CM, nullptr, 0));
+  fe_arg fa{h.F, m->M};
+  SV_TRY(fe_assemble_vec(c, s->ksrc[r.degree], m->cells, h.B, m->M, 1, m->XY, m->CM, &fa, 1, m->sp));
+  if (launch_dirichlet(r.nnodes, m->sp->rowptr, m->sp->colidx, h.A->values, (double *)h.d_b,
+                       (const uint8_t *)m->d_bc, nullptr, st) != cudaSuccess)
     return FE_ECUDA;
-  // transient buffers of the build: staging of the row-owner sums and the pattern scratch
+  // transient buffers of the assembly: staging of the row-owner sums (the vector staging sits on
+  // the shared sparsity but is this request's: freed before the next request uses the mesh)
   dev_free(c, h.A->stage);
   h.A->stage = nullptr;
   h.A->stage_bytes = 0;
-  dev_free(c, h.sp->vstage);
-  h.sp->vstage = nullptr;
-  h.sp->vstage_bytes = 0;
-  dev_free(c, h.sp->coltmp);
-  h.sp->coltmp = nullptr;
+  dev_free(c, m->sp->vstage);
+  m->sp->vstage = nullptr;
+  m->sp->vstage_bytes = 0;
   h.big = r.nnodes > cg_one_wave_rows(s->cg);
   SV_TRY(fe_cg_add(h.big ? s->cgb : s->cg, h.A, h.B, h.X, s->cfg.rtol, s->cfg.maxit, &h.slot));
   return FE_OK;
@@ -263,6 +369,10 @@ void server_free(Server *s) {
     cudaStreamSynchronize(s->ctx->stream);
   }
   for (Req &q : s->reqs) release(s, q);
+  s->owner = kOwnerCache;
+  for (MeshEntry *m : s->meshes) mesh_free(s, m);
+  s->meshes.clear();
+  s->owner = kOwnerServer;
   if (s->cg) fe_cg_destroy(s->cg);
   if (s->cgb) {
     OnStream on(s, s->hi);
@@ -372,7 +482,7 @@ fe_status server_submit(fe_server *h, const fe_solve_request *r, int64_t *id) {
   Req q;
   memset(&q.res, 0, sizeof q.res);
   q.in = *r;
-  q.estimate = estimate_bytes(*r);
+  q.estimate = estimate_bytes(*r, &q.mesh_estimate);
   q.res.estimate = q.estimate;
   q.res.status = FE_SOLVE_PENDING;
   s->reqs.push_back(q);
@@ -437,13 +547,15 @@ fe_status server_run(fe_server *h) {
       while (next < order.size() && (int)active.size() < cfg.max_active) {
         Req &q = s->reqs[order[next]];
         if (q.in.arrival_s > now_s(t0)) break;
-        if (s->base_bytes + q.estimate > cfg.hbm_budget) {
+        // a cached mesh is not charged again: the request needs only its own part
+        const size_t need = find_mesh(s, q.in) ? q.estimate - q.mesh_estimate : q.estimate;
+        if (s->base_bytes + need > cfg.hbm_budget) {
           q.res.status = FE_SOLVE_REFUSED;
           q.res.admitted_s = q.res.finished_s = now_s(t0);
           next++;
           continue;
         }
-        if (s->base_bytes + held + q.estimate > cfg.hbm_budget) break;  // wait for memory
+        if (!make_room(s, held, need)) break;  // wait for memory (unused cached meshes are evicted first)
         const int64_t id = order[next];
         q.res.admitted_s = now_s(t0);
         s->owner = id;
@@ -552,6 +664,11 @@ fe_status server_stats(const fe_server *h, fe_server_stats *out) {
   out->admit_s = s->admit_s;
   out->tick_s = s->tick_s;
   out->retire_s = s->retire_s;
+  out->cache_hits = s->cache_hits;
+  out->cache_misses = s->cache_misses;
+  out->cache_evictions = s->cache_evictions;
+  out->sparsity_builds = s->sparsity_builds;
+  out->cache_bytes = s->cache_bytes;
   for (const Req &q : s->reqs) {
     out->submitted++;
     if (q.res.status == FE_SOLVE_CONVERGED) out->converged++;

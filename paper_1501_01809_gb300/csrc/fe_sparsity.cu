@@ -630,13 +630,7 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
     cudaError_t e = cudaFuncSetAttribute(k_rows_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  int max_blocks = 152 * 32;
-  if (sp->row_blocks_per_sm > 0) {  // persistent grid, leaving room on every SM for concurrent work
-    int dev = 0, nsm = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    max_blocks = nsm * sp->row_blocks_per_sm;
-  }
-  if (sp->nrows > 0) k_rows_build<<<grid_for(sp->nrows, warps, max_blocks), warps * 32, smem, s>>>(p);
+  if (sp->nrows > 0) k_rows_build<<<grid_for(sp->nrows, warps, 152 * 32), warps * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 }  // namespace

@@ -27,7 +27,7 @@ SYMBOLS = [
     "fe_last_error", "fe_version", "fe_ctx_create", "fe_ctx_set_stream", "fe_ctx_set_allocator",
     "fe_ctx_set_checks", "fe_sync", "fe_ctx_destroy", "fe_set_create", "fe_set_size", "fe_set_destroy",
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
-    "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_set_row_blocks", "fe_sparsity_destroy", "fe_mat_create",
+    "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
     "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_elem_matrices", "fe_action_stored", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
     "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
@@ -64,7 +64,7 @@ class fe_server_config(C.Structure):
 class fe_solve_request(C.Structure):
     _fields_ = [("degree", C.c_int), ("ncell", C.c_int64), ("nnodes", C.c_int64), ("nvert", C.c_int64),
                 ("cell_node", C.c_void_p), ("cell_vertex", C.c_void_p), ("coords", C.c_void_p), ("f", C.c_void_p),
-                ("is_bc", C.c_void_p), ("x_out", C.c_void_p), ("arrival_s", C.c_double)]
+                ("is_bc", C.c_void_p), ("x_out", C.c_void_p), ("arrival_s", C.c_double), ("mesh_key", C.c_uint64)]
 
 
 class fe_solve_result(C.Structure):
@@ -77,7 +77,8 @@ class fe_server_stats(C.Structure):
     _fields_ = [("peak_bytes", C.c_size_t), ("live_bytes", C.c_size_t), ("base_bytes", C.c_size_t),
                 ("submitted", C.c_int), ("converged", C.c_int), ("refused", C.c_int), ("estimate_misses", C.c_int),
                 ("run_s", C.c_double), ("cg_launches", C.c_int64), ("admit_s", C.c_double), ("tick_s", C.c_double),
-                ("retire_s", C.c_double)]
+                ("retire_s", C.c_double), ("cache_hits", C.c_int), ("cache_misses", C.c_int),
+                ("cache_evictions", C.c_int), ("sparsity_builds", C.c_int), ("cache_bytes", C.c_size_t)]
 
 
 CG_RUNNING, CG_CONVERGED, CG_MAXIT, CG_BREAKDOWN = 0, 1, 2, 3
@@ -114,7 +115,7 @@ def load():
         "fe_sparsity_build": (I, [P, P, P, PP]), "fe_sparsity_rebuild": (I, [P]),
         "fe_sparsity_build_noalloc": (I, [P, I, P, I, I64, I64, I64, P, P, I64, P, C.POINTER(I64), P]),
         "fe_sparsity_csr": (I, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), PP, PP]),
-        "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_set_row_blocks": (I, [P, I]), "fe_sparsity_destroy": (I, [P]),
+        "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_destroy": (I, [P]),
         "fe_mat_create": (I, [P, P, PP]), "fe_mat_values": (I, [P, PP]), "fe_mat_zero": (I, [P]),
         "fe_mat_destroy": (I, [P]),
         "fe_kernel_create": (I, [P, C.POINTER(fe_form_desc), PP]), "fe_kernel_destroy": (I, [P]),
@@ -371,11 +372,6 @@ def sparsity_build_noalloc(rmap: torch.Tensor, cmap: torch.Tensor, nrows: int, n
     return nnz.value
 
 
-def sparsity_set_row_blocks(sp: Sparsity, blocks_per_sm: int) -> None:
-    """fe_sparsity_set_row_blocks: persistent row pass of at most blocks_per_sm blocks per SM."""
-    _check(load().fe_sparsity_set_row_blocks(sp.ptr, int(blocks_per_sm)))
-
-
 def sparsity_csr(sp: Sparsity):
     """(nrows, ncols, nnz, rowptr view int64 [nrows+1], colidx view int32 [nnz]) -- zero-copy views."""
     nr, nc, nnz = C.c_int64(), C.c_int64(), C.c_int64()
@@ -575,8 +571,11 @@ def server_create(ctx: Ctx, hbm_budget: int, max_active: int = 64, iters_per_tic
     return Server(out, ctx, keep=([],))
 
 
-def server_submit(srv: Server, degree: int, cell_node, cell_vertex, coords, f, is_bc, x_out, arrival_s: float) -> int:
-    """Queue one Poisson solve; the host arrays are kept alive by the server handle until it is destroyed."""
+def server_submit(srv: Server, degree: int, cell_node, cell_vertex, coords, f, is_bc, x_out, arrival_s: float,
+                  mesh_key: int = 0) -> int:
+    """Queue one Poisson solve; the host arrays are kept alive by the server handle until it is destroyed.
+    Requests with the same non-zero mesh_key must be on the same mesh; they share its device copy and
+    sparsity."""
     arrs = [np.ascontiguousarray(cell_node, np.int32), np.ascontiguousarray(cell_vertex, np.int32),
             np.ascontiguousarray(coords, np.float64), np.ascontiguousarray(f, np.float64),
             np.ascontiguousarray(is_bc, np.uint8)]
@@ -586,7 +585,7 @@ def server_submit(srv: Server, degree: int, cell_node, cell_vertex, coords, f, i
         raise ValueError("x_out must hold one value per node")
     req = fe_solve_request(int(degree), arrs[0].shape[0], arrs[3].size, arrs[2].shape[0], arrs[0].ctypes.data,
                            arrs[1].ctypes.data, arrs[2].ctypes.data, arrs[3].ctypes.data, arrs[4].ctypes.data,
-                           x_out.ctypes.data, float(arrival_s))
+                           x_out.ctypes.data, float(arrival_s), int(mesh_key))
     rid = C.c_int64()
     _check(load().fe_server_submit(srv.ptr, C.byref(req), C.byref(rid)))
     srv._keep[0].append((arrs, x_out))

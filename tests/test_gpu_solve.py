@@ -200,15 +200,15 @@ def _requests(specs):
     return out
 
 
-def _serve(reqs, budget, max_active, tick=8):
+def _serve(reqs, budget, max_active, tick=8, keys=None):
     from paper_1501_01809_gb300 import fe
     ctx = _ctx()
     srv = fe.server_create(ctx, budget, max_active=max_active, iters_per_tick=tick, rtol=1e-8)
     xs, ids = [], []
-    for r in reqs:
+    for i, r in enumerate(reqs):
         x = np.full(r["nn"], np.nan)
         ids.append(fe.server_submit(srv, r["p"], r["cmap"], r["mesh"].cell_vertex, r["mesh"].coords, r["f"], r["bc"],
-                                    x, r["t"]))
+                                    x, r["t"], mesh_key=keys[i] if keys else 0))
         xs.append(x)
     fe.server_run(srv)
     return [fe.server_result(srv, i) for i in ids], xs, fe.server_stats(srv)
@@ -284,3 +284,44 @@ def test_server_large_system_beside_small_ones(gpu):
     v, b = O.dirichlet_apply(rp, ci, v, b, r["bc"])
     A = sp.csr_matrix((v, ci, rp), shape=(r["nn"], r["nn"]))
     assert np.linalg.norm(b - A @ x_mix[0]) <= 1.5e-8 * np.linalg.norm(b)
+
+
+def test_server_mesh_cache_skips_the_sparsity_build(gpu):
+    """Requests that name the same mesh (mesh_key) share its device copy and sparsity: a cache hit
+    builds no sparsity and copies no mesh, and the solutions are bitwise those of the same requests
+    served without keys (every mesh built for its own request), mixed or one at a time."""
+    from paper_1501_01809_gb300 import fe
+    specs = [(0.0, 24, 2, 1, 2), (0.0, 10, 1, 3, 1), (0.001, 24, 2, 2, 1), (0.002, 17, 2, 4, 3),
+             (0.002, 10, 1, 1, 1), (0.004, 24, 2, 3, 3)]
+    keys = [7, 9, 7, 0, 9, 7]  # two shared meshes and one without a key
+    reqs = _requests(specs)
+    res_c, x_c, st_c = _serve(reqs, 1 << 34, 16, keys=keys)
+    res_1, x_1, st_1 = _serve(reqs, 1 << 34, 1, keys=keys)
+    res_n, x_n, st_n = _serve(reqs, 1 << 34, 16)
+    for st in (st_c, st_1):
+        assert st["converged"] == len(reqs) and st["estimate_misses"] == 0
+        assert (st["sparsity_builds"], st["cache_misses"], st["cache_hits"]) == (3, 2, 3), st
+    assert st_n["sparsity_builds"] == len(reqs) and st_n["cache_hits"] == 0
+    for i in range(len(reqs)):
+        assert res_c[i]["status"] == fe.SOLVE_CONVERGED
+        np.testing.assert_array_equal(x_c[i], x_n[i], err_msg=f"request {i}: cached mesh vs its own")
+        np.testing.assert_array_equal(x_c[i], x_1[i], err_msg=f"request {i}: mixed vs alone")
+    # a hit holds only its own system: less than the request that built the mesh
+    assert res_c[2]["bytes"] < res_c[0]["bytes"] + 1
+
+
+def test_server_mesh_cache_evicts_under_the_budget(gpu):
+    """With room for one mesh and one system, requests alternating between two meshes evict the
+    unused cached mesh to admit the next one; every request converges within the budget."""
+    from paper_1501_01809_gb300 import fe
+    specs = [(0.0, 40, 2, 1, 1), (0.0, 41, 2, 2, 1), (0.0, 40, 2, 1, 2), (0.0, 41, 2, 2, 2)]
+    reqs = _requests(specs)
+    probe_res, _, probe = _serve(reqs[1:2], 1 << 34, 1)
+    budget = int(probe["base_bytes"] + probe_res[0]["estimate"] + 4096)
+    res, xs, st = _serve(reqs, budget, 4, keys=[1, 2, 1, 2])
+    assert st["converged"] == len(reqs), st
+    assert st["peak_bytes"] <= budget, (st, budget)
+    assert st["cache_evictions"] >= 2 and st["sparsity_builds"] == 4, st
+    ref, xr, _ = _serve(reqs, 1 << 34, 1)
+    for a, b in zip(xs, xr):
+        np.testing.assert_array_equal(a, b)
