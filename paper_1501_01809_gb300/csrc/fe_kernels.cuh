@@ -415,46 +415,91 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_elem(const AsmArgs a, type
   for (int i = 0; i < ND; i++) out[i] = b[i];
 }
 
-// Row owners of a Mat: y-independent.  Shared memory: per thread rowcap accumulators, element q of
-// thread t at q*T + t.  INC semantics: the row's values are read once (unless zero_first) and
-// written once.
+// Row owners of a Mat.  Each warp holds NG = 32 / ND groups of ND lanes, and each group owns a
+// row at a time (rows r = group, group + groups, ...).  A group walks its row's incidence list
+// {(e, i)} -- ascending (sparsity_canonical, before the launch) -- U incidences per round: lane j
+// of the group loads entry j of row i of cell e's staged element matrix (one contiguous ND-value
+// row per incidence) and its lookup-table slot for all U incidences first, then adds them into
+// the row's shared-memory accumulators one incidence after another.  Every slot therefore
+// receives its contributions in incidence order, as a single row owner would add them: the
+// result is bitwise reproducible.  The groups of a warp advance independently (a group that
+// finishes its row writes it out and starts its next one), and one FP64 add instruction serves
+// all of them, so the FP64 pipe -- 1/16 of a warp instruction per clock on this GPU -- is not
+// spent on idle lanes.  INC semantics: the row's values are read once (unless zero_first) and
+// written once.  Shared memory: rowcap accumulators per group.
 template <int ND, class Ops>
-__global__ void k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr, const int32_t *__restrict__ adj,
-                           const int64_t *__restrict__ rowptr, const uint8_t *__restrict__ lut,
-                           const typename Ops::T *__restrict__ stage, double *__restrict__ vals, int rowcap,
-                           int zero_first, int *err, int checks) {
+__global__ void __launch_bounds__(256) k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr,
+                                                  const int32_t *__restrict__ adj, const int64_t *__restrict__ rowptr,
+                                                  const uint8_t *__restrict__ lut,
+                                                  const typename Ops::T *__restrict__ stage, double *__restrict__ vals,
+                                                  int rowcap, int zero_first, int *err, int checks) {
   using T = typename Ops::T;
+  constexpr int NG = 32 / ND > 0 ? 32 / ND : 1;  // row groups per warp
+  constexpr int U = 4;                           // incidences per round
   extern __shared__ __align__(16) unsigned char smp[];
-  T *acc = reinterpret_cast<T *>(smp) + threadIdx.x;
-  const int TB = blockDim.x;
-  for (int64_t r = blockIdx.x * (int64_t)TB + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * TB) {
-    const int64_t b = rowptr[r];
-    const int len = (int)(rowptr[r + 1] - b);
-    if (len > rowcap) {
-      flag(err, ERR_ROW_TOO_LONG, r);
-      continue;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int gi = lane / ND, j = lane - (lane / ND) * ND;
+  const bool on = gi < NG;  // lanes beyond NG groups idle (and take part in the warp-wide steps)
+  T *buf = reinterpret_cast<T *>(smp) + ((size_t)wid * NG + (on ? gi : 0)) * rowcap;
+  const int64_t groups = (int64_t)gridDim.x * wpb * NG;
+  int64_t r = ((int64_t)blockIdx.x * wpb + wid) * NG + gi;
+  int64_t b = 0, a0 = 0;
+  int len = 0, na = 0, a = 0;
+  bool have = false;
+  auto start_row = [&]() {  // the group's next row: its range, incidence list and zeroed slots
+    have = on && r < nrows;
+    a = 0;
+    if (have) {
+      b = rowptr[r];
+      len = (int)(rowptr[r + 1] - b);
+      a0 = adjptr[r];
+      na = (int)(adjptr[r + 1] - a0);
+      if (len > rowcap) {
+        if (j == 0) flag(err, ERR_ROW_TOO_LONG, r);
+        len = 0;
+        na = 0;
+      }
+      for (int q = j; q < len; q += ND) buf[q] = Ops::zero();
     }
-    for (int q = 0; q < len; q++) acc[q * TB] = Ops::zero();
-    const int64_t a0 = adjptr[r], a1 = adjptr[r + 1];
-    for (int64_t ai = a0; ai < a1; ai++) {
-      const int32_t k = adj[ai];  // incidence (e, i) = e ND + i
-      const T *Krow = stage + (int64_t)k * ND;  // row i of cell e's element matrix, contiguous
-      const uint8_t *L = lut + (int64_t)k * ND;
+  };
+  start_row();
+  __syncwarp();
+  while (__any_sync(0xffffffffu, have)) {
+    // one round: each group with incidences left loads up to U of them, then adds them in order
+    T v[U];
+    int q[U];
+    bool act[U];
 #pragma unroll
-      for (int j = 0; j < ND; j++) {
-        const int q = L[j];
-        if (checks && q >= len) {  // check mode: a lookup-table entry beyond the row is skipped
+    for (int u = 0; u < U; u++) {
+      act[u] = have && a + u < na;
+      v[u] = Ops::zero();
+      q[u] = 0;
+      if (act[u]) {
+        const int64_t k = adj[a0 + a + u];  // incidence (e, i) = e ND + i
+        v[u] = stage[k * ND + j];           // row i of cell e's element matrix, contiguous
+        q[u] = lut[k * ND + j];
+        if (checks && q[u] >= len) {  // check mode: a lookup-table entry beyond the row is skipped
           flag(err, ERR_LUT, k / ND);
-          continue;
+          act[u] = false;
         }
-        acc[q * TB] = Ops::add(acc[q * TB], Krow[j]);
       }
     }
-    double *out = vals + b;
-    for (int q = 0; q < len; q++) {
-      const double v = Ops::to_f64(acc[q * TB]);
-      out[q] = zero_first ? v : out[q] + v;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (act[u]) buf[q[u]] = Ops::add(buf[q[u]], v[u]);
+      __syncwarp();
     }
+    a += U;
+    if (have && a >= na) {  // the row is complete: write it out, take the group's next row
+      double *out = vals + b;
+      for (int qq = j; qq < len; qq += ND) {
+        const double d = Ops::to_f64(buf[qq]);
+        out[qq] = zero_first ? d : out[qq] + d;
+      }
+      r += groups;
+      start_row();
+    }
+    __syncwarp();
   }
 }
 
@@ -510,16 +555,16 @@ cudaError_t mat_pull(const AsmArgs &a, cudaStream_t s) {
   }
   if (a.ncell > 0)
     k_mat_elem<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, esm, s>>>(a, stage);
-  const int TB = 64;
-  const size_t smem = (size_t)a.rowcap * TB * sizeof(T);
+  const int TB = 256, warps = TB / 32, groups = 32 / E::ND > 0 ? 32 / E::ND : 1;
+  const size_t smem = (size_t)a.rowcap * warps * groups * sizeof(T);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_mat_pull<E::ND, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   if (a.nrows > 0)
-    k_mat_pull<E::ND, Ops><<<pull_blocks(a.nrows, TB), TB, smem, s>>>(a.nrows, a.adjptr, a.adj, a.rowptr, a.lut, stage,
-                                                                       a.vals, a.rowcap, a.zero_first, a.err,
-                                                                       a.checks);
+    k_mat_pull<E::ND, Ops><<<pull_blocks(a.nrows, warps * groups), TB, smem, s>>>(a.nrows, a.adjptr, a.adj, a.rowptr, a.lut,
+                                                                          stage, a.vals, a.rowcap, a.zero_first,
+                                                                          a.err, a.checks);
   return cudaGetLastError();
 }
 
