@@ -197,13 +197,15 @@ __device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &
 // i ^ (k - 1)), after which every half-cleaner stage sorts ascending, so compare-exchanges inside a
 // lane need no direction select.  Stages between lanes exchange with lane l ^ (stride / E); the lane
 // holding the lower index keeps the minimum.
-template <int E>
+// NL = 16 sorts 16 E values in each half-warp independently (every exchange mask is below 16).
+template <int E, int NL = 32>
 __device__ __forceinline__ void warp_bitonic_packed(uint32_t (&v)[E]) {
   const int lane = threadIdx.x & 31;
   constexpr int LG = E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : -1;
   static_assert(LG >= 0, "E must be a power of two up to 16");
+  static_assert(NL == 32 || NL == 16, "a warp or a half-warp");
 #pragma unroll
-  for (int k = 2; k <= 32 * E; k <<= 1) {
+  for (int k = 2; k <= NL * E; k <<= 1) {
     if (k <= E) {  // mirror stage inside the lane
 #pragma unroll
       for (int h = 0; h < E; h++) {
@@ -274,11 +276,12 @@ struct RowsParams {
 
 // Where row r's nu unique columns go: colidx in place when the in-place pass applies and the
 // row's length is unchanged (and inside the nnz entries), else coltmp at the incidence offset.
-__device__ __forceinline__ int32_t *row_out(const RowsParams &p, int64_t r, int64_t a0, int nu) {
+__device__ __forceinline__ int32_t *row_out(const RowsParams &p, int64_t r, int64_t a0, int nu,
+                                            bool leader = (threadIdx.x & 31) == 0) {
   if (p.colidx) {
     const int64_t b = p.rowptr[r];
     if (p.rowptr[r + 1] - b == nu && b >= 0 && b + nu <= p.nnz) return p.colidx + b;
-    if ((threadIdx.x & 31) == 0) *p.changed = 1;
+    if (leader) *p.changed = 1;
   }
   return p.coltmp + a0 * p.ndc;
 }
@@ -296,9 +299,11 @@ __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
 // of each run of equal columns, ranks
 // by a warp prefix count, unique columns (ascending) to coltmp and every candidate's rank to the
 // lookup table.  Returns the number of unique columns (valid in every lane).
+// adje (na words) and lbuf (256 bytes) are per-warp shared scratch: the cell of each incidence, and
+// each candidate's rank, which the warp then writes to the lookup table incidence by incidence.
 template <int E, int SH>
 __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
-                                           uint32_t *adjs) {
+                                           uint32_t *adjs, uint32_t *adje, uint8_t *lbuf) {
   const int lane = threadIdx.x & 31;
   const int ndc = p.ndc;
   const uint32_t tmask = (1u << SH) - 1u;
@@ -311,6 +316,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   }
   if (lane < na) {
     adjs[rk] = v;
+    adje[rk] = div_ndr(v, p);  // the incidence's cell, once per incidence
     if (p.canon) p.adj[a0 + rk] = (int32_t)v;
   }
   __syncwarp();
@@ -323,7 +329,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
     key[h] = 0xFFFFFFFFu;
     if ((int)t < ncand) {
       const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
-      key[h] = ((uint32_t)p.cmap[(int64_t)div_ndr(adjs[a], p) * ndc + j] << SH) | t;
+      key[h] = ((uint32_t)p.cmap[(int64_t)adje[a] * ndc + j] << SH) | t;
     }
   }
   warp_bitonic_packed<E>(key);
@@ -350,11 +356,86 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
     rank += f[h];
     if (key[h] == 0xFFFFFFFFu) continue;
     if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
-    if (rank < kMaxRowLen) {
-      const uint32_t t = key[h] & tmask, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
-      p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank;
+    lbuf[key[h] & tmask] = (uint8_t)rank;  // ranks past the row limit are flagged by the caller
+  }
+  __syncwarp();
+  // the lookup table in incidence order: candidate t = (a, j) goes to row a's ndc bytes, so the
+  // lanes of one store write a few contiguous segments instead of one byte per segment each
+  for (int t = lane; t < ncand; t += 32) {
+    const uint32_t a = div_ndc((uint32_t)t, p), j = (uint32_t)t - a * (uint32_t)ndc;
+    p.lut[(int64_t)adjs[a] * ndc + j] = lbuf[t];
+  }
+  __syncwarp();
+  return nu;
+}
+
+// Two rows at once, one per half-warp: the steps of row_by_sort inside each half (16 lanes, E keys
+// per lane, at most 16 E candidates and 16 incidences per row).  Every shuffle has width 16, so
+// the halves never exchange values; adjs, adje (16 words) and lbuf (16 E bytes) are this half's
+// scratch.  Returns this half's number of unique columns.
+template <int E, int SH>
+__device__ __forceinline__ int row_by_sort_half(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
+                                                uint32_t *adjs, uint32_t *adje, uint8_t *lbuf) {
+  const int hl = threadIdx.x & 15;
+  const unsigned full = 0xffffffffu;
+  const int ndc = p.ndc;
+  const uint32_t tmask = (1u << SH) - 1u;
+  const uint32_t v = hl < na ? (uint32_t)p.adj[a0 + hl] : 0xFFFFFFFFu;
+  int rk = hl;
+  if (p.canon) {
+    rk = 0;
+    for (int q = 0; q < 16; q++) {
+      const uint32_t w = __shfl_sync(full, v, q, 16);
+      rk += (q < na) && (w < v);
     }
   }
+  if (hl < na) {
+    adjs[rk] = v;
+    adje[rk] = div_ndr(v, p);
+    if (p.canon) p.adj[a0 + rk] = (int32_t)v;
+  }
+  __syncwarp();
+  uint32_t key[E];
+#pragma unroll
+  for (int h = 0; h < E; h++) {
+    const uint32_t t = (uint32_t)(16 * h + hl);
+    key[h] = 0xFFFFFFFFu;
+    if ((int)t < ncand) {
+      const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+      key[h] = ((uint32_t)p.cmap[(int64_t)adje[a] * ndc + j] << SH) | t;
+    }
+  }
+  warp_bitonic_packed<E, 16>(key);
+  const uint32_t prev = __shfl_up_sync(full, key[E - 1], 1, 16);
+  int f[E], c = 0;
+#pragma unroll
+  for (int h = 0; h < E; h++) {
+    const uint32_t before = h == 0 ? prev : key[h - 1];
+    f[h] = key[h] != 0xFFFFFFFFu && ((h == 0 && hl == 0) || (key[h] >> SH) != (before >> SH));
+    c += f[h];
+  }
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const int n = __shfl_up_sync(full, incl, o, 16);
+    if (hl >= o) incl += n;
+  }
+  const int nu = __shfl_sync(full, incl, 15, 16);
+  int32_t *outc = row_out(p, r, a0, nu, hl == 0);
+  int rank = incl - c - 1;
+#pragma unroll
+  for (int h = 0; h < E; h++) {
+    rank += f[h];
+    if (key[h] == 0xFFFFFFFFu) continue;
+    if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
+    lbuf[key[h] & tmask] = (uint8_t)rank;
+  }
+  __syncwarp();
+  for (int t = hl; t < ncand; t += 16) {
+    const uint32_t a = div_ndc((uint32_t)t, p), j = (uint32_t)t - a * (uint32_t)ndc;
+    p.lut[(int64_t)adjs[a] * ndc + j] = lbuf[t];
+  }
+  __syncwarp();
   return nu;
 }
 
@@ -376,102 +457,129 @@ __global__ void __launch_bounds__(256, 6) k_rows_build(const RowsParams p) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int cap = p.cap;
   if (p.colidx && blockIdx.x == 0 && threadIdx.x == 0 && p.rowptr[p.nrows] != p.nnz) *p.changed = 1;
-  // per warp: hash tables (5 cap words) unless every row is sorted, then the incidence lists
-  int32_t *hkey = smem_i + (size_t)wid * ((p.sort_only ? 0 : 5 * cap) + 2 * p.acap);
+  // per warp: hash tables (5 cap words) unless every row is sorted, then the incidence lists, then
+  // 64 words of rank bytes for the sort path, then 96 words for the half-warp rows (incidences,
+  // cells and rank bytes of each half)
+  int32_t *hkey = smem_i + (size_t)wid * ((p.sort_only ? 0 : 5 * cap) + 2 * p.acap + 64 + 96);
   int32_t *hrank = hkey + cap;
   uint32_t *ucol = reinterpret_cast<uint32_t *>(hrank + cap);
   int32_t *uslot = reinterpret_cast<int32_t *>(ucol + cap);
   int32_t *cslot = uslot + cap;
   uint32_t *adju = p.sort_only ? reinterpret_cast<uint32_t *>(hkey) : reinterpret_cast<uint32_t *>(cslot + cap);
   uint32_t *adjs = adju + p.acap;
+  uint8_t *lbuf = reinterpret_cast<uint8_t *>(adjs + p.acap);
+  const int half = lane >> 4;
+  uint32_t *hadjs = reinterpret_cast<uint32_t *>(lbuf + 256) + 16 * half;
+  uint32_t *hadje = reinterpret_cast<uint32_t *>(lbuf + 256) + 32 + 16 * half;
+  uint8_t *hlbuf = lbuf + 256 + 256 + 64 * half;
   const int ndc = p.ndc;
-  for (int64_t r = (int64_t)blockIdx.x * wpb + wid; r < p.nrows; r += (int64_t)gridDim.x * wpb) {
-    const int64_t a0 = p.adjptr[r];
-    const int na = (int)(p.adjptr[r + 1] - a0);
-    const int ncand = na * ndc;
-    if (na > p.acap || ncand > cap) {
-      if (lane == 0) {
-        flag(p.err, ERR_CAND_OVERFLOW, r);
-        p.rowlen[r] = 0;
+  // Rows go to warps in pairs.  When both rows of a pair have at most 64 candidates (every edge
+  // row of a P2 tetrahedral mesh), each half-warp sorts one of them, four keys per lane; any other
+  // pair is done row by row by the whole warp.
+  for (int64_t pr = (int64_t)blockIdx.x * wpb + wid; 2 * pr < p.nrows; pr += (int64_t)gridDim.x * wpb) {
+    const int64_t r0 = 2 * pr, r1 = r0 + 1;
+    const int64_t rh = half ? r1 : r0;
+    int64_t ah = 0;
+    int nh = 0;
+    if (rh < p.nrows) {
+      ah = p.adjptr[rh];
+      nh = (int)(p.adjptr[rh + 1] - ah);
+    }
+    const bool mine_ok = rh < p.nrows && nh > 0 && nh <= 16 && nh * ndc <= 64;
+    if (p.packed_ok && __all_sync(0xffffffffu, mine_ok)) {
+      const int nu = row_by_sort_half<4, 6>(p, rh, ah, nh, nh * ndc, hadjs, hadje, hlbuf);
+      if ((lane & 15) == 0) p.rowlen[rh] = nu;  // at most 64 columns: within the row limit
+      __syncwarp();
+      continue;
+    }
+    for (int64_t r = r0; r <= r1 && r < p.nrows; r++) {
+      const int64_t a0 = p.adjptr[r];
+      const int na = (int)(p.adjptr[r + 1] - a0);
+      const int ncand = na * ndc;
+      if (na > p.acap || ncand > cap) {
+        if (lane == 0) {
+          flag(p.err, ERR_CAND_OVERFLOW, r);
+          p.rowlen[r] = 0;
+        }
+        continue;
       }
-      continue;
-    }
-    if (na == 0) {
-      if (lane == 0) p.rowlen[r] = 0;
-      continue;
-    }
-    if (p.packed_ok && na <= 32 && ncand <= 256) {
-      // rows of up to 256 candidates (every row of P1 and P2 meshes and of P3 triangles): sort packed values
-      const int nu = ncand <= 64    ? row_by_sort<2, 6>(p, r, a0, na, ncand, adjs)
-                     : ncand <= 128 ? row_by_sort<4, 7>(p, r, a0, na, ncand, adjs)
-                                    : row_by_sort<8, 8>(p, r, a0, na, ncand, adjs);
+      if (na == 0) {
+        if (lane == 0) p.rowlen[r] = 0;
+        continue;
+      }
+      if (p.packed_ok && na <= 32 && ncand <= 256) {
+        // rows of up to 256 candidates (every row of P1 and P2 meshes and of P3 triangles): sort packed values
+        const int nu = ncand <= 64    ? row_by_sort<2, 6>(p, r, a0, na, ncand, adjs, adju, lbuf)
+                       : ncand <= 128 ? row_by_sort<4, 7>(p, r, a0, na, ncand, adjs, adju, lbuf)
+                                      : row_by_sort<8, 8>(p, r, a0, na, ncand, adjs, adju, lbuf);
+        if (lane == 0) {
+          p.rowlen[r] = nu;
+          if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
+        }
+        __syncwarp();
+        continue;
+      }
+      const int H = next_pow2(ncand);  // <= cap
+      int logH = 5;
+      while ((1 << logH) < H) logH++;
+      // 1. the row's incidences (in ascending order when canonicalising)
+      for (int t = lane; t < na; t += 32) adju[t] = (uint32_t)p.adj[a0 + t];
+      for (int t = lane; t < H; t += 32) hkey[t] = -1;
+      __syncwarp();
+      if (p.canon) {
+        warp_rank_distinct(adju, na, [&](int q, int rk) { adjs[rk] = adju[q]; });
+        __syncwarp();
+        for (int t = lane; t < na; t += 32) p.adj[a0 + t] = (int32_t)adjs[t];
+      } else {
+        for (int t = lane; t < na; t += 32) adjs[t] = adju[t];
+      }
+      // 2. insert candidates, remember their slots
+      for (int t = lane; t < ncand; t += 32) {
+        const uint32_t a = div_ndc((uint32_t)t, p);
+        const uint32_t j = (uint32_t)t - a * (uint32_t)ndc;
+        const uint32_t e = div_ndr(adjs[a], p);
+        const int32_t col = p.cmap[(int64_t)e * ndc + j];
+        uint32_t h = hash_slot((uint32_t)col, logH);
+        for (int q = 0; q < H; q++) {
+          const int32_t prev = atomicCAS(&hkey[h], -1, col);
+          if (prev == -1 || prev == col) break;
+          h = (h + 1) & (H - 1);
+        }
+        cslot[t] = (int32_t)h;
+      }
+      __syncwarp();
+      // 3. compact the unique columns, rank them, write them in ascending order
+      int nu = 0;
+      for (int b = 0; b < H; b += 32) {
+        const int32_t key = hkey[b + lane];
+        const unsigned m = __ballot_sync(0xffffffffu, key >= 0);
+        if (key >= 0) {
+          const int pos = nu + __popc(m & ((1u << lane) - 1u));
+          ucol[pos] = (uint32_t)key;
+          uslot[pos] = b + lane;
+        }
+        nu += __popc(m);
+      }
+      __syncwarp();
+      int32_t *outc = row_out(p, r, a0, nu);
+      warp_rank_distinct(ucol, nu, [&](int q, int rk) {
+        hrank[uslot[q]] = rk;
+        outc[rk] = (int32_t)ucol[q];
+      });
+      __syncwarp();
+      // 4. rank of every candidate -> lookup table (candidate t = (a, j) of incident k = adjs[a])
+      for (int t = lane; t < ncand; t += 32) {
+        const uint32_t a = div_ndc((uint32_t)t, p);
+        const uint32_t j = (uint32_t)t - a * (uint32_t)ndc;
+        const int rank = hrank[cslot[t]];
+        if (rank < kMaxRowLen) p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank;
+      }
       if (lane == 0) {
         p.rowlen[r] = nu;
         if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
       }
       __syncwarp();
-      continue;
     }
-    const int H = next_pow2(ncand);  // <= cap
-    int logH = 5;
-    while ((1 << logH) < H) logH++;
-    // 1. the row's incidences (in ascending order when canonicalising)
-    for (int t = lane; t < na; t += 32) adju[t] = (uint32_t)p.adj[a0 + t];
-    for (int t = lane; t < H; t += 32) hkey[t] = -1;
-    __syncwarp();
-    if (p.canon) {
-      warp_rank_distinct(adju, na, [&](int q, int rk) { adjs[rk] = adju[q]; });
-      __syncwarp();
-      for (int t = lane; t < na; t += 32) p.adj[a0 + t] = (int32_t)adjs[t];
-    } else {
-      for (int t = lane; t < na; t += 32) adjs[t] = adju[t];
-    }
-    // 2. insert candidates, remember their slots
-    for (int t = lane; t < ncand; t += 32) {
-      const uint32_t a = div_ndc((uint32_t)t, p);
-      const uint32_t j = (uint32_t)t - a * (uint32_t)ndc;
-      const uint32_t e = div_ndr(adjs[a], p);
-      const int32_t col = p.cmap[(int64_t)e * ndc + j];
-      uint32_t h = hash_slot((uint32_t)col, logH);
-      for (int q = 0; q < H; q++) {
-        const int32_t prev = atomicCAS(&hkey[h], -1, col);
-        if (prev == -1 || prev == col) break;
-        h = (h + 1) & (H - 1);
-      }
-      cslot[t] = (int32_t)h;
-    }
-    __syncwarp();
-    // 3. compact the unique columns, rank them, write them in ascending order
-    int nu = 0;
-    for (int b = 0; b < H; b += 32) {
-      const int32_t key = hkey[b + lane];
-      const unsigned m = __ballot_sync(0xffffffffu, key >= 0);
-      if (key >= 0) {
-        const int pos = nu + __popc(m & ((1u << lane) - 1u));
-        ucol[pos] = (uint32_t)key;
-        uslot[pos] = b + lane;
-      }
-      nu += __popc(m);
-    }
-    __syncwarp();
-    int32_t *outc = row_out(p, r, a0, nu);
-    warp_rank_distinct(ucol, nu, [&](int q, int rk) {
-      hrank[uslot[q]] = rk;
-      outc[rk] = (int32_t)ucol[q];
-    });
-    __syncwarp();
-    // 4. rank of every candidate -> lookup table (candidate t = (a, j) of incident k = adjs[a])
-    for (int t = lane; t < ncand; t += 32) {
-      const uint32_t a = div_ndc((uint32_t)t, p);
-      const uint32_t j = (uint32_t)t - a * (uint32_t)ndc;
-      const int rank = hrank[cslot[t]];
-      if (rank < kMaxRowLen) p.lut[(int64_t)adjs[a] * ndc + j] = (uint8_t)rank;
-    }
-    if (lane == 0) {
-      p.rowlen[r] = nu;
-      if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
-    }
-    __syncwarp();
   }
 }
 
@@ -622,7 +730,7 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
   p.changed = changed;
   p.gate = gate;
   p.canon = 0;
-  const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap) * sizeof(int32_t);
+  const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap + 64 + 96) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
   const size_t smem = warps * per_warp;

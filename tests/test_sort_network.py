@@ -8,12 +8,14 @@ import numpy as np
 import pytest
 
 
-def warp_sort(vals, E):
-    v = vals.reshape(32, E).copy()
-    lanes = np.arange(32)
+def warp_sort(vals, E, nl=32):
+    """The kernel's schedule on nl lanes (32: a warp; 16: each half of a warp, whose exchange masks
+    all stay below 16 so that the two halves sort independently)."""
+    v = vals.reshape(nl, E).copy()
+    lanes = np.arange(nl)
     lg = E.bit_length() - 1
     k = 2
-    while k <= 32 * E:
+    while k <= nl * E:
         if k <= E:  # mirror stage inside a lane
             for h in range(E):
                 ph = h ^ (k - 1)
@@ -51,6 +53,33 @@ def test_network_sorts(E):
         ncand = int(rng.integers(1, n + 1))
         x[ncand:] = 0xFFFFFFFF  # padding keys sort last, as in the kernel
         np.testing.assert_array_equal(warp_sort(x, E), np.sort(x))
+
+
+def test_half_warp_network_sorts_each_half():
+    """The half-warp variant (warp_bitonic_packed<E, 16>, four keys per lane in the row kernel):
+    run on a whole warp, each half ends sorted on its own and nothing crosses between halves."""
+    rng = np.random.default_rng(16)
+    for E in (1, 2, 4):
+        for t in range(100):
+            halves = []
+            for _ in range(2):
+                x = rng.integers(0, 30 if t % 2 else 2**32 - 1, 16 * E, dtype=np.uint64)
+                x[int(rng.integers(1, 16 * E + 1)):] = 0xFFFFFFFF
+                halves.append(x)
+            lanes = np.concatenate(halves).reshape(32, E)  # lanes 0-15: first row, 16-31: second
+            for h, x in enumerate(halves):
+                np.testing.assert_array_equal(warp_sort(lanes[16 * h:16 * h + 16].reshape(-1), E, nl=16), np.sort(x))
+        # every exchange mask of the half-warp schedule (mirror stages (k >> lg) - 1, half-cleaners
+        # j >> lg) is below 16, so lane l ^ mask stays in l's half
+        lg = E.bit_length() - 1
+        k = 2
+        while k <= 16 * E:
+            assert k <= E or (k >> lg) - 1 < 16
+            j = k >> 2
+            while j > 0:
+                assert j < E or (j >> lg) < 16
+                j >>= 1
+            k <<= 1
 
 
 def test_packed_keys_rank_runs():
