@@ -69,9 +69,10 @@ TRAFFIC = {
     ("assemble", "push", "f32x2"): (1.020e9, "c827e6c081c1",
                                     "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
     # one sparsity rebuild (zeros, k_inc_count, scans, k_inc_fill, the in-place k_rows_build pass and the
-    # gated launches that return at once): 195.4 MB at 40^3, scaled x4.096 to 64^3
-    ("sparsity", None, None): (0.8002e9, "20c3e3db29db",
-                               "integer instruction issue (ncu at 40^3, row pass: issue active 71%, ALU pipe 71%)"),
+    # gated launches that return at once): 167.3 MB at 40^3, scaled x4.096 to 64^3
+    ("sparsity", None, None): (0.6853e9, "e0a00628050a",
+                               "integer instruction issue (ncu at 40^3, row pass: issue active 74%, ALU pipe 69%, "
+                               "422 warp instructions per row)"),
 }
 
 
