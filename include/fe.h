@@ -156,8 +156,9 @@ fe_status fe_dat_destroy(fe_dat *dat);
  * row -> (cell, local index) incidence used by the row-owner (pull) kernels (put into ascending
  * order by the first pull or wave call after each build, which is what makes their sums
  * bitwise reproducible; push calls never need it).  rmap and cmap
- * must share their source set (the cells).  Owned buffers.  Synchronises the stream once to
- * learn nnz.  Errors: FE_EINVAL (different source sets), FE_ERANGE (map value out of range),
+ * must share their source set (the cells).  Owned buffers.  Synchronises the stream twice (the
+ * longest incidence list and the maps' range checks, then nnz and the longest row); the last
+ * kernel, the colidx compaction, is still in flight on the stream when it returns.  Errors: FE_EINVAL (different source sets), FE_ERANGE (map value out of range),
  * FE_EUNSUPPORTED (a row with more than 256 columns or more than 4096 candidate entries). */
 fe_status fe_sparsity_build(fe_ctx *ctx, fe_map *rmap, fe_map *cmap, fe_sparsity **out);
 /* Recomputes pattern, lookup table and incidence from the (possibly rewritten) map values into

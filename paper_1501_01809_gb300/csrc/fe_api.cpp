@@ -313,8 +313,11 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
     delete sp;
     return fail(FE_ENOMEM, "fe_sparsity_build: device allocation failed");
   }
-  // 1. incidence (validates the row map), learn the longest incidence list
+  // 1. incidence (validates the row map), the column map's range check, and the longest incidence
+  //    list: one host synchronisation for all three (the build synchronises twice in all)
   cudaError_t e = fe::sparsity_incidence(sp, c->stream, c->d_err);
+  if (e == cudaSuccess && cmap->to->size > 0 && ncell > 0)
+    e = fe::launch_map_validate(cmap->values, ncell * cmap->arity, cmap->to->size, c->d_err, c->stream);
   int maxcnt = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&maxcnt, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) {
@@ -323,10 +326,6 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
     return cuda_fail(e, "fe_sparsity_build");
   }
   fe_status st = check_device_flags(c, "fe_sparsity_build");
-  if (st == FE_OK && cmap->to->size > 0 && ncell > 0) {
-    e = fe::launch_map_validate(cmap->values, ncell * cmap->arity, cmap->to->size, c->d_err, c->stream);
-    st = e != cudaSuccess ? cuda_fail(e, "fe_sparsity_build") : check_device_flags(c, "fe_sparsity_build");
-  }
   if (st != FE_OK) {
     sparsity_free(sp);
     delete sp;
@@ -343,10 +342,13 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
   while (sp->cap < maxcand) sp->cap <<= 1;
   sp->acap = 4;
   while (sp->acap < maxcnt) sp->acap += 4;
-  // 2. rows: sort, ranks, row lengths, rowptr
+  // 2. rows: sort, ranks, row lengths, rowptr; nnz and the longest row read back together
   int64_t nnz = 0;
+  int mr = 0;
   e = fe::sparsity_rows(sp, c->stream, c->d_err);
+  if (e == cudaSuccess) e = fe::launch_max_i32(sp->rowcnt, sp->nrows, sp->d_maxcnt, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&nnz, sp->rowptr + sp->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&mr, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) {
     sparsity_free(sp);
     delete sp;
@@ -359,36 +361,20 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
     return st;
   }
   sp->nnz = nnz;
-  {
-    int mr = 0;
-    e = fe::launch_max_i32(sp->rowcnt, sp->nrows, sp->d_maxcnt, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&mr, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) {
-      sparsity_free(sp);
-      delete sp;
-      return cuda_fail(e, "fe_sparsity_build");
-    }
-    sp->maxrow = mr;
-  }
+  sp->maxrow = mr;
   sp->colidx = (int32_t *)dev_alloc(c, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
   if (!sp->colidx) {
     sparsity_free(sp);
     delete sp;
     return fail(FE_ENOMEM, "fe_sparsity_build: colidx allocation");
   }
-  // 3. compact the unique columns into colidx
+  // 3. compact the unique columns into colidx (stream-ordered: it raises no flag, so the build
+  //    returns without waiting for it)
   e = fe::sparsity_compact(sp, c->stream, c->d_err, 0);
   if (e != cudaSuccess) {
     sparsity_free(sp);
     delete sp;
     return cuda_fail(e, "fe_sparsity_build");
-  }
-  st = check_device_flags(c, "fe_sparsity_build");
-  if (st != FE_OK) {
-    sparsity_free(sp);
-    delete sp;
-    return st;
   }
   *out = sp;
   return ok();
@@ -886,7 +872,8 @@ fe_status fe_cg_add(fe_cg *cg, fe_mat *A, fe_dat *b, fe_dat *x, double rtol, int
     return fail(FE_EINVAL, "%s: b and x must be distinct scalar Dats on A's rows", who);
   if (!(rtol >= 0.0) || maxit < 0 || !slot) return fail(FE_EINVAL, "%s: bad rtol, maxit or slot", who);
   DeviceGuard g(c->device);
-  fe_status st = fe::cg_add(cg, sp->rowptr, sp->colidx, A->values, sp->nrows, b->data, x->data, rtol, maxit, slot);
+  fe_status st =
+      fe::cg_add(cg, sp->rowptr, sp->colidx, A->values, sp->nrows, b->data, x->data, rtol, maxit, slot, sp->maxrow);
   if (st != FE_OK) return fail(st, "%s", fe::solve_message());
   return ok();
 }

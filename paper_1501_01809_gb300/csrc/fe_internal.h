@@ -169,7 +169,8 @@ int cg_grid(const fe_cg *h);
 fe_status cg_limit_grid(fe_cg *h, int grid);
 fe_ctx *cg_ctx(const fe_cg *h);
 fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const double *vals, int64_t nrows,
-                 const double *b, double *x, double rtol, int maxit, int *slot);
+                 const double *b, double *x, double rtol, int maxit, int *slot,
+                 int maxrow = 0);
 fe_status cg_iterate(fe_cg *h, int iters, int use_graph);
 fe_status cg_poll(fe_cg *h, int n, int *status, int *iters, double *rnorm, double *bnorm);
 fe_status cg_remove(fe_cg *h, int slot);

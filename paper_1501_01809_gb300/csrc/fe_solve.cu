@@ -540,7 +540,7 @@ fe_status cg_create(fe_ctx *c, int max_systems, fe_cg **out) {
 }
 
 fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const double *vals, int64_t nrows,
-                 const double *b, double *x, double rtol, int maxit, int *slot) {
+                 const double *b, double *x, double rtol, int maxit, int *slot, int maxrow) {
   CgEngine *e = h->e;
   g_smsg[0] = 0;
   int s = -1;
@@ -597,8 +597,14 @@ fe_status cg_add(fe_cg *h, const int64_t *rowptr, const int32_t *colidx, const d
     err0 = cudaGetLastError();
   }
   if (err0 == cudaSuccess) err0 = exclusive_scan_i32_to_i64(width, sptr, nsl, tmp, st0);
-  if (err0 == cudaSuccess) err0 = cudaMemcpyAsync(&ncol, sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, st0);
-  if (err0 == cudaSuccess) err0 = cudaStreamSynchronize(st0);
+  if (maxrow > 0) {
+    // every slice is at most the longest row wide: size the copy for that and do not wait for
+    // the exact total (no host synchronisation in the set-up)
+    ncol = nsl * (int64_t)maxrow;
+  } else {
+    if (err0 == cudaSuccess) err0 = cudaMemcpyAsync(&ncol, sptr + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, st0);
+    if (err0 == cudaSuccess) err0 = cudaStreamSynchronize(st0);
+  }
   dev_free(e->ctx, width);
   dev_free(e->ctx, tmp);
   if (err0 == cudaSuccess) {
