@@ -318,7 +318,8 @@ def run_ours(args, wl, rank, world):
     # reads the rebuilt incidence and stays on the main stream).
     side = None
     if args.overlap != "off" and not pull:
-        side = torch.cuda.Stream(dev, priority=-1 if args.overlap == "hi" else 0)
+        side = torch.cuda.Stream(dev, priority=-1 if args.overlap in ("hi", "asm-hi") else 0)
+    beside_asm = args.overlap in ("asm", "asm-hi")  # the action beside the assembly, after the rebuild
 
     def compute(sp_, A_, X_, Y_, M_, XY_, CM_, ev=None, sev=None):
         """One pass of the hot path: sparsity rebuild, Mat zero, assembly, action.  ev: 5 events on the
@@ -338,6 +339,30 @@ def run_ours(args, wl, rank, world):
             if ev is not None:
                 ev[3].record(stream)
             fe.action(ctx, kcur[0], cells, X_, Y_, M_, XY_, CM_, zero_first=True, sp=sp_)
+            if ev is not None:
+                ev[4].record(stream)
+            return
+        if beside_asm:  # rebuild; then zero + assembly on the main stream, the action beside them
+            e1 = ev[1] if ev is not None else torch.cuda.Event()
+            ea = sev[1] if sev is not None else torch.cuda.Event()
+            fe.sparsity_rebuild(sp_)
+            e1.record(stream)
+            side.wait_event(e1)
+            if sev is not None:
+                sev[0].record(side)
+            fe.ctx_set_stream(ctx, side)
+            try:
+                fe.action(ctx, kcur[0], cells, X_, Y_, M_, XY_, CM_, zero_first=True, sp=sp_)
+                ea.record(side)
+            finally:
+                fe.ctx_set_stream(ctx, stream)
+            fe.mat_zero(A_)
+            if ev is not None:
+                ev[2].record(stream)
+            fe.assemble_mat(ctx, kcur[0], cells, A_, XY_, CM_, zero_first=False)
+            if ev is not None:
+                ev[3].record(stream)
+            stream.wait_event(ea)
             if ev is not None:
                 ev[4].record(stream)
             return
@@ -420,6 +445,9 @@ def run_ours(args, wl, rank, world):
             if side is None:
                 for q in range(4):
                     out[q] += ev[q].elapsed_time(ev[q + 1])
+            elif beside_asm:  # zero and assembly on the main stream, the action beside them
+                out += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                        sev[0].elapsed_time(sev[1])]
             else:  # live durations of the concurrent phases (sparsity on the main stream, zero and action beside it)
                 out += [ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(sev[0]), ev[2].elapsed_time(ev[3]),
                         sev[0].elapsed_time(sev[1])]
@@ -675,7 +703,8 @@ def run_ours(args, wl, rank, world):
         "dtype": "f64" if args.precision == "fp64" else "f32x2 element / f64 accumulate", "data": "synthetic",
         "config": {"workload": wl["name"], "cells_per_gpu": ncell, "dofs": nn, "nnz": nnz,
                    "strategy": args.strategy,
-                   "schedule": (("Mat zero and action on a second stream, concurrent with the sparsity rebuild"
+                   "schedule": (("action on a second stream, concurrent with the Mat zero and assembly" if beside_asm
+                                 else "Mat zero and action on a second stream, concurrent with the sparsity rebuild"
                                  if side is not None else
                                  "serial on one stream") +
                                 (", one CUDA graph per step (phases from a launch-by-launch pass)"
@@ -1546,9 +1575,10 @@ def main():
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
                     help="p2-3d/p1-2d: replay the step as one captured CUDA graph (auto: push strategy on one "
                          "stream)")
-    ap.add_argument("--overlap", default="off", choices=["off", "on", "hi"],
+    ap.add_argument("--overlap", default="off", choices=["off", "on", "hi", "asm", "asm-hi"],
                     help="p2-3d push: Mat zero and action on a second stream beside the sparsity rebuild "
-                         "(hi: that stream at high priority)")
+                         "(hi: that stream at high priority); asm: the action on a second stream beside the "
+                         "Mat zero and assembly, after the rebuild")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stored", action="store_true", help="skip the stored-matrix action measurement")
     ap.add_argument("--log", default=None, help="also append the JSON line to this JSONL file")
