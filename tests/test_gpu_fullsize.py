@@ -183,3 +183,25 @@ def test_batch_2048_items_full(gpu):
         what = f"batch item {i} (n={host[i][0][0]}, P{host[i][0][1]})"
         PB.assert_close_scaled(v, wv, wa, 1e-12, what + " Mat")
         PB.assert_close_scaled(r, wb, wba, 1e-12, what + " RHS")
+
+
+def test_p1_square_64_full(gpu):
+    """P1 UnitSquareMesh 64x64 Helmholtz (8192 cells, 4225 nodes, nnz 29,057; the small workload):
+    pattern and lookup table, the whole matrix and RHS (f in P1, seed 1) with push and pull, and
+    the action on the benchmark's x."""
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+    pr = PB.make(2, 1, 64, 0.0)
+    g = PB.GpuProblem(pr)
+    rp, ci = _pattern_and_lut(fe, g, pr)
+    assert len(ci) == 7 * 64 * 64 + 6 * 64 + 1
+    want, scale = O.assemble_mat(2, 1, O.HELMHOLTZ, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, rp, ci)
+    f = mg.uniform_dat(pr.nnodes, 1)
+    bw, bs = O.assemble_vec(2, 1, 1, pr.cmap, pr.nnodes, pr.mesh.coords, pr.mesh.cell_vertex, f, pr.cmap)
+    for strat in (fe.STRATEGY_PUSH, fe.STRATEGY_PULL):
+        PB.assert_close_scaled(g.assemble(fe.FORM_HELMHOLTZ, strategy=strat), want, scale, 1e-12, "P1 64x64")
+        PB.assert_close_scaled(g.rhs(f, pr.cmap, 1, pr.nnodes, strategy=strat), bw, bs, 1e-12, "P1 64x64 RHS")
+    x = mg.uniform_dat(pr.nnodes, 2)
+    yw, ys = O.action(2, 1, O.HELMHOLTZ, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, x)
+    for strat in (fe.STRATEGY_PUSH, fe.STRATEGY_PULL):
+        PB.assert_close_scaled(g.action(fe.FORM_HELMHOLTZ, x, strategy=strat), yw, ys, 1e-12, "P1 64x64 action")
