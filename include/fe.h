@@ -164,11 +164,12 @@ fe_status fe_sparsity_build(fe_ctx *ctx, fe_map *rmap, fe_map *cmap, fe_sparsity
 /* Recomputes pattern, lookup table and incidence from the (possibly rewritten) map values into
  * the existing buffers, asynchronously (no host synchronisation).  The caller guarantees the
  * pattern size is unchanged; a changed nnz is flagged on the device and reported by fe_sync as
- * FE_EINVAL.  This is the per-step sparsity build of the benchmark.  A first row pass writes
- * every row whose length is unchanged straight into colidx; only when some row changed length
- * (same nnz, e.g. relabelled nodes) do the full row pass, the row-pointer scan and the colidx
- * compaction run (their launches are gated on a device flag, so the call stays asynchronous).
- * The result is the same either way. */
+ * FE_EINVAL.  This is the per-step sparsity build of the benchmark.  The incidence is filled
+ * against the previous row offsets, and a first row pass checks every row's incidence count and
+ * writes every row whose length is unchanged straight into colidx; only when some count or row
+ * length changed (e.g. relabelled nodes) do the full incidence (count, scan, fill), the full row
+ * pass, the row-pointer scan and the colidx compaction run (their launches are gated on a device
+ * flag, so the call stays asynchronous).  The result is the same either way. */
 fe_status fe_sparsity_rebuild(fe_sparsity *sp);
 /* Read-only views of the CSR pattern (device pointers owned by sp). */
 fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols, int64_t *nnz,

@@ -388,9 +388,12 @@ fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
   if (!sp->coltmp) return fail(FE_EINVAL, "fe_sparsity_rebuild: the pattern's build scratch was released");
   // In-place pass first: rows that keep their lengths go straight to colidx.  Only when a row's
   // length changed do the full row pass, its scan and the compaction run (gated on the device).
+  // The incidence is filled against the previous row offsets first; the in-place pass checks each
+  // row's count, and a changed count sends the rebuild through the full incidence too.
   FE_CHECK_CUDA(cudaMemsetAsync(sp->d_changed, 0, sizeof(int), c->stream), "fe_sparsity_rebuild");
-  FE_CHECK_CUDA(fe::sparsity_incidence(sp, c->stream, c->d_err, 0), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_incidence_reuse(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_rows_inplace(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(fe::sparsity_incidence_gated(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_rows(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_compact(sp, c->stream, c->d_err, 1, sp->d_changed), "fe_sparsity_rebuild");
   return ok();

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kTcThreads) k_mat_push_tc_kappa_p4(const AsmAr
         const int q = 32 * k + lane;
         const int i = q / ND, j = q - (q / ND) * ND;
         const int64_t base = __shfl_sync(0xffffffffu, rp, i < ND ? i : 0);
-        const int64_t len = __shfl_sync(0xffffffffu, rl, i < ND ? i : 0);
+        // the row length is needed (and shuffled) only in check mode; a.checks is uniform
+        const int64_t len = a.checks ? __shfl_sync(0xffffffffu, rl, i < ND ? i : 0) : 0;
         if (q < ND * ND) {
           const int lo = i < j ? i : j, hi = i < j ? j : i;
           const int n = lo * ND - lo * (lo - 1) / 2 + (hi - lo);  // upper-triangle index of (lo, hi)

@@ -112,6 +112,10 @@ cudaError_t launch_map_validate(const int32_t *v, int64_t n, int64_t limit, int 
 // incidence: counts -> adjptr (scan) -> adj fill; with_max: also the longest incidence list
 // (d_maxcnt, needed to size the row kernel at build time only)
 cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int with_max = 1);
+// rebuild: fill against the previous row offsets (counts checked by the in-place row pass), and
+// the full incidence gated on the device flag that pass sets
+cudaError_t sparsity_incidence_reuse(fe_sparsity *sp, cudaStream_t s, int *err);
+cudaError_t sparsity_incidence_gated(fe_sparsity *sp, cudaStream_t s, int *err, const int *gate);
 // sort rows, write lut, unique columns (coltmp at incidence-based offsets), row lengths -> rowptr
 // (scan).  gate as for the scan.
 cudaError_t sparsity_rows(fe_sparsity *sp, cudaStream_t s, int *err, const int *gate = nullptr);

@@ -109,7 +109,8 @@ __global__ void k_map_validate(const int32_t *__restrict__ v, int64_t n, int64_t
   }
 }
 
-__global__ void k_zero_i32(int32_t *p, int64_t n) {
+__global__ void k_zero_i32(int32_t *p, int64_t n, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = 0;
 }
@@ -133,7 +134,9 @@ __global__ void k_zero_f64(double *__restrict__ p, int64_t n) {
 }
 
 // incidence counts: rowcnt[r] = #(e, i) with rmap(e)[i] = r
-__global__ void k_inc_count(const int32_t *__restrict__ rmap, int64_t n, int64_t nrows, int32_t *cnt, int *err) {
+__global__ void k_inc_count(const int32_t *__restrict__ rmap, int64_t n, int64_t nrows, int32_t *cnt, int *err,
+                            const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     int32_t r = rmap[k];
     if (r < 0 || r >= nrows) {
@@ -155,13 +158,35 @@ __global__ void k_max_count(const int32_t *__restrict__ cnt, int64_t n, int *out
 
 // incidence fill: adj[adjptr[r] + slot] = k (k = e*ndr + i); slot order is arbitrary here and
 // made canonical by sparsity_canonical when an order-sensitive kernel needs it.
+// Each thread takes four incidences per round and issues their four cursor atomics before it
+// needs any result, so that the round trips of the returning atomics overlap.  guarded (a rebuild
+// filling against the previous row offsets): a slot past the row's previous length is not written
+// (the row pass then sees the changed count), and a map value out of range is flagged.
 __global__ void k_inc_fill(const int32_t *__restrict__ rmap, int64_t n, int64_t nrows,
-                           const int64_t *__restrict__ adjptr, int32_t *cursor, int32_t *__restrict__ adj) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    int32_t r = rmap[k];
-    if (r < 0 || r >= nrows) continue;
-    int slot = atomicAdd(&cursor[r], 1);
-    adj[adjptr[r] + slot] = (int32_t)k;
+                           const int64_t *__restrict__ adjptr, int32_t *cursor, int32_t *__restrict__ adj,
+                           int guarded = 0, int *err = nullptr, const int *gate = nullptr) {
+  if (gate && *gate == 0) return;
+  constexpr int U = 4;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < n; k0 += U * st) {
+    int32_t r[U];
+    int slot[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t k = k0 + u * st;
+      r[u] = k < n ? rmap[k] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) slot[u] = (r[u] >= 0 && r[u] < nrows) ? atomicAdd(&cursor[r[u]], 1) : 0;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (r[u] >= 0 && r[u] < nrows) {
+        const int64_t b = adjptr[r[u]];
+        if (!guarded || b + slot[u] < adjptr[r[u] + 1]) adj[b + slot[u]] = (int32_t)(k0 + u * st);
+      } else if (guarded && k0 + u * st < n) {
+        flag(err, ERR_RANGE, k0 + u * st);
+      }
+    }
   }
 }
 
@@ -272,6 +297,8 @@ struct RowsParams {
   int *changed;
   const int *gate;  // NULL, or a device flag: 0 = return without work
   int canon;        // also put every row's incidence list in ascending order (else it stays in fill order)
+  int check_counts; // rowlen holds a guarded fill's incidence counts: a row whose count differs from its
+                    // previous range sets *changed (read before the row's length overwrites it)
 };
 
 // Where row r's nu unique columns go: colidx in place when the in-place pass applies and the
@@ -485,6 +512,10 @@ __global__ void __launch_bounds__(256, 6) k_rows_build(const RowsParams p) {
       ah = p.adjptr[rh];
       nh = (int)(p.adjptr[rh + 1] - ah);
     }
+    if (p.check_counts) {  // the guarded fill's count against the range it was filled into
+      if ((lane & 15) == 0 && rh < p.nrows && p.rowlen[rh] != nh) *p.changed = 1;
+      __syncwarp();
+    }
     const bool mine_ok = rh < p.nrows && nh > 0 && nh <= 16 && nh * ndc <= 64;
     if (p.packed_ok && __all_sync(0xffffffffu, mine_ok)) {
       const int nu = row_by_sort_half<4, 6>(p, rh, ah, nh, nh * ndc, hadjs, hadje, hlbuf);
@@ -686,6 +717,31 @@ cudaError_t launch_zero_f64(double *p, int64_t n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Rebuild: the incidence filled against the previous row offsets (no count, no scan); the
+// in-place row pass checks every row's count, and sparsity_incidence_gated redoes the incidence
+// from scratch when some count changed.
+cudaError_t sparsity_incidence_reuse(fe_sparsity *sp, cudaStream_t s, int *err) {
+  const int64_t n = sp->ncell * sp->ndr;
+  k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows);
+  if (n > 0)
+    k_inc_fill<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj, 1,
+                                                 err);
+  return cudaGetLastError();
+}
+
+cudaError_t sparsity_incidence_gated(fe_sparsity *sp, cudaStream_t s, int *err, const int *gate) {
+  const int64_t n = sp->ncell * sp->ndr;
+  k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows, gate);
+  if (n > 0) k_inc_count<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->rowcnt, err, gate);
+  cudaError_t e = exclusive_scan_i32_to_i64(sp->rowcnt, sp->adjptr, sp->nrows, sp->scan_tmp, s, gate);
+  if (e != cudaSuccess) return e;
+  k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows, gate);
+  if (n > 0)
+    k_inc_fill<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj, 0,
+                                                 nullptr, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int with_max) {
   const int64_t n = sp->ncell * sp->ndr;
   k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows);
@@ -730,6 +786,7 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
   p.changed = changed;
   p.gate = gate;
   p.canon = 0;
+  p.check_counts = changed != nullptr;  // the in-place pass of a rebuild follows a guarded fill
   const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap + 64 + 96) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
