@@ -154,20 +154,33 @@ __global__ void __launch_bounds__(kTcThreads) k_mat_push_tc_kappa_p4(const AsmAr
       if (!__all_sync(0xffffffffu, ok)) continue;
       const uint8_t *L = a.lut + e * (ND * ND);
       const float *Sm = S + (size_t)m * kTcStride;
+      if (a.checks) {  // check mode (a separate loop, so that the normal scatter stays as it is)
+#pragma unroll
+        for (int k = 0; k < (ND * ND + 31) / 32; k++) {
+          const int q = 32 * k + lane;
+          const int i = q / ND, j = q - (q / ND) * ND;
+          const int64_t base = __shfl_sync(0xffffffffu, rp, i < ND ? i : 0);
+          const int64_t len = __shfl_sync(0xffffffffu, rl, i < ND ? i : 0);
+          if (q < ND * ND) {
+            const int lo = i < j ? i : j, hi = i < j ? j : i;
+            const int n = lo * ND - lo * (lo - 1) / 2 + (hi - lo);  // upper-triangle index of (lo, hi)
+            if (L[q] >= len)  // a lookup-table entry beyond its row is skipped
+              flag(a.err, ERR_LUT, e);
+            else
+              red_add_f64(a.vals + base + L[q], f32_to_f64_exact(Sm[n]));
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int k = 0; k < (ND * ND + 31) / 32; k++) {
         const int q = 32 * k + lane;
         const int i = q / ND, j = q - (q / ND) * ND;
         const int64_t base = __shfl_sync(0xffffffffu, rp, i < ND ? i : 0);
-        // the row length is needed (and shuffled) only in check mode; a.checks is uniform
-        const int64_t len = a.checks ? __shfl_sync(0xffffffffu, rl, i < ND ? i : 0) : 0;
         if (q < ND * ND) {
           const int lo = i < j ? i : j, hi = i < j ? j : i;
           const int n = lo * ND - lo * (lo - 1) / 2 + (hi - lo);  // upper-triangle index of (lo, hi)
-          if (a.checks && L[q] >= len)  // check mode: a lookup-table entry beyond its row is skipped
-            flag(a.err, ERR_LUT, e);
-          else
-            red_add_f64(a.vals + base + L[q], f32_to_f64_exact(Sm[n]));
+          red_add_f64(a.vals + base + L[q], f32_to_f64_exact(Sm[n]));
         }
       }
     }
