@@ -273,8 +273,17 @@ static void sparsity_free(fe_sparsity *sp) {
   dev_free(c, sp->vstage);
 }
 
-fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out) {
-  Range nvtx_range("fe_sparsity_build");
+}  // extern "C"
+
+namespace fe {
+
+// The sparsity build in three stages, each only launching work and asynchronous read-backs into
+// the caller's host slots (pinned ones keep every stage free of host synchronisation), so that a
+// caller building several patterns waits once per stage for all of them: begin (buffers,
+// incidence, the maps' range checks, the longest incidence list), rows (sort, ranks, row
+// lengths, rowptr; nnz and the longest row), finish (colidx and its compaction).  The caller
+// reads the device flags (check_device_flags) between the stages and discards a failed build.
+fe_status sparsity_build_begin(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out, int *h_maxcnt) {
   if (!valid(c)) return fail(FE_EHANDLE, "fe_sparsity_build: invalid context");
   if (!valid(rmap) || !valid(cmap) || rmap->ctx != c || cmap->ctx != c)
     return fail(FE_EHANDLE, "fe_sparsity_build: maps belong to another context");
@@ -313,68 +322,76 @@ fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity *
     delete sp;
     return fail(FE_ENOMEM, "fe_sparsity_build: device allocation failed");
   }
-  // 1. incidence (validates the row map), the column map's range check, and the longest incidence
-  //    list: one host synchronisation for all three (the build synchronises twice in all)
+  // incidence (validates the row map), the column map's range check, the longest incidence list
   cudaError_t e = fe::sparsity_incidence(sp, c->stream, c->d_err);
   if (e == cudaSuccess && cmap->to->size > 0 && ncell > 0)
     e = fe::launch_map_validate(cmap->values, ncell * cmap->arity, cmap->to->size, c->d_err, c->stream);
-  int maxcnt = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&maxcnt, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_maxcnt, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) {
     sparsity_free(sp);
     delete sp;
     return cuda_fail(e, "fe_sparsity_build");
   }
-  fe_status st = check_device_flags(c, "fe_sparsity_build");
-  if (st != FE_OK) {
-    sparsity_free(sp);
-    delete sp;
-    return st;
-  }
+  *out = sp;
+  return FE_OK;
+}
+
+fe_status sparsity_build_rows(fe_sparsity *sp, int maxcnt, int64_t *h_nnz, int *h_maxrow) {
+  fe_ctx *c = sp->ctx;
+  DeviceGuard g(c->device);
   const int64_t maxcand = (int64_t)maxcnt * sp->ndc;
-  if (maxcand > fe::kMaxCand) {
-    sparsity_free(sp);
-    delete sp;
+  if (maxcand > fe::kMaxCand)
     return fail(FE_EUNSUPPORTED, "fe_sparsity_build: a row has %lld candidate entries (limit %d)", (long long)maxcand,
                 fe::kMaxCand);
-  }
   sp->cap = 32;
   while (sp->cap < maxcand) sp->cap <<= 1;
   sp->acap = 4;
   while (sp->acap < maxcnt) sp->acap += 4;
-  // 2. rows: sort, ranks, row lengths, rowptr; nnz and the longest row read back together
-  int64_t nnz = 0;
-  int mr = 0;
-  e = fe::sparsity_rows(sp, c->stream, c->d_err);
+  cudaError_t e = fe::sparsity_rows(sp, c->stream, c->d_err);
   if (e == cudaSuccess) e = fe::launch_max_i32(sp->rowcnt, sp->nrows, sp->d_maxcnt, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&nnz, sp->rowptr + sp->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&mr, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  if (e != cudaSuccess) {
-    sparsity_free(sp);
-    delete sp;
-    return cuda_fail(e, "fe_sparsity_build");
-  }
-  st = check_device_flags(c, "fe_sparsity_build");
-  if (st != FE_OK) {
-    sparsity_free(sp);
-    delete sp;
-    return st;
-  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_nnz, sp->rowptr + sp->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_maxrow, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  return e != cudaSuccess ? cuda_fail(e, "fe_sparsity_build") : FE_OK;
+}
+
+fe_status sparsity_build_finish(fe_sparsity *sp, int64_t nnz, int maxrow) {
+  fe_ctx *c = sp->ctx;
+  DeviceGuard g(c->device);
   sp->nnz = nnz;
-  sp->maxrow = mr;
+  sp->maxrow = maxrow;
   sp->colidx = (int32_t *)dev_alloc(c, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
-  if (!sp->colidx) {
-    sparsity_free(sp);
-    delete sp;
-    return fail(FE_ENOMEM, "fe_sparsity_build: colidx allocation");
-  }
-  // 3. compact the unique columns into colidx (stream-ordered: it raises no flag, so the build
-  //    returns without waiting for it)
-  e = fe::sparsity_compact(sp, c->stream, c->d_err, 0);
-  if (e != cudaSuccess) {
-    sparsity_free(sp);
-    delete sp;
-    return cuda_fail(e, "fe_sparsity_build");
+  if (!sp->colidx) return fail(FE_ENOMEM, "fe_sparsity_build: colidx allocation");
+  // stream-ordered: the compaction raises no flag, so nothing waits for it
+  cudaError_t e = fe::sparsity_compact(sp, c->stream, c->d_err, 0);
+  return e != cudaSuccess ? cuda_fail(e, "fe_sparsity_build") : FE_OK;
+}
+
+fe_status sparsity_check_flags(fe_ctx *c, const char *where) { return check_device_flags(c, where); }
+
+void sparsity_discard(fe_sparsity *sp) {
+  if (!sp) return;
+  sparsity_free(sp);
+  delete sp;
+}
+
+}  // namespace fe
+
+extern "C" {
+
+fe_status fe_sparsity_build(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out) {
+  Range nvtx_range("fe_sparsity_build");
+  fe_sparsity *sp = nullptr;
+  int maxcnt = 0, mr = 0;
+  int64_t nnz = 0;
+  fe_status st = fe::sparsity_build_begin(c, rmap, cmap, &sp, &maxcnt);
+  if (st != FE_OK) return st;
+  st = check_device_flags(c, "fe_sparsity_build");  // waits for the incidence and the checks
+  if (st == FE_OK) st = fe::sparsity_build_rows(sp, maxcnt, &nnz, &mr);
+  if (st == FE_OK) st = check_device_flags(c, "fe_sparsity_build");  // waits for the row pass
+  if (st == FE_OK) st = fe::sparsity_build_finish(sp, nnz, mr);
+  if (st != FE_OK) {
+    fe::sparsity_discard(sp);
+    return st;
   }
   *out = sp;
   return ok();

@@ -111,6 +111,13 @@ cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n
 cudaError_t launch_map_validate(const int32_t *v, int64_t n, int64_t limit, int *err, cudaStream_t s);
 // incidence: counts -> adjptr (scan) -> adj fill; with_max: also the longest incidence list
 // (d_maxcnt, needed to size the row kernel at build time only)
+// the sparsity build in stages (fe_api.cpp): asynchronous read-backs into the caller's host slots;
+// the caller checks the device flags between stages and discards a failed build
+fe_status sparsity_build_begin(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsity **out, int *h_maxcnt);
+fe_status sparsity_build_rows(fe_sparsity *sp, int maxcnt, int64_t *h_nnz, int *h_maxrow);
+fe_status sparsity_build_finish(fe_sparsity *sp, int64_t nnz, int maxrow);
+fe_status sparsity_check_flags(fe_ctx *c, const char *where);
+void sparsity_discard(fe_sparsity *sp);
 cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int with_max = 1);
 // rebuild: fill against the previous row offsets (counts checked by the in-place row pass), and
 // the full incidence gated on the device flag that pass sets
@@ -231,6 +238,26 @@ cudaError_t launch_assemble_mat(const fe_form_desc &d, const AsmArgs &a, cudaStr
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 bool kernel_supported(const fe_form_desc &d);
+
+// ---- assembly of the systems a request loop admits together (fe_serve_asm.cu) ----
+// One system: a P1 or P2 Laplace Mat on its pattern (mat: staged pull arguments, zero_first) with
+// the flagged rows and columns eliminated, and its source right-hand side (vec: f in the same
+// space, y = b).  Tiles are numbered across the systems: cells in tiles of kServeCellTile, rows in
+// tiles of kServeRowTile; cell_tile0 / row_tile0 are a system's first tiles (non-decreasing).
+constexpr int kServeCellTile = 128, kServeRowTile = 256;
+struct ServeItem {
+  AsmArgs mat, vec;
+  void *mstage, *vstage;  // element matrices (full rows) and element vectors, arithmetic type
+  const int32_t *colidx;
+  const uint8_t *is_bc;
+  int p;
+  int64_t cell_tile0, row_tile0;
+};
+// Shared memory of the row launch for a system (rowcap accumulators per row group).
+size_t serve_row_smem(int p, int rowcap, int precision);
+// Two launches on s: element tensors of every cell, then every row (Mat, elimination, RHS).
+cudaError_t launch_serve_assembly(const ServeItem *d_items, int nitems, int64_t cell_tiles, int64_t row_tiles,
+                                  size_t row_smem, int precision, cudaStream_t s);
 
 // ---- stored element matrices (fe_stored_f64.cu, fe_stored_dd.cu) ----
 // Ke: [nd(nd+1)/2][ncell] FP64, entry-major (see fe_stored.cuh)

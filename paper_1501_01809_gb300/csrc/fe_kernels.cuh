@@ -380,13 +380,13 @@ __global__ void __launch_bounds__(kPushThreads) k_action_elem(const AsmArgs a, t
   for (int i = 0; i < ND; i++) out[i] = ye[i];
 }
 
+// One cell's source vector (f v dx) to the staging buffer (ND values at e ND); false (the error
+// flagged) on a bad map value.
 template <int DIM, int P, int Q, class Ops>
-__global__ void __launch_bounds__(kPushThreads) k_vec_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+__device__ __forceinline__ bool vec_elem_cell(const AsmArgs &a, typename Ops::T *__restrict__ stage, int64_t e) {
   using T = typename Ops::T;
   using S = fe_gen::Source<DIM, P, Q>;
   constexpr int ND = S::ND, NF = S::NF;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= a.ncell) return;
   double x[DIM + 1][DIM];
   int32_t v[DIM + 1];
   bool ok = gather_coords<DIM>(a, e, x, v);
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_elem(const AsmArgs a, type
   }
   if (!ok) {
     flag(a.err, ERR_RANGE, e);
-    return;
+    return false;
   }
   T Lam[Geo<DIM>::NLAM], vol, fe[NF];
   Geo<DIM>::template compute<Ops>(x, Lam, vol);
@@ -413,41 +413,38 @@ __global__ void __launch_bounds__(kPushThreads) k_vec_elem(const AsmArgs a, type
   T *out = stage + e * ND;
 #pragma unroll
   for (int i = 0; i < ND; i++) out[i] = b[i];
+  return true;
 }
 
-// Row owners of a Mat.  Each warp holds NG = 32 / ND groups of ND lanes, and each group owns a
-// row at a time (rows r = group, group + groups, ...).  A group walks its row's incidence list
-// {(e, i)} -- ascending (sparsity_canonical, before the launch) -- U incidences per round: lane j
-// of the group loads entry j of row i of cell e's staged element matrix (one contiguous ND-value
-// row per incidence) and its lookup-table slot for all U incidences first, then adds them into
-// the row's shared-memory accumulators one incidence after another.  Every slot therefore
-// receives its contributions in incidence order, as a single row owner would add them: the
-// result is bitwise reproducible.  The groups of a warp advance independently (a group that
-// finishes its row writes it out and starts its next one), and one FP64 add instruction serves
-// all of them, so the FP64 pipe -- 1/16 of a warp instruction per clock on this GPU -- is not
-// spent on idle lanes.  INC semantics: the row's values are read once (unless zero_first) and
-// written once.  Shared memory: rowcap accumulators per group.
-template <int ND, class Ops>
-__global__ void __launch_bounds__(256) k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr,
-                                                  const int32_t *__restrict__ adj, const int64_t *__restrict__ rowptr,
-                                                  const uint8_t *__restrict__ lut,
-                                                  const typename Ops::T *__restrict__ stage, double *__restrict__ vals,
-                                                  int rowcap, int zero_first, int *err, int checks) {
+template <int DIM, int P, int Q, class Ops>
+__global__ void __launch_bounds__(kPushThreads) k_vec_elem(const AsmArgs a, typename Ops::T *__restrict__ stage) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < a.ncell) vec_elem_cell<DIM, P, Q, Ops>(a, stage, e);
+}
+
+// The row-owner loop itself, for one group of ND lanes (lane j of it, `on` false for the lanes
+// beyond the warp's NG groups, which still take part in its warp-wide steps): rows first,
+// first + step, ... below rend, accumulated in buf (rowcap slots).  Called by every lane of the
+// warp.  With BC, the rows and columns of the nodes flagged in is_bc are eliminated as each row
+// is written out (symmetric elimination for u = 0 on the boundary: a flagged row keeps 1 on its
+// diagonal and 0 elsewhere, a flagged column 0), exactly the values the separate elimination
+// kernel writes.
+template <int ND, class Ops, bool BC = false>
+__device__ __forceinline__ void pull_mat_rows(int64_t first, int64_t step, int64_t rend, bool on, int j,
+                                              typename Ops::T *buf, const int64_t *__restrict__ adjptr,
+                                              const int32_t *__restrict__ adj, const int64_t *__restrict__ rowptr,
+                                              const uint8_t *__restrict__ lut,
+                                              const typename Ops::T *__restrict__ stage, double *__restrict__ vals,
+                                              int rowcap, int zero_first, int *err, int checks,
+                                              const int32_t *__restrict__ colidx = nullptr,
+                                              const uint8_t *__restrict__ is_bc = nullptr) {
   using T = typename Ops::T;
-  constexpr int NG = 32 / ND > 0 ? 32 / ND : 1;  // row groups per warp
-  constexpr int U = 4;                           // incidences per round
-  extern __shared__ __align__(16) unsigned char smp[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int gi = lane / ND, j = lane - (lane / ND) * ND;
-  const bool on = gi < NG;  // lanes beyond NG groups idle (and take part in the warp-wide steps)
-  T *buf = reinterpret_cast<T *>(smp) + ((size_t)wid * NG + (on ? gi : 0)) * rowcap;
-  const int64_t groups = (int64_t)gridDim.x * wpb * NG;
-  int64_t r = ((int64_t)blockIdx.x * wpb + wid) * NG + gi;
-  int64_t b = 0, a0 = 0;
+  constexpr int U = 4;  // incidences per round
+  int64_t r = first, b = 0, a0 = 0;
   int len = 0, na = 0, a = 0;
   bool have = false;
   auto start_row = [&]() {  // the group's next row: its range, incidence list and zeroed slots
-    have = on && r < nrows;
+    have = on && r < rend;
     a = 0;
     if (have) {
       b = rowptr[r];
@@ -492,15 +489,52 @@ __global__ void __launch_bounds__(256) k_mat_pull(int64_t nrows, const int64_t *
     a += U;
     if (have && a >= na) {  // the row is complete: write it out, take the group's next row
       double *out = vals + b;
+      bool bc_row = false;
+      if constexpr (BC) bc_row = is_bc[r] != 0;
       for (int qq = j; qq < len; qq += ND) {
-        const double d = Ops::to_f64(buf[qq]);
+        double d = Ops::to_f64(buf[qq]);
+        if constexpr (BC) {
+          const int32_t col = colidx[b + qq];
+          if (bc_row) d = col == r ? 1.0 : 0.0;
+          else if (is_bc[col]) d = 0.0;
+        }
         out[qq] = zero_first ? d : out[qq] + d;
       }
-      r += groups;
+      r += step;
       start_row();
     }
     __syncwarp();
   }
+}
+
+// Row owners of a Mat.  Each warp holds NG = 32 / ND groups of ND lanes, and each group owns a
+// row at a time (rows r = group, group + groups, ...).  A group walks its row's incidence list
+// {(e, i)} -- ascending (sparsity_canonical, before the launch) -- U incidences per round: lane j
+// of the group loads entry j of row i of cell e's staged element matrix (one contiguous ND-value
+// row per incidence) and its lookup-table slot for all U incidences first, then adds them into
+// the row's shared-memory accumulators one incidence after another.  Every slot therefore
+// receives its contributions in incidence order, as a single row owner would add them: the
+// result is bitwise reproducible.  The groups of a warp advance independently (a group that
+// finishes its row writes it out and starts its next one), and one FP64 add instruction serves
+// all of them, so the FP64 pipe -- 1/16 of a warp instruction per clock on this GPU -- is not
+// spent on idle lanes.  INC semantics: the row's values are read once (unless zero_first) and
+// written once.  Shared memory: rowcap accumulators per group.
+template <int ND, class Ops>
+__global__ void __launch_bounds__(256) k_mat_pull(int64_t nrows, const int64_t *__restrict__ adjptr,
+                                                  const int32_t *__restrict__ adj, const int64_t *__restrict__ rowptr,
+                                                  const uint8_t *__restrict__ lut,
+                                                  const typename Ops::T *__restrict__ stage, double *__restrict__ vals,
+                                                  int rowcap, int zero_first, int *err, int checks) {
+  using T = typename Ops::T;
+  constexpr int NG = 32 / ND > 0 ? 32 / ND : 1;  // row groups per warp
+  extern __shared__ __align__(16) unsigned char smp[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int gi = lane / ND, j = lane - (lane / ND) * ND;
+  const bool on = gi < NG;  // lanes beyond NG groups idle (and take part in the warp-wide steps)
+  T *buf = reinterpret_cast<T *>(smp) + ((size_t)wid * NG + (on ? gi : 0)) * rowcap;
+  const int64_t groups = (int64_t)gridDim.x * wpb * NG;
+  pull_mat_rows<ND, Ops>(((int64_t)blockIdx.x * wpb + wid) * NG + gi, groups, nrows, on, j, buf, adjptr, adj, rowptr,
+                         lut, stage, vals, rowcap, zero_first, err, checks);
 }
 
 // Row owners of a Dat: y[r] (+)= sum over the row's incidence list of stage[e*ND + i], in order.

@@ -18,8 +18,11 @@
 //   2. meanwhile admit, in arrival order, requests that have arrived while a slot is free and the
 //      request's worst-case device footprint fits in the budget beside what is held (a request
 //      larger than the whole budget is refused; a request that does not fit yet waits, and so do
-//      the ones behind it).  Admission runs on a second stream, so the systems already iterating
-//      are not paused by it; the server's stream waits for it before the next tick;
+//      the ones behind it).  The requests admitted together form a round, built in three stages
+//      with one host wait between stages whatever their number (admit_round), and assembled in
+//      two launches for all of them (fe_serve_asm.cu).  Admission runs on a second stream, so the
+//      systems already iterating are not paused by it; the server's stream waits for it before
+//      the next tick;
 //   3. poll the tick: converged systems copy their solution to the host and free everything they
 //      held.  With nothing iterating and nothing admitted, sleep until the next arrival.
 // Memory is accounted exactly: the server routes its allocations through a counting allocator that
@@ -54,6 +57,7 @@ struct MeshEntry {
   void *d_map = nullptr, *d_cv = nullptr, *d_xy = nullptr, *d_bc = nullptr;
   int refs = 0;           // admitted requests using it
   uint64_t last_use = 0;  // admission counter at the last use (least recently used is evicted first)
+  bool ready = false;     // its sparsity is complete (false while the round that builds it runs)
 };
 
 struct Holding {  // device objects of one admitted request
@@ -63,7 +67,9 @@ struct Holding {  // device objects of one admitted request
   fe_mat *A = nullptr;
   void *d_f = nullptr, *d_b = nullptr, *d_x = nullptr;
   int slot = -1;
-  bool big = false;  // iterating in the large-system engine (high-priority stream)
+  bool big = false;    // iterating in the large-system engine (high-priority stream)
+  bool build = false;  // builds its mesh in its admission round
+  void *mstage = nullptr, *vstage = nullptr;  // element tensors of the round's assembly (transient)
 };
 
 struct Req {
@@ -93,6 +99,13 @@ struct Server {
   std::vector<Req> reqs;
   std::vector<MeshEntry *> meshes;  // the cache: entries with a key (private ones are not listed)
   uint64_t admissions = 0;
+  // pinned host slots for the staged sparsity builds of one admission round (one per request)
+  int *h_maxcnt = nullptr, *h_maxrow = nullptr;
+  int64_t *h_nnz = nullptr;
+  // the table of the round's batched assembly: pinned host copy, device copy, and the event after
+  // which the host copy may be rewritten
+  ServeItem *h_items = nullptr, *d_items = nullptr;
+  cudaEvent_t items_read = nullptr;
   int cache_hits = 0, cache_misses = 0, cache_evictions = 0, sparsity_builds = 0;
   // accounting
   // pointer -> (bytes, owner; kOwnerServer = server tables, kOwnerCache = cached meshes, else request)
@@ -232,7 +245,7 @@ void release(Server *s, Req &q) {
   if (h.A) fe_mat_destroy(h.A);
   for (fe_dat *d : {h.F, h.B, h.X})
     if (d) fe_dat_destroy(d);
-  for (void *p : {h.d_f, h.d_b, h.d_x}) dev_free(s->ctx, p);
+  for (void *p : {h.d_f, h.d_b, h.d_x, h.mstage, h.vstage}) dev_free(s->ctx, p);
   if (h.mesh) {
     if (h.private_mesh) mesh_free(s, h.mesh);
     else h.mesh->refs--;  // a cached mesh stays until evicted
@@ -242,7 +255,10 @@ void release(Server *s, Req &q) {
 }
 
 // Evicts unused cached meshes, least recently used first, until `need` more bytes fit in the
-// budget beside what is held; returns whether they fit.
+// budget beside what is held; returns whether they fit.  Nothing waits: an entry without
+// references has no work in flight.  Its last users have retired, each after a wait on the stream
+// it iterated on, whose ticks had waited for their admission; its frees are stream-ordered on the
+// admission stream (the context's stream while the loop admits).
 bool make_room(Server *s, size_t held, size_t need) {
   auto fits = [&]() { return s->base_bytes + s->cache_bytes + held + need <= s->cfg.hbm_budget; };
   while (!fits()) {
@@ -250,9 +266,6 @@ bool make_room(Server *s, size_t held, size_t need) {
     for (MeshEntry *m : s->meshes)
       if (m->refs == 0 && (!victim || m->last_use < victim->last_use)) victim = m;
     if (!victim) return false;
-    cudaStreamSynchronize(s->adm);
-    cudaStreamSynchronize(s->main_stream);
-    cudaStreamSynchronize(s->hi);
     s->meshes.erase(std::find(s->meshes.begin(), s->meshes.end(), victim));
     const int64_t saved = s->owner;
     s->owner = kOwnerCache;
@@ -270,9 +283,10 @@ MeshEntry *find_mesh(Server *s, const fe_solve_request &r) {
   return nullptr;
 }
 
-// Builds a mesh entry on the device: copies of the maps, coordinates and boundary flags, and the
-// sparsity (incidence, pattern, lookup table; its scratch columns are freed at once).
-fe_status mesh_build(Server *s, const fe_solve_request &r, MeshEntry *m) {
+// Starts a mesh entry on the device: copies of the maps, coordinates and boundary flags, its sets,
+// maps and coordinate Dat, and the first stage of its sparsity build (the longest incidence list
+// read back into the server's pinned slot k); admit_round finishes it.
+fe_status mesh_begin(Server *s, const fe_solve_request &r, MeshEntry *m, int k) {
   fe_ctx *c = s->ctx;
   const int nd = nodes_p(r.degree);
   SV_TRY(copy_in(s, &m->d_map, r.cell_node, sizeof(int32_t) * r.ncell * nd));
@@ -282,81 +296,210 @@ fe_status mesh_build(Server *s, const fe_solve_request &r, MeshEntry *m) {
   SV_TRY(fe_set_create(c, r.ncell, &m->cells));
   SV_TRY(fe_set_create(c, r.nnodes, &m->nodes));
   SV_TRY(fe_set_create(c, r.nvert, &m->verts));
-  SV_TRY(fe_map_create(c, m->cells, m->nodes, nd, (const int32_t *)m->d_map, 1, &m->M));
-  SV_TRY(fe_map_create(c, m->cells, m->verts, 3, (const int32_t *)m->d_cv, 1, &m->CM));
+  // the range checks are launched without waiting: the flags are read once per stage of the round,
+  // before any kernel indexes through the maps (the sparsity build checks the cell-node map)
+  SV_TRY(fe_map_create(c, m->cells, m->nodes, nd, (const int32_t *)m->d_map, 0, &m->M));
+  SV_TRY(fe_map_create(c, m->cells, m->verts, 3, (const int32_t *)m->d_cv, 0, &m->CM));
+  if (r.ncell > 0 && launch_map_validate((const int32_t *)m->d_cv, r.ncell * 3, r.nvert, c->d_err, c->stream) != cudaSuccess)
+    return FE_ECUDA;
   SV_TRY(fe_dat_create(c, m->verts, 2, (double *)m->d_xy, &m->XY));
-  SV_TRY(fe_sparsity_build(c, m->M, m->M, &m->sp));
-  s->sparsity_builds++;
-  dev_free(c, m->sp->coltmp);  // the build's scratch columns
-  m->sp->coltmp = nullptr;
+  SV_TRY(sparsity_build_begin(c, m->M, m->M, &m->sp, &s->h_maxcnt[k]));
   return FE_OK;
 }
 
-// Build one request's system on the device and hand it to the CG engine.  Its mesh comes from
-// the cache when an entry with its key is there (no copies of the mesh, no sparsity build);
-// otherwise it is built, and kept in the cache when the request has a key.
-fe_status admit(Server *s, Req &q) {
-  const fe_solve_request &r = q.in;
-  Holding &h = q.h;
+// The request at fault when a stage's range check failed (the device flags are the context's, so
+// they do not say whose map it was): the first new mesh of the round with a map value outside
+// its target set, read from the request's host arrays.
+int64_t culprit(const Server *s, const std::vector<int64_t> &ids) {
+  for (int64_t id : ids) {
+    const fe_solve_request &r = s->reqs[id].in;
+    if (!s->reqs[id].h.build) continue;
+    const int64_t nc = r.ncell * nodes_p(r.degree), nv = r.ncell * 3;
+    for (int64_t k = 0; k < nc; k++)
+      if (r.cell_node[k] < 0 || r.cell_node[k] >= r.nnodes) return id;
+    for (int64_t k = 0; k < nv; k++)
+      if (r.cell_vertex[k] < 0 || r.cell_vertex[k] >= r.nvert) return id;
+  }
+  return ids[0];
+}
+
+// Builds the systems of one admission round on the device and hands them to the CG engines.  The
+// loop has planned the round: each request fits in the budget, its mesh entry is referenced (a
+// cached one, or a new one that the request builds: h.build), so that no later request of the
+// round evicts it.  Stages, each only launching work on the admission stream:
+//   1. the new meshes' copies and range checks and the first stage of their sparsity builds (the
+//      longest incidence list read back into a pinned slot); every request's vectors;
+//   2. after one wait for all of them, the row pass of every new pattern (nnz and the longest
+//      row read back);
+//   3. after a second wait, the column compaction, every request's Mat and staging, then ONE
+//      element-tensor launch and ONE row launch for the whole round (Laplace Mat with the
+//      boundary rows and columns eliminated, source right-hand side), then each system's CG
+//      set-up.
+// A round without new meshes does not wait at all.  On failure *failed is the request at fault.
+fe_status admit_round(Server *s, const std::vector<int64_t> &ids, int64_t *failed) {
   fe_ctx *c = s->ctx;
   cudaStream_t st = c->stream;
-  const int64_t self = s->owner;
-  MeshEntry *m = find_mesh(s, r);
-  if (m) {
-    s->cache_hits++;
-  } else {
-    m = new (std::nothrow) MeshEntry();
-    if (!m) return FE_ENOMEM;
-    m->key = r.mesh_key;
-    if (r.mesh_key != 0) {
-      s->cache_misses++;
-      s->meshes.push_back(m);
-      s->owner = kOwnerCache;  // its memory is the cache's from here on
-    } else {
+  const int n = (int)ids.size();
+  std::vector<int> slot(n, -1);  // pinned slot of each mesh built in the round
+  auto mesh_owner = [&](int k) { return s->reqs[ids[k]].h.private_mesh ? ids[k] : kOwnerCache; };
+  int nb = 0;
+  for (int k = 0; k < n; k++) {  // stage 1
+    Req &q = s->reqs[ids[k]];
+    const fe_solve_request &r = q.in;
+    Holding &h = q.h;
+    *failed = ids[k];
+    if (h.build) {
+      slot[k] = nb++;
+      s->owner = mesh_owner(k);
+      const fe_status bs = mesh_begin(s, r, h.mesh, slot[k]);
+      s->owner = ids[k];
+      if (bs != FE_OK) return bs;
+    }
+    s->owner = ids[k];
+    MeshEntry *m = h.mesh;
+    SV_TRY(copy_in(s, &h.d_f, r.f, sizeof(double) * r.nnodes));
+    h.d_b = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
+    h.d_x = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
+    if (!h.d_b || !h.d_x) return FE_ENOMEM;
+    if (cudaMemsetAsync(h.d_x, 0, sizeof(double) * r.nnodes, st) != cudaSuccess) return FE_ECUDA;
+    SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_f, &h.F));
+    SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_b, &h.B));
+    SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_x, &h.X));
+  }
+  if (nb > 0) {
+    fe_status fs = sparsity_check_flags(c, "fe_server_run");  // the one wait of stage 1
+    if (fs != FE_OK) {
+      *failed = culprit(s, ids);
+      return fs;
+    }
+    for (int k = 0; k < n; k++) {                        // stage 2
+      if (slot[k] < 0) continue;
+      *failed = ids[k];
+      SV_TRY(sparsity_build_rows(s->reqs[ids[k]].h.mesh->sp, s->h_maxcnt[slot[k]], &s->h_nnz[slot[k]],
+                                 &s->h_maxrow[slot[k]]));
+    }
+    fs = sparsity_check_flags(c, "fe_server_run");  // the one wait of stage 2
+    if (fs != FE_OK) {
+      *failed = culprit(s, ids);
+      return fs;
+    }
+    for (int k = 0; k < n; k++) {
+      if (slot[k] < 0) continue;
+      MeshEntry *m = s->reqs[ids[k]].h.mesh;
+      *failed = ids[k];
+      s->owner = mesh_owner(k);
+      fs = sparsity_build_finish(m->sp, s->h_nnz[slot[k]], s->h_maxrow[slot[k]]);
+      s->owner = ids[k];
+      if (fs != FE_OK) return fs;
+      m->ready = true;
+      s->sparsity_builds++;
+    }
+  }
+  // stage 3: the round's table (the host copy is rewritten once the previous round's copy has
+  // been read), the Mats and the transient element staging
+  if (cudaEventSynchronize(s->items_read) != cudaSuccess) return FE_ECUDA;
+  int64_t cell_tiles = 0, row_tiles = 0;
+  size_t row_smem = 0;
+  for (int k = 0; k < n; k++) {
+    Req &q = s->reqs[ids[k]];
+    const fe_solve_request &r = q.in;
+    Holding &h = q.h;
+    MeshEntry *m = h.mesh;
+    *failed = ids[k];
+    s->owner = ids[k];
+    if (sparsity_canonical(m->sp, st) != cudaSuccess) return FE_ECUDA;  // the row owners sum in incidence order
+    SV_TRY(fe_mat_create(c, m->sp, &h.A));
+    const fe_form_desc d{FE_FORM_LAPLACE, 2, r.degree, 0, s->cfg.precision, FE_STRATEGY_PULL};
+    const int nd = nodes_p(r.degree);
+    h.mstage = dev_alloc(c, std::max<size_t>(stage_bytes_mat(d, r.ncell), 16));
+    h.vstage = dev_alloc(c, std::max<size_t>(stage_bytes_vec(d, r.ncell, nd), 16));
+    if (!h.mstage || !h.vstage) return FE_ENOMEM;
+    const size_t smem = serve_row_smem(r.degree, m->sp->maxrow, s->cfg.precision);
+    if (smem > 227 * 1024) {
+      snprintf(g_vmsg, sizeof g_vmsg, "a row of %d entries is too long for the batched assembly", m->sp->maxrow);
+      return FE_EUNSUPPORTED;
+    }
+    row_smem = std::max(row_smem, smem);
+    ServeItem &it = s->h_items[k];
+    memset(&it, 0, sizeof it);
+    AsmArgs &a = it.mat;
+    a.ncell = r.ncell;
+    a.map = (const int32_t *)m->d_map;
+    a.coords = (const double *)m->d_xy;
+    a.cmapv = (const int32_t *)m->d_cv;
+    a.nvert = r.nvert;
+    a.nrows = r.nnodes;
+    a.rowptr = m->sp->rowptr;
+    a.lut = m->sp->lut;
+    a.vals = h.A->values;
+    a.adjptr = m->sp->adjptr;
+    a.adj = m->sp->adj;
+    a.err = c->d_err;
+    a.checks = c->checks;
+    a.rowcap = m->sp->maxrow;
+    a.zero_first = 1;
+    it.vec = a;
+    it.vec.rowptr = nullptr;
+    it.vec.lut = nullptr;
+    it.vec.vals = nullptr;
+    it.vec.coef = (const double *)h.d_f;  // f in the same space: its map is the cell-node map
+    it.vec.coefmap = (const int32_t *)m->d_map;
+    it.vec.ncoef = r.nnodes;
+    it.vec.y = (double *)h.d_b;
+    it.mstage = h.mstage;
+    it.vstage = h.vstage;
+    it.colidx = m->sp->colidx;
+    it.is_bc = (const uint8_t *)m->d_bc;
+    it.p = r.degree;
+    it.cell_tile0 = cell_tiles;
+    it.row_tile0 = row_tiles;
+    cell_tiles += (r.ncell + kServeCellTile - 1) / kServeCellTile;
+    row_tiles += (r.nnodes + kServeRowTile - 1) / kServeRowTile;
+  }
+  *failed = ids[0];
+  if (cudaMemcpyAsync(s->d_items, s->h_items, sizeof(ServeItem) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaEventRecord(s->items_read, st) != cudaSuccess ||
+      launch_serve_assembly(s->d_items, n, cell_tiles, row_tiles, row_smem, s->cfg.precision, st) != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_vmsg, sizeof g_vmsg, "launching the batched assembly of %d systems", n);
+    return FE_ECUDA;
+  }
+  for (int k = 0; k < n; k++) {  // the staging is read by the launches above alone (frees are stream-ordered)
+    Holding &h = s->reqs[ids[k]].h;
+    dev_free(c, h.mstage);
+    dev_free(c, h.vstage);
+    h.mstage = h.vstage = nullptr;
+  }
+  for (int k = 0; k < n; k++) {  // CG set-up
+    Req &q = s->reqs[ids[k]];
+    Holding &h = q.h;
+    *failed = ids[k];
+    s->owner = ids[k];
+    h.big = q.in.nnodes > cg_one_wave_rows(s->cg);
+    SV_TRY(fe_cg_add(h.big ? s->cgb : s->cg, h.A, h.B, h.X, s->cfg.rtol, s->cfg.maxit, &h.slot));
+  }
+  return FE_OK;
+}
+
+// Undoes a failed round (the admission stream idle): requests that reference a mesh which the
+// round did not finish drop that reference, the partly built entries leave the cache and go
+// with the request that built them, then every request of the round releases what it holds.
+void fail_round(Server *s, const std::vector<int64_t> &ids) {
+  for (int64_t id : ids) {
+    Holding &h = s->reqs[id].h;
+    if (h.mesh && !h.mesh->ready && !h.build) {
+      h.mesh->refs--;
+      h.mesh = nullptr;
+    }
+  }
+  for (int64_t id : ids) {
+    Holding &h = s->reqs[id].h;
+    if (h.build && !h.mesh->ready && !h.private_mesh) {
+      s->meshes.erase(std::find(s->meshes.begin(), s->meshes.end(), h.mesh));
       h.private_mesh = true;
     }
-    h.mesh = m;  // released with the request if the build fails
-    m->refs++;
-    const fe_status bs = mesh_build(s, r, m);
-    s->owner = self;
-    if (bs != FE_OK) {  // a partly built entry never stays in the cache: freed with the request
-      if (!h.private_mesh) {
-        s->meshes.erase(std::find(s->meshes.begin(), s->meshes.end(), m));
-        h.private_mesh = true;
-      }
-      return bs;
-    }
-    m->refs--;
   }
-  h.mesh = m;
-  m->refs++;
-  m->last_use = ++s->admissions;
-  SV_TRY(copy_in(s, &h.d_f, r.f, sizeof(double) * r.nnodes));
-  h.d_b = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
-  h.d_x = dev_alloc(c, sizeof(double) * (r.nnodes > 0 ? r.nnodes : 1));
-  if (!h.d_b || !h.d_x) return FE_ENOMEM;
-  if (cudaMemsetAsync(h.d_x, 0, sizeof(double) * r.nnodes, st) != cudaSuccess) return FE_ECUDA;
-  SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_f, &h.F));
-  SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_b, &h.B));
-  SV_TRY(fe_dat_create(c, m->nodes, 1, (double *)h.d_x, &h.X));
-  SV_TRY(fe_mat_create(c, m->sp, &h.A));
-  SV_TRY(fe_assemble_mat(c, s->klap[r.degree], m->cells, h.A, 1, m->XY, m->CM, nullptr, 0));
-  fe_arg fa{h.F, m->M};
-  SV_TRY(fe_assemble_vec(c, s->ksrc[r.degree], m->cells, h.B, m->M, 1, m->XY, m->CM, &fa, 1, m->sp));
-  if (launch_dirichlet(r.nnodes, m->sp->rowptr, m->sp->colidx, h.A->values, (double *)h.d_b,
-                       (const uint8_t *)m->d_bc, nullptr, st) != cudaSuccess)
-    return FE_ECUDA;
-  // transient buffers of the assembly: staging of the row-owner sums (the vector staging sits on
-  // the shared sparsity but is this request's: freed before the next request uses the mesh)
-  dev_free(c, h.A->stage);
-  h.A->stage = nullptr;
-  h.A->stage_bytes = 0;
-  dev_free(c, m->sp->vstage);
-  m->sp->vstage = nullptr;
-  m->sp->vstage_bytes = 0;
-  h.big = r.nnodes > cg_one_wave_rows(s->cg);
-  SV_TRY(fe_cg_add(h.big ? s->cgb : s->cg, h.A, h.B, h.X, s->cfg.rtol, s->cfg.maxit, &h.slot));
-  return FE_OK;
+  for (int64_t id : ids) release(s, s->reqs[id]);
 }
 
 void server_free(Server *s) {
@@ -385,9 +528,13 @@ void server_free(Server *s) {
   if (s->hi) cudaStreamSynchronize(s->hi);
   if (s->ctx) {
     s->ctx->stream = s->main_stream ? s->main_stream : s->ctx->stream;
+    if (s->d_items) dev_free(s->ctx, s->d_items);
     cudaStreamSynchronize(s->ctx->stream);
     fe_ctx_destroy(s->ctx);
   }
+  for (void *p : {(void *)s->h_maxcnt, (void *)s->h_maxrow, (void *)s->h_nnz, (void *)s->h_items})
+    if (p) cudaFreeHost(p);
+  if (s->items_read) cudaEventDestroy(s->items_read);
   if (s->adm_done) cudaEventDestroy(s->adm_done);
   if (s->adm) cudaStreamDestroy(s->adm);
   if (s->hi) cudaStreamDestroy(s->hi);
@@ -438,6 +585,21 @@ fe_status server_create(fe_ctx *parent, const fe_server_config *cfg, fe_server *
     }
   }
   if (st == FE_OK) st = fe_ctx_set_allocator(s->ctx, count_alloc, count_free, s);
+  if (st == FE_OK) {  // the admission rounds' read-back slots and assembly table
+    const size_t na = (size_t)cfg->max_active;
+    if (cudaHostAlloc((void **)&s->h_maxcnt, sizeof(int) * na, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_maxrow, sizeof(int) * na, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_nnz, sizeof(int64_t) * na, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->h_items, sizeof(ServeItem) * na, cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->items_read, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      st = FE_ECUDA;
+    }
+    if (st == FE_OK) {
+      s->d_items = (ServeItem *)dev_alloc(s->ctx, sizeof(ServeItem) * na);
+      if (!s->d_items) st = FE_ENOMEM;
+    }
+  }
   for (int p = 1; p <= 2 && st == FE_OK; p++) {
     fe_form_desc d{FE_FORM_LAPLACE, 2, p, 0, cfg->precision, FE_STRATEGY_PULL};
     st = fe_kernel_create(s->ctx, &d, &s->klap[p]);
@@ -538,48 +700,73 @@ fe_status server_run(fe_server *h) {
       }
     }
     s->tick_s += now_s(t0) - tt0;
-    // 2. admission, in arrival order, on the admission stream while the tick runs
+    // 2. admission, in arrival order, on the admission stream while the tick runs: plan a round
+    //    of every request that has arrived and fits, then build the round together
     bool admitted = false;
-    fe_status adm_st = FE_OK;
-    int64_t adm_failed = -1;
     {
       OnStream on(s, s->adm);
-      while (next < order.size() && (int)active.size() < cfg.max_active) {
+      std::vector<int64_t> round;
+      size_t pending = 0;  // planned bytes of the round (a new mesh counted in its request's)
+      while (next < order.size() && (int)(active.size() + round.size()) < cfg.max_active) {
         Req &q = s->reqs[order[next]];
         if (q.in.arrival_s > now_s(t0)) break;
+        MeshEntry *m = find_mesh(s, q.in);
         // a cached mesh is not charged again: the request needs only its own part
-        const size_t need = find_mesh(s, q.in) ? q.estimate - q.mesh_estimate : q.estimate;
+        const size_t need = m ? q.estimate - q.mesh_estimate : q.estimate;
         if (s->base_bytes + need > cfg.hbm_budget) {
           q.res.status = FE_SOLVE_REFUSED;
           q.res.admitted_s = q.res.finished_s = now_s(t0);
           next++;
           continue;
         }
-        if (!make_room(s, held, need)) break;  // wait for memory (unused cached meshes are evicted first)
-        const int64_t id = order[next];
-        q.res.admitted_s = now_s(t0);
-        s->owner = id;
-        fe_status st = admit(s, q);
-        s->owner = -1;
-        s->admit_s += now_s(t0) - q.res.admitted_s;
-        if (st != FE_OK) {
-          snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)id, fe_last_error());
-          adm_st = st;
-          adm_failed = id;
-          break;
+        if (!make_room(s, held + pending, need)) break;  // wait for memory (unused cached meshes are evicted first)
+        Holding &h = q.h;
+        if (m) {
+          s->cache_hits++;
+        } else {
+          m = new (std::nothrow) MeshEntry();
+          if (!m) break;  // admitted later, if ever (the round so far goes ahead)
+          m->key = q.in.mesh_key;
+          h.build = true;
+          if (m->key != 0) {  // cached from now on: later requests of the round with its key share it
+            s->cache_misses++;
+            s->meshes.push_back(m);
+          } else {
+            h.private_mesh = true;
+          }
         }
-        if (s->owner_bytes[id] > q.estimate) s->estimate_misses++;
-        q.res.bytes = s->owner_bytes[id];
-        held += q.res.bytes;
-        active.push_back(id);
-        admitted = true;
+        h.mesh = m;
+        m->refs++;
+        m->last_use = ++s->admissions;
+        q.res.admitted_s = now_s(t0);
+        pending += need;
+        round.push_back(order[next]);
         next++;
       }
-    }
-    if (adm_st != FE_OK) {
-      cudaStreamSynchronize(s->adm);  // the failed request's work on the admission stream has ended
-      release(s, s->reqs[adm_failed]);
-      return adm_st;
+      if (!round.empty()) {
+        const double tr0 = now_s(t0);
+        int64_t failed = round[0];
+        g_vmsg[0] = 0;
+        const fe_status st = admit_round(s, round, &failed);
+        s->owner = -1;
+        s->admit_s += now_s(t0) - tr0;
+        if (st != FE_OK) {
+          char why[384];
+          snprintf(why, sizeof why, "%s", g_vmsg[0] ? g_vmsg : fe_last_error());
+          snprintf(g_vmsg, sizeof g_vmsg, "fe_server_run: request %lld: %s", (long long)failed, why);
+          cudaStreamSynchronize(s->adm);  // the round's work on the admission stream has ended
+          fail_round(s, round);
+          return st;
+        }
+        for (int64_t id : round) {
+          Req &q = s->reqs[id];
+          if (s->owner_bytes[id] > q.estimate) s->estimate_misses++;
+          q.res.bytes = s->owner_bytes[id];
+          held += q.res.bytes;
+          active.push_back(id);
+        }
+        admitted = true;
+      }
     }
     if (admitted && (cudaEventRecord(s->adm_done, s->adm) != cudaSuccess ||
                      cudaStreamWaitEvent(s->main_stream, s->adm_done, 0) != cudaSuccess ||

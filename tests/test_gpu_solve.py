@@ -240,13 +240,56 @@ def test_server_mix_equals_alone_and_oracle(gpu):
         assert res_mix[i]["finished_s"] >= res_mix[i]["admitted_s"] >= specs[i][0]
 
 
+def test_server_round_equals_per_request_launches(gpu):
+    """Requests admitted together form one round: one element launch and one row launch assemble
+    all of their systems, the boundary elimination fused into the row write-out.  Each system is
+    bitwise the one the per-request calls give (pull assembly of the Mat and of the right-hand
+    side, then the elimination kernel): its served solution and iteration count equal those of
+    the same system built through the public calls and solved by the same CG, alone."""
+    from paper_1501_01809_gb300 import fe
+    specs = [(0.0, 24, 2, 1, 2), (0.0, 10, 1, 3, 1), (0.0, 50, 1, 2, 2), (0.0, 17, 2, 4, 3), (0.0, 2, 1, 1, 1),
+             (0.0, 33, 2, 2, 4), (0.0, 3, 2, 1, 1)]
+    reqs = _requests(specs)
+    res, xs, stats = _serve(reqs, 1 << 34, 16)
+    assert stats["converged"] == len(reqs) and stats["sparsity_builds"] == len(reqs)
+    ctx = _ctx()
+    for i, (_, n, p, k, m) in enumerate(specs):
+        s = System(ctx, n, p, k=k, m=m)
+        fe.dirichlet_apply(ctx, s.A, s.B, s.t["bc"])
+        cg = fe.cg_create(ctx, 16)
+        slot = fe.cg_add(cg, s.A, s.B, s.X, rtol=1e-8)
+        st, it, _, _ = _run_engine(cg, [slot])
+        assert st[slot] == fe.CG_CONVERGED and res[i]["iters"] == int(it[slot]), (i, res[i]["iters"], it[slot])
+        np.testing.assert_array_equal(xs[i], s.t["x"].cpu().numpy(), err_msg=f"request {i}")
+
+
+def test_server_request_out_of_range_fails_its_round(gpu):
+    """A request whose cell-vertex map points past its vertices fails the round at the range
+    check, before any kernel reads through that map: server_run reports FE_ERANGE naming the
+    request, and the context serves the next server's requests as before."""
+    from paper_1501_01809_gb300 import fe
+    specs = [(0.0, 12, 2, 1, 1), (0.0, 9, 1, 2, 1), (0.0, 12, 1, 1, 2)]
+    reqs = _requests(specs)
+    bad = dict(reqs[1])
+    bad["mesh"] = mg.unit_square_mesh(9)
+    bad["mesh"].cell_vertex[5, 1] = bad["mesh"].nvert  # one past the last vertex
+    with pytest.raises(fe.FeError) as ei:
+        _serve([reqs[0], bad, reqs[2]], 1 << 34, 8, keys=[0, 3, 0])
+    assert ei.value.code == fe.FE_ERANGE and "request 1" in str(ei.value), str(ei.value)
+    res, xs, stats = _serve(reqs, 1 << 34, 8)
+    assert stats["converged"] == len(reqs)
+    ref, xr, _ = _serve(reqs, 1 << 34, 1)
+    for a, b in zip(xs, xr):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_server_budget_binds_and_refuses(gpu):
     from paper_1501_01809_gb300 import fe
     specs = [(0.0, 40, 2, 1, 1), (0.0, 40, 2, 2, 1), (0.0, 40, 2, 1, 2), (0.0, 20, 1, 1, 1), (0.0, 300, 2, 1, 1)]
     reqs = _requests(specs)
     # room for one 40x40 P2 request at a time (its worst case plus half of what it holds once
     # built); the 300x300 one can never fit
-    probe_res, _, probe = _serve(reqs[:1], 1 << 34, 1)
+    probe_res, _, probe = _serve(reqs[:1], 1 << 34, 8)  # the server's own tables at 8 slots
     budget = int(probe["base_bytes"] + probe_res[0]["estimate"] + probe_res[0]["bytes"] // 2)
     res, xs, stats = _serve(reqs, budget, 8)
     assert stats["peak_bytes"] <= budget, (stats, budget)
@@ -316,7 +359,7 @@ def test_server_mesh_cache_evicts_under_the_budget(gpu):
     from paper_1501_01809_gb300 import fe
     specs = [(0.0, 40, 2, 1, 1), (0.0, 41, 2, 2, 1), (0.0, 40, 2, 1, 2), (0.0, 41, 2, 2, 2)]
     reqs = _requests(specs)
-    probe_res, _, probe = _serve(reqs[1:2], 1 << 34, 1)
+    probe_res, _, probe = _serve(reqs[1:2], 1 << 34, 4)  # the server's own tables at 4 slots
     budget = int(probe["base_bytes"] + probe_res[0]["estimate"] + 4096)
     res, xs, st = _serve(reqs, budget, 4, keys=[1, 2, 1, 2])
     assert st["converged"] == len(reqs), st
