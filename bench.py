@@ -68,11 +68,11 @@ TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 249.0 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
     ("assemble", "push", "f32x2"): (1.020e9, "c827e6c081c1",
                                     "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
-    # one sparsity rebuild (zeros, k_inc_count, scans, k_inc_fill, the in-place k_rows_build pass and the
-    # gated launches that return at once): 167.3 MB at 40^3, scaled x4.096 to 64^3
-    ("sparsity", None, None): (0.6853e9, "e0a00628050a",
+    # one sparsity rebuild (zero, the guarded k_inc_fill, the in-place k_rows_build pass and the gated
+    # launches that return at once): 146.7 MB at 40^3, scaled x4.096 to 64^3
+    ("sparsity", None, None): (0.6010e9, "7dd39adb5058",
                                "integer instruction issue (ncu at 40^3, row pass: issue active 74%, ALU pipe 69%, "
-                               "422 warp instructions per row)"),
+                               "432 warp instructions per row)"),
 }
 
 
@@ -543,10 +543,13 @@ def run_ours(args, wl, rank, world):
     # ------------------------------------------------------------------- e2e through host buffers
     # Every step copies its inputs (maps, coordinates, x) from pinned host memory and its outputs
     # (rowptr, colidx, CSR values, y) back.  The copies of neighbouring steps overlap the compute on
-    # separate streams: two device slots of inputs and outputs, ordered by events.
+    # separate streams: two device slots of inputs and outputs, ordered by events.  Each direction's
+    # bytes are cut into --copy-streams pieces of about equal size, each on its own stream, so that
+    # more than one copy engine can serve a direction.
     e2e = None
     if not args.no_e2e:
         host_cpus = bind_to_gpu_cpus(dev.index)  # pinned buffers on the GPU's own socket
+        ncs = max(1, args.copy_streams)
         pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t.cpu())
         host_in = [pin(t) for t in (t_map, t_cv, t_xy, t_x)]
         slots = []
@@ -566,33 +569,59 @@ def run_ours(args, wl, rank, world):
             _, _, _, rps, cis = fe.sparsity_csr(sps)
             outs = [rps, cis, fe.mat_values(As), d_y]
             h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
-            ev = {k: torch.cuda.Event() for k in ("in", "comp", "out")}
+            ev = {"in": [torch.cuda.Event() for _ in range(ncs)], "comp": torch.cuda.Event(),
+                  "out": [torch.cuda.Event() for _ in range(ncs)]}
             slots.append(dict(d_in=d_in, M=Ms, CM=CMs, XY=XYs, X=Xs, Y=Ys, sp=sps, A=As, outs=outs, h_out=h_out, ev=ev,
                               used=False))
-        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        s_in = [torch.cuda.Stream(dev) for _ in range(ncs)]
+        s_out = [torch.cuda.Stream(dev) for _ in range(ncs)]
         h2d = sum(h.numel() * h.element_size() for h in host_in)
         d2h = sum(h.numel() * h.element_size() for h in slots[0]["h_out"])
+
+        def pieces(pairs):
+            """(destination, source) pairs cut into ncs lists of flat slices of about equal bytes."""
+            flat = [(a.view(-1), b.view(-1)) for a, b in pairs]
+            total = sum(a.numel() * a.element_size() for a, _ in flat)
+            out, acc, k = [[] for _ in range(ncs)], 0, 0
+            for a, b in flat:
+                n, es, i = a.numel(), a.element_size(), 0
+                while i < n:
+                    room = (k + 1) * total // ncs - acc  # bytes left for list k
+                    take = n - i if k == ncs - 1 else max(1, min(n - i, room // es))
+                    out[k].append((a[i:i + take], b[i:i + take]))
+                    i += take
+                    acc += take * es
+                    if k < ncs - 1 and acc >= (k + 1) * total // ncs:
+                        k += 1
+            return out
+
+        for sl in slots:
+            sl["in_pieces"] = pieces(list(zip(sl["d_in"], host_in)))
+            sl["out_pieces"] = pieces(list(zip(sl["h_out"], sl["outs"])))
 
         def e2e_step(k):
             sl = slots[k % 2]
             ev = sl["ev"]
+            for q, st in enumerate(s_in):
+                if sl["used"]:
+                    st.wait_event(ev["comp"])    # the slot's previous compute has read its inputs
+                with torch.cuda.stream(st):
+                    for d, h in sl["in_pieces"][q]:
+                        d.copy_(h, non_blocking=True)
+                    ev["in"][q].record(st)
+                stream.wait_event(ev["in"][q])
             if sl["used"]:
-                s_in.wait_event(ev["comp"])      # the slot's previous compute has read its inputs
-            with torch.cuda.stream(s_in):
-                for d, h in zip(sl["d_in"], host_in):
-                    d.copy_(h, non_blocking=True)
-                ev["in"].record(s_in)
-            stream.wait_event(ev["in"])
-            if sl["used"]:
-                stream.wait_event(ev["out"])     # the slot's previous outputs have been read back
+                for e in ev["out"]:
+                    stream.wait_event(e)         # the slot's previous outputs have been read back
             with torch.cuda.stream(stream):
                 compute(sl["sp"], sl["A"], sl["X"], sl["Y"], sl["M"], sl["XY"], sl["CM"])
                 ev["comp"].record(stream)
-            s_out.wait_event(ev["comp"])
-            with torch.cuda.stream(s_out):
-                for h, d in zip(sl["h_out"], sl["outs"]):
-                    h.copy_(d, non_blocking=True)
-                ev["out"].record(s_out)
+            for q, st in enumerate(s_out):
+                st.wait_event(ev["comp"])
+                with torch.cuda.stream(st):
+                    for h, d in sl["out_pieces"][q]:
+                        h.copy_(d, non_blocking=True)
+                    ev["out"][q].record(st)
             sl["used"] = True
 
         for k in range(2):
@@ -600,17 +629,22 @@ def run_ours(args, wl, rank, world):
         torch.cuda.synchronize()
         ksteps = max(3, min(args.steps, 20))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s_in)
+        for st in s_in[1:]:
+            st.wait_stream(s_in[0])
+        a.record(s_in[0])
         for k in range(ksteps):
             e2e_step(k)
-        b.record(s_out)
+        for st in s_out[1:]:
+            s_out[0].wait_stream(st)
+        b.record(s_out[0])
         b.synchronize()
         e2e_ms = a.elapsed_time(b) / ksteps
         if dist:
             e2e_ms = max_over_ranks(e2e_ms, dev)
         e2e = {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "pipelining": "copies of neighbouring steps overlap the compute (two device slots, three streams)",
+               "pipelining": f"copies of neighbouring steps overlap the compute (two device slots; each direction's "
+                             f"copies cut into {ncs} pieces on {ncs} streams)",
                "host_cpus": host_cpus or "unchanged (no local CPU list in sysfs)"}
         fe.sync(ctx)
 
@@ -1572,6 +1606,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle seconds per step (batch workload)")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size (profiling on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--copy-streams", type=int, default=1,
+                    help="streams per copy direction in the end-to-end leg (each direction's bytes cut evenly)")
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
                     help="p2-3d/p1-2d: replay the step as one captured CUDA graph (auto: push strategy on one "
                          "stream)")
