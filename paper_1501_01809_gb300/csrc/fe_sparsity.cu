@@ -222,13 +222,14 @@ __device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &
 // i ^ (k - 1)), after which every half-cleaner stage sorts ascending, so compare-exchanges inside a
 // lane need no direction select.  Stages between lanes exchange with lane l ^ (stride / E); the lane
 // holding the lower index keeps the minimum.
-// NL = 16 sorts 16 E values in each half-warp independently (every exchange mask is below 16).
+// NL = 16 (or 8) sorts NL E values in each group of NL lanes independently (every exchange mask
+// is below NL).
 template <int E, int NL = 32>
 __device__ __forceinline__ void warp_bitonic_packed(uint32_t (&v)[E]) {
   const int lane = threadIdx.x & 31;
   constexpr int LG = E == 1 ? 0 : E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : -1;
   static_assert(LG >= 0, "E must be a power of two up to 16");
-  static_assert(NL == 32 || NL == 16, "a warp or a half-warp");
+  static_assert(NL == 32 || NL == 16 || NL == 8, "a warp, a half-warp or a quarter-warp");
 #pragma unroll
   for (int k = 2; k <= NL * E; k <<= 1) {
     if (k <= E) {  // mirror stage inside the lane
@@ -396,27 +397,28 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   return nu;
 }
 
-// Two rows at once, one per half-warp: the steps of row_by_sort inside each half (16 lanes, E keys
-// per lane, at most 16 E candidates and 16 incidences per row).  Every shuffle has width 16, so
-// the halves never exchange values; adjs, adje (16 words) and lbuf (16 E bytes) are this half's
-// scratch.  Returns this half's number of unique columns.
-template <int E, int SH>
-__device__ __forceinline__ int row_by_sort_half(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
-                                                uint32_t *adjs, uint32_t *adje, uint8_t *lbuf) {
-  const int hl = threadIdx.x & 15;
+// Up to 32 / NL rows at once, one per group of NL lanes: the steps of row_by_sort inside each
+// group (E keys per lane, at most NL E candidates and NL incidences per row).  Every shuffle has
+// width NL, so the groups never exchange values; adjs, adje (NL words) and lbuf (NL E bytes) are
+// this group's scratch.  A group without a row (r < 0, na = ncand = 0) takes part in the warp-wide
+// steps with padding keys only and writes nothing.  Returns this group's number of unique columns.
+template <int E, int SH, int NL>
+__device__ __forceinline__ int row_by_sort_group(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
+                                                 uint32_t *adjs, uint32_t *adje, uint8_t *lbuf) {
+  const int gl = threadIdx.x & (NL - 1);
   const unsigned full = 0xffffffffu;
   const int ndc = p.ndc;
   const uint32_t tmask = (1u << SH) - 1u;
-  const uint32_t v = hl < na ? (uint32_t)p.adj[a0 + hl] : 0xFFFFFFFFu;
-  int rk = hl;
+  const uint32_t v = gl < na ? (uint32_t)p.adj[a0 + gl] : 0xFFFFFFFFu;
+  int rk = gl;
   if (p.canon) {
     rk = 0;
-    for (int q = 0; q < 16; q++) {
-      const uint32_t w = __shfl_sync(full, v, q, 16);
+    for (int q = 0; q < NL; q++) {
+      const uint32_t w = __shfl_sync(full, v, q, NL);
       rk += (q < na) && (w < v);
     }
   }
-  if (hl < na) {
+  if (gl < na) {
     adjs[rk] = v;
     adje[rk] = div_ndr(v, p);
     if (p.canon) p.adj[a0 + rk] = (int32_t)v;
@@ -425,40 +427,42 @@ __device__ __forceinline__ int row_by_sort_half(const RowsParams &p, int64_t r, 
   uint32_t key[E];
 #pragma unroll
   for (int h = 0; h < E; h++) {
-    const uint32_t t = (uint32_t)(16 * h + hl);
+    const uint32_t t = (uint32_t)(NL * h + gl);
     key[h] = 0xFFFFFFFFu;
     if ((int)t < ncand) {
       const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
       key[h] = ((uint32_t)p.cmap[(int64_t)adje[a] * ndc + j] << SH) | t;
     }
   }
-  warp_bitonic_packed<E, 16>(key);
-  const uint32_t prev = __shfl_up_sync(full, key[E - 1], 1, 16);
+  warp_bitonic_packed<E, NL>(key);
+  const uint32_t prev = __shfl_up_sync(full, key[E - 1], 1, NL);
   int f[E], c = 0;
 #pragma unroll
   for (int h = 0; h < E; h++) {
     const uint32_t before = h == 0 ? prev : key[h - 1];
-    f[h] = key[h] != 0xFFFFFFFFu && ((h == 0 && hl == 0) || (key[h] >> SH) != (before >> SH));
+    f[h] = key[h] != 0xFFFFFFFFu && ((h == 0 && gl == 0) || (key[h] >> SH) != (before >> SH));
     c += f[h];
   }
   int incl = c;
 #pragma unroll
-  for (int o = 1; o < 16; o <<= 1) {
-    const int n = __shfl_up_sync(full, incl, o, 16);
-    if (hl >= o) incl += n;
+  for (int o = 1; o < NL; o <<= 1) {
+    const int n = __shfl_up_sync(full, incl, o, NL);
+    if (gl >= o) incl += n;
   }
-  const int nu = __shfl_sync(full, incl, 15, 16);
-  int32_t *outc = row_out(p, r, a0, nu, hl == 0);
-  int rank = incl - c - 1;
+  const int nu = __shfl_sync(full, incl, NL - 1, NL);
+  if (r >= 0) {
+    int32_t *outc = row_out(p, r, a0, nu, gl == 0);
+    int rank = incl - c - 1;
 #pragma unroll
-  for (int h = 0; h < E; h++) {
-    rank += f[h];
-    if (key[h] == 0xFFFFFFFFu) continue;
-    if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
-    lbuf[key[h] & tmask] = (uint8_t)rank;
+    for (int h = 0; h < E; h++) {
+      rank += f[h];
+      if (key[h] == 0xFFFFFFFFu) continue;
+      if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
+      lbuf[key[h] & tmask] = (uint8_t)rank;
+    }
   }
   __syncwarp();
-  for (int t = hl; t < ncand; t += 16) {
+  for (int t = gl; t < ncand; t += NL) {
     const uint32_t a = div_ndc((uint32_t)t, p), j = (uint32_t)t - a * (uint32_t)ndc;
     p.lut[(int64_t)adjs[a] * ndc + j] = lbuf[t];
   }
@@ -466,8 +470,10 @@ __device__ __forceinline__ int row_by_sort_half(const RowsParams &p, int64_t r, 
   return nu;
 }
 
-// One warp per row r of the pattern (rows = target set of the row map).  Rows of at most 256
-// candidates and 32 incidences go through row_by_sort; the others:
+// The rows of the pattern (rows = target set of the row map), eight consecutive rows per warp at
+// a time.  Rows of at most 8 incidences and 64 candidates go four at a time through
+// row_by_sort_group (one per quarter-warp); other rows take the whole warp, one at a time: rows of
+// at most 256 candidates and 32 incidences through row_by_sort, the others:
 //  1. load the row's incidence list {e*ndr + i : rmap(e)[i] = r} (all distinct) into shared
 //     memory (ranked into ascending order and written back when p.canon is set);
 //  2. insert every candidate column cmap(e)[j] of every incident cell into a shared-memory hash
@@ -478,16 +484,16 @@ __device__ __forceinline__ int row_by_sort_half(const RowsParams &p, int64_t r, 
 //  4. lut[(e*ndr + i)*ndc + j] = rank of the candidate's slot; rowlen[r] = number of unique columns.
 // Shared memory per warp (32-bit words): hkey[cap], hrank[cap], ucol[cap], uslot[cap], cslot[cap],
 // adju[acap], adjs[acap].
-__global__ void __launch_bounds__(256, 6) k_rows_build(const RowsParams p) {
+__global__ void __launch_bounds__(256, 5) k_rows_build(const RowsParams p) {
   extern __shared__ __align__(16) int32_t smem_i[];
   if (p.gate && *p.gate == 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int cap = p.cap;
   if (p.colidx && blockIdx.x == 0 && threadIdx.x == 0 && p.rowptr[p.nrows] != p.nnz) *p.changed = 1;
   // per warp: hash tables (5 cap words) unless every row is sorted, then the incidence lists, then
-  // 64 words of rank bytes for the sort path, then 96 words for the half-warp rows (incidences,
-  // cells and rank bytes of each half)
-  int32_t *hkey = smem_i + (size_t)wid * ((p.sort_only ? 0 : 5 * cap) + 2 * p.acap + 64 + 96);
+  // 64 words of rank bytes for the sort path, then 128 words for the quarter-warp rows (incidences,
+  // cells and rank bytes of each quarter)
+  int32_t *hkey = smem_i + (size_t)wid * ((p.sort_only ? 0 : 5 * cap) + 2 * p.acap + 64 + 128);
   int32_t *hrank = hkey + cap;
   uint32_t *ucol = reinterpret_cast<uint32_t *>(hrank + cap);
   int32_t *uslot = reinterpret_cast<int32_t *>(ucol + cap);
@@ -495,35 +501,51 @@ __global__ void __launch_bounds__(256, 6) k_rows_build(const RowsParams p) {
   uint32_t *adju = p.sort_only ? reinterpret_cast<uint32_t *>(hkey) : reinterpret_cast<uint32_t *>(cslot + cap);
   uint32_t *adjs = adju + p.acap;
   uint8_t *lbuf = reinterpret_cast<uint8_t *>(adjs + p.acap);
-  const int half = lane >> 4;
-  uint32_t *hadjs = reinterpret_cast<uint32_t *>(lbuf + 256) + 16 * half;
-  uint32_t *hadje = reinterpret_cast<uint32_t *>(lbuf + 256) + 32 + 16 * half;
-  uint8_t *hlbuf = lbuf + 256 + 256 + 64 * half;
+  const int grp = lane >> 3;
+  uint32_t *gadjs = reinterpret_cast<uint32_t *>(lbuf + 256) + 8 * grp;
+  uint32_t *gadje = reinterpret_cast<uint32_t *>(lbuf + 256) + 32 + 8 * grp;
+  uint8_t *glbuf = lbuf + 256 + 256 + 64 * grp;
   const int ndc = p.ndc;
-  // Rows go to warps in pairs.  When both rows of a pair have at most 64 candidates (every edge
-  // row of a P2 tetrahedral mesh), each half-warp sorts one of them, four keys per lane; any other
-  // pair is done row by row by the whole warp.
-  for (int64_t pr = (int64_t)blockIdx.x * wpb + wid; 2 * pr < p.nrows; pr += (int64_t)gridDim.x * wpb) {
-    const int64_t r0 = 2 * pr, r1 = r0 + 1;
-    const int64_t rh = half ? r1 : r0;
-    int64_t ah = 0;
-    int nh = 0;
-    if (rh < p.nrows) {
-      ah = p.adjptr[rh];
-      nh = (int)(p.adjptr[rh + 1] - ah);
+  const unsigned full = 0xffffffffu;
+  // Rows go to warps in chunks of 8.  The rows of at most 8 incidences and 64 candidates (every
+  // edge row of a P2 tetrahedral mesh, every row of P1-P3 triangles) are sorted four at a time,
+  // one per quarter-warp, eight keys per lane (four when no row of the four has more than 32
+  // candidates); every other row takes the whole warp.
+  for (int64_t ch = (int64_t)blockIdx.x * wpb + wid; 8 * ch < p.nrows; ch += (int64_t)gridDim.x * wpb) {
+    const int64_t rb = 8 * ch;
+    const int64_t rl = rb + (lane & 7);  // lanes k and k + 8, k + 16, k + 24 look at row rb + k
+    int64_t al = 0;
+    int nl = 0;
+    if (rl < p.nrows) {
+      al = p.adjptr[rl];
+      nl = (int)(p.adjptr[rl + 1] - al);
     }
     if (p.check_counts) {  // the guarded fill's count against the range it was filled into
-      if ((lane & 15) == 0 && rh < p.nrows && p.rowlen[rh] != nh) *p.changed = 1;
+      if (lane < 8 && rl < p.nrows && p.rowlen[rl] != nl) *p.changed = 1;
       __syncwarp();
     }
-    const bool mine_ok = rh < p.nrows && nh > 0 && nh <= 16 && nh * ndc <= 64;
-    if (p.packed_ok && __all_sync(0xffffffffu, mine_ok)) {
-      const int nu = row_by_sort_half<4, 6>(p, rh, ah, nh, nh * ndc, hadjs, hadje, hlbuf);
-      if ((lane & 15) == 0) p.rowlen[rh] = nu;  // at most 64 columns: within the row limit
+    const bool small = p.packed_ok && rl < p.nrows && nl > 0 && nl <= 8 && nl * ndc <= 64;
+    unsigned qmask = __ballot_sync(full, small) & 0xFFu;                     // bit k: row rb + k
+    unsigned wmask = (__ballot_sync(full, rl < p.nrows) & 0xFFu) & ~qmask;  // the rows left
+    while (qmask) {
+      unsigned m = qmask;  // quarter g takes the (g + 1)-th remaining small row, if there is one
+      for (int g = 0; g < grp; g++) m &= m - 1;
+      const bool have = m != 0;
+      const int k = have ? __ffs(m) - 1 : 0;
+      const int na = __shfl_sync(full, nl, k);
+      const int64_t a0 = __shfl_sync(full, al, k);
+      const int nag = have ? na : 0;
+      const int64_t r = have ? rb + k : -1;
+      const bool wide = __any_sync(full, nag * ndc > 32);
+      const int nu = wide ? row_by_sort_group<8, 6, 8>(p, r, a0, nag, nag * ndc, gadjs, gadje, glbuf)
+                          : row_by_sort_group<4, 6, 8>(p, r, a0, nag, nag * ndc, gadjs, gadje, glbuf);
+      if (have && (lane & 7) == 0) p.rowlen[r] = nu;  // at most 64 columns: within the row limit
       __syncwarp();
-      continue;
+      for (int g = 0; g < 4; g++) qmask &= qmask - 1;  // the (up to) four rows just done
     }
-    for (int64_t r = r0; r <= r1 && r < p.nrows; r++) {
+    while (wmask) {
+      const int64_t r = rb + (__ffs(wmask) - 1);
+      wmask &= wmask - 1;
       const int64_t a0 = p.adjptr[r];
       const int na = (int)(p.adjptr[r + 1] - a0);
       const int ncand = na * ndc;
@@ -787,7 +809,7 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
   p.gate = gate;
   p.canon = 0;
   p.check_counts = changed != nullptr;  // the in-place pass of a rebuild follows a guarded fill
-  const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap + 64 + 96) * sizeof(int32_t);
+  const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap + 64 + 128) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
   const size_t smem = warps * per_warp;

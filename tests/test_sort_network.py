@@ -9,8 +9,8 @@ import pytest
 
 
 def warp_sort(vals, E, nl=32):
-    """The kernel's schedule on nl lanes (32: a warp; 16: each half of a warp, whose exchange masks
-    all stay below 16 so that the two halves sort independently)."""
+    """The kernel's schedule on nl lanes (32: a warp; 16 or 8: each group of nl lanes of a warp,
+    whose exchange masks all stay below nl so that the groups sort independently)."""
     v = vals.reshape(nl, E).copy()
     lanes = np.arange(nl)
     lg = E.bit_length() - 1
@@ -55,29 +55,32 @@ def test_network_sorts(E):
         np.testing.assert_array_equal(warp_sort(x, E), np.sort(x))
 
 
-def test_half_warp_network_sorts_each_half():
-    """The half-warp variant (warp_bitonic_packed<E, 16>, four keys per lane in the row kernel):
-    run on a whole warp, each half ends sorted on its own and nothing crosses between halves."""
-    rng = np.random.default_rng(16)
-    for E in (1, 2, 4):
+@pytest.mark.parametrize("nl,Es", [(16, (1, 2, 4)), (8, (2, 4, 8))])
+def test_lane_group_network_sorts_each_group(nl, Es):
+    """The half-warp and quarter-warp variants (warp_bitonic_packed<E, 16> and <E, 8>: two or four
+    rows per warp in the row kernel): run on a whole warp, each group of nl lanes ends sorted on
+    its own and nothing crosses between groups."""
+    rng = np.random.default_rng(nl)
+    ng = 32 // nl
+    for E in Es:
         for t in range(100):
-            halves = []
-            for _ in range(2):
-                x = rng.integers(0, 30 if t % 2 else 2**32 - 1, 16 * E, dtype=np.uint64)
-                x[int(rng.integers(1, 16 * E + 1)):] = 0xFFFFFFFF
-                halves.append(x)
-            lanes = np.concatenate(halves).reshape(32, E)  # lanes 0-15: first row, 16-31: second
-            for h, x in enumerate(halves):
-                np.testing.assert_array_equal(warp_sort(lanes[16 * h:16 * h + 16].reshape(-1), E, nl=16), np.sort(x))
-        # every exchange mask of the half-warp schedule (mirror stages (k >> lg) - 1, half-cleaners
-        # j >> lg) is below 16, so lane l ^ mask stays in l's half
+            groups = []
+            for _ in range(ng):
+                x = rng.integers(0, 30 if t % 2 else 2**32 - 1, nl * E, dtype=np.uint64)
+                x[int(rng.integers(0, nl * E + 1)):] = 0xFFFFFFFF  # a group may hold no row at all
+                groups.append(x)
+            lanes = np.concatenate(groups).reshape(32, E)  # lanes nl g .. nl g + nl - 1: row g
+            for g, x in enumerate(groups):
+                np.testing.assert_array_equal(warp_sort(lanes[nl * g:nl * g + nl].reshape(-1), E, nl=nl), np.sort(x))
+        # every exchange mask of the group schedule (mirror stages (k >> lg) - 1, half-cleaners
+        # j >> lg) is below nl, so lane l ^ mask stays in l's group
         lg = E.bit_length() - 1
         k = 2
-        while k <= 16 * E:
-            assert k <= E or (k >> lg) - 1 < 16
+        while k <= nl * E:
+            assert k <= E or (k >> lg) - 1 < nl
             j = k >> 2
             while j > 0:
-                assert j < E or (j >> lg) < 16
+                assert j < E or (j >> lg) < nl
                 j >>= 1
             k <<= 1
 
