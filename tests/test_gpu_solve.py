@@ -33,7 +33,7 @@ def gpu():
 class System:
     """A Poisson system assembled on the GPU (pull, FP64) with its device objects."""
 
-    def __init__(self, ctx, n, p, k=1, m=2, jitter=0.0, seed=0):
+    def __init__(self, ctx, n, p, k=1, m=2, jitter=0.0, seed=0, precision=0):
         import torch
         from paper_1501_01809_gb300 import fe
         self.fe, self.torch = fe, torch
@@ -57,8 +57,9 @@ class System:
         self.X = fe.dat_create(ctx, self.nodes, self.t["x"])
         self.sp = fe.sparsity_build(ctx, self.M, self.M)
         self.A = fe.mat_create(ctx, self.sp)
-        kl = fe.kernel_create(ctx, fe.FORM_LAPLACE, 2, p, strategy=fe.STRATEGY_PULL)
-        ks = fe.kernel_create(ctx, fe.FORM_SOURCE, 2, p, coeff_degree=p, strategy=fe.STRATEGY_PULL)
+        kl = fe.kernel_create(ctx, fe.FORM_LAPLACE, 2, p, precision=precision, strategy=fe.STRATEGY_PULL)
+        ks = fe.kernel_create(ctx, fe.FORM_SOURCE, 2, p, coeff_degree=p, precision=precision,
+                              strategy=fe.STRATEGY_PULL)
         fe.assemble_mat(ctx, kl, self.cells, self.A, self.XY, self.CM, zero_first=True)
         fe.assemble_vec(ctx, ks, self.cells, self.B, self.M, self.XY, self.CM, [(self.F, self.M)], zero_first=True,
                         sp=self.sp)
@@ -200,10 +201,10 @@ def _requests(specs):
     return out
 
 
-def _serve(reqs, budget, max_active, tick=8, keys=None):
+def _serve(reqs, budget, max_active, tick=8, keys=None, precision=0):
     from paper_1501_01809_gb300 import fe
     ctx = _ctx()
-    srv = fe.server_create(ctx, budget, max_active=max_active, iters_per_tick=tick, rtol=1e-8)
+    srv = fe.server_create(ctx, budget, max_active=max_active, iters_per_tick=tick, rtol=1e-8, precision=precision)
     xs, ids = [], []
     for i, r in enumerate(reqs):
         x = np.full(r["nn"], np.nan)
@@ -240,21 +241,23 @@ def test_server_mix_equals_alone_and_oracle(gpu):
         assert res_mix[i]["finished_s"] >= res_mix[i]["admitted_s"] >= specs[i][0]
 
 
-def test_server_round_equals_per_request_launches(gpu):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_server_round_equals_per_request_launches(gpu, precision):
     """Requests admitted together form one round: one element launch and one row launch assemble
     all of their systems, the boundary elimination fused into the row write-out.  Each system is
     bitwise the one the per-request calls give (pull assembly of the Mat and of the right-hand
     side, then the elimination kernel): its served solution and iteration count equal those of
-    the same system built through the public calls and solved by the same CG, alone."""
+    the same system built through the public calls and solved by the same CG, alone.  Element
+    tensors in FP64 (precision 0) and in double-float (1)."""
     from paper_1501_01809_gb300 import fe
     specs = [(0.0, 24, 2, 1, 2), (0.0, 10, 1, 3, 1), (0.0, 50, 1, 2, 2), (0.0, 17, 2, 4, 3), (0.0, 2, 1, 1, 1),
              (0.0, 33, 2, 2, 4), (0.0, 3, 2, 1, 1)]
     reqs = _requests(specs)
-    res, xs, stats = _serve(reqs, 1 << 34, 16)
+    res, xs, stats = _serve(reqs, 1 << 34, 16, precision=precision)
     assert stats["converged"] == len(reqs) and stats["sparsity_builds"] == len(reqs)
     ctx = _ctx()
     for i, (_, n, p, k, m) in enumerate(specs):
-        s = System(ctx, n, p, k=k, m=m)
+        s = System(ctx, n, p, k=k, m=m, precision=precision)
         fe.dirichlet_apply(ctx, s.A, s.B, s.t["bc"])
         cg = fe.cg_create(ctx, 16)
         slot = fe.cg_add(cg, s.A, s.B, s.X, rtol=1e-8)

@@ -101,6 +101,45 @@ def test_random_maps_sparsity(gpu, ncell, ar, ac, nr, nc):
     np.testing.assert_array_equal(ci[pos], np.broadcast_to(cmap[:, None, :], pos.shape))
 
 
+@pytest.mark.parametrize("ncell,ar,ac,nr,nc,nhub", [(3000, 3, 5, 3000, 400, 0), (2000, 4, 6, 1500, 1500, 12),
+                                                    (1200, 2, 9, 900, 300, 6)])
+def test_random_maps_small_rows_with_repeats(gpu, ncell, ar, ac, nr, nc, nhub):
+    """Random maps whose rows mostly hold a few incidences (the row kernel sorts those four at a
+    time, one per quarter-warp), targets repeated within a cell in both maps, and nhub rows that
+    appear in 20 more cells each (those take the whole warp, beside small rows of their chunk of
+    eight).  Pattern bitwise equal to the oracle's; every lookup-table entry names its column."""
+    from paper_1501_01809_gb300 import fe
+    torch = gpu
+    rng = np.random.default_rng(ncell + ar)
+    rmap = rng.integers(0, nr, (ncell, ar)).astype(np.int32)
+    cmap = rng.integers(0, nc, (ncell, ac)).astype(np.int32)
+    if nhub:
+        hubs = 8 * rng.choice(nr // 8, nhub, replace=False) + rng.integers(0, 8, nhub)
+        rmap[:20 * nhub, 0] = np.repeat(hubs, 20)
+    assert (rmap[:, :1] == rmap[:, 1:]).any() and (cmap[:, :1] == cmap[:, 1:]).any()  # repeats occur
+    ctx = fe.ctx_create(0)
+    cells, rows, cols = fe.set_create(ctx, ncell), fe.set_create(ctx, nr), fe.set_create(ctx, nc)
+    R = fe.map_create(ctx, cells, rows, torch.from_numpy(rmap).cuda(), validate=True)
+    Cm = fe.map_create(ctx, cells, cols, torch.from_numpy(cmap).cuda(), validate=True)
+    sp = fe.sparsity_build(ctx, R, Cm)
+    _, _, nnz, rp, ci = fe.sparsity_csr(sp)
+    rp, ci = rp.cpu().numpy(), ci.cpu().numpy()
+    orp, oci = O.sparsity(rmap, cmap, nr, nc)
+    np.testing.assert_array_equal(rp, orp)
+    np.testing.assert_array_equal(ci, oci)
+    lut = fe.sparsity_lut(sp, ncell, ar, ac).cpu().numpy().reshape(-1, ar, ac).astype(np.int64)
+    pos = rp[rmap][:, :, None] + lut
+    assert (lut < (rp[rmap + 1] - rp[rmap])[:, :, None]).all()
+    np.testing.assert_array_equal(ci[pos], np.broadcast_to(cmap[:, None, :], pos.shape))
+    # a rebuild from the same maps (in-place pass, counts checked) gives the same pattern and table
+    fe.sparsity_rebuild(sp)
+    _, _, _, rp2, ci2 = fe.sparsity_csr(sp)
+    np.testing.assert_array_equal(rp2.cpu().numpy(), orp)
+    np.testing.assert_array_equal(ci2.cpu().numpy(), oci)
+    lut2 = fe.sparsity_lut(sp, ncell, ar, ac).cpu().numpy().reshape(-1, ar, ac).astype(np.int64)
+    np.testing.assert_array_equal(lut2, lut)
+
+
 def test_rows_beyond_the_limits_are_refused(gpu):
     from paper_1501_01809_gb300 import fe
     torch = gpu
