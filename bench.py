@@ -69,10 +69,10 @@ TRAFFIC = {
     ("assemble", "push", "f32x2"): (1.020e9, "c827e6c081c1",
                                     "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
     # one sparsity rebuild (zero, the guarded k_inc_fill, the in-place k_rows_build pass and the gated
-    # launches that return at once): 146.7 MB at 40^3, scaled x4.096 to 64^3
-    ("sparsity", None, None): (0.6010e9, "7dd39adb5058",
-                               "integer instruction issue (ncu at 40^3, row pass: issue active 74%, ALU pipe 69%, "
-                               "432 warp instructions per row)"),
+    # launches that return at once): 129.1 MB at 40^3, scaled x4.096 to 64^3
+    ("sparsity", None, None): (0.5288e9, "38eb0ca824bd",
+                               "integer instruction issue (ncu at 40^3, row pass: issue active 67%, ALU pipe 66%, "
+                               "362 warp instructions per row)"),
 }
 
 
