@@ -242,6 +242,39 @@ fe_status fe_action(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat 
                     int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
                     int ncoeffs, const fe_sparsity *sp);
 
+/* ---------------------------------------------------------------- Global (Sec. 4.3, 4.4)
+ * A Global is a tuple of values tied to no set (a 0-linear operator beside the Dat and the Mat,
+ * Sec. 4.3).  par_loops reach it either by READ or through a reduction: SUM, MIN or MAX
+ * ("Global arguments", Sec. 4.4), for integrated quantities such as an energy.  Every reduction
+ * here sums (or takes the minimum or maximum of) per-cell values in a fixed order: one partial
+ * per block of cells, then the partials in block order, so its result is the same on every run.
+ * fe_global_create: dim FP64 values on the device, library-owned, zeroed on the context's
+ * stream.  fe_global_data: their device pointer (read them after fe_sync).
+ * Errors: FE_EINVAL (dim < 1, out == NULL), FE_EHANDLE, FE_ENOMEM. */
+typedef struct fe_global fe_global;
+enum { FE_REDUCE_SUM = 0, FE_REDUCE_MIN = 1, FE_REDUCE_MAX = 2 };
+fe_status fe_global_create(fe_ctx *ctx, int dim, fe_global **out);
+fe_status fe_global_data(const fe_global *g, double **values);
+fe_status fe_global_destroy(fe_global *g);
+/* fe_assemble_global: a form of rank 0 into g[0] with SUM access (zero_first != 0 overwrites,
+ * else adds).  With a bilinear kernel both arguments become the Function x (READ through map):
+ * g = a(x, x) = sum_e x_e^T K_e x_e, the energy of x (the action of Sec. 6.3 applied twice).
+ * With FE_FORM_SOURCE the test argument becomes x: g = L(x) = sum_e b_e . x_e, the integral of
+ * f x (coeffs[0] = f as for fe_assemble_vec).  Element tensors in FE_PREC_FP64 (every compiled
+ * element) or FE_PREC_F32X2 (P1, P2); the sum over cells in FP64.  Scratch (an element stage of
+ * ncell * nd values and the partials) is held by g and grows to the largest call.
+ * Errors: FE_EINVAL, FE_EARITY, FE_EHANDLE, FE_EUNSUPPORTED, FE_ENOMEM. */
+fe_status fe_assemble_global(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_global *g, int zero_first,
+                             fe_dat *x, fe_map *map, fe_dat *coords, fe_map *coord_map,
+                             const fe_arg *coeffs, int ncoeffs);
+/* fe_reduce_cell_volume: g[0] (op)= op over the cells of |det J| / dim! (op = FE_REDUCE_SUM: the
+ * domain's volume; MIN / MAX: the smallest / largest cell), coordinates READ through coord_map
+ * (arity dim + 1, dim 2 or 3).  zero_first != 0 overwrites g[0] with the reduction; with no
+ * cells that is 0 (SUM), +inf (MIN) or -inf (MAX).
+ * Errors: FE_EINVAL (op, dim), FE_EARITY, FE_EHANDLE, FE_ENOMEM. */
+fe_status fe_reduce_cell_volume(fe_ctx *ctx, fe_set *cells, fe_global *g, int op, int zero_first,
+                                fe_dat *coords, fe_map *coord_map);
+
 /* ---------------------------------------------------------------- stored element matrices
  * The stored-matrix alternative to fe_action, which recomputes every element matrix at each
  * application.  fe_elem_matrices runs the local kernel of a bilinear form once per cell (the

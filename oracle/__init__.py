@@ -201,6 +201,31 @@ def assemble_rows(dim, p, form, cmap, coords, coord_map, nrows, rows, sel_rowptr
     return vals, absv
 
 
+def functional(dim, p, form, cmap, coords, coord_map, x, kappa=None):
+    """A form of rank 0 (a Global, Sec. 4.3): the bilinear form with both arguments the Function x,
+    a(x, x) = sum_e x_e^T K_e x_e = x . (A x), from the oracle's cell-by-cell action.  Returns the
+    value and its scale sum_i |x_i| (sum_e |K_e| |x_e|)_i, which bounds the rounding of any
+    summation order."""
+    y, absy = action(dim, p, form, cmap, coords, coord_map, x, kappa=kappa)
+    return float(np.dot(x, y)), float(np.dot(np.abs(x), absy))
+
+
+def linear_functional(dim, p, pf, cmap, coords, coord_map, f, fmap, x):
+    """The linear form with its test argument the Function x: L(x) = sum_e b_e . x_e = b . x (b the
+    assembled f v dx), and its scale sum_i |x_i| (sum_e |b_e|)_i."""
+    x = _c(x, np.float64)
+    b, absb = assemble_vec(dim, p, pf, cmap, x.size, coords, coord_map, f, fmap)
+    return float(np.dot(b, x)), float(np.dot(absb, np.abs(x)))
+
+
+def cell_volumes(dim, coords, coord_map):
+    """|T| of every cell: the oracle's quadrature weights w |det J| of each cell added up (its rule
+    integrates constants exactly)."""
+    cv = _c(coord_map, np.int32)
+    _, w, _ = eval_function(dim, 1, 1, cv, coords, cv, np.zeros(_c(coords, np.float64).shape[0]))
+    return w.reshape(cv.shape[0], -1).sum(axis=1)
+
+
 def eval_function(dim, p, qdeg, cmap, coords, coord_map, u):
     """Physical quadrature points, weights (w |detJ|) and values of the P_p function u."""
     cmap = _c(cmap, np.int32)

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -69,6 +70,7 @@ bool valid(const fe_dat *d) { return d && d->magic == fe::kMagicDat && valid(d->
 bool valid(const fe_sparsity *s) { return s && s->magic == fe::kMagicSp && valid(s->ctx); }
 bool valid(const fe_mat *m) { return m && m->magic == fe::kMagicMat && valid(m->ctx); }
 bool valid(const fe_kernel *k) { return k && k->magic == fe::kMagicKer && valid(k->ctx); }
+bool valid(const fe_global *g) { return g && g->magic == fe::kMagicGlobal && valid(g->ctx); }
 
 struct DeviceGuard {
   int prev = -1;
@@ -695,6 +697,110 @@ fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y
   int unsup = 0;
   FE_CHECK_CUDA(fe::launch_action(k->d, a, c->stream, &unsup), who);
   if (unsup) return fail(FE_EUNSUPPORTED, "%s: no kernel for this form/strategy", who);
+  return ok();
+}
+
+// ------------------------------------------------------------------------------------ Global
+fe_status fe_global_create(fe_ctx *c, int dim, fe_global **out) {
+  if (!valid(c)) return fail(FE_EHANDLE, "fe_global_create: invalid context");
+  if (!out || dim < 1) return fail(FE_EINVAL, "fe_global_create: bad arguments (dim %d)", dim);
+  DeviceGuard g(c->device);
+  double *v = (double *)dev_alloc(c, sizeof(double) * dim);
+  if (!v) return fail(FE_ENOMEM, "fe_global_create: device allocation failed");
+  FE_CHECK_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * dim, c->stream), "fe_global_create");
+  fe_global *h = new (std::nothrow) fe_global{fe::kMagicGlobal, c, dim, v, nullptr, 0, nullptr, 0};
+  if (!h) {
+    dev_free(c, v);
+    return fail(FE_ENOMEM, "fe_global_create: host allocation");
+  }
+  *out = h;
+  return ok();
+}
+
+fe_status fe_global_data(const fe_global *g, double **values) {
+  if (!valid(g)) return fail(FE_EHANDLE, "fe_global_data: invalid global");
+  if (!values) return fail(FE_EINVAL, "fe_global_data: values == NULL");
+  *values = g->data;
+  return ok();
+}
+
+fe_status fe_global_destroy(fe_global *g) {
+  if (!valid(g)) return fail(FE_EHANDLE, "fe_global_destroy: invalid global");
+  DeviceGuard dg(g->ctx->device);
+  cudaStreamSynchronize(g->ctx->stream);
+  dev_free(g->ctx, g->data);
+  dev_free(g->ctx, g->stage);
+  dev_free(g->ctx, g->part);
+  g->magic = fe::kDead;
+  delete g;
+  return ok();
+}
+
+// Rank-0 forms: the element stage of the pull kernels (K_e x_e, or b_e for the linear form), then
+// the deterministic sum of x_e . stage_e over the cells.
+fe_status fe_assemble_global(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_global *g, int zero_first, fe_dat *x,
+                             fe_map *map, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs, int ncoeffs) {
+  Range nvtx_range("fe_assemble_global");
+  const char *who = "fe_assemble_global";
+  fe::AsmArgs a;
+  fe_status st = common_args(who, c, k, cells, map, coords, coord_map, a);
+  if (st != FE_OK) return st;
+  if (!valid(g) || g->ctx != c) return fail(FE_EHANDLE, "%s: invalid global", who);
+  if (!valid(x) || x->ctx != c || x->set != map->to || x->dim != 1)
+    return fail(FE_EINVAL, "%s: x must be a scalar Dat on the map's target", who);
+  if (k->d.form == FE_FORM_SOURCE) {
+    if (ncoeffs < 1 || !coeffs || !valid(coeffs[0].dat) || !valid(coeffs[0].map) || coeffs[0].map->from != cells ||
+        coeffs[0].map->arity != k->nf || coeffs[0].dat->set != coeffs[0].map->to || coeffs[0].dat->dim != 1)
+      return fail(FE_EARITY, "%s: f must be a scalar Dat with a map of arity %d", who, k->nf);
+    a.coef = coeffs[0].dat->data;
+    a.coefmap = coeffs[0].map->values;
+    a.ncoef = coeffs[0].dat->set->size;
+  } else {
+    st = kappa_arg(who, c, k, cells, coeffs, ncoeffs, a);
+    if (st != FE_OK) return st;
+    a.x = x->data;
+  }
+  DeviceGuard dg(c->device);
+  st = ensure_stage(c, &g->stage, &g->stage_bytes,
+                    std::max<size_t>(fe::stage_bytes_vec(k->d, cells->size, k->nd), 16), who);
+  if (st != FE_OK) return st;
+  void *part = g->part;
+  st = ensure_stage(c, &part, &g->part_bytes, sizeof(double) * (size_t)fe::global_parts(cells->size), who);
+  g->part = static_cast<double *>(part);
+  if (st != FE_OK) return st;
+  a.stage = g->stage;
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_elem_stage(k->d, a, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no element kernel for this form and precision", who);
+  FE_CHECK_CUDA(fe::launch_global_dot(k->d.precision, cells->size, k->nd, map->values, g->stage, x->data,
+                                      x->set->size, g->part, g->data, zero_first, c->checks, c->d_err, c->stream),
+                who);
+  return ok();
+}
+
+fe_status fe_reduce_cell_volume(fe_ctx *c, fe_set *cells, fe_global *g, int op, int zero_first, fe_dat *coords,
+                                fe_map *coord_map) {
+  Range nvtx_range("fe_reduce_cell_volume");
+  const char *who = "fe_reduce_cell_volume";
+  if (!valid(c)) return fail(FE_EHANDLE, "%s: invalid context", who);
+  if (!valid(cells) || cells->ctx != c) return fail(FE_EHANDLE, "%s: invalid cell set", who);
+  if (!valid(g) || g->ctx != c) return fail(FE_EHANDLE, "%s: invalid global", who);
+  if (!valid(coords) || coords->ctx != c) return fail(FE_EHANDLE, "%s: invalid coordinate dat", who);
+  if (!valid(coord_map) || coord_map->ctx != c) return fail(FE_EHANDLE, "%s: invalid coordinate map", who);
+  if (op != FE_REDUCE_SUM && op != FE_REDUCE_MIN && op != FE_REDUCE_MAX) return fail(FE_EINVAL, "%s: op %d", who, op);
+  const int dim = coords->dim;
+  if (dim != 2 && dim != 3) return fail(FE_EINVAL, "%s: coordinates of dimension %d", who, dim);
+  if (coord_map->from != cells || coords->set != coord_map->to)
+    return fail(FE_EINVAL, "%s: the coordinate map must go from the cells to the coordinates' set", who);
+  if (coord_map->arity != dim + 1) return fail(FE_EARITY, "%s: coordinate map arity %d", who, coord_map->arity);
+  DeviceGuard dg(c->device);
+  void *part = g->part;
+  fe_status st = ensure_stage(c, &part, &g->part_bytes, sizeof(double) * (size_t)fe::global_parts(cells->size), who);
+  g->part = static_cast<double *>(part);
+  if (st != FE_OK) return st;
+  FE_CHECK_CUDA(fe::launch_cell_volume_reduce(dim, op, cells->size, coord_map->values, coords->data, coords->set->size,
+                                              g->part, g->data, zero_first, c->checks, c->d_err, c->stream),
+                who);
   return ok();
 }
 

@@ -37,6 +37,16 @@ LaunchFn pick_vec_pull_dd2(const fe_form_desc &d) {
   FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1)
   return nullptr;
 }
+LaunchFn pick_action_elem_dd2(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(action_elem)
+  return nullptr;
+}
+#undef VEC
+#define VEC vec_elem
+LaunchFn pick_vec_elem_dd2(const fe_form_desc &d) {
+  FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1)
+  return nullptr;
+}
 #undef VEC
 
 }  // namespace fe

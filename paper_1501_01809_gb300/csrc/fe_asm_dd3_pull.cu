@@ -22,6 +22,16 @@ LaunchFn pick_vec_pull_dd3(const fe_form_desc &d) {
   FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
   return nullptr;
 }
+LaunchFn pick_action_elem_dd3(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(action_elem)
+  return nullptr;
+}
+#undef VEC
+#define VEC vec_elem
+LaunchFn pick_vec_elem_dd3(const fe_form_desc &d) {
+  FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
+  return nullptr;
+}
 #undef VEC
 
 }  // namespace fe

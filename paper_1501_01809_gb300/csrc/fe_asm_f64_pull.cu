@@ -23,6 +23,16 @@ LaunchFn pick_vec_pull_f64(const fe_form_desc &d) {
   FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1) FE_SRC_FOR(2, 4, 1) FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
   return nullptr;
 }
+LaunchFn pick_action_elem_f64(const fe_form_desc &d) {
+  FE_BILINEAR_TABLE(action_elem)
+  return nullptr;
+}
+#undef VEC
+#define VEC vec_elem
+LaunchFn pick_vec_elem_f64(const fe_form_desc &d) {
+  FE_SRC_FOR(2, 1, 1) FE_SRC_FOR(2, 2, 2) FE_SRC_FOR(2, 2, 1) FE_SRC_FOR(2, 4, 1) FE_SRC_FOR(3, 1, 1) FE_SRC_FOR(3, 2, 2) FE_SRC_FOR(3, 2, 1)
+  return nullptr;
+}
 #undef VEC
 
 }  // namespace fe

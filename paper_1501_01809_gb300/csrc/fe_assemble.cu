@@ -27,6 +27,12 @@ LaunchFn pick_mat_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_action_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_vec_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_mat_push_tc(const fe_form_desc &d);
+LaunchFn pick_action_elem_f64(const fe_form_desc &d);
+LaunchFn pick_vec_elem_f64(const fe_form_desc &d);
+LaunchFn pick_action_elem_dd2(const fe_form_desc &d);
+LaunchFn pick_vec_elem_dd2(const fe_form_desc &d);
+LaunchFn pick_action_elem_dd3(const fe_form_desc &d);
+LaunchFn pick_vec_elem_dd3(const fe_form_desc &d);
 StoreFn pick_elem_store_f64(const fe_form_desc &d);
 StoreFn pick_elem_store_dd(const fe_form_desc &d);
 StoredActionFn pick_action_stored_f64(int nd);
@@ -112,6 +118,18 @@ cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t 
 
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
   LaunchFn f = pick_vec(d, resolve_strategy(d, a.adj != nullptr));
+  *unsupported = f == nullptr;
+  return f ? f(a, s) : cudaSuccess;
+}
+
+// The element stage of a rank-0 form: K_e x_e per cell (bilinear kernels) or b_e (linear), in the
+// precisions that have pull kernels (FP64, double-float).
+cudaError_t launch_elem_stage(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
+  LaunchFn f = nullptr;
+  const bool lin = d.form == FE_FORM_SOURCE;
+  if (d.precision == FE_PREC_FP64) f = lin ? pick_vec_elem_f64(d) : pick_action_elem_f64(d);
+  else if (d.precision == FE_PREC_F32X2 && d.dim == 2) f = lin ? pick_vec_elem_dd2(d) : pick_action_elem_dd2(d);
+  else if (d.precision == FE_PREC_F32X2 && d.dim == 3) f = lin ? pick_vec_elem_dd3(d) : pick_action_elem_dd3(d);
   *unsupported = f == nullptr;
   return f ? f(a, s) : cudaSuccess;
 }

@@ -9,7 +9,7 @@ namespace fe {
 
 constexpr uint32_t kMagicCtx = 0xFE0C7A11u, kMagicSet = 0xFE05E7u, kMagicMap = 0xFE0AA9u,
                    kMagicDat = 0xFE0DA7u, kMagicSp = 0xFE05BA25u, kMagicMat = 0xFE0AA7u,
-                   kMagicKer = 0xFE0CE2u, kDead = 0xDEADu;
+                   kMagicKer = 0xFE0CE2u, kMagicGlobal = 0xFE061Bu, kDead = 0xDEADu;
 
 // device error-flag bits (ctx->d_err[0]); d_err[1] keeps the first offending index (low 32 bits)
 enum : int { ERR_RANGE = 1, ERR_ROW_TOO_LONG = 2, ERR_NNZ_CHANGED = 4, ERR_CAND_OVERFLOW = 8, ERR_TC_TIMEOUT = 16,
@@ -88,6 +88,17 @@ struct fe_mat {
   double *values;
   void *stage;  // staging of element matrices for pull assembly (lazily allocated)
   size_t stage_bytes;
+};
+
+struct fe_global {
+  uint32_t magic;
+  fe_ctx *ctx;
+  int dim;
+  double *data;  // dim values (library-owned)
+  void *stage;   // element stage of a rank-0 form (lazily allocated)
+  size_t stage_bytes;
+  double *part;  // per-block partial reductions (lazily allocated)
+  size_t part_bytes;
 };
 
 struct fe_kernel {
@@ -258,6 +269,19 @@ size_t serve_row_smem(int p, int rowcap, int precision);
 // Two launches on s: element tensors of every cell, then every row (Mat, elimination, RHS).
 cudaError_t launch_serve_assembly(const ServeItem *d_items, int nitems, int64_t cell_tiles, int64_t row_tiles,
                                   size_t row_smem, int precision, cudaStream_t s);
+
+// ---- Globals (fe_global.cu): reductions over cells in a fixed order ----
+// element stage of a rank-0 form: K_e x_e (bilinear) or b_e (linear) into a.stage, ND per cell
+cudaError_t launch_elem_stage(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
+int64_t global_parts(int64_t ncell);  // partial sums of a cell reduction (one per block of cells)
+// *g (+)= sum over cells e of sum_i x[map(e)[i]] stage[e nd + i] (stage in the precision's type)
+cudaError_t launch_global_dot(int precision, int64_t ncell, int nd, const int32_t *map, const void *stage,
+                              const double *x, int64_t nx, double *part, double *g, int zero_first, int checks,
+                              int *err, cudaStream_t s);
+// *g (op)= reduction (FE_REDUCE_SUM/MIN/MAX) of the cells' volumes |det J| / dim!
+cudaError_t launch_cell_volume_reduce(int dim, int op, int64_t ncell, const int32_t *cmapv, const double *coords,
+                                      int64_t nvert, double *part, double *g, int zero_first, int checks, int *err,
+                                      cudaStream_t s);
 
 // ---- stored element matrices (fe_stored_f64.cu, fe_stored_dd.cu) ----
 // Ke: [nd(nd+1)/2][ncell] FP64, entry-major (see fe_stored.cuh)

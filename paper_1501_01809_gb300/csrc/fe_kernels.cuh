@@ -624,6 +624,23 @@ cudaError_t vec_pull(const AsmArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The element stage alone (no row pass): each cell's K_e x_e (action) or b_e (linear form) into
+// a.stage, ND values per cell at e ND, for reductions that consume them directly (rank-0 forms).
+template <int DIM, int P, int FORM, class Ops>
+cudaError_t action_elem(const AsmArgs &a, cudaStream_t s) {
+  using T = typename Ops::T;
+  if (a.ncell > 0)
+    k_action_elem<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a, static_cast<T *>(a.stage));
+  return cudaGetLastError();
+}
+template <int DIM, int P, int Q, class Ops>
+cudaError_t vec_elem(const AsmArgs &a, cudaStream_t s) {
+  using T = typename Ops::T;
+  if (a.ncell > 0)
+    k_vec_elem<DIM, P, Q, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a, static_cast<T *>(a.stage));
+  return cudaGetLastError();
+}
+
 template <int DIM, int P, int Q, class Ops>
 cudaError_t vec_push(const AsmArgs &a, cudaStream_t s) {
   if (a.ncell > 0) k_vec_push<DIM, P, Q, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);

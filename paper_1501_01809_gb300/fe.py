@@ -22,6 +22,7 @@ FE_OK, FE_EINVAL, FE_EHANDLE, FE_ERANGE, FE_EARITY, FE_ENOMEM, FE_ECUDA, FE_ETIM
 FORM_MASS, FORM_LAPLACE, FORM_HELMHOLTZ, FORM_KAPPA_DIFFUSION, FORM_SOURCE = 1, 2, 3, 4, 5
 PREC_FP64, PREC_F32X2, PREC_FP32, PREC_TF32X3 = 0, 1, 2, 3
 STRATEGY_AUTO, STRATEGY_PUSH, STRATEGY_PULL = 0, 1, 2
+REDUCE_SUM, REDUCE_MIN, REDUCE_MAX = 0, 1, 2
 
 SYMBOLS = [
     "fe_last_error", "fe_version", "fe_ctx_create", "fe_ctx_set_stream", "fe_ctx_set_allocator",
@@ -29,7 +30,9 @@ SYMBOLS = [
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
     "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
-    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_elem_matrices", "fe_action_stored", "fe_batch_create", "fe_batch_values", "fe_batch_tune",
+    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_global_create", "fe_global_data", "fe_global_destroy",
+    "fe_assemble_global", "fe_reduce_cell_volume", "fe_elem_matrices", "fe_action_stored", "fe_batch_create",
+    "fe_batch_values", "fe_batch_tune",
     "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
     "fe_cg_poll", "fe_cg_remove", "fe_cg_destroy", "fe_server_create", "fe_server_submit", "fe_server_run",
     "fe_server_result", "fe_server_stats_get", "fe_server_destroy", "fe_wave_steps",
@@ -122,6 +125,9 @@ def load():
         "fe_assemble_mat": (I, [P, P, P, P, I, P, P, C.POINTER(fe_arg), I]),
         "fe_assemble_vec": (I, [P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
         "fe_action": (I, [P, P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
+        "fe_global_create": (I, [P, I, PP]), "fe_global_data": (I, [P, PP]), "fe_global_destroy": (I, [P]),
+        "fe_assemble_global": (I, [P, P, P, P, I, P, P, P, P, C.POINTER(fe_arg), I]),
+        "fe_reduce_cell_volume": (I, [P, P, P, I, I, P, P]),
         "fe_elem_matrices": (I, [P, P, P, P, P, P, C.POINTER(fe_arg), I]),
         "fe_action_stored": (I, [P, P, P, P, P, P, P, I]),
         "fe_batch_create": (I, [P, I, C.POINTER(fe_batch_item), PP]),
@@ -223,6 +229,10 @@ class Mat(Handle):
 
 class Kernel(Handle):
     _destroy = "fe_kernel_destroy"
+
+
+class Global(Handle):
+    _destroy = "fe_global_destroy"
 
 
 class Batch(Handle):
@@ -444,6 +454,36 @@ def action(ctx: Ctx, k: Kernel, cells: Set, x: Dat, y: Dat, map_: Map, coords: D
     _check(load().fe_action(ctx.ptr, k.ptr, cells.ptr, x.ptr, y.ptr, map_.ptr, int(bool(zero_first)),
                             coords.ptr, coord_map.ptr, arr, n, sp.ptr if sp is not None else None))
 
+
+def global_create(ctx: Ctx, dim: int = 1) -> Global:
+    """fe_global_create: dim FP64 values on the device, zeroed."""
+    out = C.c_void_p()
+    _check(load().fe_global_create(ctx.ptr, int(dim), C.byref(out)))
+    g = Global(out, ctx)
+    g.dim = int(dim)
+    return g
+
+
+def global_values(g: Global) -> torch.Tensor:
+    """A device view of the Global's values (read after sync)."""
+    p = C.c_void_p()
+    _check(load().fe_global_data(g.ptr, C.byref(p)))
+    return _view(p.value, g.dim, torch.float64, g, torch.device("cuda", g.ctx.device))
+
+
+def assemble_global(ctx: Ctx, k: Kernel, cells: Set, g: Global, x: Dat, map_: Map, coords: Dat, coord_map: Map,
+                    coeffs=(), zero_first: bool = True) -> None:
+    """fe_assemble_global: g[0] (+)= a(x, x) for a bilinear kernel, or L(x) for a linear one (SUM)."""
+    arr, n = _args(coeffs)
+    _check(load().fe_assemble_global(ctx.ptr, k.ptr, cells.ptr, g.ptr, int(bool(zero_first)), x.ptr, map_.ptr,
+                                     coords.ptr, coord_map.ptr, arr, n))
+
+
+def reduce_cell_volume(ctx: Ctx, cells: Set, g: Global, op: int, coords: Dat, coord_map: Map,
+                       zero_first: bool = True) -> None:
+    """fe_reduce_cell_volume: g[0] (op)= SUM, MIN or MAX over the cells of their volumes."""
+    _check(load().fe_reduce_cell_volume(ctx.ptr, cells.ptr, g.ptr, int(op), int(bool(zero_first)), coords.ptr,
+                                        coord_map.ptr))
 
 
 def _stored_tensor(Ke, k: Kernel, cells: Set):

@@ -106,6 +106,40 @@ class GpuProblem:
         fe.sync(self.ctx)
         return tb.cpu().numpy()
 
+    def functional(self, form, x: np.ndarray, precision=0, zero_first=True, g=None):
+        """a(x, x) into a Global (fe_assemble_global with a bilinear kernel); returns (value, Global)."""
+        fe, torch = self.fe, self.torch
+        k = fe.kernel_create(self.ctx, form, self.pr.dim, self.pr.p, precision=precision)
+        tx = torch.from_numpy(x).cuda()
+        X = fe.dat_create(self.ctx, self.nodes, tx)
+        g = g or fe.global_create(self.ctx)
+        fe.assemble_global(self.ctx, k, self.cells, g, X, self.map, self.coords, self.coord_map, self.coeffs(form),
+                           zero_first=zero_first)
+        fe.sync(self.ctx)
+        return float(fe.global_values(g)[0].item()), g
+
+    def linear_functional(self, f: np.ndarray, fmap: np.ndarray, pf: int, fset_size: int, x: np.ndarray,
+                          precision=0):
+        """L(x) = integral of f x (fe_assemble_global with a linear kernel)."""
+        fe, torch = self.fe, self.torch
+        k = fe.kernel_create(self.ctx, fe.FORM_SOURCE, self.pr.dim, self.pr.p, coeff_degree=pf, precision=precision)
+        fset = fe.set_create(self.ctx, fset_size)
+        tf, tfm = torch.from_numpy(f).cuda(), torch.from_numpy(np.ascontiguousarray(fmap)).cuda()
+        F, Fm = fe.dat_create(self.ctx, fset, tf), fe.map_create(self.ctx, self.cells, fset, tfm)
+        tx = torch.from_numpy(x).cuda()
+        X = fe.dat_create(self.ctx, self.nodes, tx)
+        g = fe.global_create(self.ctx)
+        fe.assemble_global(self.ctx, k, self.cells, g, X, self.map, self.coords, self.coord_map, [(F, Fm)])
+        fe.sync(self.ctx)
+        return float(fe.global_values(g)[0].item())
+
+    def volume(self, op, g=None, zero_first=True):
+        fe = self.fe
+        g = g or fe.global_create(self.ctx)
+        fe.reduce_cell_volume(self.ctx, self.cells, g, op, self.coords, self.coord_map, zero_first=zero_first)
+        fe.sync(self.ctx)
+        return float(fe.global_values(g)[0].item()), g
+
 
 def assert_close_scaled(got, want, scale, rtol=1e-12, what=""):
     """Per-entry |got - want| <= rtol * scale (scale = sum of |contributions|) and relative Frobenius."""
