@@ -242,6 +242,18 @@ fe_status fe_action(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat 
                     int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
                     int ncoeffs, const fe_sparsity *sp);
 
+/* fe_assemble_mat_action: fe_assemble_mat and fe_action of the same bilinear kernel in one pass
+ * over the cells.  A(INC, (map, map)) += K_e and y(INC, map) += K_e x_e, x READ through map:
+ * each cell's element matrix is computed once, in registers, for both outputs, and no assembled
+ * matrix is read for y (the action stays matrix-free, Sec. 6.3).  zero_first != 0 clears A and y
+ * first.  The push strategy only (AUTO or PUSH), FE_PREC_FP64 (every compiled element) or
+ * FE_PREC_F32X2 (P1, P2); the results equal the two separate calls' within rounding (y's products
+ * are summed in another order).
+ * Errors: FE_EINVAL (x and y alias, sets), FE_EARITY, FE_EHANDLE, FE_EUNSUPPORTED. */
+fe_status fe_assemble_mat_action(fe_ctx *ctx, fe_kernel *k, fe_set *cells, fe_mat *A, fe_dat *x, fe_dat *y,
+                                 fe_map *map, int zero_first, fe_dat *coords, fe_map *coord_map,
+                                 const fe_arg *coeffs, int ncoeffs);
+
 /* ---------------------------------------------------------------- Global (Sec. 4.3, 4.4)
  * A Global is a tuple of values tied to no set (a 0-linear operator beside the Dat and the Mat,
  * Sec. 4.3).  par_loops reach it either by READ or through a reduction: SUM, MIN or MAX

@@ -18,7 +18,7 @@ GEN = os.path.join(CSRC, "generated", "fe_local.cuh")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libfe.so")
 SOURCES = ["fe_api.cpp", "fe_sparsity.cu", "fe_assemble.cu", "fe_asm_f64_push.cu", "fe_asm_f64_pull.cu",
-           "fe_asm_dd2.cu", "fe_asm_dd3_push.cu", "fe_asm_dd3_pull.cu", "fe_asm_f32.cu", "fe_asm_tc.cu", "fe_batch.cu", "fe_solve.cu", "fe_serve.cpp", "fe_serve_asm.cu", "fe_global.cu", "fe_wave.cu",
+           "fe_asm_dd2.cu", "fe_asm_dd3_push.cu", "fe_asm_dd3_pull.cu", "fe_asm_fused_f64.cu", "fe_asm_fused_dd.cu", "fe_asm_f32.cu", "fe_asm_tc.cu", "fe_batch.cu", "fe_solve.cu", "fe_serve.cpp", "fe_serve_asm.cu", "fe_global.cu", "fe_wave.cu",
            "fe_noalloc.cu", "fe_stored_f64.cu", "fe_stored_dd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

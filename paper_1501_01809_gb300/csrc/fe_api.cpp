@@ -700,6 +700,40 @@ fe_status fe_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_dat *x, fe_dat *y
   return ok();
 }
 
+fe_status fe_assemble_mat_action(fe_ctx *c, fe_kernel *k, fe_set *cells, fe_mat *A, fe_dat *x, fe_dat *y,
+                                 fe_map *map, int zero_first, fe_dat *coords, fe_map *coord_map, const fe_arg *coeffs,
+                                 int ncoeffs) {
+  Range nvtx_range("fe_assemble_mat_action");
+  const char *who = "fe_assemble_mat_action";
+  if (!valid(A) || A->ctx != c) return fail(FE_EHANDLE, "%s: invalid mat", who);
+  fe::AsmArgs a;
+  fe_status st = common_args(who, c, k, cells, map, coords, coord_map, a);
+  if (st != FE_OK) return st;
+  if (A->sp->rmap != map || A->sp->cmap != map)
+    return fail(FE_EINVAL, "%s: the Mat's sparsity must be built from (map, map)", who);
+  if (k->d.form == FE_FORM_SOURCE) return fail(FE_EINVAL, "%s: the kernel must be a bilinear form", who);
+  if (!valid(x) || !valid(y) || x->ctx != c || y->ctx != c || x->set != map->to || y->set != map->to || x->dim != 1 ||
+      y->dim != 1)
+    return fail(FE_EINVAL, "%s: x and y must be scalar Dats on the map's target", who);
+  if (x->data == y->data) return fail(FE_EINVAL, "%s: x and y must not alias", who);
+  st = kappa_arg(who, c, k, cells, coeffs, ncoeffs, a);
+  if (st != FE_OK) return st;
+  a.rowptr = A->sp->rowptr;
+  a.lut = A->sp->lut;
+  a.vals = A->values;
+  a.x = x->data;
+  a.y = y->data;
+  DeviceGuard g(c->device);
+  if (zero_first) {
+    FE_CHECK_CUDA(fe::launch_zero_f64(A->values, A->sp->nnz, c->stream), who);
+    FE_CHECK_CUDA(fe::launch_zero_f64(y->data, y->set->size, c->stream), who);
+  }
+  int unsup = 0;
+  FE_CHECK_CUDA(fe::launch_mat_action(k->d, a, c->stream, &unsup), who);
+  if (unsup) return fail(FE_EUNSUPPORTED, "%s: no fused kernel for this form, precision or strategy", who);
+  return ok();
+}
+
 // ------------------------------------------------------------------------------------ Global
 fe_status fe_global_create(fe_ctx *c, int dim, fe_global **out) {
   if (!valid(c)) return fail(FE_EHANDLE, "fe_global_create: invalid context");

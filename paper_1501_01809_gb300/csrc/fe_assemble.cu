@@ -27,6 +27,8 @@ LaunchFn pick_mat_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_action_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_vec_pull_dd3(const fe_form_desc &d);
 LaunchFn pick_mat_push_tc(const fe_form_desc &d);
+LaunchFn pick_mat_action_f64(const fe_form_desc &d);
+LaunchFn pick_mat_action_dd(const fe_form_desc &d);
 LaunchFn pick_action_elem_f64(const fe_form_desc &d);
 LaunchFn pick_vec_elem_f64(const fe_form_desc &d);
 LaunchFn pick_action_elem_dd2(const fe_form_desc &d);
@@ -118,6 +120,17 @@ cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t 
 
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
   LaunchFn f = pick_vec(d, resolve_strategy(d, a.adj != nullptr));
+  *unsupported = f == nullptr;
+  return f ? f(a, s) : cudaSuccess;
+}
+
+// Assembly and action in one pass (push): FP64 or double-float element arithmetic.
+cudaError_t launch_mat_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported) {
+  LaunchFn f = nullptr;
+  if (d.form != FE_FORM_SOURCE && resolve_strategy(d, false) == FE_STRATEGY_PUSH) {
+    if (d.precision == FE_PREC_FP64) f = pick_mat_action_f64(d);
+    else if (d.precision == FE_PREC_F32X2) f = pick_mat_action_dd(d);
+  }
   *unsupported = f == nullptr;
   return f ? f(a, s) : cudaSuccess;
 }

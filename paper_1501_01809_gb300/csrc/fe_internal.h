@@ -248,6 +248,8 @@ size_t stage_bytes_vec(const fe_form_desc &d, int64_t ncell, int nd);
 cudaError_t launch_assemble_mat(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_assemble_vec(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 cudaError_t launch_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
+// assembly and matrix-free action in one pass (push strategy; FP64 and double-float)
+cudaError_t launch_mat_action(const fe_form_desc &d, const AsmArgs &a, cudaStream_t s, int *unsupported);
 bool kernel_supported(const fe_form_desc &d);
 
 // ---- assembly of the systems a request loop admits together (fe_serve_asm.cu) ----

@@ -157,6 +157,63 @@ __global__ void __launch_bounds__(kPushThreads, MatOcc<Ops>::kMinBlocks) k_mat_p
   if (e < a.ncell) mat_push_cell<DIM, P, FORM, Ops>(a, e);
 }
 
+// ---------------------------------------------------------------------------- assembly + action, push
+// The CSR assembly and the matrix-free action of the same form in one pass over the cells: each
+// cell's element matrix is built once, in registers, and serves both outputs.  Its entries go into
+// the CSR values through the lookup table (as k_mat_push), and y_e = K_e x_e into y (as
+// k_action_push); the action still reads no assembled matrix.  Row i's products with x_e are
+// formed beside that row's reductions, in the kernel's arithmetic (FP64 or double-float), and
+// added to y[rows[i]] with one FP64 reduction.
+template <int DIM, int P, int FORM, class Ops>
+__device__ __forceinline__ void mat_action_push_cell(const AsmArgs &a, int64_t e) {
+  using T = typename Ops::T;
+  using E = fe_gen::Elem<DIM, P>;
+  constexpr int ND = E::ND;
+  double x[DIM + 1][DIM], kap[DIM + 1];
+  int32_t v[DIM + 1], rows[ND];
+  bool ok = gather_coords<DIM>(a, e, x, v);
+  ok &= gather_rows<ND>(a, e, rows);
+  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) ok &= gather_kappa<DIM>(a, e, kap);
+  if (!ok) {
+    flag(a.err, ERR_RANGE, e);
+    return;
+  }
+  T xe[ND];
+#pragma unroll
+  for (int j = 0; j < ND; j++) xe[j] = Ops::from_f64(a.x[rows[j]]);
+  T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
+  Geo<DIM>::template compute<Ops>(x, Lam, vol);
+#pragma unroll
+  for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
+  T K[E::NUP];
+  element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
+  const uint8_t *L = a.lut + e * (ND * ND);
+#pragma unroll
+  for (int i = 0; i < ND; i++) {
+    const int64_t b = a.rowptr[rows[i]];
+    const int64_t len = a.checks ? a.rowptr[rows[i] + 1] - b : 0;
+    T yi = Ops::mul(K[E::upper_index(i, 0)], xe[0]);
+#pragma unroll
+    for (int j = 1; j < ND; j++) yi = Ops::fma3(K[E::upper_index(i, j)], xe[j], yi);
+#pragma unroll
+    for (int j = 0; j < ND; j++) {
+      const int q = L[i * ND + j];
+      if (a.checks && q >= len) {  // check mode: a lookup-table entry beyond its row is skipped
+        flag(a.err, ERR_LUT, e);
+        continue;
+      }
+      red_add_f64(a.vals + b + q, Ops::to_f64(K[E::upper_index(i, j)]));
+    }
+    red_add_f64(a.y + rows[i], Ops::to_f64(yi));
+  }
+}
+
+template <int DIM, int P, int FORM, class Ops>
+__global__ void __launch_bounds__(kPushThreads, MatOcc<Ops>::kMinBlocks) k_mat_action_push(const AsmArgs a) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < a.ncell) mat_action_push_cell<DIM, P, FORM, Ops>(a, e);
+}
+
 // ---------------------------------------------------------------------------- action, push
 // Blocks per SM the push action is compiled for.  Double-float element arithmetic fits 96
 // registers (five 128-thread blocks per SM) with at most a few words spilled, which measured 3%
@@ -555,6 +612,11 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 template <int DIM, int P, int FORM, class Ops>
 cudaError_t mat_push(const AsmArgs &a, cudaStream_t s) {
   if (a.ncell > 0) k_mat_push<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <int DIM, int P, int FORM, class Ops>
+cudaError_t mat_action_push(const AsmArgs &a, cudaStream_t s) {
+  if (a.ncell > 0) k_mat_action_push<DIM, P, FORM, Ops><<<blocks_for(a.ncell, kPushThreads), kPushThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 template <int DIM, int P, int FORM, class Ops>

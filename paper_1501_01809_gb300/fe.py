@@ -30,7 +30,7 @@ SYMBOLS = [
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
     "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
-    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_global_create", "fe_global_data", "fe_global_destroy",
+    "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_assemble_mat_action", "fe_global_create", "fe_global_data", "fe_global_destroy",
     "fe_assemble_global", "fe_reduce_cell_volume", "fe_elem_matrices", "fe_action_stored", "fe_batch_create",
     "fe_batch_values", "fe_batch_tune",
     "fe_batch_assemble", "fe_batch_destroy", "fe_dirichlet_apply", "fe_cg_create", "fe_cg_add", "fe_cg_iterate",
@@ -125,6 +125,7 @@ def load():
         "fe_assemble_mat": (I, [P, P, P, P, I, P, P, C.POINTER(fe_arg), I]),
         "fe_assemble_vec": (I, [P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
         "fe_action": (I, [P, P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I, P]),
+        "fe_assemble_mat_action": (I, [P, P, P, P, P, P, P, I, P, P, C.POINTER(fe_arg), I]),
         "fe_global_create": (I, [P, I, PP]), "fe_global_data": (I, [P, PP]), "fe_global_destroy": (I, [P]),
         "fe_assemble_global": (I, [P, P, P, P, I, P, P, P, P, C.POINTER(fe_arg), I]),
         "fe_reduce_cell_volume": (I, [P, P, P, I, I, P, P]),
@@ -453,6 +454,14 @@ def action(ctx: Ctx, k: Kernel, cells: Set, x: Dat, y: Dat, map_: Map, coords: D
     arr, n = _args(coeffs)
     _check(load().fe_action(ctx.ptr, k.ptr, cells.ptr, x.ptr, y.ptr, map_.ptr, int(bool(zero_first)),
                             coords.ptr, coord_map.ptr, arr, n, sp.ptr if sp is not None else None))
+
+
+def assemble_mat_action(ctx: Ctx, k: Kernel, cells: Set, A: Mat, x: Dat, y: Dat, map_: Map, coords: Dat,
+                        coord_map: Map, coeffs=(), zero_first: bool = True) -> None:
+    """fe_assemble_mat_action: A(INC) += K_e and y(INC) += K_e x_e in one pass over the cells."""
+    arr, n = _args(coeffs)
+    _check(load().fe_assemble_mat_action(ctx.ptr, k.ptr, cells.ptr, A.ptr, x.ptr, y.ptr, map_.ptr,
+                                         int(bool(zero_first)), coords.ptr, coord_map.ptr, arr, n))
 
 
 def global_create(ctx: Ctx, dim: int = 1) -> Global:
