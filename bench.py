@@ -68,6 +68,11 @@ TRAFFIC = {
     # k_mat_push<3,2,HELMHOLTZ,f32x2>: 249.0 MB at 40^3 (384,000 cells), scaled x4.096 to 64^3
     ("assemble", "push", "f32x2"): (1.020e9, "c827e6c081c1",
                                     "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
+    # the fused phase: the Mat zero (54.7 MB written at 40^3) and k_mat_action_push<3,2,HELMHOLTZ,FP64>
+    # (193.9 MB read, 68.4 MB written at 40^3), 317.1 MB, scaled x4.096 to 64^3
+    ("assemble_action", "push", "fp64"): (1.299e9, "ae76b03bc824",
+                                          "FP64 pipe 68% busy beside FP64 reductions in L2 (ncu at 40^3: L2 52%, "
+                                          "17.6% warps active at 162 registers)"),
     # one sparsity rebuild (zero, the guarded k_inc_fill, the in-place k_rows_build pass and the gated
     # launches that return at once): 129.1 MB at 40^3, scaled x4.096 to 64^3
     ("sparsity", None, None): (0.5288e9, "38eb0ca824bd",
@@ -320,6 +325,10 @@ def run_ours(args, wl, rank, world):
     if args.overlap != "off" and not pull:
         side = torch.cuda.Stream(dev, priority=-1 if args.overlap in ("hi", "asm-hi") else 0)
     beside_asm = args.overlap in ("asm", "asm-hi")  # the action beside the assembly, after the rebuild
+    # --fuse on (FP64 push on one stream): the Mat zero, assembly and action as one call,
+    # fe_assemble_mat_action, each cell's element matrix built once for both outputs; fuse[0] is
+    # switched off while the double-float extra runs (its separate kernels are the faster ones)
+    fuse = [args.fuse == "on" and not pull and side is None and args.precision == "fp64"]
 
     def compute(sp_, A_, X_, Y_, M_, XY_, CM_, ev=None, sev=None):
         """One pass of the hot path: sparsity rebuild, Mat zero, assembly, action.  ev: 5 events on the
@@ -327,6 +336,16 @@ def run_ours(args, wl, rank, world):
         side stream (after the zero, after the action)."""
         if ev is not None:
             ev[0].record(stream)
+        if side is None and fuse[0]:  # phases: rebuild | (zero, in the fused call) | fused | (action, in it)
+            fe.sparsity_rebuild(sp_)
+            if ev is not None:
+                ev[1].record(stream)
+                ev[2].record(stream)
+            fe.assemble_mat_action(ctx, kcur[0], cells, A_, X_, Y_, M_, XY_, CM_, zero_first=True)
+            if ev is not None:
+                ev[3].record(stream)
+                ev[4].record(stream)
+            return
         if side is None:
             fe.sparsity_rebuild(sp_)
             if ev is not None:
@@ -491,6 +510,7 @@ def run_ours(args, wl, rank, world):
     if args.precision == "fp64" and graph is not None and not args.no_f32x2:
         K32 = fe.kernel_create(ctx, fe.FORM_HELMHOLTZ, wl["dim"], wl["p"], precision=fe.PREC_F32X2, strategy=strat)
         kcur[0] = K32
+        fused_main, fuse[0] = fuse[0], False
         for _ in range(args.warmup):
             step()
         fe.sync(ctx)
@@ -527,18 +547,20 @@ def run_ours(args, wl, rank, world):
                  "dtype": "f32x2 element / f64 accumulate",
                  "precision": "element tensors in FP32 pairs (double-float, about 2^-46 relative), FP64 CSR and y",
                  "phases_ms": {"sparsity": ph32[0], "zero": ph32[1], "assemble": ph32[2], "action": ph32[3]},
+                 "schedule": "serial on one stream, assembly and action as separate kernels (faster in double-float)",
                  "note": "labelled extra, not the step of record: same step and graph schedule, narrower element "
                          "arithmetic"}
         kcur[0] = K
+        fuse[0] = fused_main
         del g32
         # the step of record leaves A and y in FP64: restore them for the checks below
         step()
         fe.sync(ctx)
     # launches of libfe kernels per step: sparsity rebuild 13 (zero, count, scan x3, zero, fill, in-place
     # row pass, then the gated full row pass, scan x3 and compact, which return at once when no row
-    # changed length); push: mat zero 1, assembly 1, action zero + action 2; pull: assembly 2
-    # (element, row), action 2 (element, row)
-    launches = (13 + 4) * args.steps
+    # changed length); push: mat zero 1, assembly 1, action zero + action 2, or fused: the two zeros
+    # and the fused kernel 3; pull: assembly 2 (element, row), action 2 (element, row)
+    launches = (13 + (3 if fuse[0] else 4)) * args.steps
 
     # ------------------------------------------------------------------- e2e through host buffers
     # Every step copies its inputs (maps, coordinates, x) from pinned host memory and its outputs
@@ -693,12 +715,22 @@ def run_ours(args, wl, rank, world):
     # sparsity build, the method's own bytes: the map read once, rowptr, colidx and the lookup table
     # written once (the incidence lists the design builds on the way are overhead, not counted)
     bytes_sp = ncell * nd * 4 + (nn + 1) * 8 + nnz * 4 + ncell * nd * nd
-    kern = {
-        "sparsity": {"ms": phase_ms[0], "bytes": bytes_sp},
-        "zero": {"ms": phase_ms[1], "bytes": nnz * 8 if not pull else 0},
-        "assemble": {"ms": phase_ms[2], "bytes": bytes_mat, "flops": ncell * fl_mat},
-        "action": {"ms": phase_ms[3], "bytes": bytes_act, "flops": ncell * fl_act},
-    }
+    if fuse[0]:
+        # one pass: the maps and coordinates read once, the zeros, the CSR values, x read, y written;
+        # the FP64 work of one element matrix and its nd^2 products with x_e per cell
+        bytes_fused = bytes_mat + nnz * 8 + 3 * nn * 8
+        kern = {
+            "sparsity": {"ms": phase_ms[0], "bytes": bytes_sp},
+            "assemble_action": {"ms": phase_ms[2], "bytes": bytes_fused, "flops": ncell * fl_act,
+                                "includes": "Mat and y zeros, assembly, matrix-free action (fe_assemble_mat_action)"},
+        }
+    else:
+        kern = {
+            "sparsity": {"ms": phase_ms[0], "bytes": bytes_sp},
+            "zero": {"ms": phase_ms[1], "bytes": nnz * 8 if not pull else 0},
+            "assemble": {"ms": phase_ms[2], "bytes": bytes_mat, "flops": ncell * fl_mat},
+            "action": {"ms": phase_ms[3], "bytes": bytes_act, "flops": ncell * fl_act},
+        }
     for k, v in kern.items():
         if "bytes" in v and v["ms"] > 0 and v["bytes"] > 0:
             v["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
@@ -740,6 +772,9 @@ def run_ours(args, wl, rank, world):
                    "schedule": (("action on a second stream, concurrent with the Mat zero and assembly" if beside_asm
                                  else "Mat zero and action on a second stream, concurrent with the sparsity rebuild"
                                  if side is not None else
+                                 "serial on one stream: sparsity rebuild, then the Mat and y zeros, assembly and "
+                                 "matrix-free action in one pass (fe_assemble_mat_action: each cell's element "
+                                 "matrix built once for both outputs)" if fuse[0] else
                                  "serial on one stream") +
                                 (", one CUDA graph per step (phases from a launch-by-launch pass)"
                                  if graph is not None else "")),
@@ -1606,6 +1641,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=2.0, help="oracle seconds per step (batch workload)")
     ap.add_argument("--n", type=int, default=0, help="override the mesh size (profiling on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fuse", default="on", choices=["on", "off"],
+                    help="FP64 push step: assembly and action in one pass (on) or as separate kernels (off)")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams per copy direction in the end-to-end leg (each direction's bytes cut evenly)")
     ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
