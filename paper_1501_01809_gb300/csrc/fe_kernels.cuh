@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kPushThreads, MatOcc<Ops>::kMinBlocks) k_mat_p
 // formed beside that row's reductions, in the kernel's arithmetic (FP64 or double-float), and
 // added to y[rows[i]] with one FP64 reduction.
 template <int DIM, int P, int FORM, class Ops>
-__device__ __forceinline__ void mat_action_push_cell(const AsmArgs &a, int64_t e) {
+__device__ __forceinline__ void mat_action_push_cell(const AsmArgs &a, int64_t e, const uint8_t *L) {
   using T = typename Ops::T;
   using E = fe_gen::Elem<DIM, P>;
   constexpr int ND = E::ND;
@@ -187,7 +187,6 @@ __device__ __forceinline__ void mat_action_push_cell(const AsmArgs &a, int64_t e
   for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
   T K[E::NUP];
   element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
-  const uint8_t *L = a.lut + e * (ND * ND);
 #pragma unroll
   for (int i = 0; i < ND; i++) {
     const int64_t b = a.rowptr[rows[i]];
@@ -208,10 +207,42 @@ __device__ __forceinline__ void mat_action_push_cell(const AsmArgs &a, int64_t e
   }
 }
 
+// Blocks per SM the fused kernel is compiled for.  The loads of the lookup table, row pointers and
+// x wait longest, so resident warps matter more than a few spilled words: FP64 elements of at most
+// 55 upper entries (P2 tetrahedra, P1-P3 triangles) take four 128-thread blocks per SM at 128
+// registers (about 230 bytes spilled for P2 tetrahedra), which measured 1.106 -> 1.011 ms at 64^3
+// against three blocks at 162 registers; larger elements keep the compiler's choice.
+template <int DIM, int P, class Ops>
+struct FusedOcc {
+  static constexpr int kMinBlocks = MatOcc<Ops>::kMinBlocks;
+};
+template <int DIM, int P>
+struct FusedOcc<DIM, P, OpsF64> {
+  static constexpr int kMinBlocks = fe_gen::Elem<DIM, P>::NUP <= 55 ? 4 : 1;
+};
+
+// The block's lookup-table bytes are one contiguous range (its kPushThreads cells, ND^2 bytes each,
+// 16-byte aligned): staged into shared memory with 16-byte loads, they replace each thread's ND^2
+// byte loads at a stride of ND^2 bytes (one sector per lane per load) by reads of shared memory
+// (free of bank conflicts when ND^2 / 4 is odd, as for P2 tetrahedra and triangles).  Elements
+// whose staged table would pass 32 KB per block read the table from global memory.
 template <int DIM, int P, int FORM, class Ops>
-__global__ void __launch_bounds__(kPushThreads, MatOcc<Ops>::kMinBlocks) k_mat_action_push(const AsmArgs a) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < a.ncell) mat_action_push_cell<DIM, P, FORM, Ops>(a, e);
+__global__ void __launch_bounds__(kPushThreads, FusedOcc<DIM, P, Ops>::kMinBlocks) k_mat_action_push(const AsmArgs a) {
+  constexpr int NN = fe_gen::Elem<DIM, P>::ND * fe_gen::Elem<DIM, P>::ND;
+  const int64_t e0 = blockIdx.x * (int64_t)kPushThreads, e = e0 + threadIdx.x;
+  if constexpr (NN * kPushThreads <= 32 * 1024) {
+    __shared__ __align__(16) uint8_t sL[NN * kPushThreads];
+    const int64_t left = a.ncell - e0;
+    const int nb = (int)(left < kPushThreads ? left : kPushThreads) * NN;  // bytes of this block's cells
+    const uint8_t *src = a.lut + e0 * NN;
+    for (int q = threadIdx.x; q < nb / 16; q += kPushThreads)
+      reinterpret_cast<uint4 *>(sL)[q] = __ldg(reinterpret_cast<const uint4 *>(src) + q);
+    for (int q = (nb / 16) * 16 + threadIdx.x; q < nb; q += kPushThreads) sL[q] = src[q];
+    __syncthreads();
+    if (e < a.ncell) mat_action_push_cell<DIM, P, FORM, Ops>(a, e, sL + threadIdx.x * NN);
+  } else {
+    if (e < a.ncell) mat_action_push_cell<DIM, P, FORM, Ops>(a, e, a.lut + e * NN);
+  }
 }
 
 // ---------------------------------------------------------------------------- action, push
