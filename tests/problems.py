@@ -90,6 +90,19 @@ class GpuProblem:
         fe.sync(self.ctx)
         return ty.cpu().numpy()
 
+    def fused(self, form, x: np.ndarray, precision=0):
+        """fe_assemble_mat_action: the Mat values and y = A x of one pass (zero_first)."""
+        fe, torch = self.fe, self.torch
+        k = fe.kernel_create(self.ctx, form, self.pr.dim, self.pr.p, precision=precision)
+        A = fe.mat_create(self.ctx, self.sparsity())
+        tx = torch.from_numpy(x).cuda()
+        ty = torch.full_like(tx, np.nan)
+        X, Y = fe.dat_create(self.ctx, self.nodes, tx), fe.dat_create(self.ctx, self.nodes, ty)
+        fe.assemble_mat_action(self.ctx, k, self.cells, A, X, Y, self.map, self.coords, self.coord_map,
+                               self.coeffs(form), zero_first=True)
+        fe.sync(self.ctx)
+        return fe.mat_values(A).cpu().numpy(), ty.cpu().numpy()
+
     def rhs(self, f: np.ndarray, fmap: np.ndarray, pf: int, fset_size: int, precision=0, strategy=0):
         fe, torch = self.fe, self.torch
         k = fe.kernel_create(self.ctx, fe.FORM_SOURCE, self.pr.dim, self.pr.p, coeff_degree=pf,

@@ -85,7 +85,7 @@ def _pattern_and_lut(fe, g, pr):
 def test_p2_cube_64_full(gpu):
     """P2 UnitCubeMesh 64^3, +-0.2h jitter seed 0 (1,572,864 cells, 2,146,689 dofs, nnz 60,859,905):
     the whole pattern, lookup table, Mat (FP64 push and pull, double-float push) and action (FP64,
-    double-float) of the benchmark step."""
+    double-float) of the benchmark step, and both outputs of the step's fused pass (FP64)."""
     from paper_1501_01809_gb300 import fe
     from paper_1501_01809_gb300 import meshgen as mg
     pr = PB.make(3, 2, 64, 0.2, seed=0)
@@ -97,11 +97,14 @@ def test_p2_cube_64_full(gpu):
         got = g.assemble(fe.FORM_HELMHOLTZ, precision=prec, strategy=strat)
         PB.assert_close_scaled(got, want, scale, 1e-12, f"P2 64^3 Mat, FP64, strategy {strat}")
     check_double_float(g.assemble(fe.FORM_HELMHOLTZ, precision=fe.PREC_F32X2), want, scale, "P2 64^3 Mat")
-    del want, scale
     x = mg.uniform_dat(pr.nnodes, 2)  # the benchmark's x
+    fused_vals, fused_y = g.fused(fe.FORM_HELMHOLTZ, x)
+    PB.assert_close_scaled(fused_vals, want, scale, 1e-12, "P2 64^3 Mat, fused with the action")
+    del want, scale, fused_vals
     yw, ys = OP.action_full(3, 2, O.HELMHOLTZ, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, x)
     PB.assert_close_scaled(g.action(fe.FORM_HELMHOLTZ, x, precision=fe.PREC_FP64), yw, ys, 1e-12,
                            "P2 64^3 action, FP64")
+    PB.assert_close_scaled(fused_y, yw, ys, 1e-12, "P2 64^3 action, fused with the assembly")
     check_double_float(g.action(fe.FORM_HELMHOLTZ, x, precision=fe.PREC_F32X2), yw, ys, "P2 64^3 action")
 
 
