@@ -649,22 +649,28 @@ def run_ours(args, wl, rank, world):
         for k in range(2):
             e2e_step(k)
         torch.cuda.synchronize()
+        # three windows of ksteps steps each; the median window is the figure (the host side of the
+        # copies is shared with other work on the machine, and one stall can double a short window)
         ksteps = max(3, min(args.steps, 20))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for st in s_in[1:]:
-            st.wait_stream(s_in[0])
-        a.record(s_in[0])
-        for k in range(ksteps):
-            e2e_step(k)
-        for st in s_out[1:]:
-            s_out[0].wait_stream(st)
-        b.record(s_out[0])
-        b.synchronize()
-        e2e_ms = a.elapsed_time(b) / ksteps
+        windows = []
+        for w in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for st in s_in[1:]:
+                st.wait_stream(s_in[0])
+            a.record(s_in[0])
+            for k in range(ksteps):
+                e2e_step(k)
+            for st in s_out[1:]:
+                s_out[0].wait_stream(st)
+            b.record(s_out[0])
+            b.synchronize()
+            windows.append(a.elapsed_time(b) / ksteps)
+        e2e_ms = sorted(windows)[1]
         if dist:
             e2e_ms = max_over_ranks(e2e_ms, dev)
         e2e = {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "windows_ms_per_step": windows, "window_steps": ksteps,
                "pipelining": f"copies of neighbouring steps overlap the compute (two device slots; each direction's "
                              f"copies cut into {ncs} pieces on {ncs} streams)",
                "host_cpus": host_cpus or "unchanged (no local CPU list in sysfs)"}
