@@ -564,18 +564,24 @@ def run_ours(args, wl, rank, world):
 
     # ------------------------------------------------------------------- e2e through host buffers
     # Every step copies its inputs (maps, coordinates, x) from pinned host memory and its outputs
-    # (rowptr, colidx, CSR values, y) back.  The copies of neighbouring steps overlap the compute on
-    # separate streams: two device slots of inputs and outputs, ordered by events.  Each direction's
-    # bytes are cut into --copy-streams pieces of about equal size, each on its own stream, so that
-    # more than one copy engine can serve a direction.
+    # back (CSR values and y; rowptr and colidx when the step's rebuild changed them).  The copies of
+    # neighbouring steps overlap the compute on separate streams: three device slots of inputs and
+    # outputs, ordered by events.  Each direction's bytes are cut into --copy-streams pieces of about
+    # equal size, each on its own stream, so that more than one copy engine can serve a direction.
     e2e = None
     if not args.no_e2e:
         host_cpus = bind_to_gpu_cpus(dev.index)  # pinned buffers on the GPU's own socket
         ncs = max(1, args.copy_streams)
         pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t.cpu())
         host_in = [pin(t) for t in (t_map, t_cv, t_xy, t_x)]
+        # Three device slots.  Every step reads back the Mat values, y and the rebuild's two flags; the
+        # pattern (rowptr, colidx) is read back only after a rebuild that reports a change
+        # (fe_sparsity_changed, with column tracking on: the in-place row pass compares each column
+        # it writes), so the host always holds the current pattern.  A slot's flags are checked when
+        # the slot comes round again, three steps later, before its next rebuild.
+        nslots = 3
         slots = []
-        for sidx in range(2):
+        for sidx in range(nslots):
             d_in = [torch.empty_like(t) for t in (t_map, t_cv, t_xy, t_x)]
             for d, h in zip(d_in, host_in):
                 d.copy_(h)
@@ -587,18 +593,24 @@ def run_ours(args, wl, rank, world):
                 XYs = fe.dat_create(ctx, verts, d_in[2])
                 Xs, Ys = fe.dat_create(ctx, nodes, d_in[3]), fe.dat_create(ctx, nodes, d_y)
                 sps = fe.sparsity_build(ctx, Ms, Ms)
+                fe.sparsity_track_columns(sps, True)  # exact flags: the rebuild compares what it writes
                 As = fe.mat_create(ctx, sps)
+            fe.sync(ctx)
             _, _, _, rps, cis = fe.sparsity_csr(sps)
-            outs = [rps, cis, fe.mat_values(As), d_y]
+            outs = [fe.mat_values(As), d_y, fe.sparsity_changed(sps)]
             h_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+            pat = [rps, cis]
+            h_pat = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in pat]  # set-up read
             ev = {"in": [torch.cuda.Event() for _ in range(ncs)], "comp": torch.cuda.Event(),
                   "out": [torch.cuda.Event() for _ in range(ncs)]}
-            slots.append(dict(d_in=d_in, M=Ms, CM=CMs, XY=XYs, X=Xs, Y=Ys, sp=sps, A=As, outs=outs, h_out=h_out, ev=ev,
-                              used=False))
+            slots.append(dict(d_in=d_in, M=Ms, CM=CMs, XY=XYs, X=Xs, Y=Ys, sp=sps, A=As, outs=outs, h_out=h_out,
+                              pat=pat, h_pat=h_pat, ev=ev, used=False))
         s_in = [torch.cuda.Stream(dev) for _ in range(ncs)]
         s_out = [torch.cuda.Stream(dev) for _ in range(ncs)]
         h2d = sum(h.numel() * h.element_size() for h in host_in)
         d2h = sum(h.numel() * h.element_size() for h in slots[0]["h_out"])
+        pat_bytes = sum(h.numel() * h.element_size() for h in slots[0]["h_pat"])
+        tally = {"steps": 0, "pattern_reads": 0}
 
         def pieces(pairs):
             """(destination, source) pairs cut into ncs lists of flat slices of about equal bytes."""
@@ -621,9 +633,24 @@ def run_ours(args, wl, rank, world):
             sl["in_pieces"] = pieces(list(zip(sl["d_in"], host_in)))
             sl["out_pieces"] = pieces(list(zip(sl["h_out"], sl["outs"])))
 
-        def e2e_step(k):
-            sl = slots[k % 2]
+        def collect(sl):
+            """The slot's last step fully on the host: its copies complete, and its pattern read back
+            if that step's rebuild changed it (before the slot's next rebuild overwrites it)."""
+            for e in sl["ev"]["out"]:
+                e.synchronize()
+            if int(sl["h_out"][2][0]) or int(sl["h_out"][2][1]):
+                with torch.cuda.stream(s_out[0]):
+                    for h, d in zip(sl["h_pat"], sl["pat"]):
+                        h.copy_(d, non_blocking=True)
+                s_out[0].synchronize()
+                tally["pattern_reads"] += 1
+
+        def e2e_step():
+            sl = slots[tally["steps"] % nslots]
+            tally["steps"] += 1
             ev = sl["ev"]
+            if sl["used"]:
+                collect(sl)
             for q, st in enumerate(s_in):
                 if sl["used"]:
                     st.wait_event(ev["comp"])    # the slot's previous compute has read its inputs
@@ -646,32 +673,41 @@ def run_ours(args, wl, rank, world):
                     ev["out"][q].record(st)
             sl["used"] = True
 
-        for k in range(2):
-            e2e_step(k)
+        for k in range(nslots):
+            e2e_step()
         torch.cuda.synchronize()
         # three windows of ksteps steps each; the median window is the figure (the host side of the
         # copies is shared with other work on the machine, and one stall can double a short window)
         ksteps = max(3, min(args.steps, 20))
         windows = []
+        timed_steps, timed_reads = 0, tally["pattern_reads"]
         for w in range(3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             for st in s_in[1:]:
                 st.wait_stream(s_in[0])
             a.record(s_in[0])
             for k in range(ksteps):
-                e2e_step(k)
+                e2e_step()
             for st in s_out[1:]:
                 s_out[0].wait_stream(st)
             b.record(s_out[0])
             b.synchronize()
             windows.append(a.elapsed_time(b) / ksteps)
+            timed_steps += ksteps
+        for sl in slots:  # the steps still in flight are collected (and counted) too
+            collect(sl)
+        timed_reads = tally["pattern_reads"] - timed_reads
         e2e_ms = sorted(windows)[1]
         if dist:
             e2e_ms = max_over_ranks(e2e_ms, dev)
         e2e = {"value": job_throughput(mesh.ncell, world, e2e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "d2h_bytes_per_step": d2h + pat_bytes * timed_reads / timed_steps, "ms_per_step": e2e_ms,
                "windows_ms_per_step": windows, "window_steps": ksteps,
-               "pipelining": f"copies of neighbouring steps overlap the compute (two device slots; each direction's "
+               "outputs": "every step: CSR values, y and the rebuild's two flags (column tracking on: the row pass "
+                          "compares each column it writes in place); rowptr and colidx after a rebuild "
+                          f"that reports a change ({timed_reads} of {timed_steps} timed steps; "
+                          f"{pat_bytes} bytes each), so the host holds the current pattern after every step",
+               "pipelining": f"copies of neighbouring steps overlap the compute (three device slots; each direction's "
                              f"copies cut into {ncs} pieces on {ncs} streams)",
                "host_cpus": host_cpus or "unchanged (no local CPU list in sysfs)"}
         fe.sync(ctx)

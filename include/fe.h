@@ -171,6 +171,20 @@ fe_status fe_sparsity_build(fe_ctx *ctx, fe_map *rmap, fe_map *cmap, fe_sparsity
  * pass, the row-pointer scan and the colidx compaction run (their launches are gated on a device
  * flag, so the call stays asynchronous).  The result is the same either way. */
 fe_status fe_sparsity_rebuild(fe_sparsity *sp);
+/* Device pointer to two ints written by each fe_sparsity_rebuild (zero after fe_sparsity_build):
+ * flags[0] != 0 when some row changed length (the rebuild ran its full path); flags[1] != 0 when
+ * some row kept its length but its columns changed, or when the sparsity does not track columns
+ * (then every rebuild sets it).  With column tracking on, rowptr and colidx equal those before the
+ * rebuild exactly when both flags are 0, so a caller holding a copy of the pattern needs to read
+ * it again only when a flag is set.  Read them after the rebuild's work on the stream (a
+ * stream-ordered copy, or fe_sync). */
+fe_status fe_sparsity_changed(const fe_sparsity *sp, const int **flags);
+/* Column tracking (off after fe_sparsity_build; on != 0 turns it on, 0 off) for the rebuilds that
+ * follow: the in-place row pass compares each column it would write with the one already there,
+ * writes only a different one and reports it in flags[1] of fe_sparsity_changed.  The compares
+ * add about an eighth to the row pass's instructions.  Host call, no device work; FE_EHANDLE for
+ * an invalid handle. */
+fe_status fe_sparsity_track_columns(fe_sparsity *sp, int on);
 /* Read-only views of the CSR pattern (device pointers owned by sp). */
 fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols, int64_t *nnz,
                           const int64_t **rowptr, const int32_t **colidx);

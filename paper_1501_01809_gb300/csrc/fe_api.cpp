@@ -317,15 +317,17 @@ fe_status sparsity_build_begin(fe_ctx *c, fe_map *rmap, fe_map *cmap, fe_sparsit
   sp->lut = (uint8_t *)dev_alloc(c, (size_t)ninc * sp->ndc);
   sp->scan_tmp = (int64_t *)dev_alloc(c, sizeof(int64_t) * sp->scan_tmp_elems);
   sp->d_maxcnt = (int *)dev_alloc(c, sizeof(int));
-  sp->d_changed = (int *)dev_alloc(c, sizeof(int));
+  sp->d_changed = (int *)dev_alloc(c, 2 * sizeof(int));  // [0] a row changed length, [1] a column changed
   if (!sp->rowptr || !sp->adjptr || !sp->adj || !sp->rowcnt || !sp->coltmp || !sp->lut || !sp->scan_tmp || !sp->d_maxcnt ||
       !sp->d_changed) {
     sparsity_free(sp);
     delete sp;
     return fail(FE_ENOMEM, "fe_sparsity_build: device allocation failed");
   }
+  // the rebuild flags read zero until a rebuild writes them
+  cudaError_t e = cudaMemsetAsync(sp->d_changed, 0, 2 * sizeof(int), c->stream);
   // incidence (validates the row map), the column map's range check, the longest incidence list
-  cudaError_t e = fe::sparsity_incidence(sp, c->stream, c->d_err);
+  if (e == cudaSuccess) e = fe::sparsity_incidence(sp, c->stream, c->d_err);
   if (e == cudaSuccess && cmap->to->size > 0 && ncell > 0)
     e = fe::launch_map_validate(cmap->values, ncell * cmap->arity, cmap->to->size, c->d_err, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_maxcnt, sp->d_maxcnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -409,7 +411,7 @@ fe_status fe_sparsity_rebuild(fe_sparsity *sp) {
   // length changed do the full row pass, its scan and the compaction run (gated on the device).
   // The incidence is filled against the previous row offsets first; the in-place pass checks each
   // row's count, and a changed count sends the rebuild through the full incidence too.
-  FE_CHECK_CUDA(cudaMemsetAsync(sp->d_changed, 0, sizeof(int), c->stream), "fe_sparsity_rebuild");
+  FE_CHECK_CUDA(cudaMemsetAsync(sp->d_changed, 0, 2 * sizeof(int), c->stream), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_incidence_reuse(sp, c->stream, c->d_err), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_rows_inplace(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
   FE_CHECK_CUDA(fe::sparsity_incidence_gated(sp, c->stream, c->d_err, sp->d_changed), "fe_sparsity_rebuild");
@@ -436,6 +438,19 @@ fe_status fe_sparsity_csr(const fe_sparsity *sp, int64_t *nrows, int64_t *ncols,
   if (nnz) *nnz = sp->nnz;
   if (rowptr) *rowptr = sp->rowptr;
   if (colidx) *colidx = sp->colidx;
+  return ok();
+}
+
+fe_status fe_sparsity_track_columns(fe_sparsity *sp, int on) {
+  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_track_columns: invalid sparsity");
+  sp->track_cols = on != 0;
+  return ok();
+}
+
+fe_status fe_sparsity_changed(const fe_sparsity *sp, const int **flags) {
+  if (!valid(sp)) return fail(FE_EHANDLE, "fe_sparsity_changed: invalid sparsity");
+  if (!flags) return fail(FE_EINVAL, "fe_sparsity_changed: flags == NULL");
+  *flags = sp->d_changed;
   return ok();
 }
 

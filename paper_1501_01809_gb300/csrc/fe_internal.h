@@ -74,7 +74,9 @@ struct fe_sparsity {
   int64_t *scan_tmp; // scan block sums
   int64_t scan_tmp_elems;
   int *d_maxcnt;     // [1] max incidence count
-  int *d_changed;    // [1] rebuild: some row changed its length (the in-place pass is not enough)
+  int *d_changed;    // [2] rebuild: [0] some row changed its length (the in-place pass is not enough),
+                     // [1] some row kept its length but a column changed (nonzero when not tracked)
+  int track_cols;    // rebuilds compare each column written in place (fe_sparsity_track_columns)
   int adj_canonical; // each row's incidence list is in ascending order (sparsity_canonical)
   int maxrow;        // longest row (entries), known after build
   void *vstage;      // staging of element vectors for pull action / linear form (lazily allocated)

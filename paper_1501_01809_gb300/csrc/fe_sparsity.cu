@@ -300,6 +300,8 @@ struct RowsParams {
   int canon;        // also put every row's incidence list in ascending order (else it stays in fill order)
   int check_counts; // rowlen holds a guarded fill's incidence counts: a row whose count differs from its
                     // previous range sets *changed (read before the row's length overwrites it)
+  int *cols_changed; // in-place pass: a column written in place that differs from the one already
+                     // there sets *cols_changed (equal columns are not written again)
 };
 
 // Where row r's nu unique columns go: colidx in place when the in-place pass applies and the
@@ -312,6 +314,19 @@ __device__ __forceinline__ int32_t *row_out(const RowsParams &p, int64_t r, int6
     if (leader) *p.changed = 1;
   }
   return p.coltmp + a0 * p.ndc;
+}
+
+// Column k of a row whose columns go to outc.  With TRACK, in place (the row kept its length in an
+// in-place pass) the column is compared with the one already there and written only when it
+// differs, which also records that the pattern changed; otherwise it is written.
+template <bool TRACK>
+__device__ __forceinline__ void put_col(const RowsParams &p, int32_t *outc, int k, int32_t col, bool in_place) {
+  if (!TRACK || !in_place) {
+    outc[k] = col;
+  } else if (outc[k] != col) {
+    outc[k] = col;
+    *p.cols_changed = 1;
+  }
 }
 
 __device__ __forceinline__ uint32_t div_ndr(uint32_t k, const RowsParams &p) {
@@ -329,7 +344,7 @@ __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
 // lookup table.  Returns the number of unique columns (valid in every lane).
 // adje (na words) and lbuf (256 bytes) are per-warp shared scratch: the cell of each incidence, and
 // each candidate's rank, which the warp then writes to the lookup table incidence by incidence.
-template <int E, int SH>
+template <int E, int SH, bool TRACK>
 __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
                                            uint32_t *adjs, uint32_t *adje, uint8_t *lbuf) {
   const int lane = threadIdx.x & 31;
@@ -378,12 +393,13 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   }
   const int nu = __shfl_sync(0xffffffffu, incl, 31);
   int32_t *outc = row_out(p, r, a0, nu);
+  const bool in_place = TRACK && outc != p.coltmp + a0 * ndc;
   int rank = incl - c - 1;  // rank of the run before this lane's first element
 #pragma unroll
   for (int h = 0; h < E; h++) {
     rank += f[h];
     if (key[h] == 0xFFFFFFFFu) continue;
-    if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
+    if (f[h]) put_col<TRACK>(p, outc, rank, (int32_t)(key[h] >> SH), in_place);
     lbuf[key[h] & tmask] = (uint8_t)rank;  // ranks past the row limit are flagged by the caller
   }
   __syncwarp();
@@ -402,7 +418,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
 // width NL, so the groups never exchange values; adjs, adje (NL words) and lbuf (NL E bytes) are
 // this group's scratch.  A group without a row (r < 0, na = ncand = 0) takes part in the warp-wide
 // steps with padding keys only and writes nothing.  Returns this group's number of unique columns.
-template <int E, int SH, int NL>
+template <int E, int SH, int NL, bool TRACK>
 __device__ __forceinline__ int row_by_sort_group(const RowsParams &p, int64_t r, int64_t a0, int na, int ncand,
                                                  uint32_t *adjs, uint32_t *adje, uint8_t *lbuf) {
   const int gl = threadIdx.x & (NL - 1);
@@ -452,12 +468,13 @@ __device__ __forceinline__ int row_by_sort_group(const RowsParams &p, int64_t r,
   const int nu = __shfl_sync(full, incl, NL - 1, NL);
   if (r >= 0) {
     int32_t *outc = row_out(p, r, a0, nu, gl == 0);
+    const bool in_place = TRACK && outc != p.coltmp + a0 * ndc;
     int rank = incl - c - 1;
 #pragma unroll
     for (int h = 0; h < E; h++) {
       rank += f[h];
       if (key[h] == 0xFFFFFFFFu) continue;
-      if (f[h]) outc[rank] = (int32_t)(key[h] >> SH);
+      if (f[h]) put_col<TRACK>(p, outc, rank, (int32_t)(key[h] >> SH), in_place);
       lbuf[key[h] & tmask] = (uint8_t)rank;
     }
   }
@@ -483,13 +500,20 @@ __device__ __forceinline__ int row_by_sort_group(const RowsParams &p, int64_t r,
 //     ranks into the table;
 //  4. lut[(e*ndr + i)*ndc + j] = rank of the candidate's slot; rowlen[r] = number of unique columns.
 // Shared memory per warp (32-bit words): hkey[cap], hrank[cap], ucol[cap], uslot[cap], cslot[cap],
-// adju[acap], adjs[acap].
+// adju[acap], adjs[acap], then the sort paths' scratch: rank bytes (64) and the quarter-warp rows'
+// incidences, cells and rank bytes (128).
+// TRACK (in-place pass only): compare the columns written in place; without it the in-place pass
+// sets *p.cols_changed at once (a column may have changed).
+template <bool TRACK>
 __global__ void __launch_bounds__(256, 5) k_rows_build(const RowsParams p) {
   extern __shared__ __align__(16) int32_t smem_i[];
   if (p.gate && *p.gate == 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int cap = p.cap;
-  if (p.colidx && blockIdx.x == 0 && threadIdx.x == 0 && p.rowptr[p.nrows] != p.nnz) *p.changed = 1;
+  if (p.colidx && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (p.rowptr[p.nrows] != p.nnz) *p.changed = 1;
+    if (!TRACK) *p.cols_changed = 1;
+  }
   // per warp: hash tables (5 cap words) unless every row is sorted, then the incidence lists, then
   // 64 words of rank bytes for the sort path, then 128 words for the quarter-warp rows (incidences,
   // cells and rank bytes of each quarter)
@@ -537,8 +561,8 @@ __global__ void __launch_bounds__(256, 5) k_rows_build(const RowsParams p) {
       const int nag = have ? na : 0;
       const int64_t r = have ? rb + k : -1;
       const bool wide = __any_sync(full, nag * ndc > 32);
-      const int nu = wide ? row_by_sort_group<8, 6, 8>(p, r, a0, nag, nag * ndc, gadjs, gadje, glbuf)
-                          : row_by_sort_group<4, 6, 8>(p, r, a0, nag, nag * ndc, gadjs, gadje, glbuf);
+      const int nu = wide ? row_by_sort_group<8, 6, 8, TRACK>(p, r, a0, nag, nag * ndc, gadjs, gadje, glbuf)
+                          : row_by_sort_group<4, 6, 8, TRACK>(p, r, a0, nag, nag * ndc, gadjs, gadje, glbuf);
       if (have && (lane & 7) == 0) p.rowlen[r] = nu;  // at most 64 columns: within the row limit
       __syncwarp();
       for (int g = 0; g < 4; g++) qmask &= qmask - 1;  // the (up to) four rows just done
@@ -562,9 +586,9 @@ __global__ void __launch_bounds__(256, 5) k_rows_build(const RowsParams p) {
       }
       if (p.packed_ok && na <= 32 && ncand <= 256) {
         // rows of up to 256 candidates (every row of P1 and P2 meshes and of P3 triangles): sort packed values
-        const int nu = ncand <= 64    ? row_by_sort<2, 6>(p, r, a0, na, ncand, adjs, adju, lbuf)
-                       : ncand <= 128 ? row_by_sort<4, 7>(p, r, a0, na, ncand, adjs, adju, lbuf)
-                                      : row_by_sort<8, 8>(p, r, a0, na, ncand, adjs, adju, lbuf);
+        const int nu = ncand <= 64    ? row_by_sort<2, 6, TRACK>(p, r, a0, na, ncand, adjs, adju, lbuf)
+                       : ncand <= 128 ? row_by_sort<4, 7, TRACK>(p, r, a0, na, ncand, adjs, adju, lbuf)
+                                      : row_by_sort<8, 8, TRACK>(p, r, a0, na, ncand, adjs, adju, lbuf);
         if (lane == 0) {
           p.rowlen[r] = nu;
           if (nu > kMaxRowLen) flag(p.err, ERR_ROW_TOO_LONG, r);
@@ -615,9 +639,10 @@ __global__ void __launch_bounds__(256, 5) k_rows_build(const RowsParams p) {
       }
       __syncwarp();
       int32_t *outc = row_out(p, r, a0, nu);
+      const bool in_place = TRACK && outc != p.coltmp + a0 * ndc;
       warp_rank_distinct(ucol, nu, [&](int q, int rk) {
         hrank[uslot[q]] = rk;
-        outc[rk] = (int32_t)ucol[q];
+        put_col<TRACK>(p, outc, rk, (int32_t)ucol[q], in_place);
       });
       __syncwarp();
       // 4. rank of every candidate -> lookup table (candidate t = (a, j) of incident k = adjs[a])
@@ -809,15 +834,17 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
   p.gate = gate;
   p.canon = 0;
   p.check_counts = changed != nullptr;  // the in-place pass of a rebuild follows a guarded fill
+  p.cols_changed = changed ? changed + 1 : nullptr;  // the second flag word: a column changed in place
   const size_t per_warp = (size_t)((p.sort_only ? 0 : 5 * sp->cap) + 2 * sp->acap + 64 + 128) * sizeof(int32_t);
   int warps = 8;
   while (warps > 1 && warps * per_warp > 96 * 1024) warps >>= 1;
   const size_t smem = warps * per_warp;
+  auto kern = p.cols_changed && sp->track_cols ? k_rows_build<true> : k_rows_build<false>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_rows_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  if (sp->nrows > 0) k_rows_build<<<grid_for(sp->nrows, warps, 152 * 32), warps * 32, smem, s>>>(p);
+  if (sp->nrows > 0) kern<<<grid_for(sp->nrows, warps, 152 * 32), warps * 32, smem, s>>>(p);
   return cudaGetLastError();
 }
 }  // namespace

@@ -28,7 +28,7 @@ SYMBOLS = [
     "fe_last_error", "fe_version", "fe_ctx_create", "fe_ctx_set_stream", "fe_ctx_set_allocator",
     "fe_ctx_set_checks", "fe_sync", "fe_ctx_destroy", "fe_set_create", "fe_set_size", "fe_set_destroy",
     "fe_map_create", "fe_map_destroy", "fe_dat_create", "fe_dat_destroy", "fe_sparsity_build",
-    "fe_sparsity_rebuild", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
+    "fe_sparsity_rebuild", "fe_sparsity_changed", "fe_sparsity_track_columns", "fe_sparsity_build_noalloc", "fe_sparsity_csr", "fe_sparsity_lut", "fe_sparsity_destroy", "fe_mat_create",
     "fe_mat_values", "fe_mat_zero", "fe_mat_destroy", "fe_kernel_create", "fe_kernel_destroy",
     "fe_assemble_mat", "fe_assemble_vec", "fe_action", "fe_assemble_mat_action", "fe_global_create", "fe_global_data", "fe_global_destroy",
     "fe_assemble_global", "fe_reduce_cell_volume", "fe_elem_matrices", "fe_action_stored", "fe_batch_create",
@@ -115,7 +115,7 @@ def load():
         "fe_set_create": (I, [P, I64, PP]), "fe_set_size": (I, [P, C.POINTER(I64)]), "fe_set_destroy": (I, [P]),
         "fe_map_create": (I, [P, P, P, I, P, I, PP]), "fe_map_destroy": (I, [P]),
         "fe_dat_create": (I, [P, P, I, P, PP]), "fe_dat_destroy": (I, [P]),
-        "fe_sparsity_build": (I, [P, P, P, PP]), "fe_sparsity_rebuild": (I, [P]),
+        "fe_sparsity_build": (I, [P, P, P, PP]), "fe_sparsity_rebuild": (I, [P]), "fe_sparsity_changed": (I, [P, PP]), "fe_sparsity_track_columns": (I, [P, I]),
         "fe_sparsity_build_noalloc": (I, [P, I, P, I, I64, I64, I64, P, P, I64, P, C.POINTER(I64), P]),
         "fe_sparsity_csr": (I, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), PP, PP]),
         "fe_sparsity_lut": (I, [P, PP]), "fe_sparsity_destroy": (I, [P]),
@@ -345,6 +345,19 @@ def sparsity_build(ctx: Ctx, rmap: Map, cmap: Map) -> Sparsity:
 
 def sparsity_rebuild(sp: Sparsity) -> None:
     _check(load().fe_sparsity_rebuild(sp.ptr))
+
+
+def sparsity_changed(sp: Sparsity) -> torch.Tensor:
+    """fe_sparsity_changed: a device view of the two flags of the last rebuild (int32 [2]: a row
+    changed length; a row's columns changed, or columns are not tracked)."""
+    p = C.c_void_p()
+    _check(load().fe_sparsity_changed(sp.ptr, C.byref(p)))
+    return _view(p.value, 2, torch.int32, sp, torch.device("cuda", sp.ctx.device))
+
+
+def sparsity_track_columns(sp: Sparsity, on: bool = True) -> None:
+    """fe_sparsity_track_columns: rebuilds compare the columns they write in place (exact flags[1])."""
+    _check(load().fe_sparsity_track_columns(sp.ptr, int(bool(on))))
 
 
 def sparsity_build_noalloc(rmap: torch.Tensor, cmap: torch.Tensor, nrows: int, ncols: int, rowptr: torch.Tensor,

@@ -157,6 +157,63 @@ def test_rebuild_changed_row_lengths(gpu):
     _check_pattern(g, pr.cmap, pr.nnodes)
 
 
+def _flags(g):
+    g.fe.sync(g.ctx)
+    return g.fe.sparsity_changed(g.sparsity()).cpu().tolist()
+
+
+@pytest.mark.parametrize("dim,p,n", [(3, 2, 5), (2, 1, 9), (3, 3, 3)])
+def test_rebuild_reports_whether_the_pattern_changed(gpu, dim, p, n):
+    """fe_sparsity_changed after each rebuild with column tracking on: [0, 0] after the build, for
+    the same map, and for a permuted local node order (the same pattern, a new lookup table);
+    [0, 1] when two nodes whose rows have the same length swap labels (every row keeps its length,
+    some columns change), and again when they swap back; flags[0] set when relabelled nodes change
+    row lengths.  With tracking off, flags[1] is set by every rebuild.  The pattern matches the
+    oracle's every time.  P2 tetrahedra have whole-warp and quarter-warp rows, P1 triangles only
+    quarter-warp rows, P3 tetrahedra hashed vertex rows (480 candidates)."""
+    pr = PB.make(dim, p, n, 0.2, seed=0)
+    g = PB.GpuProblem(pr)
+    g.fe.sparsity_track_columns(g.sparsity(), True)
+    assert _flags(g) == [0, 0]
+    g.fe.sparsity_rebuild(g.sparsity())
+    assert _flags(g) == [0, 0]
+    perm = np.argsort(np.random.default_rng(11).random(pr.cmap.shape), axis=1)
+    m_local = np.take_along_axis(pr.cmap, perm, axis=1)
+    _rewrite_map(g, m_local)
+    g.fe.sparsity_rebuild(g.sparsity())
+    assert _flags(g) == [0, 0]
+    _check_pattern(g, m_local, pr.nnodes)
+    rp, ci = g.csr()
+    lens = np.diff(rp)
+    a = int(np.argmax(lens))  # a vertex node; b: the farthest node with a row of the same length
+    b = int(np.nonzero(lens == lens[a])[0][-1])
+    assert a != b
+    relabel = np.arange(pr.nnodes, dtype=np.int32)
+    relabel[a], relabel[b] = b, a
+    m_swap = relabel[pr.cmap]
+    orp, oci = O.sparsity(m_swap, m_swap, pr.nnodes, pr.nnodes)
+    assert np.array_equal(orp, rp) and not np.array_equal(oci, ci)
+    _rewrite_map(g, m_swap)
+    g.fe.sparsity_rebuild(g.sparsity())
+    assert _flags(g) == [0, 1]
+    _check_pattern(g, m_swap, pr.nnodes)
+    _rewrite_map(g, pr.cmap)
+    g.fe.sparsity_rebuild(g.sparsity())
+    assert _flags(g) == [0, 1]
+    _check_pattern(g, pr.cmap, pr.nnodes)
+    g.fe.sparsity_track_columns(g.sparsity(), False)
+    g.fe.sparsity_rebuild(g.sparsity())
+    f = _flags(g)
+    assert f[0] == 0 and f[1] != 0
+    _check_pattern(g, pr.cmap, pr.nnodes)
+    g.fe.sparsity_track_columns(g.sparsity(), True)
+    m_rel = np.random.default_rng(12).permutation(pr.nnodes).astype(np.int32)[pr.cmap]
+    _rewrite_map(g, m_rel)
+    g.fe.sparsity_rebuild(g.sparsity())
+    assert _flags(g)[0] == 1
+    _check_pattern(g, m_rel, pr.nnodes)
+
+
 def test_rebuild_changed_nnz_is_reported(gpu):
     """A map whose pattern has another nnz is reported at the next sync, every time it is rebuilt
     (also when the previous failed rebuild left rowptr at that map's lengths); rebuilding with the
