@@ -289,6 +289,8 @@ struct RowsParams {
   uint32_t mdiv_ndc;  // floor(2^32 / ndc) + 1: exact t / ndc = __umulhi(t, mdiv_ndc) for t < 2^26
   int packed_ok;      // ncols < 2^24 - 1: (column << 8 | candidate) fits 32 bits below the padding value
   int sort_only;      // every row takes the sort path: shared memory holds only the incidence lists
+  int pairs;          // ndc even and cmap 8-byte aligned: the sort paths load candidates two at a time
+  int lut_pairs;      // ndc even and lut 2-byte aligned: the sort paths write the table two bytes at a time
   int *err;
   // in-place rebuild pass (colidx != NULL): a row whose length equals rowptr[r+1] - rowptr[r]
   // writes its columns to colidx + rowptr[r]; any other row sets *changed
@@ -337,6 +339,59 @@ __device__ __forceinline__ uint32_t div_ndc(uint32_t t, const RowsParams &p) {
 }
 
 
+// The packed keys (column << SH | candidate t) of one row's ncand candidates, E per lane of a group
+// of W lanes (lane l of the group: candidates W h + l, or with p.pairs 2 (W h' + l) and the next,
+// both of one incidence, from one 8-byte load); slots past ncand hold the padding value.  Candidate
+// t = (a, j) is column j of incidence a, whose cell is adje[a].
+template <int E, int SH, int W>
+__device__ __forceinline__ void load_keys(const RowsParams &p, int l, int ncand, const uint32_t *adje,
+                                          uint32_t (&key)[E]) {
+  const int ndc = p.ndc;
+  if (p.pairs) {
+#pragma unroll
+    for (int hp = 0; hp < E / 2; hp++) {
+      const uint32_t t = 2u * (uint32_t)(W * hp + l);  // ncand is even: t < ncand covers t + 1
+      key[2 * hp] = key[2 * hp + 1] = 0xFFFFFFFFu;
+      if ((int)t < ncand) {
+        const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+        const int2 c = *reinterpret_cast<const int2 *>(p.cmap + (int64_t)adje[a] * ndc + j);
+        key[2 * hp] = ((uint32_t)c.x << SH) | t;
+        key[2 * hp + 1] = ((uint32_t)c.y << SH) | (t + 1);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int h = 0; h < E; h++) {
+      const uint32_t t = (uint32_t)(W * h + l);
+      key[h] = 0xFFFFFFFFu;
+      if ((int)t < ncand) {
+        const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+        key[h] = ((uint32_t)p.cmap[(int64_t)adje[a] * ndc + j] << SH) | t;
+      }
+    }
+  }
+}
+
+// lut[(adjs[a]) ndc + j] = lbuf[t] for the row's candidates t = (a, j), lane l of a group of W
+// taking t = l, l + W, ... (with p.lut_pairs: the pairs 2 q, 2 q + 1 of one incidence, q = l, l + W,
+// ..., as one 2-byte store).
+template <int W>
+__device__ __forceinline__ void store_lut(const RowsParams &p, int l, int ncand, const uint32_t *adjs,
+                                          const uint8_t *lbuf) {
+  const int ndc = p.ndc;
+  if (p.lut_pairs) {
+    for (int q = l; 2 * q < ncand; q += W) {
+      const uint32_t t = 2u * (uint32_t)q, a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
+      *reinterpret_cast<uint16_t *>(p.lut + (int64_t)adjs[a] * ndc + j) = *reinterpret_cast<const uint16_t *>(lbuf + t);
+    }
+  } else {
+    for (int t = l; t < ncand; t += W) {
+      const uint32_t a = div_ndc((uint32_t)t, p), j = (uint32_t)t - a * (uint32_t)ndc;
+      p.lut[(int64_t)adjs[a] * ndc + j] = lbuf[t];
+    }
+  }
+}
+
 // One row by sorting packed (column << SH | candidate) values, E per lane (32 E >= ncand, na <= 32):
 // the incidence list (ranked into ascending order when p.canon), candidates, sort, first element
 // of each run of equal columns, ranks
@@ -366,15 +421,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   // 2. candidates t = 32 h + lane (consecutive lanes read consecutive map entries), packed
   //    (column << SH | t); padding sorts last.  The sort does not depend on the starting slots.
   uint32_t key[E];
-#pragma unroll
-  for (int h = 0; h < E; h++) {
-    const uint32_t t = (uint32_t)(32 * h + lane);
-    key[h] = 0xFFFFFFFFu;
-    if ((int)t < ncand) {
-      const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
-      key[h] = ((uint32_t)p.cmap[(int64_t)adje[a] * ndc + j] << SH) | t;
-    }
-  }
+  load_keys<E, SH, 32>(p, lane, ncand, adje, key);
   warp_bitonic_packed<E>(key);
   // 3. first element of each run of equal columns, ranks by a warp prefix count
   const uint32_t prev = __shfl_up_sync(0xffffffffu, key[E - 1], 1);
@@ -405,10 +452,7 @@ __device__ __forceinline__ int row_by_sort(const RowsParams &p, int64_t r, int64
   __syncwarp();
   // the lookup table in incidence order: candidate t = (a, j) goes to row a's ndc bytes, so the
   // lanes of one store write a few contiguous segments instead of one byte per segment each
-  for (int t = lane; t < ncand; t += 32) {
-    const uint32_t a = div_ndc((uint32_t)t, p), j = (uint32_t)t - a * (uint32_t)ndc;
-    p.lut[(int64_t)adjs[a] * ndc + j] = lbuf[t];
-  }
+  store_lut<32>(p, lane, ncand, adjs, lbuf);
   __syncwarp();
   return nu;
 }
@@ -441,15 +485,7 @@ __device__ __forceinline__ int row_by_sort_group(const RowsParams &p, int64_t r,
   }
   __syncwarp();
   uint32_t key[E];
-#pragma unroll
-  for (int h = 0; h < E; h++) {
-    const uint32_t t = (uint32_t)(NL * h + gl);
-    key[h] = 0xFFFFFFFFu;
-    if ((int)t < ncand) {
-      const uint32_t a = div_ndc(t, p), j = t - a * (uint32_t)ndc;
-      key[h] = ((uint32_t)p.cmap[(int64_t)adje[a] * ndc + j] << SH) | t;
-    }
-  }
+  load_keys<E, SH, NL>(p, gl, ncand, adje, key);
   warp_bitonic_packed<E, NL>(key);
   const uint32_t prev = __shfl_up_sync(full, key[E - 1], 1, NL);
   int f[E], c = 0;
@@ -479,10 +515,7 @@ __device__ __forceinline__ int row_by_sort_group(const RowsParams &p, int64_t r,
     }
   }
   __syncwarp();
-  for (int t = gl; t < ncand; t += NL) {
-    const uint32_t a = div_ndc((uint32_t)t, p), j = (uint32_t)t - a * (uint32_t)ndc;
-    p.lut[(int64_t)adjs[a] * ndc + j] = lbuf[t];
-  }
+  store_lut<NL>(p, gl, ncand, adjs, lbuf);
   __syncwarp();
   return nu;
 }
@@ -827,6 +860,8 @@ cudaError_t launch_rows(fe_sparsity *sp, cudaStream_t s, int *err, int *changed,
   p.err = err;
   // rows of at most 256 candidates and 32 incidences are sorted (no hash tables needed)
   p.sort_only = p.packed_ok && sp->cap <= 256 && sp->acap <= 32;
+  p.pairs = sp->ndc % 2 == 0 && (reinterpret_cast<uintptr_t>(p.cmap) & 7) == 0;
+  p.lut_pairs = sp->ndc % 2 == 0 && (reinterpret_cast<uintptr_t>(p.lut) & 1) == 0;
   p.colidx = changed ? sp->colidx : nullptr;
   p.rowptr = sp->rowptr;
   p.nnz = sp->nnz;

@@ -120,6 +120,26 @@ def _rewrite_map(g, cmap):
     g.t_map.copy_(g.torch.from_numpy(np.ascontiguousarray(cmap)))
 
 
+@pytest.mark.parametrize("dim,p,n", [(3, 2, 5), (2, 2, 9)])
+def test_map_values_not_8_byte_aligned(gpu, dim, p, n):
+    """Map values that start 4 bytes past an 8-byte boundary (a view one int32 into a larger tensor):
+    the row pass then loads candidates one at a time instead of in 8-byte pairs (even ndc).  The
+    pattern and every lookup-table entry still match the oracle, after the build and a rebuild."""
+    pr = PB.make(dim, p, n, 0.2, seed=3)
+    g = PB.GpuProblem(pr)
+    torch = g.torch
+    flat = torch.empty(pr.cmap.size + 1, dtype=torch.int32, device="cuda")
+    view = flat[1:].view(pr.cmap.shape)
+    view.copy_(torch.from_numpy(np.ascontiguousarray(pr.cmap)))
+    torch.cuda.synchronize()
+    assert view.data_ptr() % 8 == 4 and pr.cmap.shape[1] % 2 == 0
+    g.t_map, g.map = view, g.fe.map_create(g.ctx, g.cells, g.nodes, view)
+    _check_pattern(g, pr.cmap, pr.nnodes)
+    g.fe.sparsity_rebuild(g.sparsity())
+    g.fe.sync(g.ctx)
+    _check_pattern(g, pr.cmap, pr.nnodes)
+
+
 def test_rebuild_same_row_lengths_in_place(gpu):
     """Local node order permuted within each cell: the pattern is unchanged (rows keep their
     lengths, the in-place pass writes colidx directly) while the lookup table changes."""

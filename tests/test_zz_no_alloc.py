@@ -60,6 +60,30 @@ def test_two_calls_match_the_allocating_build(env):
             np.testing.assert_array_equal(a, b)
 
 
+def test_unaligned_map_and_table(env):
+    """A map 4 bytes past an 8-byte boundary and a lookup table at an odd address (views into larger
+    tensors): the row pass takes its one-at-a-time loads and byte stores; the result is the same."""
+    torch, fe = env
+    pr = PB.make(3, 2, 5, 0.2, seed=5)
+    want = _reference(pr)
+    dev = torch.device("cuda", 0)
+    nd = pr.cmap.shape[1]
+    flat = torch.empty(pr.cmap.size + 1, dtype=torch.int32, device=dev)
+    m = flat[1:].view(pr.cmap.shape)
+    m.copy_(torch.from_numpy(np.ascontiguousarray(pr.cmap)))
+    lbig = torch.full((pr.mesh.ncell * nd * nd + 1,), 255, dtype=torch.uint8, device=dev)
+    lut = lbig[1:]
+    assert m.data_ptr() % 8 == 4 and lut.data_ptr() % 2 == 1
+    rowptr = torch.empty(pr.nnodes + 1, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    nnz = fe.sparsity_build_noalloc(m, m, pr.nnodes, pr.nnodes, rowptr, None, lut)
+    colidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+    fe.sparsity_build_noalloc(m, m, pr.nnodes, pr.nnodes, rowptr, colidx, lut)
+    torch.cuda.synchronize()
+    for a, b in zip((rowptr.cpu().numpy(), colidx.cpu().numpy(), lut.cpu().numpy()), want):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_second_call_allocates_nothing(env):
     """After the first call (module loaded, scratch address looked up), a further build changes
     neither torch's allocator statistics nor the device's free memory."""
