@@ -217,6 +217,15 @@ __device__ __forceinline__ void warp_rank_distinct(const uint32_t *v, int n, F &
 }
 
 
+// lower ? min(v, o) : max(v, o) as two predicated instructions (the lanes of one stage split
+// between them) instead of a minimum, a maximum and a select.
+__device__ __forceinline__ uint32_t keep_min_or_max(uint32_t v, uint32_t o, bool lower) {
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p min.u32 %0, %0, %1;\n\t@!p max.u32 %0, %0, %1;\n\t}"
+      : "+r"(v)
+      : "r"(o), "r"((uint32_t)lower));
+  return v;
+}
+
 // Bitonic sort of 32 E packed 32-bit values across a warp, ascending: lane l holds elements
 // E l .. E l + E - 1 in v[0..E).  Each merge of size k starts with a mirror stage (element i against
 // i ^ (k - 1)), after which every half-cleaner stage sorts ascending, so compare-exchanges inside a
@@ -249,7 +258,7 @@ __device__ __forceinline__ void warp_bitonic_packed(uint32_t (&v)[E]) {
 #pragma unroll
       for (int h = 0; h < E; h++) o[h] = __shfl_xor_sync(0xffffffffu, v[E - 1 - h], m);
 #pragma unroll
-      for (int h = 0; h < E; h++) v[h] = lower ? umin(v[h], o[h]) : umax(v[h], o[h]);
+      for (int h = 0; h < E; h++) v[h] = keep_min_or_max(v[h], o[h], lower);
     }
 #pragma unroll
     for (int j = k >> 2; j > 0; j >>= 1) {
@@ -268,7 +277,7 @@ __device__ __forceinline__ void warp_bitonic_packed(uint32_t (&v)[E]) {
 #pragma unroll
         for (int h = 0; h < E; h++) {
           const uint32_t o = __shfl_xor_sync(0xffffffffu, v[h], m);
-          v[h] = lower ? umin(v[h], o) : umax(v[h], o);
+          v[h] = keep_min_or_max(v[h], o, lower);
         }
       }
     }
