@@ -446,22 +446,26 @@ __global__ void __launch_bounds__(kPushThreads) k_action_elem(const AsmArgs a, t
   T xe[ND];
 #pragma unroll
   for (int j = 0; j < ND; j++) xe[j] = Ops::from_f64(a.x[rows[j]]);
-  T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
-  Geo<DIM>::template compute<Ops>(x, Lam, vol);
   T ye[ND];
-  if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) {
-#pragma unroll
-    for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
-    T K[E::NUP];
-    element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
-#pragma unroll
-    for (int i = 0; i < ND; i++) {
-      ye[i] = Ops::mul(K[E::upper_index(i, 0)], xe[0]);
-#pragma unroll
-      for (int j = 1; j < ND; j++) ye[i] = Ops::fma3(K[E::upper_index(i, j)], xe[j], ye[i]);
-    }
+  if constexpr (P == 1 && FORM == FE_FORM_LAPLACE) {
+    p1_laplace_action<DIM, Ops>(x, xe, ye);  // through grad(u): no element matrix
   } else {
-    E::template action_upper<Ops, FORM != FE_FORM_MASS, FORM != FE_FORM_LAPLACE>(Lam, vol, xe, ye);
+    T Lam[Geo<DIM>::NLAM], vol, kp[DIM + 1];
+    Geo<DIM>::template compute<Ops>(x, Lam, vol);
+    if constexpr (FORM == FE_FORM_KAPPA_DIFFUSION) {
+#pragma unroll
+      for (int m = 0; m <= DIM; m++) kp[m] = Ops::from_f64(kap[m]);
+      T K[E::NUP];
+      element_upper<DIM, P, FORM, Ops>(Lam, vol, kp, K);
+#pragma unroll
+      for (int i = 0; i < ND; i++) {
+        ye[i] = Ops::mul(K[E::upper_index(i, 0)], xe[0]);
+#pragma unroll
+        for (int j = 1; j < ND; j++) ye[i] = Ops::fma3(K[E::upper_index(i, j)], xe[j], ye[i]);
+      }
+    } else {
+      E::template action_upper<Ops, FORM != FE_FORM_MASS, FORM != FE_FORM_LAPLACE>(Lam, vol, xe, ye);
+    }
   }
   T *out = stage + e * ND;
 #pragma unroll
