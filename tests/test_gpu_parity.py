@@ -406,6 +406,29 @@ def test_pull_action_and_rhs_match_oracle(gpu, dim, p, n, jit, prec):
     PB.assert_close_scaled(got, want, scale, 1e-12, "pull rhs")
 
 
+@pytest.mark.parametrize("dim,n", [(2, 37), (3, 9)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pull_p1_laplace_action(gpu, dim, n, prec):
+    """The P1 Laplace element stage (formed through grad(u), without the element matrix) against the
+    oracle per entry within 1e-12 of its scale; and for u = x, the assembled action vanishes at
+    every interior node (the integral of d(phi_i)/dx over the support of phi_i is zero)."""
+    from paper_1501_01809_gb300 import fe
+    from paper_1501_01809_gb300 import meshgen as mg
+    pr = PB.make(dim, 1, n, 0.2, seed=4)
+    g = PB.GpuProblem(pr)
+    x = np.random.default_rng(5).uniform(-1, 1, pr.nnodes)
+    got = g.action(fe.FORM_LAPLACE, x, precision=prec, strategy=fe.STRATEGY_PULL)
+    want, scale = O.action(dim, 1, O.LAPLACE, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, x)
+    PB.assert_close_scaled(got, want, scale, 1e-12, f"P1 Laplace pull action dim {dim} prec {prec}")
+    xn = mg.node_coordinates(pr.mesh, 1)
+    u = xn[:, 0].copy()
+    y = g.action(fe.FORM_LAPLACE, u, precision=prec, strategy=fe.STRATEGY_PULL)
+    _, su = O.action(dim, 1, O.LAPLACE, pr.cmap, pr.mesh.coords, pr.mesh.cell_vertex, u)
+    interior = np.all((xn > 1e-12) & (xn < 1 - 1e-12), axis=1)
+    assert interior.sum() > 0
+    assert np.all(np.abs(y[interior]) <= 1e-13 * su[interior]), np.max(np.abs(y[interior]) / su[interior])
+
+
 def test_pull_is_bitwise_reproducible(gpu):
     """Row owners sum in the fixed incidence order: repeated assemblies and actions are bitwise equal."""
     from paper_1501_01809_gb300 import fe
