@@ -70,7 +70,7 @@ TRAFFIC = {
                                     "FP64 atomics in L2 (ncu at 40^3: L2 throughput 50%, 24% warps active)"),
     # the fused phase: the Mat zero (54.7 MB written at 40^3) and k_mat_action_push<3,2,HELMHOLTZ,FP64>
     # (193.9 MB read, 76.8 MB written at 40^3), 325.4 MB, scaled x4.096 to 64^3
-    ("assemble_action", "push", "fp64"): (1.333e9, "19391aeb1329",
+    ("assemble_action", "push", "fp64"): (1.333e9, "47eb134234aa",
                                           "FP64 pipe 76% busy beside FP64 reductions in L2 (ncu at 40^3: L2 58%, "
                                           "23.4% warps active at 128 registers, table staged in shared memory)"),
     # one sparsity rebuild (zero, the guarded k_inc_fill, the in-place k_rows_build pass and the gated
