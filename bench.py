@@ -74,8 +74,8 @@ TRAFFIC = {
                                           "FP64 pipe 76% busy beside FP64 reductions in L2 (ncu at 40^3: L2 58%, "
                                           "23.4% warps active at 128 registers, table staged in shared memory)"),
     # one sparsity rebuild (zero, the guarded k_inc_fill, the in-place k_rows_build pass and the gated
-    # launches that return at once; column tracking off): 116.8 MB at 40^3, scaled x4.096 to 64^3
-    ("sparsity", None, None): (0.4785e9, "ab665899b16c",
+    # launches that return at once; column tracking off): 117.3 MB at 40^3, scaled x4.096 to 64^3
+    ("sparsity", None, None): (0.4804e9, "f848f281fef1",
                                "integer instruction issue (ncu at 40^3, row pass: issue active 64%, ALU pipe 65%, "
                                "314 warp instructions per row)"),
 }

@@ -159,7 +159,8 @@ __global__ void k_max_count(const int32_t *__restrict__ cnt, int64_t n, int *out
 // incidence fill: adj[adjptr[r] + slot] = k (k = e*ndr + i); slot order is arbitrary here and
 // made canonical by sparsity_canonical when an order-sensitive kernel needs it.
 // Each thread takes four incidences per round and issues their four cursor atomics before it
-// needs any result, so that the round trips of the returning atomics overlap.  guarded (a rebuild
+// needs any result, so that the round trips of the returning atomics overlap.  Launched with one
+// round per thread (up to 152 * 256 blocks), so that blocks start as SMs free up.  guarded (a rebuild
 // filling against the previous row offsets): a slot past the row's previous length is not written
 // (the row pass then sees the changed count), and a map value out of range is flagged.
 __global__ void k_inc_fill(const int32_t *__restrict__ rmap, int64_t n, int64_t nrows,
@@ -813,7 +814,7 @@ cudaError_t sparsity_incidence_reuse(fe_sparsity *sp, cudaStream_t s, int *err) 
   const int64_t n = sp->ncell * sp->ndr;
   k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows);
   if (n > 0)
-    k_inc_fill<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj, 1,
+    k_inc_fill<<<grid_for((n + 3) / 4, 256, 152 * 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj, 1,
                                                  err);
   return cudaGetLastError();
 }
@@ -826,7 +827,7 @@ cudaError_t sparsity_incidence_gated(fe_sparsity *sp, cudaStream_t s, int *err, 
   if (e != cudaSuccess) return e;
   k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows, gate);
   if (n > 0)
-    k_inc_fill<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj, 0,
+    k_inc_fill<<<grid_for((n + 3) / 4, 256, 152 * 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj, 0,
                                                  nullptr, gate);
   return cudaGetLastError();
 }
@@ -844,7 +845,7 @@ cudaError_t sparsity_incidence(fe_sparsity *sp, cudaStream_t s, int *err, int wi
   if (e != cudaSuccess) return e;
   k_zero_i32<<<grid_for(sp->nrows, 256), 256, 0, s>>>(sp->rowcnt, sp->nrows);
   if (n > 0)
-    k_inc_fill<<<grid_for(n, 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj);
+    k_inc_fill<<<grid_for((n + 3) / 4, 256, 152 * 256), 256, 0, s>>>(sp->rmap->values, n, sp->nrows, sp->adjptr, sp->rowcnt, sp->adj);
   return cudaGetLastError();
 }
 
